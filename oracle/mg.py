@@ -1,0 +1,148 @@
+"""Oracle: multigrid hierarchy, transfers, smoother, coarse solve, V-cycle.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* Transfers (Sec. 4.1.4, Eq. "prolongation"): the prolongation is the natural
+  embedding of the coarse Q1 space into the fine one, u_fine(x_i) =
+  sum_j chi_ij u_coarse_j, written as one sparse matrix P_l; the restriction
+  is its transpose R = P^T.  With hanging nodes the coarse vertex values are
+  first completed by H (Sec. 2.2), and rows/columns of constrained dofs are
+  zero: P_eff = Z_f E H_c Z_c.
+* Smoother (Sec. 4.1.4): x <- x + omega S (b - A x), S = D^{-1} (Jacobi) or
+  the inverse of the n_c x n_c nodal diagonal blocks (block Jacobi).
+* Coarse problem: a direct solve A_0^{-1} b_0 (Algorithm "Geometric multigrid
+  solver", Step 0), here LU with partial pivoting in FP64.
+* Level operators: rediscretisation of the same form on every level of the
+  global hierarchy (Sec. 2.2: "an approximation of the entire problem can be
+  created on each grid level").
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from . import mesh as M
+from . import problems as PB
+
+
+def embedding(fine: M.Q1Mesh, coarse: M.Q1Mesh):
+    """E (n_fine x n_coarse): value of the coarse Q1 function (given on all
+    coarse vertices) at each fine node, by Q1 interpolation in the coarse
+    leaf that contains the node."""
+    dim = fine.dim
+    Lf = fine.L
+    X = fine.X                                         # fine lattice coords
+    n = fine.n_nodes
+    found = np.zeros(n, dtype=bool)
+    rows, cols, vals = [], [], []
+    ckeys = M._cell_keys(dim, coarse.level, coarse.anchor)
+    order = np.argsort(ckeys)
+    ckeys_sorted = ckeys[order]
+    off = coarse.corners_offsets()
+    for l in np.unique(coarse.level):
+        s = 1 << (Lf - int(l))
+        ncell = fine.macro << int(l)
+        a = np.minimum(X >> (Lf - int(l)), ncell[None, :] - 1)
+        k = M._cell_keys(dim, np.full(n, l), a)
+        pos = np.minimum(np.searchsorted(ckeys_sorted, k), ckeys_sorted.size - 1)
+        hit = (ckeys_sorted[pos] == k) & ~found
+        idx = np.nonzero(hit)[0]
+        if idx.size == 0:
+            continue
+        found[idx] = True
+        t = (X[idx] - a[idx] * s) / float(s)           # local coordinates in [0,1]
+        for c in range(1 << dim):
+            w = np.ones(idx.size)
+            for d in range(dim):
+                w *= t[:, d] if off[c, d] else 1.0 - t[:, d]
+            corner = (a[idx] + off[c][None, :]) << (coarse.L - int(l))
+            cn = coarse.lookup(coarse.key(corner))
+            assert np.all(cn >= 0)
+            nz = w != 0.0
+            rows.append(idx[nz]); cols.append(cn[nz]); vals.append(w[nz])
+    assert found.all(), "fine node outside the coarse mesh"
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, coarse.n_nodes))
+
+
+class Level:
+    def __init__(self, leaf_level, leaf_anchor, leafmesh, prob, lattice_level=None):
+        self.mesh = M.Q1Mesh(leafmesh.dim, leafmesh.origin, leafmesh.extent, leafmesh.macro,
+                             leaf_level, leaf_anchor, lattice_level)
+        self.sys = PB.build_system(self.mesh, prob, with_load=False)
+        self.A = self.sys.A
+        self.nc = prob.nc
+        self.P = None          # prolongation from the next coarser level
+        self.R = None
+
+    def smoother_matrix(self):
+        """S of the smoothing step: D^-1 (nc=1) or block-diagonal inverse."""
+        nc = self.nc
+        if nc == 1:
+            return sp.diags(1.0 / self.A.diagonal())
+        n = self.A.shape[0] // nc
+        blocks = []
+        Ad = self.A.tocsr()
+        for i in range(n):
+            B = Ad[i * nc:(i + 1) * nc, i * nc:(i + 1) * nc].toarray()
+            blocks.append(np.linalg.inv(B))
+        return sp.bsr_matrix((np.array(blocks), np.arange(n), np.arange(n + 1)),
+                             shape=self.A.shape).tocsr()
+
+
+class Hierarchy:
+    """Levels 0 (coarsest) .. L (finest) of the global coarsening."""
+
+    def __init__(self, leafmesh, prob, min_level=None, max_levels=0, omega=0.8, nu1=2, nu2=2):
+        if min_level is None:
+            min_level = M.default_min_level(leafmesh.macro)
+        sets = M.hierarchy(leafmesh.dim, leafmesh.macro, leafmesh.level, leafmesh.anchor,
+                           min_level, max_levels)[::-1]
+        self.levels = [Level(l, a, leafmesh, prob) for (l, a) in sets]
+        self.prob = prob
+        self.omega, self.nu1, self.nu2 = omega, nu1, nu2
+        nc = prob.nc
+        for lc, lf in zip(self.levels[:-1], self.levels[1:]):
+            E = mesh_E = embedding(lf.mesh, lc.mesh)
+            Hc = lc.mesh.H()
+            P = fem_expand(mesh_E @ Hc, nc)
+            zf = sp.diags((~lf.sys.fixed).astype(np.float64))
+            zc = sp.diags((~lc.sys.fixed).astype(np.float64))
+            lf.P = (zf @ P @ zc).tocsr()
+            lf.P.eliminate_zeros()
+            lf.R = lf.P.T.tocsr()
+            del E
+        for lv in self.levels:
+            lv.S = lv.smoother_matrix()
+        A0 = self.levels[0].A.toarray()
+        self.coarse_lu = sla.lu_factor(A0)
+
+    @property
+    def fine(self):
+        return self.levels[-1]
+
+    def smooth(self, l, x, b, sweeps):
+        lv = self.levels[l]
+        for _ in range(sweeps):
+            x = x + self.omega * (lv.S @ (b - lv.A @ x))
+        return x
+
+    def gmg(self, l, x, b):
+        """Algorithm "Geometric multigrid solver" (Steps 0-5)."""
+        if l == 0:
+            return sla.lu_solve(self.coarse_lu, b)                 # Step 0
+        lv = self.levels[l]
+        x = self.smooth(l, x, b, self.nu1)                         # Step 1
+        d = lv.R @ (b - lv.A @ x)                                  # Step 2
+        y = self.gmg(l - 1, np.zeros_like(d), d)                   # Step 3
+        x = x + lv.P @ y                                           # Step 4
+        return self.smooth(l, x, b, self.nu2)                      # Step 5
+
+    def precondition(self, r):
+        """One V-cycle with zero initial guess: z = M^-1 r."""
+        return self.gmg(len(self.levels) - 1, np.zeros_like(r), r)
+
+
+def fem_expand(Msc, nc):
+    return sp.kron(Msc, sp.identity(nc), format="csr") if nc > 1 else Msc.tocsr()

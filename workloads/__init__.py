@@ -1,0 +1,244 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds no part of the solver's arithmetic.  It only produces the
+*inputs* of a solve: leaf meshes (levels and integer anchors of the cells of a
+1-irregular quadtree/octree over a box), coefficient sets, right-hand-side
+functions and request streams.  Both the CPU oracle and the GPU library derive
+nodes, hanging-node constraints, matrices and the multigrid hierarchy from the
+leaf list on their own.
+
+Mesh convention (the one the C-ABI's ``mg_mesh`` uses as well): the domain is
+the box ``origin + [0, extent]``; level 0 is a ``macro[0] x macro[1] (x
+macro[2])`` grid of cells; a cell of level ``l`` has integer anchor ``a`` with
+``0 <= a[d] < macro[d] * 2**l`` and covers
+``origin + extent/(macro*2**l) * [a, a+1]``.
+
+Workloads (Sec. 5 of the paper motivates the problem classes; sizes follow
+the benchmark configurations restated in the repository design notes):
+
+* ``poisson64``      2D uniform 64x64 Q1 mesh on the unit square.
+* ``td_adaptive``    2D mesh refined around 16 seeded points (1-irregular).
+* ``elasticity3d``   3D uniform n^3 hexahedral mesh on the unit cube.
+* ``oseen_channel``  2D channel [0,2.2]x[0,0.41] refined towards a circle.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MASTER_SEED = 20240508
+
+
+@dataclass
+class LeafMesh:
+    """A leaf set of a 1-irregular quadtree (dim=2) or octree (dim=3)."""
+
+    dim: int
+    origin: tuple
+    extent: tuple
+    macro: tuple
+    level: np.ndarray          # (n,) int32
+    anchor: np.ndarray         # (n, dim) int32
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_leaves(self) -> int:
+        return int(self.level.shape[0])
+
+
+# ---------------------------------------------------------------------------
+# leaf-set helpers (pure integer bookkeeping)
+# ---------------------------------------------------------------------------
+
+_SHIFT = {2: (56, 28), 3: (58, 19)}
+
+
+def _keys(dim, level, anchor):
+    lshift, bits = _SHIFT[dim]
+    k = level.astype(np.int64) << lshift
+    for d in range(dim):
+        k |= anchor[:, d].astype(np.int64) << (bits * (dim - 1 - d))
+    return k
+
+
+def uniform_leaves(dim, macro, level, origin=None, extent=None) -> LeafMesh:
+    """All cells of one level of the macro grid."""
+    macro = tuple(int(m) for m in macro)
+    n = [m << level for m in macro]
+    grids = np.meshgrid(*[np.arange(k, dtype=np.int32) for k in n], indexing="ij")
+    anchor = np.stack([g.ravel() for g in grids], axis=1).astype(np.int32)
+    lev = np.full(anchor.shape[0], level, dtype=np.int32)
+    origin = tuple(origin) if origin is not None else (0.0,) * dim
+    extent = tuple(extent) if extent is not None else (1.0,) * dim
+    return LeafMesh(dim, origin, extent, macro, lev, anchor)
+
+
+def refine(mesh: LeafMesh, mask: np.ndarray) -> LeafMesh:
+    """Replace every marked leaf by its 2**dim children."""
+    dim = mesh.dim
+    keep_l, keep_a = mesh.level[~mask], mesh.anchor[~mask]
+    par_l, par_a = mesh.level[mask], mesh.anchor[mask]
+    kids_l, kids_a = [], []
+    for c in range(1 << dim):
+        off = np.array([(c >> d) & 1 for d in range(dim)], dtype=np.int32)
+        kids_l.append(par_l + 1)
+        kids_a.append(2 * par_a + off)
+    level = np.concatenate([keep_l] + kids_l).astype(np.int32)
+    anchor = np.concatenate([keep_a] + kids_a).astype(np.int32)
+    return LeafMesh(dim, mesh.origin, mesh.extent, mesh.macro, level, anchor, dict(mesh.meta))
+
+
+def balance_2to1(mesh: LeafMesh) -> LeafMesh:
+    """Refine until face-neighbouring leaves differ by at most one level."""
+    dim = mesh.dim
+    while True:
+        lev, anc = mesh.level, mesh.anchor
+        # every existing cell: leaves and all their ancestors
+        exist = []
+        for up in range(int(lev.max()) + 1):
+            ok = lev >= up
+            exist.append(_keys(dim, lev[ok] - up, anc[ok] >> up))
+        exist = np.unique(np.concatenate(exist))
+        leaf_keys = np.sort(_keys(dim, lev, anc))
+        mark = np.zeros(lev.shape[0], dtype=bool)
+        for d in range(dim):
+            for s in (-1, 1):
+                sel = lev >= 1
+                nl = lev[sel]
+                na = anc[sel].copy()
+                na[:, d] += s
+                size = np.array(mesh.macro, dtype=np.int64)[None, :] << nl[:, None].astype(np.int64)
+                inside = np.all((na >= 0) & (na < size), axis=1)
+                nl, na = nl[inside], na[inside]
+                cl, ca = nl - 1, na >> 1
+                missing = ~np.isin(_keys(dim, cl, ca), exist)
+                cl, ca = cl[missing], ca[missing]
+                # walk up from the missing cell to the leaf that contains it
+                for up in range(1, int(lev.max()) + 1):
+                    if cl.size == 0:
+                        break
+                    pl, pa = cl - up, ca >> up
+                    valid = pl >= 0
+                    k = _keys(dim, np.where(valid, pl, 0), np.where(valid[:, None], pa, 0))
+                    hit = valid & np.isin(k, leaf_keys)
+                    if hit.any():
+                        idx = np.searchsorted(leaf_keys, k[hit])
+                        mark_keys = leaf_keys[idx]
+                        mark |= np.isin(_keys(dim, lev, anc), mark_keys)
+                    cl, ca = cl[~hit], ca[~hit]
+        if not mark.any():
+            return mesh
+        mesh = refine(mesh, mark)
+
+
+def _cell_box(mesh: LeafMesh):
+    ext = np.array(mesh.extent, dtype=np.float64)
+    org = np.array(mesh.origin, dtype=np.float64)
+    h = ext[None, :] / (np.array(mesh.macro, dtype=np.float64)[None, :] * (2.0 ** mesh.level[:, None]))
+    lo = org[None, :] + mesh.anchor * h
+    return lo, lo + h, h
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+
+def poisson64(n: int = 64) -> LeafMesh:
+    """Uniform n x n mesh on the unit square (n a power of two)."""
+    lvl = int(round(math.log2(n)))
+    assert 1 << lvl == n
+    m = uniform_leaves(2, (1, 1), lvl)
+    m.meta.update(workload=f"poisson2d_{n}x{n}")
+    return m
+
+
+def td_points(seed: int = MASTER_SEED, n_points: int = 16) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(0.0, 1.0, size=(n_points, 2))
+
+
+def td_adaptive(rounds: int = 8, gamma: float = 0.0, base_level: int = 5, r0: float = 0.05,
+                seed: int = MASTER_SEED, n_points: int = 16) -> LeafMesh:
+    """Adaptive 2D mesh around seeded points.
+
+    Start from the uniform 2**base_level grid of the unit square; in round
+    k = 1..rounds refine every leaf whose closed cell lies within distance
+    r_k = r0 * 2**(-gamma*k) of one of the points, then restore 2:1 balance.
+    gamma = 1 is the literal radius rule r_k = r0 * 2**-k.
+    """
+    pts = td_points(seed, n_points)
+    m = uniform_leaves(2, (1, 1), base_level)
+    for k in range(1, rounds + 1):
+        r = r0 * 2.0 ** (-gamma * k)
+        lo, hi, _ = _cell_box(m)
+        mark = np.zeros(m.n_leaves, dtype=bool)
+        for p in pts:
+            dx = np.maximum(np.maximum(lo[:, 0] - p[0], 0.0), p[0] - hi[:, 0])
+            dy = np.maximum(np.maximum(lo[:, 1] - p[1], 0.0), p[1] - hi[:, 1])
+            mark |= dx * dx + dy * dy <= r * r
+        m = balance_2to1(refine(m, mark))
+    m.meta.update(workload=f"td_adaptive_r{rounds}_g{gamma:g}", points=pts, gamma=gamma)
+    return m
+
+
+def elasticity3d(n: int = 128) -> LeafMesh:
+    lvl = int(round(math.log2(n)))
+    assert 1 << lvl == n
+    m = uniform_leaves(3, (1, 1, 1), lvl)
+    m.meta.update(workload=f"elasticity3d_{n}^3")
+    return m
+
+
+def oseen_channel(uniform: int = 1, rounds: int = 0, band: float = 2.0) -> LeafMesh:
+    """Channel [0,2.2]x[0,0.41] on a 22x4 macro grid, refined `uniform` times
+    everywhere, then `rounds` times in the cells within band*h of the circle
+    |x - (0.2, 0.2)| = 0.05 (h the cell's diameter), 2:1 balanced."""
+    m = uniform_leaves(2, (22, 4), uniform, origin=(0.0, 0.0), extent=(2.2, 0.41))
+    c, rad = np.array([0.2, 0.2]), 0.05
+    for _ in range(rounds):
+        lo, hi, h = _cell_box(m)
+        near = np.clip(c[None, :], lo, hi)
+        far = np.where(np.abs(lo - c) > np.abs(hi - c), lo, hi)
+        dmin = np.linalg.norm(near - c, axis=1)
+        dmax = np.linalg.norm(far - c, axis=1)
+        diam = np.linalg.norm(h, axis=1)
+        dist = np.where((dmin <= rad) & (dmax >= rad), 0.0, np.minimum(np.abs(dmin - rad), np.abs(dmax - rad)))
+        m = balance_2to1(refine(m, dist <= band * diam))
+    m.meta.update(workload=f"oseen_channel_u{uniform}_r{rounds}")
+    return m
+
+
+# ---------------------------------------------------------------------------
+# right-hand sides and coefficient streams (the data the paper's tests use)
+# ---------------------------------------------------------------------------
+
+def f_poisson(xy: np.ndarray) -> np.ndarray:
+    """f = 2 pi^2 sin(pi x) sin(pi y): -Laplace of u = sin(pi x) sin(pi y)."""
+    return 2.0 * math.pi ** 2 * np.sin(math.pi * xy[:, 0]) * np.sin(math.pi * xy[:, 1])
+
+
+def u_manufactured(xy: np.ndarray) -> np.ndarray:
+    return np.sin(math.pi * xy[:, 0]) * np.sin(math.pi * xy[:, 1])
+
+
+def f_transport(xy: np.ndarray, eps: float, beta) -> np.ndarray:
+    """f = -eps Laplace u + beta . grad u for u = sin(pi x) sin(pi y)."""
+    x, y = xy[:, 0], xy[:, 1]
+    pi = math.pi
+    return (eps * 2.0 * pi ** 2 * np.sin(pi * x) * np.sin(pi * y)
+            + beta[0] * pi * np.cos(pi * x) * np.sin(pi * y)
+            + beta[1] * pi * np.sin(pi * x) * np.cos(pi * y))
+
+
+def random_nodal(n: int, ncomp: int = 1, seed: int = MASTER_SEED, stream: int = 0) -> np.ndarray:
+    """Seeded N(0,1) vectors for operator-level parity tests."""
+    rng = np.random.Generator(np.random.PCG64([seed, stream]))
+    return rng.standard_normal((n, ncomp)) if ncomp > 1 else rng.standard_normal(n)
+
+
+def stream_coeffs(seed: int = MASTER_SEED, modes: int = 4) -> np.ndarray:
+    """a_mn ~ N(0,1), m,n = 1..modes, for the seeded stream function."""
+    rng = np.random.Generator(np.random.PCG64([seed, 7]))
+    return rng.standard_normal((modes, modes))
