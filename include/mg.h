@@ -1,0 +1,209 @@
+/*
+ * mg.h -- C ABI of the GB300 geometric-multigrid Krylov solver for adaptive
+ * Q1 finite elements on quad/hex meshes with hanging nodes.
+ *
+ * The method is that of arXiv:2405.05047 ("An adaptive finite element
+ * multigrid solver using GPU acceleration"):
+ *   - Q1 elements on 1-irregular meshes, hanging nodes eliminated through the
+ *     interpolation matrix H_h (Sec. 2.1, 2.2);
+ *   - a hierarchy built by global coarsening of the finest mesh (Sec. 2.2);
+ *   - the V-cycle of Algorithm "Geometric multigrid solver" with a damped
+ *     (block-)Jacobi smoother x <- x + omega S (b - A x) and transfers given by
+ *     the local embedding P_l, R_l = P_l^T (Sec. 4.1.4, Eq. "prolongation");
+ *   - the V-cycle as preconditioner of a Krylov method (Sec. 4.1.5).
+ *
+ * Conventions for every entry point:
+ *   - return value: MG_OK (0) or a negative MG_ERR_* code; mg_strerror() names
+ *     it.  No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device; "host" pointers are ordinary CPU memory.  Pointers passed in are
+ *     only read during the call unless stated; the library never frees memory
+ *     it did not allocate.
+ *   - vectors are node-major: entry (node i, component c) is at i*nc + c, with
+ *     nodes in the *external order*: integer lattice coordinates of the finest
+ *     level sorted lexicographically, x fastest, then y, then z.
+ *   - a context is used from one host thread at a time; calls run on the
+ *     context's stream and return after the device work has finished unless
+ *     stated otherwise.
+ */
+#ifndef MG_GB300_H
+#define MG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  MG_OK = 0,
+  MG_PENDING = 1,              /* mg_poll: request still queued or running      */
+  MG_ERR_INVALID = -1,         /* bad argument, malformed mesh, unknown ticket  */
+  MG_ERR_OOM = -2,             /* device allocation failed                      */
+  MG_ERR_ADMISSION = -3,       /* request can never fit the HBM budget          */
+  MG_ERR_NOT_CONVERGED = -4,   /* max_it reached; x and stats are still valid   */
+  MG_ERR_BREAKDOWN = -5,       /* Krylov breakdown (zero denominator)           */
+  MG_ERR_NAN = -6,             /* NaN/Inf met in a reduction                    */
+  MG_ERR_TIMEOUT = -7,         /* a bounded device-side wait gave up            */
+  MG_ERR_CUDA = -8,            /* CUDA runtime error                            */
+  MG_ERR_CANCELLED = -9        /* mg_cancel'ed request                          */
+};
+
+typedef enum { MG_FP64 = 0, MG_MIXED_FP32 = 1, MG_MIXED_BF16 = 2 } mg_precision;
+typedef enum { MG_POISSON = 0, MG_TRANSPORT = 1, MG_ELASTICITY = 2 } mg_kind;
+typedef enum { MG_KRYLOV_AUTO = 0, MG_CG = 1, MG_BICGSTAB = 2, MG_GMRES = 3 } mg_krylov;
+
+typedef struct mg_ctx mg_ctx;
+typedef struct mg_hier mg_hier;
+
+/* Device allocator callbacks (optional).  malloc_fn returns a device pointer
+ * aligned to >= 256 bytes or NULL; free_fn releases it.  With alloc == NULL
+ * the library uses cudaMalloc/cudaFree. */
+typedef struct {
+  void* (*malloc_fn)(size_t bytes, void* user);
+  void (*free_fn)(void* ptr, void* user);
+  void* user;
+} mg_allocator;
+
+/* Leaf mesh (host memory, copied by mg_setup).  Domain: the box
+ * origin + [0, extent]; level 0 is a macro[0] x macro[1] (x macro[2]) grid;
+ * leaf k has level leaf_level[k] and integer anchor
+ * leaf_anchor[k*dim + d] in [0, macro[d] << level).  The leaves must tile the
+ * box exactly and be 1-irregular: face neighbours differ by <= 1 level
+ * (Sec. 2.2: "We allow a level jump of 1 for neighboring elements"). */
+typedef struct {
+  int dim;                     /* 2 or 3 */
+  double origin[3];
+  double extent[3];
+  int macro[3];
+  int64_t n_leaves;
+  const int32_t* leaf_level;   /* host, n_leaves */
+  const int32_t* leaf_anchor;  /* host, n_leaves * dim */
+} mg_mesh;
+
+/* Problem: bilinear form and Dirichlet faces.  Face bit 2d = face x_d = min,
+ * bit 2d+1 = face x_d = max; dirichlet_mask[c] selects the faces on which
+ * component c is fixed to 0.
+ *   POISSON      (grad u, grad v)                                  nc = 1
+ *   TRANSPORT    eps (grad u, grad v) + (beta.grad u, v)
+ *                + sum_T delta_T (beta.grad u, beta.grad v)_T,
+ *                delta_T = supg_delta0 h_T^2 / (6 eps + |beta| h_T)   nc = 1
+ *   ELASTICITY   2 mu (eps(u), eps(v)) + lambda (div u, div v), 3D  nc = 3 */
+typedef struct {
+  int kind;
+  double eps;
+  double beta[3];
+  double mu;
+  double lambda;
+  double supg_delta0;
+  uint32_t dirichlet_mask[3];
+} mg_problem;
+
+typedef struct {
+  int nu1, nu2;                /* pre/post smoothing sweeps (default 2, 2)    */
+  double omega;                /* damping of the (block-)Jacobi smoother      */
+  int min_level;               /* coarsest level allowed (-1: automatic)      */
+  int max_levels;              /* cap on the number of levels (0: no cap)     */
+  int krylov;                  /* mg_krylov                                   */
+  int restart;                 /* GMRES restart length (default 30)           */
+  int store_fp64;              /* keep FP64 level matrices (1) for MG_FP64    */
+  int store_fp32;              /* keep FP32 level matrices (1) for mixed modes*/
+} mg_opts;
+
+typedef struct {
+  int dim, nc, levels;
+  int64_t n_nodes, n_dofs, n_free;      /* finest level                        */
+  int64_t level_nodes[32];              /* [0] = coarsest                      */
+  int64_t level_nnzb[32];               /* stored blocks (incl. padding)       */
+  int64_t level_rows_nnzb[32];          /* blocks without SELL padding         */
+  size_t bytes_device;                  /* hierarchy + workspace               */
+  int64_t n_hanging;
+  double omega;
+} mg_info;
+
+typedef struct {
+  int status;                  /* MG_OK, MG_ERR_NOT_CONVERGED, ...            */
+  int iters;                   /* Krylov iterations                           */
+  int vcycles;                 /* preconditioner applications                 */
+  int precision;               /* mg_precision used                           */
+  double rel_res;              /* true ||b - A x||_2 / ||b_free||_2 (FP64)    */
+  double solve_ms;             /* device time of the solve                    */
+  double setup_ms;             /* for mg_poll: time from submit to start      */
+  int64_t launches;            /* kernels launched by the solve               */
+} mg_stats;
+
+const char* mg_strerror(int code);
+void mg_default_opts(mg_opts* opts);
+
+/* Context: one device, one stream (a cudaStream_t from the caller, e.g.
+ * torch.cuda.current_stream().cuda_stream, or NULL for a private stream),
+ * an HBM budget (bytes; 0 = no limit) that bounds every hierarchy and
+ * workspace allocated through this context.  The allocator struct is copied. */
+int mg_init(int device, size_t hbm_budget_bytes, const mg_allocator* alloc, void* stream, mg_ctx** out);
+int mg_destroy(mg_ctx* ctx);
+
+/* Build the hierarchy (Sec. 2.2 global coarsening; level operators by
+ * rediscretisation; transfers from the local embedding, Eq. "prolongation")
+ * on the host, pack it in the device layouts and upload it.  mesh, problem and
+ * opts are copied; the library owns all device memory of the hierarchy.
+ * MG_ERR_INVALID for a malformed mesh (overlap, gap, 2:1 violation),
+ * MG_ERR_ADMISSION when the hierarchy would exceed the context's budget. */
+int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* problem, const mg_opts* opts,
+             mg_hier** out);
+int mg_hier_info(const mg_hier* h, mg_info* info);
+/* Physical coordinates of the finest-level nodes, external order, host
+ * buffer of n_nodes * dim doubles. */
+int mg_node_coords(const mg_hier* h, double* xyz_host);
+int mg_free(mg_hier* h);
+
+/* b = H^T (M I_h f) (+ SUPG load term), zero on hanging and Dirichlet rows.
+ * f_nodal: device, n_nodes * nc doubles (nodal source values at every node,
+ * hanging ones included); b: device, n_nodes * nc doubles. */
+int mg_assemble_rhs(mg_hier* h, const double* f_nodal, double* b);
+
+/* Krylov solve (CG / BiCGStab / GMRES per opts.krylov) preconditioned by one
+ * V-cycle per iteration (Sec. 4.1.5).  b, x: device, n_nodes * nc doubles,
+ * caller-owned.  x in: initial guess; out: solution on all nodes, hanging
+ * values filled by H (Sec. 2.2) and Dirichlet values 0.  Stops when the true
+ * FP64 residual satisfies ||b - A x|| <= rtol ||b_free||; prec selects the
+ * V-cycle precision (MG_FP64, or FP32 inside the FP64 Krylov loop).  Returns
+ * MG_ERR_NOT_CONVERGED after max_it iterations (x and stats valid). */
+int mg_solve(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats);
+/* The same with HOST b and x: copies b to the device, solves, copies x back. */
+int mg_solve_host(mg_hier* h, const double* b_host, double* x_host, double rtol, int max_it, int prec,
+                  mg_stats* stats);
+
+/* z = M^-1 r: one V-cycle with zero initial guess (Algorithm "Geometric
+ * multigrid solver" started at the finest level).  r, z: device vectors of
+ * n_dofs entries of type double (prec = MG_FP64) or float (mixed modes). */
+int mg_vcycle(mg_hier* h, const void* r, void* z, int prec);
+
+/* Single level operators, for tests and custom outer loops.  level 0 is the
+ * coarsest.  Vectors are device arrays of double (MG_FP64) or float (mixed):
+ *   MG_OP_MATVEC       out = A_l in
+ *   MG_OP_SMOOTH       out = in + omega S_l (in2 - A_l in)     (one sweep)
+ *   MG_OP_RESTRICT     out = R_l (in2 - A_l in)   (out on level l-1)
+ *   MG_OP_PROLONG_ADD  out = in2 + P_l in         (in on level l-1)
+ *   MG_OP_COARSE       out = A_0^-1 in            (level must be 0) */
+enum { MG_OP_MATVEC = 0, MG_OP_SMOOTH = 1, MG_OP_RESTRICT = 2, MG_OP_PROLONG_ADD = 3, MG_OP_COARSE = 4 };
+int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, void* out, int prec);
+
+/* Serving: continuous batching of solves on resident hierarchies.
+ * mg_submit queues a solve of h (b, x device buffers, caller-owned, not to be
+ * touched until mg_poll returns a final status) and returns at once with a
+ * ticket; MG_ERR_ADMISSION if the request's workspace can never fit the
+ * budget.  The context's scheduler thread runs queued requests in epochs,
+ * interleaving the iterations of all admitted requests on its own streams.
+ * mg_poll returns MG_PENDING, or the final status with stats filled in.
+ * mg_cancel removes a queued request (MG_ERR_CANCELLED on its next poll). */
+int mg_submit(mg_ctx* ctx, mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec,
+              uint64_t* ticket);
+int mg_poll(mg_ctx* ctx, uint64_t ticket, mg_stats* stats);
+int mg_cancel(mg_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_GB300_H */

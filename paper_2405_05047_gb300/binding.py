@@ -1,0 +1,371 @@
+"""ctypes binding of ``include/mg.h``.
+
+The functions named like the C entry points (``mg_setup``, ``mg_solve``, ...)
+take the same arguments, with torch tensors accepted wherever the C function
+takes a device pointer and numpy arrays wherever it takes a host pointer.
+``Context`` / ``Hierarchy`` wrap them for convenience.  Device memory of the
+hierarchy comes from PyTorch's caching allocator through the ``mg_allocator``
+callbacks, and every call runs on the CUDA stream the context was created
+with (PyTorch's current stream by default).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+MG_OK, MG_PENDING = 0, 1
+MG_ERR_NOT_CONVERGED = -4
+MG_FP64, MG_MIXED_FP32, MG_MIXED_BF16 = 0, 1, 2
+MG_POISSON, MG_TRANSPORT, MG_ELASTICITY = 0, 1, 2
+MG_KRYLOV_AUTO, MG_CG, MG_BICGSTAB, MG_GMRES = 0, 1, 2, 3
+MG_OP_MATVEC, MG_OP_SMOOTH, MG_OP_RESTRICT, MG_OP_PROLONG_ADD, MG_OP_COARSE = 0, 1, 2, 3, 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libmg_gb300.so")
+
+
+class MGError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"mg error {code}: {msg}")
+        self.code = code
+
+
+class MgMesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("origin", C.c_double * 3), ("extent", C.c_double * 3),
+                ("macro", C.c_int * 3), ("n_leaves", C.c_int64),
+                ("leaf_level", C.POINTER(C.c_int32)), ("leaf_anchor", C.POINTER(C.c_int32))]
+
+
+class MgProblem(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("beta", C.c_double * 3), ("mu", C.c_double),
+                ("lambda_", C.c_double), ("supg_delta0", C.c_double), ("dirichlet_mask", C.c_uint32 * 3)]
+
+
+class MgOpts(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("min_level", C.c_int),
+                ("max_levels", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("store_fp64", C.c_int),
+                ("store_fp32", C.c_int)]
+
+
+class MgInfo(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nc", C.c_int), ("levels", C.c_int), ("n_nodes", C.c_int64),
+                ("n_dofs", C.c_int64), ("n_free", C.c_int64), ("level_nodes", C.c_int64 * 32),
+                ("level_nnzb", C.c_int64 * 32), ("level_rows_nnzb", C.c_int64 * 32),
+                ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double)]
+
+
+class MgStats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("vcycles", C.c_int), ("precision", C.c_int),
+                ("rel_res", C.c_double), ("solve_ms", C.c_double), ("setup_ms", C.c_double),
+                ("launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_MALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class MgAllocator(C.Structure):
+    _fields_ = [("malloc_fn", _MALLOC), ("free_fn", _FREE), ("user", C.c_void_p)]
+
+
+_lib = None
+
+# the C ABI: name -> (restype, argtypes)
+_SIGS = {
+    "mg_strerror": (C.c_char_p, [C.c_int]),
+    "mg_last_error": (C.c_char_p, []),
+    "mg_default_opts": (None, [C.POINTER(MgOpts)]),
+    "mg_init": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(MgAllocator), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mg_destroy": (C.c_int, [C.c_void_p]),
+    "mg_setup": (C.c_int, [C.c_void_p, C.POINTER(MgMesh), C.POINTER(MgProblem), C.POINTER(MgOpts),
+                           C.POINTER(C.c_void_p)]),
+    "mg_hier_info": (C.c_int, [C.c_void_p, C.POINTER(MgInfo)]),
+    "mg_node_coords": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mg_free": (C.c_int, [C.c_void_p]),
+    "mg_assemble_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
+                           C.POINTER(MgStats)]),
+    "mg_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
+                                C.POINTER(MgStats)]),
+    "mg_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
+                            C.POINTER(C.c_uint64)]),
+    "mg_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(MgStats)]),
+    "mg_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "mg_launch_count": (C.c_int64, [C.c_void_p]),
+}
+
+
+def load_library(path: str | None = None):
+    """Load the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise MGError(-8, f"{path} not built: run paper_2405_05047_gb300/build.py (needs nvcc)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, allow=(MG_OK,)):
+    if rc not in allow:
+        lib = load_library()
+        raise MGError(rc, f"{lib.mg_strerror(rc).decode()}: {lib.mg_last_error().decode()}")
+    return rc
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (must be contiguous) or an int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    assert t.is_contiguous(), "vectors must be contiguous"
+    return t.data_ptr()
+
+
+def _host_ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- allocator
+class _TorchAllocator:
+    """mg_allocator backed by torch.cuda.caching_allocator_alloc."""
+
+    def __init__(self, device, stream):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _m(size, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(size), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _f(ptr, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.cm = _MALLOC(_m)
+        self.cf = _FREE(_f)
+        self.struct = MgAllocator(self.cm, self.cf, None)
+
+
+# ---------------------------------------------------------------- C entry points
+def mg_init(device=0, hbm_budget_bytes=0, allocator="torch", stream=None):
+    """Returns (ctx_handle, keepalive).  stream: a torch.cuda.Stream or None
+    for PyTorch's current stream."""
+    import torch
+    lib = load_library()
+    if not torch.cuda.is_available():
+        raise MGError(-8, "no CUDA device: the GB300 library has no CPU path")
+    torch.cuda.set_device(device)
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    keep = None
+    alloc_p = None
+    if allocator == "torch":
+        keep = _TorchAllocator(device, st)
+        alloc_p = C.byref(keep.struct)
+    out = C.c_void_p()
+    _check(lib.mg_init(device, hbm_budget_bytes, alloc_p, C.c_void_p(st.cuda_stream), C.byref(out)))
+    return out, (keep, st)
+
+
+def mg_destroy(ctx):
+    return _check(load_library().mg_destroy(ctx))
+
+
+def make_mesh(leafmesh):
+    lev = np.ascontiguousarray(leafmesh.level, dtype=np.int32)
+    anc = np.ascontiguousarray(leafmesh.anchor, dtype=np.int32)
+    m = MgMesh()
+    m.dim = leafmesh.dim
+    for d in range(leafmesh.dim):
+        m.origin[d] = leafmesh.origin[d]
+        m.extent[d] = leafmesh.extent[d]
+        m.macro[d] = leafmesh.macro[d]
+    m.n_leaves = lev.shape[0]
+    m.leaf_level = lev.ctypes.data_as(C.POINTER(C.c_int32))
+    m.leaf_anchor = anc.ctypes.data_as(C.POINTER(C.c_int32))
+    return m, (lev, anc)
+
+
+def make_problem(kind=MG_POISSON, eps=1.0, beta=(0.0, 0.0, 0.0), mu=1.0, lam=1.0, supg_delta0=0.5,
+                 dirichlet=(0xFF,)):
+    p = MgProblem()
+    p.kind = kind
+    p.eps = eps
+    for d in range(3):
+        p.beta[d] = beta[d] if d < len(beta) else 0.0
+    p.mu = mu
+    p.lambda_ = lam
+    p.supg_delta0 = supg_delta0
+    nc = 3 if kind == MG_ELASTICITY else 1
+    masks = tuple(dirichlet) * (nc if len(dirichlet) == 1 else 1)
+    for c in range(3):
+        p.dirichlet_mask[c] = masks[c] if c < len(masks) else 0
+    return p
+
+
+def make_opts(**kw):
+    o = MgOpts()
+    load_library().mg_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def mg_setup(ctx, leafmesh, problem: MgProblem, opts: MgOpts | None = None):
+    lib = load_library()
+    m, keep = make_mesh(leafmesh)
+    out = C.c_void_p()
+    _check(lib.mg_setup(ctx, C.byref(m), C.byref(problem), C.byref(opts) if opts is not None else None,
+                        C.byref(out)))
+    return out
+
+
+def mg_hier_info(h) -> MgInfo:
+    info = MgInfo()
+    _check(load_library().mg_hier_info(h, C.byref(info)))
+    return info
+
+
+def mg_node_coords(h, n_nodes, dim):
+    xyz = np.zeros((n_nodes, dim), dtype=np.float64)
+    _check(load_library().mg_node_coords(h, _host_ptr(xyz)))
+    return xyz
+
+
+def mg_free(h):
+    return _check(load_library().mg_free(h))
+
+
+def mg_assemble_rhs(h, f, b):
+    return _check(load_library().mg_assemble_rhs(h, _ptr(f), _ptr(b)))
+
+
+def mg_solve(h, b, x, rtol, max_it, prec=MG_FP64):
+    st = MgStats()
+    rc = load_library().mg_solve(h, _ptr(b), _ptr(x), rtol, max_it, prec, C.byref(st))
+    _check(rc, allow=(MG_OK, MG_ERR_NOT_CONVERGED))
+    return st
+
+
+def mg_solve_host(h, b: np.ndarray, x: np.ndarray, rtol, max_it, prec=MG_FP64):
+    st = MgStats()
+    rc = load_library().mg_solve_host(h, _host_ptr(b), _host_ptr(x), rtol, max_it, prec, C.byref(st))
+    _check(rc, allow=(MG_OK, MG_ERR_NOT_CONVERGED))
+    return st
+
+
+def mg_vcycle(h, r, z, prec=MG_FP64):
+    return _check(load_library().mg_vcycle(h, _ptr(r), _ptr(z), prec))
+
+
+def mg_apply(h, level, op, x, x2, out, prec=MG_FP64):
+    return _check(load_library().mg_apply(h, level, op, _ptr(x), _ptr(x2), _ptr(out), prec))
+
+
+def mg_submit(ctx, h, b, x, rtol, max_it, prec=MG_MIXED_FP32):
+    t = C.c_uint64()
+    _check(load_library().mg_submit(ctx, h, _ptr(b), _ptr(x), rtol, max_it, prec, C.byref(t)))
+    return t.value
+
+
+def mg_poll(ctx, ticket):
+    st = MgStats()
+    rc = load_library().mg_poll(ctx, ticket, C.byref(st))
+    return rc, st
+
+
+def mg_cancel(ctx, ticket):
+    return load_library().mg_cancel(ctx, ticket)
+
+
+# ---------------------------------------------------------------- wrappers
+class Context:
+    def __init__(self, device=0, hbm_budget_bytes=0, allocator="torch", stream=None):
+        self.handle, self._keep = mg_init(device, hbm_budget_bytes, allocator, stream)
+        self.device = device
+
+    @property
+    def stream(self):
+        return self._keep[1]
+
+    def close(self):
+        if self.handle:
+            mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """A resident multigrid hierarchy for one mesh and problem."""
+
+    def __init__(self, ctx: Context, leafmesh, problem: MgProblem, opts: MgOpts | None = None):
+        self.ctx = ctx
+        self.handle = mg_setup(ctx.handle, leafmesh, problem, opts)
+        self.info = mg_hier_info(self.handle)
+        self.nc = self.info.nc
+        self.n_nodes = self.info.n_nodes
+        self.n_dofs = self.info.n_dofs
+        self.levels = self.info.levels
+
+    def coords(self):
+        return mg_node_coords(self.handle, self.n_nodes, self.info.dim)
+
+    def level_nodes(self):
+        return [self.info.level_nodes[l] for l in range(self.levels)]
+
+    def assemble_rhs(self, f, b):
+        return mg_assemble_rhs(self.handle, f, b)
+
+    def solve(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
+        return mg_solve(self.handle, b, x, rtol, max_it, prec)
+
+    def solve_host(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
+        return mg_solve_host(self.handle, b, x, rtol, max_it, prec)
+
+    def vcycle(self, r, z, prec=MG_FP64):
+        return mg_vcycle(self.handle, r, z, prec)
+
+    def apply(self, level, op, x, x2, out, prec=MG_FP64):
+        return mg_apply(self.handle, level, op, x, x2, out, prec)
+
+    def launch_count(self):
+        return int(load_library().mg_launch_count(self.handle))
+
+    def free(self):
+        if self.handle:
+            mg_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,248 @@
+"""CUDA path against the CPU oracle, through the C ABI (GB300 only).
+
+Every level operator (SpMV, fused smoother sweep, residual + restriction,
+prolongation + correction, coarse solve), one V-cycle, the right-hand-side
+assembly and the full Krylov solves are compared element by element with the
+oracle on the same seeded inputs.  Sizes span many SELL slices with a ragged
+tail (4225 = 132*32 + 1 nodes on the 64x64 mesh).
+
+Tolerances (derived from the arithmetic):
+* FP64 operators: |gpu - oracle| <= 1e-13 * (|A| |x| + |b|)_max  -- a few ulps
+  of the summed magnitudes (summation order differs).
+* FP32 operators: the same bound with 1e-5 (FP32 unit round-off 6e-8 times
+  row lengths <= 27 and FP32 rounding of the stored values).
+* Solves: FP64 solution vs the oracle's direct solve <= 1e-9 relative
+  (lumped-mass weighted L2) at rtol 1e-10; mixed precision reaches the same
+  residual with <= 1e-8 relative error.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import workloads as W
+from oracle import mg
+from oracle import problems as PB
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2405_05047_gb300 as G  # noqa: E402
+from paper_2405_05047_gb300 import binding as B  # noqa: E402
+
+CASES = {
+    "poisson64": (lambda: W.poisson64(64), PB.Problem(PB.POISSON), dict(kind=B.MG_POISSON), {}),
+    "td_adaptive": (lambda: W.td_adaptive(rounds=4, gamma=1.0),
+                    PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5)),
+                    dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)), {}),
+    "elasticity16": (lambda: W.uniform_leaves(3, (1, 1, 1), 4),
+                     PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
+                     dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), dict(omega=0.5)),
+    "elasticity_adaptive": (lambda: W.refine(W.uniform_leaves(3, (1, 1, 1), 3),
+                                             W._cell_box(W.uniform_leaves(3, (1, 1, 1), 3))[1][:, 0] <= 0.25 + 1e-12),
+                            PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
+                            dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), dict(omega=0.5)),
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+_cache = {}
+
+
+def setup_case(ctx, name):
+    if name in _cache:
+        return _cache[name]
+    mk, prob, pkw, okw = CASES[name]
+    lm = mk()
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(**okw))
+    _cache[name] = (lm, prob, oh, h)
+    return _cache[name]
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def bound(A, x, b=None):
+    s = abs(A) @ np.abs(x)
+    if b is not None:
+        s = s + np.abs(b)
+    return max(float(s.max()), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_structure_and_coords(ctx, name):
+    lm, prob, oh, h = setup_case(ctx, name)
+    assert h.levels == len(oh.levels)
+    assert h.level_nodes() == [lv.mesh.n_nodes for lv in oh.levels]
+    assert np.array_equal(h.coords(), oh.fine.mesh.coords)
+    assert h.info.n_hanging == int(oh.fine.mesh.hanging.sum())
+
+
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+@pytest.mark.parametrize("name", list(CASES))
+def test_level_operators(ctx, name, prec):
+    lm, prob, oh, h = setup_case(ctx, name)
+    nc = prob.nc
+    tdt = torch.float64 if prec == B.MG_FP64 else torch.float32
+    tol = 1e-13 if prec == B.MG_FP64 else 2e-5
+    rng = np.random.default_rng(11)
+    for l, lv in enumerate(oh.levels):
+        n = lv.A.shape[0]
+        x = rng.standard_normal(n)
+        bvec = rng.standard_normal(n)
+        x[lv.sys.fixed] = 0.0
+        bvec[lv.sys.fixed] = 0.0
+        if prec != B.MG_FP64:      # compare with FP64 evaluation of the FP32-rounded inputs
+            x = x.astype(np.float32).astype(np.float64)
+            bvec = bvec.astype(np.float32).astype(np.float64)
+        out = torch.empty(n, device="cuda", dtype=tdt)
+        h.apply(l, B.MG_OP_MATVEC, dev(x, tdt), None, out, prec)
+        ref = lv.A @ x
+        assert np.abs(out.cpu().double().numpy() - ref).max() <= tol * bound(lv.A, x), f"matvec level {l}"
+        h.apply(l, B.MG_OP_SMOOTH, dev(x, tdt), dev(bvec, tdt), out, prec)
+        ref = x + oh.omega * (lv.S @ (bvec - lv.A @ x))
+        sc = bound(abs(lv.S) @ abs(lv.A), x) + float((abs(lv.S) @ np.abs(bvec)).max()) + np.abs(x).max()
+        assert np.abs(out.cpu().double().numpy() - ref).max() <= tol * sc, f"smooth level {l}"
+        if l > 0:
+            nco = oh.levels[l - 1].A.shape[0]
+            d = torch.empty(nco, device="cuda", dtype=tdt)
+            h.apply(l, B.MG_OP_RESTRICT, dev(x, tdt), dev(bvec, tdt), d, prec)
+            ref = lv.R @ (bvec - lv.A @ x)
+            sc = float((abs(lv.R) @ (abs(lv.A) @ np.abs(x) + np.abs(bvec))).max())
+            assert np.abs(d.cpu().double().numpy() - ref).max() <= tol * sc, f"restrict level {l}"
+            y = rng.standard_normal(nco)
+            y[oh.levels[l - 1].sys.fixed] = 0.0
+            if prec != B.MG_FP64:
+                y = y.astype(np.float32).astype(np.float64)
+            h.apply(l, B.MG_OP_PROLONG_ADD, dev(y, tdt), dev(x, tdt), out, prec)
+            ref = x + lv.P @ y
+            sc = float((abs(lv.P) @ np.abs(y) + np.abs(x)).max())
+            assert np.abs(out.cpu().double().numpy() - ref).max() <= tol * sc, f"prolong level {l}"
+    # coarse direct solve
+    lv0 = oh.levels[0]
+    d0 = rng.standard_normal(lv0.A.shape[0])
+    if prec != B.MG_FP64:
+        d0 = d0.astype(np.float32).astype(np.float64)
+    z0 = torch.empty(lv0.A.shape[0], device="cuda", dtype=tdt)
+    h.apply(0, B.MG_OP_COARSE, dev(d0, tdt), None, z0, prec)
+    ref = np.linalg.solve(lv0.A.toarray(), d0)
+    ctol = 1e-11 if prec == B.MG_FP64 else 1e-6
+    assert np.abs(z0.cpu().double().numpy() - ref).max() <= ctol * max(np.abs(ref).max(), 1.0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle_fp64(ctx, name):
+    lm, prob, oh, h = setup_case(ctx, name)
+    rng = np.random.default_rng(5)
+    n = oh.fine.A.shape[0]
+    r = rng.standard_normal(n)
+    r[oh.fine.sys.fixed] = 0.0
+    z = torch.empty(n, device="cuda", dtype=torch.float64)
+    h.vcycle(dev(r), z, B.MG_FP64)
+    ref = oh.precondition(r)
+    assert np.abs(z.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_vcycle_fp32_close_to_fp64(ctx):
+    lm, prob, oh, h = setup_case(ctx, "poisson64")
+    rng = np.random.default_rng(6)
+    n = oh.fine.A.shape[0]
+    r = rng.standard_normal(n)
+    r[oh.fine.sys.fixed] = 0.0
+    r32 = r.astype(np.float32)
+    z = torch.empty(n, device="cuda", dtype=torch.float32)
+    h.vcycle(dev(r32, torch.float32), z, B.MG_MIXED_FP32)
+    ref = oh.precondition(r32.astype(np.float64))
+    assert np.abs(z.cpu().double().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def rhs_for(name, coords, nc):
+    if name.startswith("poisson"):
+        return W.f_poisson(coords)
+    if name.startswith("td"):
+        return W.f_transport(coords, 1e-3, (1.0, 0.5))
+    return np.tile([0.0, 0.0, -1.0], (coords.shape[0], 1)).ravel()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_assembly(ctx, name):
+    lm, prob, oh, h = setup_case(ctx, name)
+    s = PB.build_system(oh.fine.mesh, prob)
+    f = rhs_for(name, oh.fine.mesh.coords, prob.nc)
+    b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(dev(f), b)
+    ref = s.rhs(f)
+    assert np.abs(b.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def lumped_weights(oh, prob):
+    s = PB.build_system(oh.fine.mesh, prob)
+    m = np.asarray(s.F.sum(axis=1)).ravel()
+    return np.repeat(m, prob.nc)
+
+
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_matches_direct(ctx, name, prec):
+    lm, prob, oh, h = setup_case(ctx, name)
+    s = PB.build_system(oh.fine.mesh, prob)
+    f = rhs_for(name, oh.fine.mesh.coords, prob.nc)
+    bref = s.rhs(f)
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    b = dev(bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(b, x, rtol=1e-10, max_it=200, prec=prec)
+    assert st.status == 0, st.as_dict()
+    assert st.rel_res <= 1e-10
+    xg = x.cpu().numpy()
+    w = lumped_weights(oh, prob)
+    err = math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2))
+    assert err <= (1e-9 if prec == B.MG_FP64 else 1e-8), err
+    # the true residual of the returned solution, recomputed by the oracle
+    xr = xg.copy()
+    xr[s.hang] = 0.0
+    assert np.linalg.norm(bref - oh.fine.A @ xr) <= 1.01e-10 * np.linalg.norm(bref[~s.fixed])
+
+
+def test_solve_host_equals_device(ctx):
+    lm, prob, oh, h = setup_case(ctx, "td_adaptive")
+    s = PB.build_system(oh.fine.mesh, prob)
+    bref = s.rhs(rhs_for("td", oh.fine.mesh.coords, 1))
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st1 = h.solve(dev(bref), x, rtol=1e-10, max_it=200)
+    xh = np.zeros(h.n_dofs)
+    st2 = h.solve_host(bref.copy(), xh, rtol=1e-10, max_it=200)
+    assert st1.iters == st2.iters
+    assert np.array_equal(x.cpu().numpy(), xh)
+
+
+def test_deterministic_repeat(ctx):
+    """Fixed-order reductions: two solves give bitwise identical results."""
+    lm, prob, oh, h = setup_case(ctx, "poisson64")
+    s = PB.build_system(oh.fine.mesh, prob)
+    b = dev(s.rhs(W.f_poisson(oh.fine.mesh.coords)))
+    xs = []
+    for _ in range(2):
+        x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+        h.solve(b, x, rtol=1e-10, max_it=100, prec=B.MG_MIXED_FP32)
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
+
+
+def test_not_converged_status(ctx):
+    lm, prob, oh, h = setup_case(ctx, "poisson64")
+    s = PB.build_system(oh.fine.mesh, prob)
+    b = dev(s.rhs(W.f_poisson(oh.fine.mesh.coords)))
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(b, x, rtol=1e-14, max_it=2)
+    assert st.status == B.MG_ERR_NOT_CONVERGED and st.iters == 2

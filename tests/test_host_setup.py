@@ -1,0 +1,79 @@
+"""The library's host-built hierarchy against the oracle (CPU, no GPU).
+
+Level operators, transfers, smoother blocks, the coarse inverse and the
+right-hand-side load matrix that ``mg_setup`` would upload are compared entry
+by entry with the oracle's independently assembled matrices; the integer
+structure (levels, node counts, fixed-dof masks) must agree exactly.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import mg
+from oracle import problems as PB
+from paper_2405_05047_gb300 import binding as B
+from paper_2405_05047_gb300 import hostview as HV
+
+CASES = {
+    "poisson16": (lambda: W.uniform_leaves(2, (1, 1), 4), PB.Problem(PB.POISSON),
+                  dict(kind=B.MG_POISSON)),
+    "td_adaptive": (lambda: W.td_adaptive(rounds=3, gamma=1.0),
+                    PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5)),
+                    dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))),
+    "elasticity8": (lambda: W.uniform_leaves(3, (1, 1, 1), 3),
+                    PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
+                    dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))),
+    "elasticity_adaptive": (lambda: W.refine(W.uniform_leaves(3, (1, 1, 1), 2),
+                                             W._cell_box(W.uniform_leaves(3, (1, 1, 1), 2))[1][:, 0] <= 0.5 + 1e-12),
+                            PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
+                            dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))),
+    "channel": (lambda: W.oseen_channel(uniform=1, rounds=3),
+                PB.Problem(PB.TRANSPORT, eps=1e-2, beta=(1.0, 0.3), dirichlet=(0b1101,)),
+                dict(kind=B.MG_TRANSPORT, eps=1e-2, beta=(1.0, 0.3), dirichlet=(0b1101,))),
+}
+
+
+def close(a, b, tol=1e-13):
+    a, b = sp.csr_matrix(a), sp.csr_matrix(b)
+    d = (a - b).tocsr()
+    scale = max(abs(b).max(), 1e-300)
+    return abs(d).max() <= tol * scale if d.nnz else True
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_host_hierarchy_matches_oracle(name):
+    mk, prob, pkw = CASES[name]
+    lm = mk()
+    oh = mg.Hierarchy(lm, prob)
+    hh = HV.HostHierarchy(lm, B.make_problem(**pkw))
+    assert hh.levels == len(oh.levels)
+    nc = prob.nc
+    for l, lv in enumerate(oh.levels):
+        A = hh.matrix(l, HV.A)
+        assert A.shape == lv.A.shape
+        assert close(A, lv.A), f"A level {l}"
+        fm = hh.fixmask(l)
+        fixed = np.zeros(lv.mesh.n_nodes * nc, dtype=bool)
+        for c in range(nc):
+            fixed[c::nc] = (fm >> c) & 1
+        assert np.array_equal(fixed, lv.sys.fixed)
+        S = hh.matrix(l, HV.SMOOTHER)
+        assert close(S, lv.S, 1e-12), f"smoother level {l}"
+        if l > 0:
+            Pl = hh.matrix(l, HV.P)
+            Po = lv.P if nc == 1 else lv.P[::nc, ::nc]
+            assert close(Pl, Po, 0.0), f"P level {l}"
+            Rl = hh.matrix(l, HV.R)
+            assert (abs(Rl - Pl.T) > 0).nnz == 0
+    inv = hh.coarse_inverse()
+    A0 = oh.levels[0].A.toarray()
+    assert np.abs(inv @ A0 - np.eye(A0.shape[0])).max() < 1e-11
+    # load matrix: b = H^T F f on the finest level
+    sysf = PB.build_system(oh.fine.mesh, prob)
+    F = hh.matrix(hh.levels - 1, HV.LOAD)
+    Fo = (oh.fine.mesh.H().T @ sysf.F).tocsr()
+    hang = oh.fine.mesh.hanging
+    Fo = sp.diags((~hang).astype(float)) @ Fo
+    Fl = sp.diags((~hang).astype(float)) @ F
+    assert close(Fl, Fo), "load matrix"
