@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the GMG-preconditioned Krylov solve on GB300.
+
+Metric: DoF/s to 1e-8 relative residual = free DoFs / device time of one
+mg_solve from x0 = 0 until the true FP64 residual satisfies
+||b - A x|| <= 1e-8 ||b||, for the FP32-multigrid + FP64-Krylov path (value)
+and the plain FP64 path (reported beside it).  One "step" is one such solve.
+
+Default workload: the adaptive 2D transport-diffusion problem (eps = 1e-3,
+beta = (1, 0.5), SUPG) on a 1-irregular mesh refined around 16 seeded points
+(about 1.2 M nodes), BiCGStab preconditioned by a V(2,2) cycle with damped
+Jacobi.  Inputs are synthetic and seeded; L2 is flushed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own copy of the workload on its own GPU
+(replicas: the solve does not shard); value = all ranks' DoFs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "DoF/s to 1e-8 rel. residual (FP32-MG + FP64 Krylov)"
+GAMMA_TD = 0.18          # radius decay chosen so that the mesh has ~1.2 M nodes
+
+
+def workload(name):
+    """(leaf mesh, problem kwargs, opts kwargs, rhs function, description)."""
+    from paper_2405_05047_gb300 import binding as B
+    if name == "td_adaptive":
+        lm = W.td_adaptive(rounds=8, gamma=GAMMA_TD)
+        pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+        return lm, pk, dict(krylov=B.MG_BICGSTAB), (lambda xy: W.f_transport(xy, 1e-3, (1.0, 0.5))), (
+            "2D transport-diffusion eps=1e-3 beta=(1,0.5) Q1+SUPG, 32x32 start + 8 rounds refined within "
+            f"r_k=0.05*2^(-{GAMMA_TD}k) of 16 seeded points, 2:1, hanging nodes; BiCGStab + V(2,2) Jacobi w=0.8")
+    if name == "poisson64":
+        lm = W.poisson64(64)
+        return lm, dict(kind=B.MG_POISSON), dict(krylov=B.MG_CG), W.f_poisson, (
+            "2D Poisson 64x64 Q1, CG + V(2,2) Jacobi w=0.8, 5 levels")
+    if name.startswith("elasticity"):
+        n = int(name[len("elasticity"):] or 128)
+        lm = W.elasticity3d(n)
+        pk = dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))
+        return lm, pk, dict(krylov=B.MG_CG, omega=0.5), (
+            lambda xyz: np.tile([0.0, 0.0, -1.0], (xyz.shape[0], 1)).ravel()), (
+            f"3D linear elasticity {n}^3 Q1 hexes, mu=1 lambda=10, clamped x=0, f=(0,0,-1); "
+            "CG + V(2,2) point-block Jacobi w=0.5")
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(steps=2, rounds=5, rtol=1e-8):
+    """The oracle (numpy/scipy FP64, as it stands) on a bounded sample of the
+    same workload: the adaptive TD mesh with `rounds` refinement rounds."""
+    import threadpoolctl
+    from oracle import krylov, mg
+    from oracle import problems as PB
+    with threadpoolctl.threadpool_limits(1):
+        lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
+        prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+        t0 = time.perf_counter()
+        Hh = mg.Hierarchy(lm, prob)
+        s = PB.build_system(Hh.fine.mesh, prob)
+        b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
+        t_setup = time.perf_counter() - t0
+        n_free = int((~s.fixed).sum())
+        times, iters = [], []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            x, info = krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=rtol, maxit=500)
+            times.append(time.perf_counter() - t0)
+            iters.append(info["iters"])
+    t = statistics.mean(times)
+    return {"value": n_free / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle BiCGStab+V(2,2) FP64 solve to {rtol:g} of the same TD workload with {rounds} "
+                      f"refinement rounds ({n_free} free DoFs, {len(Hh.levels)} levels), mean of {steps} solves, "
+                      f"1 thread (setup {t_setup:.1f}s untimed)",
+            "iters": iters, "sec_per_solve": t}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    import threadpoolctl
+    from oracle import krylov, mg
+    from oracle import problems as PB
+    rounds = 5
+    with threadpoolctl.threadpool_limits(1):
+        lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
+        prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+        Hh = mg.Hierarchy(lm, prob)
+        s = PB.build_system(Hh.fine.mesh, prob)
+        b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
+        n_free = int((~s.fixed).sum())
+        for _ in range(warm):
+            krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
+        dt = (time.perf_counter() - t0) / steps
+    value = n_free / dt
+    sample = (f"oracle BiCGStab+V(2,2) FP64 solve to 1e-8 of the TD workload with {rounds} refinement rounds "
+              f"({n_free} free DoFs), 1 host thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "td_adaptive", "sample_rounds": rounds, "n_free": n_free},
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- our arm
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="td_adaptive")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2405_05047_gb300 as G
+    from paper_2405_05047_gb300 import binding as B
+    from paper_2405_05047_gb300 import build as BLD
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    BLD.build()
+    torch.cuda.set_device(local)
+
+    lm, pk, ok, ffun, desc = workload(args.workload)
+    ctx = G.Context(local)
+    stream = ctx.stream
+    t0 = time.perf_counter()
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
+    setup_s = time.perf_counter() - t0
+    info = h.info
+    n_free = info.n_free
+    coords = h.coords()
+    f = torch.from_numpy(np.ascontiguousarray(ffun(coords), dtype=np.float64)).cuda()
+    b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(f, b)
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MB > L2
+
+    def timed_solves(prec, k, warm):
+        stats = []
+        for _ in range(warm):
+            x.zero_()
+            h.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
+        ms = []
+        for _ in range(k):
+            x.zero_()
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = h.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(st)
+        return ms, stats
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        barrier()
+        ms_mixed, st_mixed = timed_solves(B.MG_MIXED_FP32, args.steps, args.warmup)
+        barrier()
+    # FP64 path of the same fused kernels (reported beside the value)
+    ms64, st64 = timed_solves(B.MG_FP64, max(2, args.steps // 2), 1)
+    barrier()
+    t_max = sum(ms_mixed)
+    if world > 1:
+        tt = torch.tensor([t_max], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n_free * args.steps / (t_max * 1e-3)
+    assert all(s.status == 0 for s in st_mixed + st64), [s.as_dict() for s in st_mixed + st64]
+
+    # end to end through the public host-buffer entry point (pinned host memory)
+    bh = torch.empty(h.n_dofs, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    xh = torch.zeros(h.n_dofs, dtype=torch.float64, pin_memory=True)
+    bhn, xhn = bh.numpy(), xh.numpy()
+    h.solve_host(bhn, xhn, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
+    e2e_ms = []
+    for _ in range(args.steps):
+        xhn[:] = 0.0
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.solve_host(bhn, xhn, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = world * n_free * args.steps / (sum(e2e_ms) * 1e-3)
+
+    # roofline of the dominant kernel: the fused FP32 smoother sweep on the
+    # finest level, cold L2 (flushed before every launch)
+    fine = h.levels - 1
+    nnz = info.level_rows_nnzb[fine] * h.nc * h.nc
+    n_rows = h.n_dofs
+    alg_bytes = nnz * (4 + 4) + n_rows * (4 + 4 + 4 + 4)
+    ker_ms = []
+    for _ in range(10):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        ker_ms.append(h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=1))
+    ker_ms_avg = statistics.mean(ker_ms)
+    hot_ms = h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=50)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / (ker_ms_avg * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        traffic = json.load(open(tr_path)).get(args.workload)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "td_adaptive":
+        try:
+            cpu = cpu_baseline()
+        except Exception as e:       # the baseline is reported, never required
+            cpu = {"error": str(e)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms_mixed), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-mg+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n_nodes": int(info.n_nodes),
+                   "n_free_dofs": int(n_free), "levels": int(info.levels), "hanging_nodes": int(info.n_hanging),
+                   "rtol": args.rtol, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "iters": [s.iters for s in st_mixed], "rel_res": max(s.rel_res for s in st_mixed),
+        "fp64": {"value": world * n_free / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
+                 "iters": [s.iters for s in st64], "rel_res": max(s.rel_res for s in st64)},
+        "speedup_mixed_vs_fp64": statistics.mean(ms64) / statistics.mean(ms_mixed),
+        "setup_s": setup_s,
+        "gpu_launches": int(sum(s.launches for s in st_mixed)),
+        "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": int(2 * 8 * h.n_dofs),
+                "d2h_bytes_per_step": int(8 * h.n_dofs), "ms_per_step": statistics.mean(e2e_ms)},
+        "roofline": {"bound": "hbm", "kernel": "k_smooth<float,1> finest level (fused residual + Jacobi sweep)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "alg_bytes_per_launch": int(alg_bytes), "ms_per_launch": ker_ms_avg,
+                     "ms_per_launch_l2_warm": hot_ms,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peaks else "fallback"},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    h.free()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

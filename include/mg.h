@@ -190,6 +190,12 @@ int mg_vcycle(mg_hier* h, const void* r, void* z, int prec);
 enum { MG_OP_MATVEC = 0, MG_OP_SMOOTH = 1, MG_OP_RESTRICT = 2, MG_OP_PROLONG_ADD = 3, MG_OP_COARSE = 4 };
 int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, void* out, int prec);
 
+/* Device time of one level operator: launches op (as mg_apply, on the
+ * library's own level buffers, FP64 or FP32 per prec) `reps` times back to
+ * back on the context's stream between two CUDA events and returns the mean
+ * milliseconds per launch in *ms.  For measurement only. */
+int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms);
+
 /* Serving: continuous batching of solves on resident hierarchies.
  * mg_submit queues a solve of h (b, x device buffers, caller-owned, not to be
  * touched until mg_poll returns a final status) and returns at once with a

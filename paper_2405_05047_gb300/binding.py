@@ -102,6 +102,7 @@ _SIGS = {
     "mg_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(MgStats)]),
     "mg_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "mg_launch_count": (C.c_int64, [C.c_void_p]),
+    "mg_time_op": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
 }
 
 
@@ -355,6 +356,11 @@ class Hierarchy:
 
     def apply(self, level, op, x, x2, out, prec=MG_FP64):
         return mg_apply(self.handle, level, op, x, x2, out, prec)
+
+    def time_op(self, level, op, prec=MG_FP64, reps=20):
+        ms = C.c_double()
+        _check(load_library().mg_time_op(self.handle, level, op, prec, reps, C.byref(ms)))
+        return ms.value
 
     def launch_count(self):
         return int(load_library().mg_launch_count(self.handle))

@@ -931,4 +931,54 @@ int mg_cancel(mg_ctx* c, uint64_t ticket) {
 
 int64_t mg_launch_count(const mg_hier* h) { return h ? h->launch_count : 0; }
 
+int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms) {
+  if (!h || !ms || level < 0 || level >= h->nlev || reps < 1) return fail(MG_ERR_INVALID, "bad argument");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  cudaStream_t s = h->ctx->stream;
+  LevelBufs& L = h->L[level];
+  const int nc = h->nc;
+  const bool d = prec == MG_FP64;
+  auto once = [&]() {
+    switch (op) {
+      case MG_OP_MATVEC:
+        if (d) launch_matvec<double>(L.A64.v, nc, L.o64, L.r64, nullptr, s);
+        else launch_matvec<float>(L.A32.v, nc, L.o32, L.r32, nullptr, s);
+        break;
+      case MG_OP_SMOOTH:
+        if (d) launch_smooth<double>(L.A64.v, nc, L.o64, L.b64, L.S64, L.t64, h->opts.omega, false, nullptr, s);
+        else launch_smooth<float>(L.A32.v, nc, L.o32, L.b32, L.S32, L.t32, h->opts.omega, false, nullptr, s);
+        break;
+      case MG_OP_RESTRICT:
+        if (level == 0) break;
+        if (d) {
+          launch_residual<double>(L.A64.v, nc, L.o64, L.b64, L.r64, nullptr, s);
+          launch_restrict<double>(L.R.t, nc, L.r64, h->L[level - 1].b64, nullptr, s);
+        } else {
+          launch_residual<float>(L.A32.v, nc, L.o32, L.b32, L.r32, nullptr, s);
+          launch_restrict<float>(L.R.t, nc, L.r32, h->L[level - 1].b32, nullptr, s);
+        }
+        break;
+      case MG_OP_PROLONG_ADD:
+        if (level == 0) break;
+        if (d) launch_prolong_add<double>(L.P.t, nc, h->L[level - 1].o64, L.o64, L.t64, nullptr, s);
+        else launch_prolong_add<float>(L.P.t, nc, h->L[level - 1].o32, L.o32, L.t32, nullptr, s);
+        break;
+      default:
+        break;
+    }
+  };
+  once();
+  CU(cudaEventRecord(h->ev0, s));
+  for (int i = 0; i < reps; ++i) once();
+  CU(cudaEventRecord(h->ev1, s));
+  CU(cudaEventSynchronize(h->ev1));
+  float t = 0;
+  CU(cudaEventElapsedTime(&t, h->ev0, h->ev1));
+  *ms = (double)t / reps;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
 }  // extern "C"
