@@ -28,6 +28,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+if "--impl" in sys.argv and "reference" in sys.argv:      # the oracle arm runs on one host thread
+    for _k, _v in {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}.items():
+        os.environ[_k] = _v
 
 import numpy as np  # noqa: E402
 
@@ -119,13 +122,26 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(steps=2, rounds=5, rtol=1e-8):
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def cpu_baseline(steps=4, rounds=7, rtol=1e-8):
     """The oracle (numpy/scipy FP64, as it stands) on a bounded sample of the
-    same workload: the adaptive TD mesh with `rounds` refinement rounds."""
-    import threadpoolctl
+    same workload (the adaptive TD mesh with `rounds` refinement rounds), run
+    in a child process pinned to one BLAS/OpenMP thread."""
+    env = dict(os.environ, **ONE_THREAD)
+    code = (f"import json, bench; print(json.dumps(bench._cpu_baseline_inproc({steps}, {rounds}, {rtol})))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_baseline_inproc(steps, rounds, rtol):
     from oracle import krylov, mg
     from oracle import problems as PB
-    with threadpoolctl.threadpool_limits(1):
+    if True:
         lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
         prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
         t0 = time.perf_counter()
@@ -154,11 +170,10 @@ def run_reference(args):
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
-    import threadpoolctl
     from oracle import krylov, mg
     from oracle import problems as PB
-    rounds = 5
-    with threadpoolctl.threadpool_limits(1):
+    rounds = 6
+    if True:
         lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
         prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
         Hh = mg.Hierarchy(lm, prob)
@@ -198,6 +213,8 @@ def main():
     ap.add_argument("--workload", default="td_adaptive")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="graph", choices=["graph", "direct"],
+                    help="direct: per-kernel launches (for profilers that cannot see inside graphs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -221,6 +238,7 @@ def main():
     ctx = G.Context(local)
     stream = ctx.stream
     t0 = time.perf_counter()
+    ok["launch_mode"] = 1 if args.launch == "direct" else 0
     h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
     setup_s = time.perf_counter() - t0
     info = h.info
@@ -306,6 +324,15 @@ def main():
         ker_ms.append(h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=1))
     ker_ms_avg = statistics.mean(ker_ms)
     hot_ms = h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=50)
+    per_level = []
+    for lvl in range(h.levels):
+        row = {"level": lvl, "nodes": int(info.level_nodes[lvl])}
+        for opn, op in (("smooth", B.MG_OP_SMOOTH), ("restrict", B.MG_OP_RESTRICT),
+                        ("prolong", B.MG_OP_PROLONG_ADD)):
+            if lvl == 0 and op != B.MG_OP_SMOOTH:
+                continue
+            row[opn + "_us"] = 1e3 * h.time_op(lvl, op, B.MG_MIXED_FP32, reps=20)
+        per_level.append(row)
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / (ker_ms_avg * 1e-3) / 1e9
@@ -343,6 +370,7 @@ def main():
                      "ms_per_launch_l2_warm": hot_ms,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peaks else "fallback"},
         "clocks": clk.summary(),
+        "per_level_fp32_us": per_level,
         "cpu_baseline": cpu,
     }
     if rank == 0:

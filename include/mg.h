@@ -110,6 +110,12 @@ typedef struct {
   int restart;                 /* GMRES restart length (default 30)           */
   int store_fp64;              /* keep FP64 level matrices (1) for MG_FP64    */
   int store_fp32;              /* keep FP32 level matrices (1) for mixed modes*/
+  int launch_mode;             /* 0: whole solve as one CUDA-graph while loop;
+                                  1: direct kernel launches, host polls the
+                                  status after every iteration (profilers)   */
+  int tail_rows;               /* levels with at most this many dofs (and all
+                                  coarser ones) run as one single-CTA kernel
+                                  per V-cycle (0: off; default 4096)          */
 } mg_opts;
 
 typedef struct {

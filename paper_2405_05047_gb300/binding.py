@@ -49,7 +49,8 @@ class MgProblem(C.Structure):
 class MgOpts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("min_level", C.c_int),
                 ("max_levels", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("store_fp64", C.c_int),
-                ("store_fp32", C.c_int)]
+                ("store_fp32", C.c_int), ("launch_mode", C.c_int),
+                ("tail_rows", C.c_int)]
 
 
 class MgInfo(C.Structure):

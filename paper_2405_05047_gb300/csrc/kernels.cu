@@ -12,6 +12,7 @@
 // atomics anywhere.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -20,6 +21,11 @@
 namespace mgi {
 
 namespace {
+
+// Programmatic dependent launch: kernels are launched while their predecessor
+// drains; every kernel waits here before it reads anything the predecessor
+// wrote.
+__device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
 
 __device__ __forceinline__ bool stopped(const int* done) { return done != nullptr && *(volatile const int*)done; }
 
@@ -57,25 +63,59 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
   return r;
 }
 
-// y_row = sum_j A(row, j) x_j for a scalar SELL row (thread = row).
-template <typename T>
-__device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x) {
-  const int64_t s0 = A.sptr[slice] + lane, s1 = A.sptr[slice + 1];
-  const T* __restrict__ val = (const T*)A.val;
-  T acc = T(0);
+// Vector loads: through the read-only path where the vector is constant for
+// the kernel's lifetime, plain (coherent) loads in the single-CTA tail kernel
+// that rewrites its vectors between __syncthreads().
+template <bool RO, typename T>
+__device__ __forceinline__ T vld(const T* p) {
+  if (RO) return __ldg(p);
+  return *p;
+}
+
+// y_row = sum_j A(row, j) x_j for a scalar SELL row (thread = row).  Slots
+// are processed in batches of 4 (column and value loads of a batch issued
+// together, then the 4 gathers, then the FMAs in slot order); the slice width
+// is the same for the 32 threads of a warp, so the remainder switch is
+// warp-uniform.  The summation order is the plain sequential one.
+template <typename AT, bool RO = true, typename VT, typename XT>
+__device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                                         const VT* __restrict__ val, int64_t slice, int lane,
+                                         const XT* __restrict__ x) {
+  const int64_t s0 = __ldg(sptr + slice) + lane, s1 = __ldg(sptr + slice + 1);
+  AT acc = AT(0);
   int64_t o = s0;
-  for (; o + 96 < s1; o += 128) {
-    const int c0 = __ldg(A.col + o), c1 = __ldg(A.col + o + 32), c2 = __ldg(A.col + o + 64),
-              c3 = __ldg(A.col + o + 96);
-    const T v0 = __ldg(val + o), v1 = __ldg(val + o + 32), v2 = __ldg(val + o + 64), v3 = __ldg(val + o + 96);
-    const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-    acc = fmad(v0, x0, acc);
-    acc = fmad(v1, x1, acc);
-    acc = fmad(v2, x2, acc);
-    acc = fmad(v3, x3, acc);
+  for (; o + 3 * 32 < s1; o += 4 * 32) {
+    const int c0 = __ldg(col + o), c1 = __ldg(col + o + 32), c2 = __ldg(col + o + 64), c3 = __ldg(col + o + 96);
+    const VT v0 = __ldg(val + o), v1 = __ldg(val + o + 32), v2 = __ldg(val + o + 64), v3 = __ldg(val + o + 96);
+    const XT x0 = vld<RO>(x + c0), x1 = vld<RO>(x + c1), x2 = vld<RO>(x + c2), x3 = vld<RO>(x + c3);
+    acc = fmad((AT)v0, (AT)x0, acc);
+    acc = fmad((AT)v1, (AT)x1, acc);
+    acc = fmad((AT)v2, (AT)x2, acc);
+    acc = fmad((AT)v3, (AT)x3, acc);
   }
-  for (; o < s1; o += 32) acc = fmad(__ldg(val + o), __ldg(x + __ldg(A.col + o)), acc);
+  const int rem = (int)((s1 - o + 31) >> 5);   // 0..3, identical across the warp
+  if (rem == 3) {
+    const int c0 = __ldg(col + o), c1 = __ldg(col + o + 32), c2 = __ldg(col + o + 64);
+    const VT v0 = __ldg(val + o), v1 = __ldg(val + o + 32), v2 = __ldg(val + o + 64);
+    const XT x0 = vld<RO>(x + c0), x1 = vld<RO>(x + c1), x2 = vld<RO>(x + c2);
+    acc = fmad((AT)v0, (AT)x0, acc);
+    acc = fmad((AT)v1, (AT)x1, acc);
+    acc = fmad((AT)v2, (AT)x2, acc);
+  } else if (rem == 2) {
+    const int c0 = __ldg(col + o), c1 = __ldg(col + o + 32);
+    const VT v0 = __ldg(val + o), v1 = __ldg(val + o + 32);
+    const XT x0 = vld<RO>(x + c0), x1 = vld<RO>(x + c1);
+    acc = fmad((AT)v0, (AT)x0, acc);
+    acc = fmad((AT)v1, (AT)x1, acc);
+  } else if (rem == 1) {
+    acc = fmad((AT)__ldg(val + o), (AT)vld<RO>(x + __ldg(col + o)), acc);
+  }
   return acc;
+}
+
+template <typename T, bool RO = true>
+__device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x) {
+  return sell_dot1x<T, RO>(A.sptr, A.col, (const T*)A.val, slice, lane, x);
 }
 
 // acc[0..2] = sum_j A(row, j) x_j for a 3x3-block SELL row.
@@ -101,7 +141,7 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
   }
 }
 
-template <typename T>
+template <typename T, bool RO = true>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
                                           T acc[3]) {
   const int64_t s0 = A.sptr[slice], s1 = A.sptr[slice + 1];
@@ -110,7 +150,7 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
   for (int64_t g = s0; g < s1; g += 32) {
     const int c = __ldg(A.col + g + lane);
     const T* __restrict__ v = val + g * 9 + lane;
-    const T x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
+    const T x0 = vld<RO>(x + 3 * c), x1 = vld<RO>(x + 3 * c + 1), x2 = vld<RO>(x + 3 * c + 2);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       T a = acc[i];
@@ -122,110 +162,257 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
   }
 }
 
-// ------------------------------------------------------------------ level ops
-// x_out = x + omega S (b - A x)  (Sec. 4.1.4), S = inverse diagonal block.
-template <typename T, int NC, bool FROM_ZERO>
-__global__ void __launch_bounds__(kBlock) k_smooth(SellView A, const T* __restrict__ x, const T* __restrict__ b,
-                                                    const T* __restrict__ Sinv, T* __restrict__ xo, T omega,
-                                                    const int* done) {
-  if (stopped(done)) return;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
-    const int64_t slice = row >> 5;
-    const int lane = (int)(row & 31);
-    if (NC == 1) {
-      T r = FROM_ZERO ? T(0) : sell_dot1<T>(A, slice, lane, x);
-      if (row < A.n) {
-        const T bi = b[row];
-        if (FROM_ZERO) xo[row] = omega * Sinv[row] * bi;
-        else xo[row] = fmad(omega * Sinv[row], bi - r, x[row]);
+// acc[c] += sum_j W(row, j) v[NC j + c] for a transfer matrix row: batches
+// of 4 slots (loads first), warp-uniform remainder, sequential summation.
+template <typename T, int NC, bool RO>
+__device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t slice, int lane, const T* v,
+                                                T acc[NC]) {
+  const int64_t s0 = __ldg(W.sptr + slice) + lane, s1 = __ldg(W.sptr + slice + 1);
+  int64_t o = s0;
+  for (; o < s1; o += 4 * 32) {
+    const int m = (int)min((int64_t)4, (s1 - o + 31) >> 5);   // warp-uniform
+    int j[4];
+    float w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < m) { j[k] = __ldg(W.col + o + 32 * k); w[k] = __ldg(W.w + o + 32 * k); }
+    T xv[4][NC];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < m)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xv[k][c] = vld<RO>(v + (int64_t)NC * j[k] + c);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < m)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fmad((T)w[k], xv[k][c], acc[c]);
+  }
+}
+
+// ------------------------------------------------------------------ row steps
+// One row (block row) of each level step.  The grid kernels below and the
+// single-CTA tail kernel call the same functions, so both produce bitwise
+// identical results.
+template <typename T, int NC, bool RO>
+__device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const T* x, const T* b, const T* Sinv,
+                                           T* xo, T omega, bool from_zero) {
+  const int64_t slice = row >> 5;
+  const int lane = (int)(row & 31);
+  if (NC == 1) {
+    T r = from_zero ? T(0) : sell_dot1<T, RO>(A, slice, lane, x);
+    if (row < A.n) {
+      const T bi = vld<RO>(b + row);
+      if (from_zero) xo[row] = omega * Sinv[row] * bi;
+      else xo[row] = fmad(omega * Sinv[row], bi - r, vld<RO>(x + row));
+    }
+  } else {
+    T acc[3] = {T(0), T(0), T(0)};
+    if (!from_zero) sell_dot3<T, RO>(A, slice, lane, x, acc);
+    if (row < A.n) {
+      T res[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) res[i] = vld<RO>(b + 3 * row + i) - acc[i];
+      const T* S = Sinv + 9 * row;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        T c = S[3 * i] * res[0];
+        c = fmad(S[3 * i + 1], res[1], c);
+        c = fmad(S[3 * i + 2], res[2], c);
+        xo[3 * row + i] = from_zero ? omega * c : fmad(omega, c, vld<RO>(x + 3 * row + i));
       }
-    } else {
-      T acc[3] = {T(0), T(0), T(0)};
-      if (!FROM_ZERO) sell_dot3<T>(A, slice, lane, x, acc);
-      if (row < A.n) {
-        T res[3];
+    }
+  }
+}
+
+template <typename T, int NC, bool RO>
+__device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y) {
+  const int64_t slice = row >> 5;
+  const int lane = (int)(row & 31);
+  if (NC == 1) {
+    T r = sell_dot1<T, RO>(A, slice, lane, x);
+    if (row < A.n) y[row] = vld<RO>(b + row) - r;
+  } else {
+    T acc[3];
+    sell_dot3<T, RO>(A, slice, lane, x, acc);
+    if (row < A.n)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) res[i] = b[3 * row + i] - acc[i];
-        const T* S = Sinv + 9 * row;
+      for (int i = 0; i < 3; ++i) y[3 * row + i] = vld<RO>(b + 3 * row + i) - acc[i];
+  }
+}
+
+template <typename T, int NC, bool RO>
+__device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row, const T* r, T* d, const T* Sinv,
+                                             T* x0, T omega) {
+  const int64_t slice = row >> 5;
+  const int lane = (int)(row & 31);
+  T acc[NC];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          T c = S[3 * i] * res[0];
-          c = fmad(S[3 * i + 1], res[1], c);
-          c = fmad(S[3 * i + 2], res[2], c);
-          xo[3 * row + i] = FROM_ZERO ? omega * c : fmad(omega, c, x[3 * row + i]);
+  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  transfer_gather<T, NC, RO>(R, slice, lane, r, acc);
+  if (row < R.n) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) d[NC * row + c] = acc[c];
+    if (x0) {
+      if (NC == 1) {
+        x0[row] = omega * Sinv[row] * acc[0];
+      } else {
+        const T* S = Sinv + NC * NC * row;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          T c = S[NC * i] * acc[0];
+#pragma unroll
+          for (int k = 1; k < NC; ++k) c = fmad(S[NC * i + k], acc[k], c);
+          x0[NC * row + i] = omega * c;
         }
       }
     }
   }
 }
 
+template <typename T, int NC, bool RO>
+__device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, const T* y, const T* xin, T* xo) {
+  const int64_t slice = row >> 5;
+  const int lane = (int)(row & 31);
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  transfer_gather<T, NC, RO>(P, slice, lane, y, acc);
+  if (row < P.n)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) xo[NC * row + c] = vld<RO>(xin + NC * row + c) + acc[c];
+}
+
+// ------------------------------------------------------------------ level ops
+// x_out = x + omega S (b - A x)  (Sec. 4.1.4), S = inverse diagonal block.
+template <typename T, int NC, bool FROM_ZERO>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, const T* __restrict__ x, const T* __restrict__ b,
+                                                    const T* __restrict__ Sinv, T* __restrict__ xo, T omega,
+                                                    const int* done) {
+  pdl_wait();
+  if (stopped(done)) return;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads)
+    row_smooth<T, NC, true>(A, row, x, b, Sinv, xo, omega, FROM_ZERO);
+}
+
 template <typename T, int NC, int MODE>   // MODE 0: y = A x; 1: y = b - A x
-__global__ void __launch_bounds__(kBlock) k_apply(SellView A, const T* __restrict__ x, const T* __restrict__ b,
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ y, const int* done) {
+  pdl_wait();
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
+    if (MODE == 1) {
+      row_residual<T, NC, true>(A, row, x, b, y);
+      continue;
+    }
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
     if (NC == 1) {
       T r = sell_dot1<T>(A, slice, lane, x);
-      if (row < A.n) y[row] = MODE ? b[row] - r : r;
+      if (row < A.n) y[row] = r;
     } else {
       T acc[3];
       sell_dot3<T>(A, slice, lane, x, acc);
       if (row < A.n)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) y[3 * row + i] = MODE ? b[3 * row + i] - acc[i] : acc[i];
+        for (int i = 0; i < 3; ++i) y[3 * row + i] = acc[i];
     }
   }
 }
 
-// d_j = sum_i R(j,i) r_i (R = P^T stored as its own gather matrix: no atomics)
-template <typename T, int NC>
-__global__ void __launch_bounds__(kBlock) k_restrict(TransferView R, const T* __restrict__ r, T* __restrict__ d,
+// d_j = sum_i R(j,i) r_i (R = P^T stored as its own gather matrix: no atomics).
+// With S0 the same pass also performs the coarser level's first smoothing
+// sweep from a zero guess, x0_j = omega S_j d_j (it needs no matrix).
+template <typename T, int NC, bool S0>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_restrict(TransferView R, const T* __restrict__ r, T* __restrict__ d,
+                                                      const T* __restrict__ Sinv, T* __restrict__ x0, T omega,
                                                       const int* done) {
+  pdl_wait();
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < R.nslices * 32; row += nthreads) {
-    const int64_t slice = row >> 5;
-    const int lane = (int)(row & 31);
-    T acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = T(0);
-    for (int64_t o = R.sptr[slice] + lane; o < R.sptr[slice + 1]; o += 32) {
-      const T w = (T)__ldg(R.w + o);
-      const int j = __ldg(R.col + o);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] = fmad(w, __ldg(r + (int64_t)NC * j + c), acc[c]);
-    }
-    if (row < R.n)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) d[NC * row + c] = acc[c];
-  }
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < R.nslices * 32; row += nthreads)
+    row_restrict<T, NC, true>(R, row, r, d, Sinv, S0 ? x0 : nullptr, omega);
 }
 
 // x_out_i = x_in_i + sum_j P(i,j) y_j   (Algorithm "Geometric multigrid solver", Step 4)
 template <typename T, int NC>
-__global__ void __launch_bounds__(kBlock) k_prolong(TransferView P, const T* __restrict__ y, const T* xin, T* xo,
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_prolong(TransferView P, const T* __restrict__ y, const T* xin, T* xo,
                                                      const int* done) {
+  pdl_wait();
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < P.nslices * 32; row += nthreads) {
-    const int64_t slice = row >> 5;
-    const int lane = (int)(row & 31);
-    T acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = T(0);
-    for (int64_t o = P.sptr[slice] + lane; o < P.sptr[slice + 1]; o += 32) {
-      const T w = (T)__ldg(P.w + o);
-      const int j = __ldg(P.col + o);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] = fmad(w, __ldg(y + (int64_t)NC * j + c), acc[c]);
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < P.nslices * 32; row += nthreads)
+    row_prolong<T, NC, true>(P, row, y, xin, xo);
+}
+
+// The V-cycle below (and including) level `nt - 1` in one CTA: every step of
+// Algorithm "Geometric multigrid solver" for the small levels, separated by
+// __syncthreads() instead of kernel boundaries.  Same row functions as the
+// grid kernels, so the result is bitwise identical to the multi-kernel cycle.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* btop, T* otop, int first_done,
+                                                        const int* done) {
+  pdl_wait();
+  if (stopped(done)) return;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int top = P.nt - 1, ns = P.nu1 + P.nu2;
+  const T om = (T)P.omega;
+  T* cur_of[kTailMax];
+  auto bvec = [&](int l) -> T* { return l == top ? const_cast<T*>(btop) : (T*)P.lv[l].b; };
+  auto ovec = [&](int l) -> T* { return l == top ? otop : (T*)P.lv[l].o; };
+  auto bufof = [&](int l, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? ovec(l) : (T*)P.lv[l].t; };
+  int fdone = first_done;
+  for (int l = top; l >= 1; --l) {
+    const TailLevel& L = P.lv[l];
+    const T* S = (const T*)L.S;
+    T* cur = nullptr;
+    for (int k = 0; k < P.nu1; ++k) {
+      T* dst = bufof(l, k);
+      if (!(k == 0 && fdone)) {
+        for (int64_t row = tid; row < L.A.nslices * 32; row += nth)
+          row_smooth<T, NC, false>(L.A, row, cur, bvec(l), S, dst, om, k == 0);
+        __syncthreads();
+      }
+      cur = dst;
     }
-    if (row < P.n)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) xo[NC * row + c] = xin[NC * row + c] + acc[c];
+    for (int64_t row = tid; row < L.A.nslices * 32; row += nth) row_residual<T, NC, false>(L.A, row, cur, bvec(l), (T*)L.r);
+    __syncthreads();
+    T* x0 = l - 1 > 0 ? bufof(l - 1, 0) : nullptr;
+    for (int64_t row = tid; row < L.R.nslices * 32; row += nth)
+      row_restrict<T, NC, false>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)P.lv[l - 1].S, x0, om);
+    __syncthreads();
+    fdone = l - 1 > 0;
+    cur_of[l] = cur;
+  }
+  {   // coarse direct solve, one warp per row
+    const int lane = tid & 31;
+    const T* d = bvec(0);
+    T* z = ovec(0);
+    for (int64_t row = tid >> 5; row < P.cn; row += nth >> 5) {
+      double acc = 0.0;
+      for (int64_t j = lane; j < P.cn; j += 32) acc = fma(P.cinv[row * P.cn + j], (double)d[j], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) z[row] = (T)acc;
+    }
+    __syncthreads();
+  }
+  for (int l = 1; l <= top; ++l) {
+    const TailLevel& L = P.lv[l];
+    T* cur = cur_of[l];
+    T* pdst = P.nu2 == 0 ? ovec(l) : cur;
+    for (int64_t row = tid; row < L.P.nslices * 32; row += nth)
+      row_prolong<T, NC, false>(L.P, row, ovec(l - 1), cur, pdst);
+    __syncthreads();
+    cur = pdst;
+    for (int k = P.nu1; k < ns; ++k) {
+      T* dst = bufof(l, k);
+      for (int64_t row = tid; row < L.A.nslices * 32; row += nth)
+        row_smooth<T, NC, false>(L.A, row, cur, bvec(l), (const T*)L.S, dst, om, false);
+      __syncthreads();
+      cur = dst;
+    }
   }
 }
 
@@ -233,6 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(TransferView P, const T* __r
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_coarse(const double* __restrict__ Ainv, int64_t n, const T* __restrict__ d,
                                                     T* __restrict__ z, const int* done) {
+  pdl_wait();
   if (stopped(done)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -247,6 +435,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse(const double* __restrict__ Ai
 // ------------------------------------------------------------------ vectors
 __global__ void k_rhs(SellView F, int nc, const double* __restrict__ f, const uint8_t* __restrict__ fix,
                       double* __restrict__ b) {
+  pdl_wait();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < F.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
@@ -267,6 +456,7 @@ __global__ void k_rhs(SellView F, int nc, const double* __restrict__ f, const ui
 // row i of the view is node Hc.rowmap...); here the view rows are all nodes
 // and regular rows are empty.
 __global__ void k_fill_hanging(TransferView Hc, int nc, double* x) {
+  pdl_wait();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < Hc.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
@@ -288,35 +478,74 @@ __global__ void k_fill_hanging(TransferView Hc, int nc, double* x) {
 
 __global__ void k_copy_fixed(int64_t n, int nc, const uint8_t* __restrict__ fix, const double* __restrict__ b,
                              const double* __restrict__ xin, double* __restrict__ x) {
+  pdl_wait();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads)
     for (int c = 0; c < nc; ++c) x[nc * i + c] = ((fix[i] >> c) & 1) ? b[nc * i + c] : xin[nc * i + c];
 }
 
-__global__ void k_norm_free(int64_t n, int nc, const uint8_t* __restrict__ fix, const double* __restrict__ b,
-                            double* __restrict__ part) {
-  __shared__ double sh[40];
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads)
-    for (int c = 0; c < nc; ++c)
-      if (!((fix[i] >> c) & 1)) acc = fma(b[nc * i + c], b[nc * i + c], acc);
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
 
 // ------------------------------------------------------------------ Krylov
-// All Krylov kernels run one thread per node (nc dofs) with the same grid as
-// the finest-level SpMV, so that every reduction has the same partial count.
+// All Krylov kernels run one thread per node (nc dofs) or per vector entry.
+// A kernel that produces dot products writes one partial per block; the block
+// that finishes last (integer arrival counter, no floating-point atomics)
+// sums the partials of every quantity in a fixed order and stores the scalars
+// in st->red[], so consumers read one double.  Kernels that end an iteration
+// run the convergence test in that last block and set the condition of the
+// CUDA-graph while loop there.
 __device__ __forceinline__ double pv(const PVec& p, int64_t i, double scale) {
   return p.f ? (double)p.f[i] * scale : p.d[i];
 }
 
+// Convergence test, thread 0 of the last block.  count: increment iter.
+__device__ void converge_step(KrylovState* st, bool count, unsigned long long cond) {
+  if (count) st->iter += 1;
+  const double rn = sqrt(st->red[Q_RR]);
+  st->rnorm = rn;
+  st->scale = rn > 0.0 ? rn : 1.0;
+  int done = 0, status = st->status;
+  if (!isfinite(rn)) { done = 1; status = status ? status : -6; }
+  else if (status != 0) done = 1;
+  else if (rn <= st->rtol * st->bnorm) { done = 1; status = 0; }
+  else if (st->iter >= st->max_it) { done = 1; status = -4; }
+  st->status = status;
+  st->done = done;
+  if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, done ? 0u : 1u);
+}
+
+// Writes this block's partials of nq quantities; returns true (in every
+// thread) in the block that arrived last, after it stored the sums in st->red.
+__device__ bool reduce_partials(double* part, int nq, const int* q, const double* v, KrylovState* st, double* sh) {
+  __shared__ int amlast;
+  for (int k = 0; k < nq; ++k) {
+    double t = block_sum(v[k], sh);
+    if (threadIdx.x == 0) part[(int64_t)q[k] * kMaxRedBlocks + blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) amlast = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+  for (int k = 0; k < nq; ++k) {
+    const double* pk = part + (int64_t)q[k] * kMaxRedBlocks;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(pk + i);
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) st->red[q[k]] = t;
+  }
+  if (threadIdx.x == 0) st->counter = 0;
+  __syncthreads();
+  return true;
+}
+
+// r = b - A x and ||r||^2; with test != 0 the initial convergence test runs
 template <int NC>
-__global__ void __launch_bounds__(kBlock) k_residual_norm(SellView A, const double* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_residual_norm(SellView A, const double* __restrict__ x,
                                                            const double* __restrict__ b, double* __restrict__ r,
-                                                           double* __restrict__ part) {
+                                                           double* part, KrylovState* st, int test) {
   __shared__ double sh[40];
+  pdl_wait();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
@@ -332,113 +561,104 @@ __global__ void __launch_bounds__(kBlock) k_residual_norm(SellView A, const doub
         for (int i = 0; i < 3; ++i) { double ri = b[3 * row + i] - a3[i]; r[3 * row + i] = ri; acc = fma(ri, ri, acc); }
     }
   }
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  const int q[1] = {Q_RR};
+  if (reduce_partials(part, 1, q, &acc, st, sh) && test && threadIdx.x == 0) converge_step(st, false, 0ull);
 }
 
-__global__ void k_init_state(KrylovState* st, const double* part_bb, int nred, double rtol, int max_it) {
+// ||b_free||^2 and the initial state of the Krylov loop
+__global__ void k_norm_init(int64_t n, int nc, const uint8_t* __restrict__ fix, const double* __restrict__ b,
+                            double* part, KrylovState* st, double rtol, int max_it) {
   __shared__ double sh[40];
-  double bb = sum_partials(part_bb, nred, sh);
-  if (threadIdx.x == 0) {
-    st->bnorm = bb > 0.0 ? sqrt(bb) : 1.0;
-    st->rtol = rtol;
-    st->max_it = max_it;
-    st->iter = 0;
-    st->done = 0;
-    st->status = 0;
-    st->rho = st->rho_prev = st->alpha = st->omega = 1.0;
-    st->beta = 0.0;
-    st->scale = 1.0;
-    st->restart_pos = 0;
+  pdl_wait();
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+    const uint8_t f = fix[i];
+    for (int c = 0; c < nc; ++c)
+      if (!((f >> c) & 1)) acc = fma(b[nc * i + c], b[nc * i + c], acc);
   }
-}
-
-__global__ void k_finalize(const double* part_rr, int nred, KrylovState* st, int first,
-                           unsigned long long cond_handle) {
-  __shared__ double sh[40];
-  if (st->done) {
-    if (threadIdx.x == 0 && cond_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, 0);
-    return;
-  }
-  double rr = sum_partials(part_rr, nred, sh);
-  if (threadIdx.x == 0) {
-    if (!first) st->iter += 1;
-    double rn = sqrt(rr);
-    st->rnorm = rn;
-    st->scale = rn > 0.0 ? rn : 1.0;
-    int done = 0, status = st->status;
-    if (!isfinite(rn)) { done = 1; status = status ? status : -6; }
-    else if (status != 0) done = 1;
-    else if (rn <= st->rtol * st->bnorm) { done = 1; status = 0; }
-    else if (st->iter >= st->max_it) { done = 1; status = -4; }
-    st->status = status;
-    st->done = done;
-    if (cond_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, done ? 0u : 1u);
+  const int q[1] = {Q_BB};
+  if (reduce_partials(part, 1, q, &acc, st, sh) && threadIdx.x == 0) {
+    st->bnorm = st->red[Q_BB] > 0.0 ? sqrt(st->red[Q_BB]) : 1.0;
+    st->rtol = rtol; st->max_it = max_it; st->iter = 0; st->done = 0; st->status = 0;
+    st->rho = st->rho_prev = st->alpha = st->omega = 1.0; st->beta = 0.0; st->scale = 1.0; st->restart_pos = 0;
+    st->gm_j = 0; st->gm_end = 0;
   }
 }
 
 __global__ void k_to_f32(int64_t n, const double* __restrict__ v, float* __restrict__ v32, const KrylovState* st) {
+  pdl_wait();
   if (st->done) return;
   const double inv = 1.0 / st->scale;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads)
-    v32[i] = __double2float_rn(v[i] * inv);
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 + 3 < n) {
+    const double2 a = *reinterpret_cast<const double2*>(v + i0), b = *reinterpret_cast<const double2*>(v + i0 + 2);
+    float4 o;
+    o.x = __double2float_rn(a.x * inv); o.y = __double2float_rn(a.y * inv);
+    o.z = __double2float_rn(b.x * inv); o.w = __double2float_rn(b.y * inv);
+    *reinterpret_cast<float4*>(v32 + i0) = o;
+  } else {
+    for (int64_t i = i0; i < n; ++i) v32[i] = __double2float_rn(v[i] * inv);
+  }
 }
 
-// (r, z) and (q, z) partials for flexible CG
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_cg_dots(int64_t nn, PVec z, const double* __restrict__ r,
-                                                     const double* __restrict__ q, double* part_rz, double* part_qz,
-                                                     const KrylovState* st) {
+// (r, z) and (q, z) for flexible CG
+__global__ void __launch_bounds__(kBlock, 4) k_cg_dots(int64_t n, PVec z, const double* __restrict__ r,
+                                                     const double* __restrict__ q, double* part, KrylovState* st) {
   __shared__ double sh[40];
+  pdl_wait();
   if (st->done) return;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   double a = 0.0, c = 0.0;
-  const int64_t lim = ((nn + 31) / 32) * 32;
-  for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < lim; node += nthreads) {
-    if (node < nn)
-      for (int k = 0; k < NC; ++k) {
-        const int64_t i = NC * node + k;
-        const double zi = pv(z, i, sc);
-        a = fma(r[i], zi, a);
-        c = fma(q[i], zi, c);
-      }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
+    double zi[4], ri[4], qi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) { zi[k] = pv(z, j, sc); ri[k] = r[j]; qi[k] = q[j]; }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i + k * nthreads < n) { a = fma(ri[k], zi[k], a); c = fma(qi[k], zi[k], c); }
   }
-  double t = block_sum(a, sh);
-  if (threadIdx.x == 0) part_rz[blockIdx.x] = t;
-  t = block_sum(c, sh);
-  if (threadIdx.x == 0) part_qz[blockIdx.x] = t;
+  const int qs[2] = {Q_RZ, Q_QZ};
+  const double v[2] = {a, c};
+  reduce_partials(part, 2, qs, v, st, sh);
 }
 
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_cg_update_p(int64_t nn, PVec z, double* __restrict__ p,
-                                                         const double* part_rz, const double* part_qz, int nred,
-                                                         KrylovState* st) {
-  __shared__ double sh[40];
+__global__ void __launch_bounds__(kBlock) k_cg_update_p(int64_t n, PVec z, double* __restrict__ p, KrylovState* st) {
+  pdl_wait();
   if (st->done) return;
-  const double rz = sum_partials(part_rz, nred, sh);
-  const double qz = sum_partials(part_qz, nred, sh);
+  const double rz = st->red[Q_RZ], qz = st->red[Q_QZ];
   const bool first = st->iter == st->restart_pos;
   // Polak-Ribiere: beta = (z_new, r_new - r_old) / rho_old, r_new - r_old = -alpha q
   const double beta = first ? 0.0 : -st->alpha * qz / st->rho_prev;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t lim = ((nn + 31) / 32) * 32;
-  for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < lim; node += nthreads)
-    if (node < nn)
-      for (int k = 0; k < NC; ++k) {
-        const int64_t i = NC * node + k;
-        p[i] = first ? pv(z, i, sc) : fma(beta, p[i], pv(z, i, sc));
-      }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
+    double zi[4], pi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) { zi[k] = pv(z, j, sc); pi[k] = first ? 0.0 : p[j]; }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) p[j] = first ? zi[k] : fma(beta, pi[k], zi[k]);
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) { st->rho = rz; st->beta = beta; }
 }
 
 // out = A p (p given as PVec), partial of (w, out) (w = p when w == nullptr)
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_spmv_dot(SellView A, PVec p, const double* __restrict__ w,
-                                                      double* __restrict__ out, double* part, const KrylovState* st) {
+template <int NC, bool F32>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_dot(SellView A, PVec p, const double* __restrict__ w,
+                                                      double* __restrict__ out, double* part, int qk,
+                                                      KrylovState* st) {
   __shared__ double sh[40];
+  pdl_wait();
   if (st->done) return;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -447,84 +667,97 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(SellView A, PVec p, const d
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
     if (NC == 1) {
-      double ax;
-      if (p.f) {
-        // A (scale * p32): accumulate in FP64 from FP32 operands
-        const int64_t s0 = A.sptr[slice] + lane, s1 = A.sptr[slice + 1];
-        const double* val = (const double*)A.val;
-        double a = 0.0;
-        for (int64_t o = s0; o < s1; o += 32) a = fma(__ldg(val + o), (double)__ldg(p.f + __ldg(A.col + o)), a);
-        ax = a * sc;
-      } else {
-        ax = sell_dot1<double>(A, slice, lane, p.d);
-      }
+      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, p.f) * sc
+                            : sell_dot1<double>(A, slice, lane, p.d);
       if (row < A.n) {
         out[row] = ax;
-        acc = fma(w ? w[row] : pv(p, row, sc), ax, acc);
+        acc = fma(w ? w[row] : (F32 ? (double)p.f[row] * sc : p.d[row]), ax, acc);
       }
     } else {
       double a3[3];
-      if (p.f) sell_dot3<double, float>(A, slice, lane, p.f, 1.0, a3);
+      if (F32) sell_dot3<double, float>(A, slice, lane, p.f, 1.0, a3);
       else sell_dot3<double>(A, slice, lane, p.d, a3);
       if (row < A.n)
         for (int i = 0; i < 3; ++i) {
-          const double y = p.f ? a3[i] * sc : a3[i];
+          const double y = F32 ? a3[i] * sc : a3[i];
           out[3 * row + i] = y;
-          acc = fma(w ? w[3 * row + i] : pv(p, 3 * row + i, sc), y, acc);
+          acc = fma(w ? w[3 * row + i] : (F32 ? (double)p.f[3 * row + i] * sc : p.d[3 * row + i]), y, acc);
         }
     }
   }
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  const int qs[1] = {qk};
+  reduce_partials(part, 1, qs, &acc, st, sh);
 }
 
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_cg_update_xr(int64_t nn, const double* __restrict__ p,
+// x += alpha p, r -= alpha q, ||r||^2, then (last block) the convergence test
+__global__ void __launch_bounds__(kBlock, 4) k_cg_update_xr(int64_t n, const double* __restrict__ p,
                                                           const double* __restrict__ q, double* __restrict__ x,
-                                                          double* __restrict__ r, const double* part_pq, int nred,
-                                                          double* part_rr, KrylovState* st) {
+                                                          double* __restrict__ r, double* part, KrylovState* st,
+                                                          unsigned long long cond) {
   __shared__ double sh[40];
+  pdl_wait();
   if (st->done) return;
-  const double pq = sum_partials(part_pq, nred, sh);
+  const double pq = st->red[Q_PQ];
   const double alpha = st->rho / pq;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t lim = ((nn + 31) / 32) * 32;
   double acc = 0.0;
-  for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < lim; node += nthreads)
-    if (node < nn)
-      for (int k = 0; k < NC; ++k) {
-        const int64_t i = NC * node + k;
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        acc = fma(ri, ri, acc);
-      }
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) {
-    part_rr[blockIdx.x] = t;
-    if (blockIdx.x == 0) {
-      st->alpha = alpha;
-      st->rho_prev = st->rho;
-      if (pq == 0.0) st->status = -5;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
+    double pi[4], qi[4], xi[4], ri[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) { pi[k] = p[j]; qi[k] = q[j]; xi[k] = x[j]; ri[k] = r[j]; }
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) {
+        x[j] = fma(alpha, pi[k], xi[k]);
+        const double rr = fma(-alpha, qi[k], ri[k]);
+        r[j] = rr;
+        acc = fma(rr, rr, acc);
+      }
+    }
+  }
+  const int qs[1] = {Q_RR};
+  if (reduce_partials(part, 1, qs, &acc, st, sh) && threadIdx.x == 0) {
+    st->alpha = alpha;
+    st->rho_prev = st->rho;
+    if (pq == 0.0) st->status = -5;
+    converge_step(st, true, cond);
   }
 }
 
-// BiCGStab (van der Vorst), right preconditioned
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_bicg_p(int64_t nn, const double* __restrict__ r,
+// BiCGStab (van der Vorst), right preconditioned.  p = r + beta (p - omega v);
+// with p32 also the FP32 preconditioner input p / scale.
+__global__ void __launch_bounds__(kBlock) k_bicg_p(int64_t n, const double* __restrict__ r,
                                                     const double* __restrict__ v, double* __restrict__ p,
-                                                    const double* part_rhr, int nred, KrylovState* st) {
-  __shared__ double sh[40];
+                                                    float* __restrict__ p32, KrylovState* st) {
+  pdl_wait();
   if (st->done) return;
-  const double rho = sum_partials(part_rhr, nred, sh);
+  const double rho = st->red[Q_RHR];
   const bool first = st->iter == st->restart_pos;
   const double beta = first ? 0.0 : (rho / st->rho_prev) * (st->alpha / st->omega);
   const double om = st->omega;
+  const double inv = 1.0 / st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n = nn * NC;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads)
-    p[i] = first ? r[i] : fma(beta, fma(-om, v[i], p[i]), r[i]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
+    double ri[4], vi[4], pi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) { ri[k] = r[j]; vi[k] = first ? 0.0 : v[j]; pi[k] = first ? 0.0 : p[j]; }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) {
+        const double pn = first ? ri[k] : fma(beta, fma(-om, vi[k], pi[k]), ri[k]);
+        p[j] = pn;
+        if (p32) p32[j] = __double2float_rn(pn * inv);
+      }
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->rho = rho;
     st->beta = beta;
@@ -532,17 +765,33 @@ __global__ void __launch_bounds__(kBlock) k_bicg_p(int64_t nn, const double* __r
   }
 }
 
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_bicg_s(int64_t nn, const double* __restrict__ r,
+// s = r - alpha v (alpha = rho / (rhat, v)); with s32 the FP32 copy s / scale
+__global__ void __launch_bounds__(kBlock) k_bicg_s(int64_t n, const double* __restrict__ r,
                                                     const double* __restrict__ v, double* __restrict__ s,
-                                                    const double* part_rhv, int nred, KrylovState* st) {
-  __shared__ double sh[40];
+                                                    float* __restrict__ s32, KrylovState* st) {
+  pdl_wait();
   if (st->done) return;
-  const double rhv = sum_partials(part_rhv, nred, sh);
+  const double rhv = st->red[Q_RHV];
   const double alpha = st->rho / rhv;
+  const double inv = 1.0 / st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n = nn * NC;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) s[i] = fma(-alpha, v[i], r[i]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
+    double ri[4], vi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) { ri[k] = r[j]; vi[k] = v[j]; }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) {
+        const double si = fma(-alpha, vi[k], ri[k]);
+        s[j] = si;
+        if (s32) s32[j] = __double2float_rn(si * inv);
+      }
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->alpha = alpha;
     if (rhv == 0.0) st->status = -5;
@@ -550,11 +799,11 @@ __global__ void __launch_bounds__(kBlock) k_bicg_s(int64_t nn, const double* __r
 }
 
 // t = A sh, partials (t, s) and (t, t)
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_spmv_2dots(SellView A, PVec shv, const double* __restrict__ sv,
-                                                        double* __restrict__ t, double* part_ts, double* part_tt,
-                                                        const KrylovState* st) {
+template <int NC, bool F32>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_2dots(SellView A, PVec shv, const double* __restrict__ sv,
+                                                        double* __restrict__ t, double* part, KrylovState* st) {
   __shared__ double sh[40];
+  pdl_wait();
   if (st->done) return;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -563,78 +812,332 @@ __global__ void __launch_bounds__(kBlock) k_spmv_2dots(SellView A, PVec shv, con
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
     if (NC == 1) {
-      double ax;
-      if (shv.f) {
-        const int64_t s0 = A.sptr[slice] + lane, s1 = A.sptr[slice + 1];
-        const double* val = (const double*)A.val;
-        double acc = 0.0;
-        for (int64_t o = s0; o < s1; o += 32) acc = fma(__ldg(val + o), (double)__ldg(shv.f + __ldg(A.col + o)), acc);
-        ax = acc * sc;
-      } else {
-        ax = sell_dot1<double>(A, slice, lane, shv.d);
-      }
+      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, shv.f) * sc
+                            : sell_dot1<double>(A, slice, lane, shv.d);
       if (row < A.n) { t[row] = ax; a = fma(ax, sv[row], a); c = fma(ax, ax, c); }
     } else {
       double a3[3];
-      if (shv.f) sell_dot3<double, float>(A, slice, lane, shv.f, 1.0, a3);
+      if (F32) sell_dot3<double, float>(A, slice, lane, shv.f, 1.0, a3);
       else sell_dot3<double>(A, slice, lane, shv.d, a3);
       if (row < A.n)
         for (int i = 0; i < 3; ++i) {
-          const double y = shv.f ? a3[i] * sc : a3[i];
+          const double y = F32 ? a3[i] * sc : a3[i];
           t[3 * row + i] = y;
           a = fma(y, sv[3 * row + i], a);
           c = fma(y, y, c);
         }
     }
   }
-  double tt = block_sum(a, sh);
-  if (threadIdx.x == 0) part_ts[blockIdx.x] = tt;
-  tt = block_sum(c, sh);
-  if (threadIdx.x == 0) part_tt[blockIdx.x] = tt;
+  const int qs[2] = {Q_TS, Q_TT};
+  const double v[2] = {a, c};
+  reduce_partials(part, 2, qs, v, st, sh);
 }
 
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_bicg_x(int64_t nn, PVec ph, PVec shv, const double* __restrict__ sv,
+// omega = (t,s)/(t,t); x += alpha ph + omega sh; r = s - omega t; (r,r), (rhat,r)
+__global__ void __launch_bounds__(kBlock, 4) k_bicg_x(int64_t n, PVec ph, PVec shv, const double* __restrict__ sv,
                                                     const double* __restrict__ t, const double* __restrict__ rhat,
-                                                    double* __restrict__ x, double* __restrict__ r,
-                                                    const double* part_ts, const double* part_tt, int nred,
-                                                    double* part_rr, double* part_rhr, KrylovState* st) {
+                                                    double* __restrict__ x, double* __restrict__ r, double* part,
+                                                    KrylovState* st, unsigned long long cond) {
   __shared__ double sh[40];
+  pdl_wait();
   if (st->done) return;
-  const double ts = sum_partials(part_ts, nred, sh);
-  const double tt = sum_partials(part_tt, nred, sh);
+  const double ts = st->red[Q_TS], tt = st->red[Q_TT];
   const double om = tt > 0.0 ? ts / tt : 0.0;
   const double alpha = st->alpha;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t lim = ((nn + 31) / 32) * 32;
   double a = 0.0, c = 0.0;
-  for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < lim; node += nthreads)
-    if (node < nn)
-      for (int k = 0; k < NC; ++k) {
-        const int64_t i = NC * node + k;
-        x[i] = fma(om, pv(shv, i, sc), fma(alpha, pv(ph, i, sc), x[i]));
-        const double ri = fma(-om, t[i], sv[i]);
-        r[i] = ri;
-        a = fma(ri, ri, a);
-        c = fma(rhat[i], ri, c);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * nthreads) {
+    double phi[2], shi[2], si[2], ti[2], rh[2], xi[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) {
+        phi[k] = pv(ph, j, sc); shi[k] = pv(shv, j, sc); si[k] = sv[j]; ti[k] = t[j]; rh[k] = rhat[j]; xi[k] = x[j];
       }
-  double s1 = block_sum(a, sh);
-  if (threadIdx.x == 0) part_rr[blockIdx.x] = s1;
-  s1 = block_sum(c, sh);
-  if (threadIdx.x == 0) {
-    part_rhr[blockIdx.x] = s1;
-    if (blockIdx.x == 0) {
-      st->omega = om;
-      st->rho_prev = st->rho;
-      if (!(tt > 0.0) || om == 0.0) st->status = -5;
     }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) {
+        x[j] = fma(om, shi[k], fma(alpha, phi[k], xi[k]));
+        const double rr = fma(-om, ti[k], si[k]);
+        r[j] = rr;
+        a = fma(rr, rr, a);
+        c = fma(rh[k], rr, c);
+      }
+    }
+  }
+  const int qs[2] = {Q_RR, Q_RHR};
+  const double v[2] = {a, c};
+  if (reduce_partials(part, 2, qs, v, st, sh) && threadIdx.x == 0) {
+    st->omega = om;
+    st->rho_prev = st->rho;
+    if (!(tt > 0.0) || om == 0.0) st->status = -5;
+    converge_step(st, true, cond);
+  }
+}
+
+
+// ------------------------------------------------------------------ GMRES
+// Flexible GMRES(m) with right preconditioning: Arnoldi on A M^-1 with the
+// preconditioned vectors z_j kept (Saad 2003, Sec. 9.4.1), orthogonalisation
+// by classical Gram-Schmidt applied twice (two sweeps of one block-dot pass
+// and one update pass each), Hessenberg QR by Givens rotations (Sec. 6.5.3).
+// The Hessenberg matrix, the rotations and the small triangular solve stay on
+// the device.  Phase flags in the state gate the cycle-start and cycle-end
+// kernels, so every Arnoldi step is the same fixed kernel sequence.
+__global__ void __launch_bounds__(kBlock) k_gm_start(int64_t n, const double* __restrict__ r, float* __restrict__ v32,
+                                                     double* __restrict__ v64, GmresView G, KrylovState* st) {
+  pdl_wait();
+  if (st->done || st->gm_j != 0) return;
+  const double rn = sqrt(st->red[Q_RR]);
+  const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+    const double v = r[i] * inv;
+    G.V[i] = v;
+    if (v32) v32[i] = __double2float_rn(v);
+    if (v64) v64[i] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x <= G.m) G.g[threadIdx.x] = threadIdx.x == 0 ? rn : 0.0;
+}
+
+template <int NC, bool F32>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_spmv(SellView A, PVec z, double* __restrict__ w,
+                                                                      GmresView G, KrylovState* st) {
+  pdl_wait();
+  if (st->done) return;
+  const int j = st->gm_j;
+  const int64_t n = A.n * NC;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
+    const int64_t slice = row >> 5;
+    const int lane = (int)(row & 31);
+    if (NC == 1) {
+      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, z.f)
+                            : sell_dot1<double>(A, slice, lane, z.d);
+      if (row < A.n) {
+        w[row] = ax;
+        if (F32) G.Z32[(int64_t)j * n + row] = z.f[row];
+        else G.Z64[(int64_t)j * n + row] = z.d[row];
+      }
+    } else {
+      double a3[3];
+      if (F32) sell_dot3<double, float>(A, slice, lane, z.f, 1.0, a3);
+      else sell_dot3<double>(A, slice, lane, z.d, a3);
+      if (row < A.n)
+        for (int i = 0; i < 3; ++i) {
+          w[3 * row + i] = a3[i];
+          if (F32) G.Z32[(int64_t)j * n + 3 * row + i] = z.f[3 * row + i];
+          else G.Z64[(int64_t)j * n + 3 * row + i] = z.d[3 * row + i];
+        }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && F32) G.zs[j] = 1.0;
+}
+
+// partial dots (v_i, w), i = blockIdx.y <= j
+__global__ void __launch_bounds__(kBlock) k_gm_dots(int64_t n, const double* __restrict__ w, GmresView G,
+                                                    KrylovState* st) {
+  __shared__ double sh[40];
+  pdl_wait();
+  if (st->done) return;
+  const int i = blockIdx.y;
+  if (i > st->gm_j) return;
+  const double* __restrict__ v = G.V + (int64_t)i * n;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += 2 * nthreads) {
+    const int64_t e2 = e + nthreads;
+    const double a0 = v[e], b0 = w[e];
+    double a1 = 0.0, b1 = 0.0;
+    if (e2 < n) { a1 = v[e2]; b1 = w[e2]; }
+    acc = fma(a0, b0, acc);
+    acc = fma(a1, b1, acc);
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) G.part[(int64_t)i * kMaxRedBlocks + blockIdx.x] = t;
+}
+
+// h_i = sum of the partials (one block per i), added into column j of H
+__global__ void k_gm_reduce(GmresView G, KrylovState* st, int nparts, int pass) {
+  __shared__ double sh[40];
+  pdl_wait();
+  if (st->done) return;
+  const int i = blockIdx.x, j = st->gm_j;
+  if (i > j) return;
+  const double* p = G.part + (int64_t)i * kMaxRedBlocks;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) acc += p[k];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    G.hv[i] = t;
+    double* Hc = G.H + (int64_t)j * (G.m + 1);
+    Hc[i] = pass == 0 ? t : Hc[i] + t;
+  }
+}
+
+// w -= sum_{i <= j} h_i v_i ; on the second sweep also ||w||^2 -> red[Q_SS]
+__global__ void __launch_bounds__(kBlock) k_gm_axpy(int64_t n, double* __restrict__ w, GmresView G, KrylovState* st,
+                                                    double* part, int pass) {
+  __shared__ double sh[40];
+  pdl_wait();
+  if (st->done) return;
+  const int j = st->gm_j;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += nthreads) {
+    double we = w[e];
+    for (int i = 0; i <= j; ++i) we = fma(-G.hv[i], G.V[(int64_t)i * n + e], we);
+    w[e] = we;
+    acc = fma(we, we, acc);
+  }
+  if (pass == 1) {
+    const int q[1] = {Q_SS};
+    reduce_partials(part, 1, q, &acc, st, sh);
+  }
+}
+
+// Givens rotations on column j, new rotation, residual estimate |g_{j+1}|;
+// at the end of a cycle the triangular system H y = g is solved here.
+__global__ void k_gm_givens(GmresView G, KrylovState* st) {
+  pdl_wait();
+  if (st->done || threadIdx.x != 0) return;
+  const int j = st->gm_j, m = G.m;
+  double* Hc = G.H + (int64_t)j * (m + 1);
+  Hc[j + 1] = sqrt(st->red[Q_SS]);
+  for (int i = 0; i < j; ++i) {
+    const double t = G.cs[i] * Hc[i] + G.sn[i] * Hc[i + 1];
+    Hc[i + 1] = -G.sn[i] * Hc[i] + G.cs[i] * Hc[i + 1];
+    Hc[i] = t;
+  }
+  const double den = hypot(Hc[j], Hc[j + 1]);
+  const double c = den > 0.0 ? Hc[j] / den : 1.0, sn = den > 0.0 ? Hc[j + 1] / den : 0.0;
+  G.cs[j] = c;
+  G.sn[j] = sn;
+  st->red[Q_TT] = Hc[j + 1];           // h_{j+1,j} before the rotation: norm of the new basis vector
+  Hc[j] = den;
+  Hc[j + 1] = 0.0;
+  G.g[j + 1] = -sn * G.g[j];
+  G.g[j] = c * G.g[j];
+  st->iter += 1;
+  const double est = fabs(G.g[j + 1]);
+  const bool end = est <= st->rtol * st->bnorm || j + 1 >= m || st->iter >= st->max_it || !(den > 0.0) ||
+                   !isfinite(est);
+  st->gm_end = end ? 1 : 0;
+  if (end) {
+    const int k = j + 1;
+    for (int r = k - 1; r >= 0; --r) {
+      double acc = G.g[r];
+      for (int c2 = r + 1; c2 < k; ++c2) acc -= G.H[(int64_t)c2 * (m + 1) + r] * G.y[c2];
+      G.y[r] = acc / G.H[(int64_t)r * (m + 1) + r];
+    }
+    st->restart_pos = k;               // number of columns used in this cycle
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_gm_next(int64_t n, const double* __restrict__ w, float* __restrict__ v32,
+                                                    double* __restrict__ v64, GmresView G, KrylovState* st) {
+  pdl_wait();
+  if (st->done || st->gm_end) return;
+  const int j = st->gm_j;
+  const double inv = 1.0 / st->red[Q_TT];
+  double* vn = G.V + (int64_t)(j + 1) * n;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += nthreads) {
+    const double v = w[e] * inv;
+    vn[e] = v;
+    if (v32) v32[e] = __double2float_rn(v);
+    if (v64) v64[e] = v;
+  }
+}
+
+// advance the column counter once every block of k_gm_next has read it
+__global__ void k_gm_advance(KrylovState* st) {
+  pdl_wait();
+  if (threadIdx.x != 0 || st->done) return;
+  if (!st->gm_end) st->gm_j += 1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_gm_update_x(int64_t n, double* __restrict__ x, GmresView G,
+                                                        KrylovState* st) {
+  pdl_wait();
+  if (st->done || !st->gm_end) return;
+  const int k = st->restart_pos;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += nthreads) {
+    double xe = x[e];
+    for (int i = 0; i < k; ++i) {
+      const double zi = G.Z32 ? (double)G.Z32[(int64_t)i * n + e] * G.zs[i] : G.Z64[(int64_t)i * n + e];
+      xe = fma(G.y[i], zi, xe);
+    }
+    x[e] = xe;
+  }
+}
+
+// cycle end: true residual, convergence test, next cycle starts at column 0
+template <int NC>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_residual(SellView A, const double* __restrict__ x,
+                                                                          const double* __restrict__ b,
+                                                                          double* __restrict__ r, double* part,
+                                                                          KrylovState* st, unsigned long long cond) {
+  __shared__ double sh[40];
+  pdl_wait();
+  if (st->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
+  if (!st->gm_end) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 1u);
+    return;
+  }
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
+    const int64_t slice = row >> 5;
+    const int lane = (int)(row & 31);
+    if (NC == 1) {
+      double ax = sell_dot1<double>(A, slice, lane, x);
+      if (row < A.n) { double ri = b[row] - ax; r[row] = ri; acc = fma(ri, ri, acc); }
+    } else {
+      double a3[3];
+      sell_dot3<double>(A, slice, lane, x, a3);
+      if (row < A.n)
+        for (int i = 0; i < 3; ++i) { double ri = b[3 * row + i] - a3[i]; r[3 * row + i] = ri; acc = fma(ri, ri, acc); }
+    }
+  }
+  const int q[1] = {Q_RR};
+  if (reduce_partials(part, 1, q, &acc, st, sh) && threadIdx.x == 0) {
+    const int iters = st->iter;
+    converge_step(st, false, cond);     // sets done / status / the while condition
+    st->iter = iters;
+    st->gm_j = 0;
+    st->gm_end = 0;
   }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+static bool g_pdl = true;
+void set_pdl(bool on) { g_pdl = on; }
+
+template <typename... KArgs, typename... Args>
+static void launch(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 int grid_for_rows(int64_t rows) {
   int64_t g = (rows + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
@@ -649,48 +1152,55 @@ void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* S
                    bool from_zero, const int* done, cudaStream_t s) {
   const int g = grid_sell(A.nslices);
   if (nc == 1) {
-    if (from_zero) k_smooth<T, 1, true><<<g, kBlock, 0, s>>>(A, x, b, Sinv, xo, (T)omega, done);
-    else k_smooth<T, 1, false><<<g, kBlock, 0, s>>>(A, x, b, Sinv, xo, (T)omega, done);
+    if (from_zero) launch(k_smooth<T, 1, true>, g, s, A, x, b, Sinv, xo, (T)omega, done);
+    else launch(k_smooth<T, 1, false>, g, s, A, x, b, Sinv, xo, (T)omega, done);
   } else {
-    if (from_zero) k_smooth<T, 3, true><<<g, kBlock, 0, s>>>(A, x, b, Sinv, xo, (T)omega, done);
-    else k_smooth<T, 3, false><<<g, kBlock, 0, s>>>(A, x, b, Sinv, xo, (T)omega, done);
+    if (from_zero) launch(k_smooth<T, 3, true>, g, s, A, x, b, Sinv, xo, (T)omega, done);
+    else launch(k_smooth<T, 3, false>, g, s, A, x, b, Sinv, xo, (T)omega, done);
   }
 }
 
 template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s) {
   const int g = grid_sell(A.nslices);
-  if (nc == 1) k_apply<T, 1, 1><<<g, kBlock, 0, s>>>(A, x, b, r, done);
-  else k_apply<T, 3, 1><<<g, kBlock, 0, s>>>(A, x, b, r, done);
+  if (nc == 1) launch(k_apply<T, 1, 1>, g, s, A, x, b, r, done);
+  else launch(k_apply<T, 3, 1>, g, s, A, x, b, r, done);
 }
 
 template <typename T>
 void launch_matvec(const SellView& A, int nc, const T* x, T* y, const int* done, cudaStream_t s) {
   const int g = grid_sell(A.nslices);
-  if (nc == 1) k_apply<T, 1, 0><<<g, kBlock, 0, s>>>(A, x, nullptr, y, done);
-  else k_apply<T, 3, 0><<<g, kBlock, 0, s>>>(A, x, nullptr, y, done);
+  if (nc == 1) launch(k_apply<T, 1, 0>, g, s, A, x, nullptr, y, done);
+  else launch(k_apply<T, 3, 0>, g, s, A, x, nullptr, y, done);
 }
 
 template <typename T>
-void launch_restrict(const TransferView& R, int nc, const T* r, T* d, const int* done, cudaStream_t s) {
+void launch_restrict(const TransferView& R, int nc, const T* r, T* d, const T* Sinv, T* x0, double omega,
+                     const int* done, cudaStream_t s) {
   const int g = grid_sell(R.nslices);
-  if (nc == 1) k_restrict<T, 1><<<g, kBlock, 0, s>>>(R, r, d, done);
-  else k_restrict<T, 3><<<g, kBlock, 0, s>>>(R, r, d, done);
+  const T om = (T)omega;
+  if (x0) {
+    if (nc == 1) launch(k_restrict<T, 1, true>, g, s, R, r, d, Sinv, x0, om, done);
+    else launch(k_restrict<T, 3, true>, g, s, R, r, d, Sinv, x0, om, done);
+  } else {
+    if (nc == 1) launch(k_restrict<T, 1, false>, g, s, R, r, d, Sinv, x0, om, done);
+    else launch(k_restrict<T, 3, false>, g, s, R, r, d, Sinv, x0, om, done);
+  }
 }
 
 template <typename T>
 void launch_prolong_add(const TransferView& P, int nc, const T* y, const T* xin, T* xo, const int* done,
                         cudaStream_t s) {
   const int g = grid_sell(P.nslices);
-  if (nc == 1) k_prolong<T, 1><<<g, kBlock, 0, s>>>(P, y, xin, xo, done);
-  else k_prolong<T, 3><<<g, kBlock, 0, s>>>(P, y, xin, xo, done);
+  if (nc == 1) launch(k_prolong<T, 1>, g, s, P, y, xin, xo, done);
+  else launch(k_prolong<T, 3>, g, s, P, y, xin, xo, done);
 }
 
 template <typename T>
 void launch_coarse(const double* Ainv, int64_t n, const T* d, T* z, const int* done, cudaStream_t s) {
   int64_t g = (n + 7) / 8;
   if (g > kMaxRedBlocks) g = kMaxRedBlocks;
-  k_coarse<T><<<(int)g, kBlock, 0, s>>>(Ainv, n, d, z, done);
+  launch(k_coarse<T>, (int)g, s, Ainv, n, d, z, done);
 }
 
 #define MGI_INST(T)                                                                                                \
@@ -698,103 +1208,152 @@ void launch_coarse(const double* Ainv, int64_t n, const T* d, T* z, const int* d
                                  cudaStream_t);                                                                    \
   template void launch_residual<T>(const SellView&, int, const T*, const T*, T*, const int*, cudaStream_t);        \
   template void launch_matvec<T>(const SellView&, int, const T*, T*, const int*, cudaStream_t);                    \
-  template void launch_restrict<T>(const TransferView&, int, const T*, T*, const int*, cudaStream_t);              \
+  template void launch_restrict<T>(const TransferView&, int, const T*, T*, const T*, T*, double, const int*,       \
+                                   cudaStream_t);                                                                  \
   template void launch_prolong_add<T>(const TransferView&, int, const T*, const T*, T*, const int*, cudaStream_t); \
   template void launch_coarse<T>(const double*, int64_t, const T*, T*, const int*, cudaStream_t);
 MGI_INST(double)
 MGI_INST(float)
 #undef MGI_INST
 
+template <typename T>
+void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  const int fd = first_done ? 1 : 0;
+  if (nc == 1) cudaLaunchKernelEx(&cfg, k_tail<T, 1>, P, b, out, fd, done);
+  else cudaLaunchKernelEx(&cfg, k_tail<T, 3>, P, b, out, fd, done);
+}
+template void launch_tail<double>(const TailParams&, int, const double*, double*, bool, const int*, cudaStream_t);
+template void launch_tail<float>(const TailParams&, int, const float*, float*, bool, const int*, cudaStream_t);
+
 void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, double* b, cudaStream_t s) {
-  k_rhs<<<grid_sell(F.nslices), kBlock, 0, s>>>(F, nc, f, fixmask, b);
+  launch(k_rhs, grid_sell(F.nslices), s, F, nc, f, fixmask, b);
 }
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s) {
-  k_fill_hanging<<<grid_sell(Hc.nslices), kBlock, 0, s>>>(Hc, nc, x);
+  launch(k_fill_hanging, grid_sell(Hc.nslices), s, Hc, nc, x);
 }
 void launch_copy_fixed(int64_t n, int nc, const uint8_t* fixmask, const double* b, const double* xin, double* x,
                        cudaStream_t s) {
-  k_copy_fixed<<<grid_for_rows(n), kBlock, 0, s>>>(n, nc, fixmask, b, xin, x);
-}
-void launch_norm_free(int64_t n, int nc, const uint8_t* fixmask, const double* b, Partials part, int k,
-                      cudaStream_t s) {
-  k_norm_free<<<grid_for_rows(((n + 31) / 32) * 32), kBlock, 0, s>>>(n, nc, fixmask, b, part.q(k));
+  launch(k_copy_fixed, grid_for_rows(n), s, n, nc, fixmask, b, xin, x);
 }
 void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
-                          int k, cudaStream_t s) {
+                          KrylovState* st, int test, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
-  if (nc == 1) k_residual_norm<1><<<g, kBlock, 0, s>>>(A64, x, b, r, part.q(k));
-  else k_residual_norm<3><<<g, kBlock, 0, s>>>(A64, x, b, r, part.q(k));
+  if (nc == 1) launch(k_residual_norm<1>, g, s, A64, x, b, r, part.p, st, test);
+  else launch(k_residual_norm<3>, g, s, A64, x, b, r, part.p, st, test);
 }
-void launch_init_state(KrylovState* st, Partials part, int k_bb, int nred, double rtol, int max_it, cudaStream_t s) {
-  k_init_state<<<1, kBlock, 0, s>>>(st, part.q(k_bb), nred, rtol, max_it);
+void launch_norm_init(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, Partials part,
+                      KrylovState* st, double rtol, int max_it, cudaStream_t s) {
+  launch(k_norm_init, grid_for_rows(n_nodes), s, n_nodes, nc, fixmask, b, part.p, st, rtol, max_it);
 }
-void launch_finalize(Partials part, int k_rr, int nred, KrylovState* st, int first, unsigned long long cond_handle,
-                     cudaStream_t s) {
-  k_finalize<<<1, kBlock, 0, s>>>(part.q(k_rr), nred, st, first, cond_handle);
+static int grid_vec4(int64_t n) {  // 4 entries per thread (k_bicg_x: 2, capped grid)
+  int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
 void launch_to_f32(int64_t n, const double* v, float* v32, const KrylovState* st, cudaStream_t s) {
-  k_to_f32<<<grid_for_rows(n), kBlock, 0, s>>>(n, v, v32, st);
+  int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
+  launch(k_to_f32, (int)std::max<int64_t>(1, g), s, n, v, v32, st);
 }
-
-// Krylov launchers: grid = the finest-level SpMV grid (one thread per node)
-static int grid_nodes(int64_t nn) { return grid_for_rows(((nn + 31) / 32) * 32); }
-
-#define MGI_NC(call1, call3) \
-  do {                          \
-    if (nc == 1) call1;         \
-    else call3;                 \
-  } while (0)
-
-void launch_cg_dots(int64_t nn, int nc, PVec z, const double* r, const double* q, Partials part,
-                    const KrylovState* st, cudaStream_t s) {
-  const int g = grid_nodes(nn);
-  MGI_NC((k_cg_dots<1><<<g, kBlock, 0, s>>>(nn, z, r, q, part.q(1), part.q(2), st)),
-         (k_cg_dots<3><<<g, kBlock, 0, s>>>(nn, z, r, q, part.q(1), part.q(2), st)));
+void launch_cg_dots(int64_t n, PVec z, const double* r, const double* q, Partials part, KrylovState* st,
+                    cudaStream_t s) {
+  launch(k_cg_dots, grid_vec4(n), s, n, z, r, q, part.p, st);
 }
-void launch_cg_update_p(int64_t nn, int nc, PVec z, double* p, Partials part, int nred, KrylovState* st,
-                        cudaStream_t s) {
-  const int g = grid_nodes(nn);
-  MGI_NC((k_cg_update_p<1><<<g, kBlock, 0, s>>>(nn, z, p, part.q(1), part.q(2), nred, st)),
-         (k_cg_update_p<3><<<g, kBlock, 0, s>>>(nn, z, p, part.q(1), part.q(2), nred, st)));
+void launch_cg_update_p(int64_t n, PVec z, double* p, KrylovState* st, cudaStream_t s) {
+  launch(k_cg_update_p, grid_vec4(n), s, n, z, p, st);
 }
 void launch_spmv_dot(const SellView& A64, int nc, PVec p, const double* w, double* out, Partials part, int k,
-                     const KrylovState* st, cudaStream_t s) {
+                     KrylovState* st, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
-  MGI_NC((k_spmv_dot<1><<<g, kBlock, 0, s>>>(A64, p, w, out, part.q(k), st)),
-         (k_spmv_dot<3><<<g, kBlock, 0, s>>>(A64, p, w, out, part.q(k), st)));
+  if (p.f) {
+    if (nc == 1) launch(k_spmv_dot<1, true>, g, s, A64, p, w, out, part.p, k, st);
+    else launch(k_spmv_dot<3, true>, g, s, A64, p, w, out, part.p, k, st);
+  } else {
+    if (nc == 1) launch(k_spmv_dot<1, false>, g, s, A64, p, w, out, part.p, k, st);
+    else launch(k_spmv_dot<3, false>, g, s, A64, p, w, out, part.p, k, st);
+  }
 }
-void launch_cg_update_xr(int64_t nn, int nc, const double* p, const double* q, double* x, double* r, Partials part,
-                         int nred, KrylovState* st, cudaStream_t s) {
-  const int g = grid_nodes(nn);
-  MGI_NC((k_cg_update_xr<1><<<g, kBlock, 0, s>>>(nn, p, q, x, r, part.q(3), nred, part.q(0), st)),
-         (k_cg_update_xr<3><<<g, kBlock, 0, s>>>(nn, p, q, x, r, part.q(3), nred, part.q(0), st)));
+void launch_cg_update_xr(int64_t n, const double* p, const double* q, double* x, double* r, Partials part,
+                         KrylovState* st, unsigned long long cond, cudaStream_t s) {
+  launch(k_cg_update_xr, grid_vec4(n), s, n, p, q, x, r, part.p, st, cond);
 }
-void launch_bicg_p(int64_t nn, int nc, const double* r, const double* v, double* p, Partials part, int nred,
-                   KrylovState* st, cudaStream_t s) {
-  const int g = grid_nodes(nn);
-  MGI_NC((k_bicg_p<1><<<g, kBlock, 0, s>>>(nn, r, v, p, part.q(9), nred, st)),
-         (k_bicg_p<3><<<g, kBlock, 0, s>>>(nn, r, v, p, part.q(9), nred, st)));
+void launch_bicg_p(int64_t n, const double* r, const double* v, double* p, float* p32, KrylovState* st,
+                   cudaStream_t s) {
+  launch(k_bicg_p, grid_vec4(n), s, n, r, v, p, p32, st);
 }
-void launch_bicg_s(int64_t nn, int nc, const double* r, const double* v, double* sv, Partials part, int nred,
-                   KrylovState* st, cudaStream_t s) {
-  const int g = grid_nodes(nn);
-  MGI_NC((k_bicg_s<1><<<g, kBlock, 0, s>>>(nn, r, v, sv, part.q(5), nred, st)),
-         (k_bicg_s<3><<<g, kBlock, 0, s>>>(nn, r, v, sv, part.q(5), nred, st)));
+void launch_bicg_s(int64_t n, const double* r, const double* v, double* sv, float* s32, KrylovState* st,
+                   cudaStream_t s) {
+  launch(k_bicg_s, grid_vec4(n), s, n, r, v, sv, s32, st);
 }
 void launch_spmv_2dots(const SellView& A64, int nc, PVec sh, const double* sv, double* t, Partials part,
-                       const KrylovState* st, cudaStream_t s) {
+                       KrylovState* st, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
-  MGI_NC((k_spmv_2dots<1><<<g, kBlock, 0, s>>>(A64, sh, sv, t, part.q(7), part.q(8), st)),
-         (k_spmv_2dots<3><<<g, kBlock, 0, s>>>(A64, sh, sv, t, part.q(7), part.q(8), st)));
+  if (sh.f) {
+    if (nc == 1) launch(k_spmv_2dots<1, true>, g, s, A64, sh, sv, t, part.p, st);
+    else launch(k_spmv_2dots<3, true>, g, s, A64, sh, sv, t, part.p, st);
+  } else {
+    if (nc == 1) launch(k_spmv_2dots<1, false>, g, s, A64, sh, sv, t, part.p, st);
+    else launch(k_spmv_2dots<3, false>, g, s, A64, sh, sv, t, part.p, st);
+  }
 }
-void launch_bicg_x(int64_t nn, int nc, PVec ph, PVec sh, const double* sv, const double* t, const double* rhat,
-                   double* x, double* r, Partials part, int nred, KrylovState* st, cudaStream_t s) {
-  const int g = grid_nodes(nn);
-  MGI_NC((k_bicg_x<1><<<g, kBlock, 0, s>>>(nn, ph, sh, sv, t, rhat, x, r, part.q(7), part.q(8), nred, part.q(0),
-                                            part.q(9), st)),
-         (k_bicg_x<3><<<g, kBlock, 0, s>>>(nn, ph, sh, sv, t, rhat, x, r, part.q(7), part.q(8), nred, part.q(0),
-                                            part.q(9), st)));
+void launch_bicg_x(int64_t n, PVec ph, PVec sh, const double* sv, const double* t, const double* rhat, double* x,
+                   double* r, Partials part, KrylovState* st, unsigned long long cond, cudaStream_t s) {
+  launch(k_bicg_x, grid_vec4(n), s, n, ph, sh, sv, t, rhat, x, r, part.p, st, cond);
 }
-#undef MGI_NC
+
+// ---- GMRES launchers
+void launch_gm_start(int64_t n, const double* r, float* v32, double* v64, GmresView G, KrylovState* st,
+                     cudaStream_t s) {
+  launch(k_gm_start, grid_for_rows(n), s, n, r, v32, v64, G, st);
+}
+void launch_gm_spmv(const SellView& A64, int nc, PVec z, double* w, GmresView G, KrylovState* st, cudaStream_t s) {
+  const int g = grid_sell(A64.nslices);
+  if (z.f) {
+    if (nc == 1) launch(k_gm_spmv<1, true>, g, s, A64, z, w, G, st);
+    else launch(k_gm_spmv<3, true>, g, s, A64, z, w, G, st);
+  } else {
+    if (nc == 1) launch(k_gm_spmv<1, false>, g, s, A64, z, w, G, st);
+    else launch(k_gm_spmv<3, false>, g, s, A64, z, w, G, st);
+  }
+}
+void launch_gm_orth(int64_t n, double* w, GmresView G, KrylovState* st, int pass, Partials part, cudaStream_t s) {
+  const int gx = grid_vec4(n);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)(G.m + 1));
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_gm_dots, n, (const double*)w, G, st);
+  }
+  launch(k_gm_reduce, G.m + 1, s, G, st, gx, pass);
+  launch(k_gm_axpy, grid_for_rows(n), s, n, w, G, st, part.p, pass);
+}
+void launch_gm_givens(GmresView G, KrylovState* st, cudaStream_t s) { launch(k_gm_givens, 1, s, G, st); }
+void launch_gm_next(int64_t n, const double* w, float* v32, double* v64, GmresView G, KrylovState* st,
+                    cudaStream_t s) {
+  launch(k_gm_next, grid_for_rows(n), s, n, w, v32, v64, G, st);
+  launch(k_gm_advance, 1, s, st);
+}
+void launch_gm_update_x(int64_t n, double* x, GmresView G, KrylovState* st, cudaStream_t s) {
+  launch(k_gm_update_x, grid_for_rows(n), s, n, x, G, st);
+}
+void launch_gm_residual(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
+                        KrylovState* st, unsigned long long cond, cudaStream_t s) {
+  const int g = grid_sell(A64.nslices);
+  if (nc == 1) launch(k_gm_residual<1>, g, s, A64, x, b, r, part.p, st, cond);
+  else launch(k_gm_residual<3>, g, s, A64, x, b, r, part.p, st, cond);
+}
 
 }  // namespace mgi

@@ -38,7 +38,27 @@ struct KrylovState {
   double rnorm, bnorm, rtol, scale;  // scale: factor of the FP32 preconditioner input
   int iter, max_it, done, status;
   int restart_pos;
-  int pad[3];
+  unsigned int counter;              // arrival counter of the last-block reductions
+  int gm_j;                          // GMRES: current Arnoldi column
+  int gm_end;                        // GMRES: 1 when the current cycle ends after this step
+  double red[16];                    // finished reductions, indexed by Q_*
+};
+
+// GMRES(m) work arrays on the device (doubles): Hessenberg (m+1) x m
+// column-major, Givens cosines/sines, rhs g, current coefficients h, y.
+struct GmresView {
+  int m = 30;
+  double* H = nullptr;               // (m+1) * m
+  double* cs = nullptr;              // m
+  double* sn = nullptr;              // m
+  double* g = nullptr;               // m + 1
+  double* hv = nullptr;              // m + 1 (projection coefficients of the current sweep)
+  double* y = nullptr;               // m
+  double* V = nullptr;               // (m+1) * n, FP64 Krylov basis
+  double* Z64 = nullptr;             // m * n preconditioned vectors (FP64 mode)
+  float* Z32 = nullptr;              // m * n preconditioned vectors (mixed mode, times zs[j])
+  double* zs = nullptr;              // m scales of Z32
+  double* part = nullptr;            // (m+1) * kMaxRedBlocks dot partials
 };
 
 // Reduction partials: one slot array per quantity, kMaxRedBlocks each.
@@ -58,23 +78,45 @@ template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s);
 template <typename T>
 void launch_matvec(const SellView& A, int nc, const T* x, T* y, const int* done, cudaStream_t s);
+// d = R r; when x0 != nullptr also x0 = omega S d (first sweep of the coarser level from zero)
 template <typename T>
-void launch_restrict(const TransferView& R, int nc, const T* r, T* d, const int* done, cudaStream_t s);
+void launch_restrict(const TransferView& R, int nc, const T* r, T* d, const T* Sinv, T* x0, double omega,
+                     const int* done, cudaStream_t s);
+void set_pdl(bool on);
 template <typename T>
 void launch_prolong_add(const TransferView& P, int nc, const T* y, const T* xin, T* xo, const int* done,
                         cudaStream_t s);
 template <typename T>
 void launch_coarse(const double* Ainv, int64_t n, const T* d, T* z, const int* done, cudaStream_t s);
 
+// ---- single-CTA tail V-cycle over the smallest levels -------------------------
+constexpr int kTailMax = 16;
+constexpr int kTailThreads = 1024;
+struct TailLevel {
+  SellView A;
+  TransferView P, R;          // P, R of this level (unused on level 0)
+  const void* S = nullptr;    // smoother blocks
+  void* b = nullptr;          // rhs (written by the restriction from level+1)
+  void* o = nullptr;          // output
+  void* t = nullptr;          // ping-pong buffer
+  void* r = nullptr;          // residual
+};
+struct TailParams {
+  TailLevel lv[kTailMax];     // [0] = coarsest level of the hierarchy
+  int nt = 0;                 // levels in the tail (top = nt - 1)
+  int nu1 = 2, nu2 = 2;
+  double omega = 0.8;
+  const double* cinv = nullptr;   // coarse inverse
+  int64_t cn = 0;
+};
+template <typename T>
+void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s);
+
 // ---- vector kernels --------------------------------------------------------
 void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, double* b, cudaStream_t s);
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s);
 void launch_copy_fixed(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, const double* xin,
                        double* x, cudaStream_t s);
-// partial of sum over free dofs of b^2 (quantity k of part)
-void launch_norm_free(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, Partials part, int k,
-                      cudaStream_t s);
-
 // ---- Krylov kernels (FP64 outer loop) --------------------------------------
 // Preconditioned vectors come either as double (zs == nullptr) or as float
 // times the scalar st->scale (z32 != nullptr).
@@ -83,31 +125,52 @@ struct PVec {
   const float* f = nullptr;
 };
 
-void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
-                          int k, cudaStream_t s);
-void launch_finalize(Partials part, int k_rr, int nred, KrylovState* st, int first, unsigned long long cond_handle,
-                     cudaStream_t s);
-void launch_init_state(KrylovState* st, Partials part, int k_bb, int nred, double rtol, int max_it, cudaStream_t s);
-void launch_to_f32(int64_t n, const double* v, float* v32, const KrylovState* st, cudaStream_t s);
-// Quantity slots of the partial arrays
+// Quantity slots of the partial arrays and of KrylovState::red
 enum { Q_RR = 0, Q_RZ = 1, Q_QZ = 2, Q_PQ = 3, Q_BB = 4, Q_RHV = 5, Q_SS = 6, Q_TS = 7, Q_TT = 8, Q_RHR = 9, Q_NUM = 10 };
-// CG (flexible, Polak-Ribiere beta): dots -> Q_RZ, Q_QZ; update_p; spmv_dot -> Q_PQ; update_xr -> Q_RR
-void launch_cg_dots(int64_t nn, int nc, PVec z, const double* r, const double* q, Partials part,
-                    const KrylovState* st, cudaStream_t s);
-void launch_cg_update_p(int64_t nn, int nc, PVec z, double* p, Partials part, int nred, KrylovState* st,
-                        cudaStream_t s);
+
+// r = b - A x and ||r||^2 -> red[Q_RR]; test: run the initial convergence test
+void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
+                          KrylovState* st, int test, cudaStream_t s);
+// ||b_free||^2 -> bnorm, and the initial Krylov state
+void launch_norm_init(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, Partials part,
+                      KrylovState* st, double rtol, int max_it, cudaStream_t s);
+void launch_to_f32(int64_t n, const double* v, float* v32, const KrylovState* st, cudaStream_t s);
+// CG (flexible, Polak-Ribiere beta): dots -> Q_RZ, Q_QZ; update_p; spmv_dot -> Q_PQ; update_xr -> Q_RR + test
+void launch_cg_dots(int64_t n, PVec z, const double* r, const double* q, Partials part, KrylovState* st,
+                    cudaStream_t s);
+void launch_cg_update_p(int64_t n, PVec z, double* p, KrylovState* st, cudaStream_t s);
 void launch_spmv_dot(const SellView& A64, int nc, PVec p, const double* w, double* out, Partials part, int k,
-                     const KrylovState* st, cudaStream_t s);
-void launch_cg_update_xr(int64_t nn, int nc, const double* p, const double* q, double* x, double* r, Partials part,
-                         int nred, KrylovState* st, cudaStream_t s);
-// BiCGStab (right preconditioned): p (Q_RHR) ; spmv_dot -> Q_RHV ; s ; spmv_2dots -> Q_TS, Q_TT ; x -> Q_RR, Q_RHR
-void launch_bicg_p(int64_t nn, int nc, const double* r, const double* v, double* p, Partials part, int nred,
-                   KrylovState* st, cudaStream_t s);
-void launch_bicg_s(int64_t nn, int nc, const double* r, const double* v, double* sv, Partials part, int nred,
-                   KrylovState* st, cudaStream_t s);
+                     KrylovState* st, cudaStream_t s);
+void launch_cg_update_xr(int64_t n, const double* p, const double* q, double* x, double* r, Partials part,
+                         KrylovState* st, unsigned long long cond, cudaStream_t s);
+// BiCGStab (right preconditioned): p ; spmv_dot -> Q_RHV ; s ; spmv_2dots -> Q_TS, Q_TT ; x -> Q_RR, Q_RHR + test.
+// p32 / s32 (optional): FP32 copies scaled by 1 / st->scale for the FP32 preconditioner
+void launch_bicg_p(int64_t n, const double* r, const double* v, double* p, float* p32, KrylovState* st,
+                   cudaStream_t s);
+void launch_bicg_s(int64_t n, const double* r, const double* v, double* sv, float* s32, KrylovState* st,
+                   cudaStream_t s);
 void launch_spmv_2dots(const SellView& A64, int nc, PVec sh, const double* sv, double* t, Partials part,
-                       const KrylovState* st, cudaStream_t s);
-void launch_bicg_x(int64_t nn, int nc, PVec ph, PVec sh, const double* sv, const double* t, const double* rhat,
-                   double* x, double* r, Partials part, int nred, KrylovState* st, cudaStream_t s);
+                       KrylovState* st, cudaStream_t s);
+void launch_bicg_x(int64_t n, PVec ph, PVec sh, const double* sv, const double* t, const double* rhat, double* x,
+                   double* r, Partials part, KrylovState* st, unsigned long long cond, cudaStream_t s);
+
+// ---- GMRES(m), flexible, right preconditioned (Sec. 4.1.5; Saad 2003) -------
+// start: v0 = r / ||r|| (+ FP32 copy), g = ||r|| e1, j = 0 (gated: cycle start)
+void launch_gm_start(int64_t n, const double* r, float* v32, double* v64, GmresView G, KrylovState* st,
+                     cudaStream_t s);
+// w = A z_j, z_j = preconditioner output (FP64 z64 or FP32 z32 x 1); also stores z_j into Z[j]
+void launch_gm_spmv(const SellView& A64, int nc, PVec z, double* w, GmresView G, KrylovState* st, cudaStream_t s);
+// one classical Gram-Schmidt sweep: h_i = (v_i, w), w -= sum h_i v_i, i <= j; pass 0 or 1
+void launch_gm_orth(int64_t n, double* w, GmresView G, KrylovState* st, int pass, Partials part, cudaStream_t s);
+// Givens update of column j, convergence test, triangular solve at the cycle end
+void launch_gm_givens(GmresView G, KrylovState* st, cudaStream_t s);
+// v_{j+1} = w / h_{j+1,j} (+ FP32 copy) when the cycle continues
+void launch_gm_next(int64_t n, const double* w, float* v32, double* v64, GmresView G, KrylovState* st,
+                    cudaStream_t s);
+// x += sum_i y_i z_i at the cycle end
+void launch_gm_update_x(int64_t n, double* x, GmresView G, KrylovState* st, cudaStream_t s);
+// r = b - A x and the convergence test at the cycle end (true residual)
+void launch_gm_residual(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
+                        KrylovState* st, unsigned long long cond, cudaStream_t s);
 
 }  // namespace mgi

@@ -123,6 +123,10 @@ struct mg_hier {
   KrylovState* st_host = nullptr;        // pinned
   int nred = 1;
   std::vector<SolveGraph> graphs;
+  int tail_top = 0;                      // levels 0..tail_top run in the single-CTA tail kernel
+  TailParams tail64, tail32;
+  GmresView gm;                          // GMRES workspace (allocated when opts.krylov == MG_GMRES)
+  double* vcur = nullptr;                // FP64 V-cycle input of the current Arnoldi vector
   int64_t launch_count = 0;              // kernels enqueued (host-side count)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::mutex solve_mu;                   // one solve at a time per hierarchy
@@ -235,6 +239,7 @@ template <typename T>
 struct Prec;
 template <>
 struct Prec<double> {
+  static const TailParams& tail(mg_hier* h) { return h->tail64; }
   static const SellView& A(LevelBufs& l) { return l.A64.v; }
   static const double* S(LevelBufs& l) { return l.S64; }
   static double* b(LevelBufs& l) { return l.b64; }
@@ -244,6 +249,7 @@ struct Prec<double> {
 };
 template <>
 struct Prec<float> {
+  static const TailParams& tail(mg_hier* h) { return h->tail32; }
   static const SellView& A(LevelBufs& l) { return l.A32.v; }
   static const float* S(LevelBufs& l) { return l.S32; }
   static float* b(LevelBufs& l) { return l.b32; }
@@ -253,8 +259,10 @@ struct Prec<float> {
 };
 
 // z = GMG(l, 0, b): the V-cycle of Algorithm "Geometric multigrid solver".
+// first_done: the first pre-smoothing sweep (from x = 0) was already written
+// into its buffer by the restriction kernel of the finer level.
 template <typename T>
-void enqueue_vcycle(mg_hier* h, int l, const T* b, T* out, const int* done, cudaStream_t s) {
+void enqueue_vcycle(mg_hier* h, int l, const T* b, T* out, const int* done, cudaStream_t s, bool first_done = false) {
   const int nc = h->nc;
   if (l == 0) {                                                  // Step 0
     launch_coarse<T>(h->coarse_inv, h->coarse_n, b, out, done, s);
@@ -263,26 +271,35 @@ void enqueue_vcycle(mg_hier* h, int l, const T* b, T* out, const int* done, cuda
   }
   LevelBufs& L = h->L[l];
   LevelBufs& C = h->L[l - 1];
+  if (l <= h->tail_top) {                                        // small levels: one CTA
+    launch_tail<T>(Prec<T>::tail(h), nc, b, out, first_done, done, s);
+    h->launch_count++;
+    return;
+  }
   const int nu1 = h->opts.nu1, nu2 = h->opts.nu2, ns = nu1 + nu2;
-  T* tmp = Prec<T>::t(L);
-  auto buf = [&](int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? out : tmp; };
+  auto bufof = [&](LevelBufs& X, T* o, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? o : Prec<T>::t(X); };
   const double om = h->opts.omega;
   T* cur = nullptr;
   for (int k = 0; k < nu1; ++k) {                                // Step 1
-    T* dst = buf(k);
-    launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
+    T* dst = bufof(L, out, k);
+    if (!(k == 0 && first_done)) {
+      launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
+      h->launch_count++;
+    }
     cur = dst;
   }
   launch_residual<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::r(L), done, s);   // Step 2
-  launch_restrict<T>(L.R.t, nc, Prec<T>::r(L), Prec<T>::b(C), done, s);
-  h->launch_count += nu1 + 2;
-  enqueue_vcycle<T>(h, l - 1, Prec<T>::b(C), Prec<T>::o(C), done, s);    // Step 3
+  const bool fuse = l - 1 > 0;
+  T* cfirst = fuse ? bufof(C, Prec<T>::o(C), 0) : nullptr;
+  launch_restrict<T>(L.R.t, nc, Prec<T>::r(L), Prec<T>::b(C), Prec<T>::S(C), cfirst, om, done, s);
+  h->launch_count += 2;
+  enqueue_vcycle<T>(h, l - 1, Prec<T>::b(C), Prec<T>::o(C), done, s, fuse);   // Step 3
   T* pdst = nu2 == 0 ? out : cur;                                          // Step 4
   launch_prolong_add<T>(L.P.t, nc, Prec<T>::o(C), cur, pdst, done, s);
   cur = pdst;
   h->launch_count++;
   for (int k = nu1; k < ns; ++k) {                               // Step 5
-    T* dst = buf(k);
+    T* dst = bufof(L, out, k);
     launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, false, done, s);
     cur = dst;
     h->launch_count++;
@@ -290,57 +307,71 @@ void enqueue_vcycle(mg_hier* h, int l, const T* b, T* out, const int* done, cuda
 }
 
 // ------------------------------------------------------------------ Krylov
-enum { M_CG = 1, M_BICG = 2 };
+enum { M_CG = 1, M_BICG = 2, M_GMRES = 3 };
 
 int method_of(const mg_hier* h) {
   int k = h->opts.krylov;
   if (k == MG_KRYLOV_AUTO) k = (h->prob.kind == MG_TRANSPORT) ? MG_BICGSTAB : MG_CG;
-  return k == MG_BICGSTAB ? M_BICG : M_CG;
+  return k == MG_BICGSTAB ? M_BICG : (k == MG_GMRES ? M_GMRES : M_CG);
 }
 
-// One Krylov iteration (the body of the graph's while node).
+// One Krylov iteration (the body of the graph's while node).  The last kernel
+// of the iteration runs the convergence test and sets the while condition.
 void enqueue_iteration(mg_hier* h, int method, int prec, unsigned long long cond, cudaStream_t s) {
   const int nc = h->nc;
   const int fine = h->nlev - 1;
-  const int64_t nn = h->n_nodes, n = h->n_dofs;
+  const int64_t n = h->n_dofs;
   const SellView& A = h->L[fine].A64.v;
   const int* done = &h->st->done;
   const bool mixed = prec != MG_FP64;
-  auto precondition = [&](const double* in, double* out64, float* out32) -> PVec {
-    PVec pv;
-    if (mixed) {
-      launch_to_f32(n, in, h->r32, h->st, s);
-      h->launch_count++;
-      enqueue_vcycle<float>(h, fine, h->r32, out32, done, s);
-      pv.f = out32;
-    } else {
-      enqueue_vcycle<double>(h, fine, in, out64, done, s);
-      pv.d = out64;
-    }
-    return pv;
-  };
   if (method == M_CG) {
-    PVec z = precondition(h->r, h->z, h->ph32);
-    launch_cg_dots(nn, nc, z, h->r, h->q, h->part, h->st, s);
-    launch_cg_update_p(nn, nc, z, h->p, h->part, h->nred, h->st, s);
+    PVec z;
+    if (mixed) {
+      launch_to_f32(n, h->r, h->r32, h->st, s);
+      enqueue_vcycle<float>(h, fine, h->r32, h->ph32, done, s);
+      z.f = h->ph32;
+      h->launch_count++;
+    } else {
+      enqueue_vcycle<double>(h, fine, h->r, h->z, done, s);
+      z.d = h->z;
+    }
+    launch_cg_dots(n, z, h->r, h->q, h->part, h->st, s);
+    launch_cg_update_p(n, z, h->p, h->st, s);
     PVec pp;
     pp.d = h->p;
     launch_spmv_dot(A, nc, pp, nullptr, h->q, h->part, Q_PQ, h->st, s);
-    launch_cg_update_xr(nn, nc, h->p, h->q, h->xi, h->r, h->part, h->nred, h->st, s);
+    launch_cg_update_xr(n, h->p, h->q, h->xi, h->r, h->part, h->st, cond, s);
     h->launch_count += 4;
+  } else if (method == M_GMRES) {
+    // one Arnoldi step of flexible GMRES(m); cycle end and restart are gated
+    // on the device (gm_end / gm_j)
+    PVec z;
+    if (mixed) { enqueue_vcycle<float>(h, fine, h->r32, h->ph32, done, s); z.f = h->ph32; }
+    else { enqueue_vcycle<double>(h, fine, h->vcur, h->z, done, s); z.d = h->z; }
+    launch_gm_spmv(A, nc, z, h->q, h->gm, h->st, s);
+    launch_gm_orth(n, h->q, h->gm, h->st, 0, h->part, s);
+    launch_gm_orth(n, h->q, h->gm, h->st, 1, h->part, s);
+    launch_gm_givens(h->gm, h->st, s);
+    launch_gm_next(n, h->q, mixed ? h->r32 : nullptr, mixed ? nullptr : h->vcur, h->gm, h->st, s);
+    launch_gm_update_x(n, h->xi, h->gm, h->st, s);
+    launch_gm_residual(A, nc, h->xi, h->bi, h->r, h->part, h->st, cond, s);
+    launch_gm_start(n, h->r, mixed ? h->r32 : nullptr, mixed ? nullptr : h->vcur, h->gm, h->st, s);
+    h->launch_count += 1 + 3 * 2 + 1 + 2 + 1 + 1 + 1;
   } else {
-    launch_bicg_p(nn, nc, h->r, h->t /* v */, h->p, h->part, h->nred, h->st, s);
-    PVec ph = precondition(h->p, h->ph, h->ph32);
+    // in mixed mode bicg_p / bicg_s also write the FP32 preconditioner input
+    launch_bicg_p(n, h->r, h->t /* v */, h->p, mixed ? h->r32 : nullptr, h->st, s);
+    PVec ph;
+    if (mixed) { enqueue_vcycle<float>(h, fine, h->r32, h->ph32, done, s); ph.f = h->ph32; }
+    else { enqueue_vcycle<double>(h, fine, h->p, h->ph, done, s); ph.d = h->ph; }
     launch_spmv_dot(A, nc, ph, h->rhat, h->t /* v */, h->part, Q_RHV, h->st, s);
-    launch_bicg_s(nn, nc, h->r, h->t, h->sv, h->part, h->nred, h->st, s);
-    PVec sh = precondition(h->sv, h->shat, h->sh32);
+    launch_bicg_s(n, h->r, h->t, h->sv, mixed ? h->r32 : nullptr, h->st, s);
+    PVec sh;
+    if (mixed) { enqueue_vcycle<float>(h, fine, h->r32, h->sh32, done, s); sh.f = h->sh32; }
+    else { enqueue_vcycle<double>(h, fine, h->sv, h->shat, done, s); sh.d = h->shat; }
     launch_spmv_2dots(A, nc, sh, h->sv, h->q /* t */, h->part, h->st, s);
-    // v must survive until the next bicg_p: keep v in t, A*shat in q
-    launch_bicg_x(nn, nc, ph, sh, h->sv, h->q, h->rhat, h->xi, h->r, h->part, h->nred, h->st, s);
+    launch_bicg_x(n, ph, sh, h->sv, h->q, h->rhat, h->xi, h->r, h->part, h->st, cond, s);
     h->launch_count += 5;
   }
-  launch_finalize(h->part, Q_RR, h->nred, h->st, 0, cond, s);
-  h->launch_count++;
 }
 
 int build_graph(mg_hier* h, int method, int prec, SolveGraph* out) {
@@ -404,38 +435,57 @@ int solve_device(mg_hier* h, double rtol, int max_it, int prec, cudaStream_t s, 
   const int fine = h->nlev - 1;
   const SellView& A = h->L[fine].A64.v;
   SolveGraph* g = nullptr;
-  int rc = get_graph(h, method, prec, &g);
-  if (rc) return rc;
+  SolveGraph direct;   // direct launches are counted as they are enqueued
+  if (h->opts.launch_mode == 1) {
+    g = &direct;
+  } else {
+    int rc = get_graph(h, method, prec, &g);
+    if (rc) return rc;
+  }
   int64_t launches = 0;
   CU(cudaEventRecord(h->ev0, s));
-  launch_norm_free(h->n_nodes, nc, h->fixmask, h->bi, h->part, Q_BB, s);
-  launch_init_state(h->st, h->part, Q_BB, h->nred, rtol, max_it, s);
-  launches += 2;
+  launch_norm_init(h->n_nodes, nc, h->fixmask, h->bi, h->part, h->st, rtol, max_it, s);
+  launches += 1;
   int total_iters = 0;
   int status = MG_OK;
   double rel = 0.0;
   for (int round = 0; round < 4; ++round) {
-    launch_residual_norm(A, nc, h->xi, h->bi, h->r, h->part, Q_RR, s);
-    launch_finalize(h->part, Q_RR, h->nred, h->st, 1, 0ull, s);
-    launches += 2;
-    if (method == M_BICG) {
+    launch_residual_norm(A, nc, h->xi, h->bi, h->r, h->part, h->st, 1, s);
+    launches += 1;
+    if (method == M_GMRES) {
+      if (!h->gm.V) return fail(MG_ERR_INVALID, "hierarchy set up without GMRES workspace (opts.krylov)");
+      launch_gm_start(h->n_dofs, h->r, prec != MG_FP64 ? h->r32 : nullptr, prec != MG_FP64 ? nullptr : h->vcur,
+                      h->gm, h->st, s);
+      launches += 1;
+    } else if (method == M_BICG) {
+      // rhat = r0, (rhat, r) = (r, r)
       CU(cudaMemcpyAsync(h->rhat, h->r, h->n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      CU(cudaMemcpyAsync(h->part.q(Q_RHR), h->part.q(Q_RR), h->nred * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CU(cudaMemcpyAsync(&h->st->red[Q_RHR], &h->st->red[Q_RR], sizeof(double), cudaMemcpyDeviceToDevice, s));
       CU(cudaMemsetAsync(h->t, 0, h->n_dofs * sizeof(double), s));
     } else {
       CU(cudaMemsetAsync(h->q, 0, h->n_dofs * sizeof(double), s));
     }
-    CU(cudaGraphLaunch(g->exec, s));
+    if (h->opts.launch_mode == 1) {
+      // direct launches: one iteration at a time, status read back after each
+      const int64_t before = h->launch_count;
+      for (int it = 0; it < max_it + 1; ++it) {
+        CU(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (h->st_host->done) break;
+        enqueue_iteration(h, method, prec, 0ull, s);
+      }
+      launches += h->launch_count - before;
+      h->launch_count = before;
+    } else {
+      CU(cudaGraphLaunch(g->exec, s));
+    }
     // true residual of the final iterate
-    launch_residual_norm(A, nc, h->xi, h->bi, h->r, h->part, Q_RR, s);
+    launch_residual_norm(A, nc, h->xi, h->bi, h->r, h->part, h->st, 0, s);
     launches += 1;
     CU(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
-    std::vector<double> pr(h->nred);
-    CU(cudaMemcpyAsync(pr.data(), h->part.q(Q_RR), h->nred * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    double rr = 0;
-    for (double v : pr) rr += v;
     const KrylovState& S = *h->st_host;
+    const double rr = S.red[Q_RR];
     int it_round = S.iter;
     launches += (int64_t)it_round * g->launches_per_iter + (it_round == 0 ? 0 : 0);
     total_iters = it_round;
@@ -450,6 +500,8 @@ int solve_device(mg_hier* h, double rtol, int max_it, int prec, cudaStream_t s, 
     fix.done = 0;
     fix.status = 0;
     fix.restart_pos = fix.iter;
+    fix.gm_j = 0;
+    fix.gm_end = 0;
     CU(cudaMemcpyAsync(h->st, &fix, sizeof(KrylovState), cudaMemcpyHostToDevice, s));
     CU(cudaStreamSynchronize(s));
     status = MG_ERR_NOT_CONVERGED;
@@ -563,6 +615,8 @@ void mg_default_opts(mg_opts* o) {
   o->restart = 30;
   o->store_fp64 = 1;
   o->store_fp32 = 1;
+  o->launch_mode = 0;
+  o->tail_rows = 4096;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -621,6 +675,15 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
     if (opts.store_fp64) need += sell_bytes(lv.A, 8) + rnd(lv.topo.n_nodes * nb * 8) + 4 * rnd(m * 8);
     if (opts.store_fp32) need += sell_bytes(lv.A, 4) + rnd(lv.topo.n_nodes * nb * 4) + 4 * rnd(m * 4);
     if (l > 0) need += sell_bytes(lv.P, 4) + sell_bytes(lv.R, 4);
+  }
+  {
+    int kk = opts.krylov;
+    if (kk == MG_KRYLOV_AUTO) kk = prob->kind == MG_TRANSPORT ? MG_BICGSTAB : MG_CG;
+    if (kk == MG_GMRES) {
+      const int64_t m = std::max(2, std::min(opts.restart > 0 ? opts.restart : 30, 64));
+      need += rnd((m + 1) * n * 8) + (opts.store_fp64 ? rnd(m * n * 8) : 0) + (opts.store_fp32 ? rnd(m * n * 4) : 0) +
+              rnd(n * 8) + rnd((m + 1) * kMaxRedBlocks * 8) + 8 * rnd((m + 1) * m * 8);
+    }
   }
   need += rnd(H.coarse_inv.size() * 8) + sell_bytes(H.load, 8) + rnd(nn) + 16 * rnd(n * 8) + 3 * rnd(n * 4) +
           rnd(Q_NUM * kMaxRedBlocks * 8) + rnd(sizeof(KrylovState));
@@ -726,6 +789,25 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
     *v = alloc_vec<float>(h, n);
     if (!*v) return bail(fail(MG_ERR_OOM, "alloc"));
   }
+  if (method_of(h) == M_GMRES) {
+    const int m = std::max(2, std::min(opts.restart > 0 ? opts.restart : 30, 64));
+    GmresView& G = h->gm;
+    G.m = m;
+    G.H = alloc_vec<double>(h, (int64_t)(m + 1) * m);
+    G.cs = alloc_vec<double>(h, m);
+    G.sn = alloc_vec<double>(h, m);
+    G.g = alloc_vec<double>(h, m + 1);
+    G.hv = alloc_vec<double>(h, m + 1);
+    G.y = alloc_vec<double>(h, m);
+    G.zs = alloc_vec<double>(h, m);
+    G.part = alloc_vec<double>(h, (int64_t)(m + 1) * kMaxRedBlocks);
+    G.V = alloc_vec<double>(h, (int64_t)(m + 1) * n);
+    if (opts.store_fp64) G.Z64 = alloc_vec<double>(h, (int64_t)m * n);
+    if (opts.store_fp32) G.Z32 = alloc_vec<float>(h, (int64_t)m * n);
+    h->vcur = alloc_vec<double>(h, n);
+    if (!G.H || !G.V || !G.part || !h->vcur || (opts.store_fp64 && !G.Z64) || (opts.store_fp32 && !G.Z32))
+      return bail(fail(MG_ERR_OOM, "alloc"));
+  }
   h->part.p = alloc_vec<double>(h, Q_NUM * kMaxRedBlocks);
   h->st = (KrylovState*)dev_alloc(h, sizeof(KrylovState));
   if (!h->part.p || !h->st) return bail(fail(MG_ERR_OOM, "alloc"));
@@ -735,6 +817,35 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   CU(cudaEventCreate(&h->ev0));
   CU(cudaEventCreate(&h->ev1));
   h->nred = grid_for_rows(((nn + 31) / 32) * 32);
+  // tail: the largest prefix of levels (from the coarsest) with <= tail_rows dofs
+  h->tail_top = 0;
+  if (opts.tail_rows > 0)
+    for (int l = 1; l < nlev && l < kTailMax; ++l)
+      if (h->L[l].n * nc <= opts.tail_rows) h->tail_top = l;
+      else break;
+  for (int pi = 0; pi < 2; ++pi) {
+    TailParams& P = pi == 0 ? h->tail64 : h->tail32;
+    const bool d = pi == 0;
+    if (d ? !opts.store_fp64 : !opts.store_fp32) continue;
+    P.nt = h->tail_top + 1;
+    P.nu1 = opts.nu1;
+    P.nu2 = opts.nu2;
+    P.omega = opts.omega;
+    P.cinv = h->coarse_inv;
+    P.cn = h->coarse_n;
+    for (int l = 0; l <= h->tail_top; ++l) {
+      LevelBufs& B = h->L[l];
+      TailLevel& T = P.lv[l];
+      T.A = d ? B.A64.v : B.A32.v;
+      T.P = B.P.t;
+      T.R = B.R.t;
+      T.S = d ? (const void*)B.S64 : (const void*)B.S32;
+      T.b = d ? (void*)B.b64 : (void*)B.b32;
+      T.o = d ? (void*)B.o64 : (void*)B.o32;
+      T.t = d ? (void*)B.t64 : (void*)B.t32;
+      T.r = d ? (void*)B.r64 : (void*)B.r32;
+    }
+  }
   CU(cudaDeviceSynchronize());
   *out = h;
   return MG_OK;
@@ -854,10 +965,10 @@ int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, voi
       if (level == 0 || !in2) return fail(MG_ERR_INVALID, "restrict needs level >= 1 and b");
       if (d) {
         launch_residual<double>(L.A64.v, nc, (const double*)in, (const double*)in2, L.r64, nullptr, s);
-        launch_restrict<double>(L.R.t, nc, L.r64, (double*)out, nullptr, s);
+        launch_restrict<double>(L.R.t, nc, L.r64, (double*)out, nullptr, nullptr, 0.0, nullptr, s);
       } else {
         launch_residual<float>(L.A32.v, nc, (const float*)in, (const float*)in2, L.r32, nullptr, s);
-        launch_restrict<float>(L.R.t, nc, L.r32, (float*)out, nullptr, s);
+        launch_restrict<float>(L.R.t, nc, L.r32, (float*)out, nullptr, nullptr, 0.0, nullptr, s);
       }
       break;
     case MG_OP_PROLONG_ADD:
@@ -954,10 +1065,10 @@ int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms) {
         if (level == 0) break;
         if (d) {
           launch_residual<double>(L.A64.v, nc, L.o64, L.b64, L.r64, nullptr, s);
-          launch_restrict<double>(L.R.t, nc, L.r64, h->L[level - 1].b64, nullptr, s);
+          launch_restrict<double>(L.R.t, nc, L.r64, h->L[level - 1].b64, nullptr, nullptr, 0.0, nullptr, s);
         } else {
           launch_residual<float>(L.A32.v, nc, L.o32, L.b32, L.r32, nullptr, s);
-          launch_restrict<float>(L.R.t, nc, L.r32, h->L[level - 1].b32, nullptr, s);
+          launch_restrict<float>(L.R.t, nc, L.r32, h->L[level - 1].b32, nullptr, nullptr, 0.0, nullptr, s);
         }
         break;
       case MG_OP_PROLONG_ADD:

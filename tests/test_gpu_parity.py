@@ -246,3 +246,72 @@ def test_not_converged_status(ctx):
     x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
     st = h.solve(b, x, rtol=1e-14, max_it=2)
     assert st.status == B.MG_ERR_NOT_CONVERGED and st.iters == 2
+
+
+@pytest.mark.parametrize("name", ["td_adaptive", "elasticity16"])
+def test_tail_kernel_bitwise_equals_level_kernels(ctx, name):
+    """The single-CTA tail V-cycle runs the same row steps as the grid
+    kernels: identical bits with and without it, FP64 and FP32."""
+    mk, prob, pkw, okw = CASES[name]
+    lm = mk()
+    hs = [G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(tail_rows=t, **okw)) for t in (0, 1 << 20)]
+    n = hs[0].n_dofs
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal(n)
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
+    r[oh.fine.sys.fixed] = 0.0
+    for prec, dt in ((B.MG_FP64, torch.float64), (B.MG_MIXED_FP32, torch.float32)):
+        outs = []
+        for hh in hs:
+            z = torch.empty(n, device="cuda", dtype=dt)
+            hh.vcycle(dev(r, dt), z, prec)
+            outs.append(z.cpu().numpy())
+        assert np.array_equal(outs[0], outs[1])
+    for hh in hs:
+        hh.free()
+
+
+def test_direct_launch_mode_equals_graph(ctx):
+    lm = W.td_adaptive(rounds=4, gamma=1.0)
+    pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    hs = [G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(launch_mode=m)) for m in (0, 1)]
+    coords = hs[0].coords()
+    f = dev(W.f_transport(coords, 1e-3, (1.0, 0.5)))
+    xs, its = [], []
+    for hh in hs:
+        b = torch.empty(hh.n_dofs, device="cuda", dtype=torch.float64)
+        hh.assemble_rhs(f, b)
+        x = torch.zeros_like(b)
+        st = hh.solve(b, x, rtol=1e-10, max_it=100, prec=B.MG_MIXED_FP32)
+        xs.append(x.cpu().numpy())
+        its.append(st.iters)
+    assert its[0] == its[1] and np.array_equal(xs[0], xs[1])
+    for hh in hs:
+        hh.free()
+
+
+@pytest.mark.parametrize("restart", [30, 4])
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+def test_gmres_matches_direct(ctx, prec, restart):
+    """Device GMRES(m) (flexible, CGS2, Givens on the device), including
+    restarts (m = 4), against the oracle's direct solve."""
+    lm = W.td_adaptive(rounds=4, gamma=1.0)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    h = G.Hierarchy(ctx, lm, B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)),
+                    B.make_opts(krylov=B.MG_GMRES, restart=restart))
+    oh = mg.Hierarchy(lm, prob)
+    s = PB.build_system(oh.fine.mesh, prob)
+    bref = s.rhs(W.f_transport(oh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(dev(bref), x, rtol=1e-10, max_it=300, prec=prec)
+    assert st.status == 0 and st.rel_res <= 1e-10, st.as_dict()
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    err = math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2))
+    assert err <= (1e-9 if prec == B.MG_FP64 else 1e-8), err
+    # the oracle's GMRES with the same restart needs a comparable number of steps
+    _, info = __import__("oracle.krylov", fromlist=["gmres"]).gmres(oh.fine.A, bref, oh.precondition, rtol=1e-10,
+                                                                    restart=restart, maxit=300)
+    assert abs(info["iters"] - st.iters) <= max(3, info["iters"] // 3), (info["iters"], st.iters)
+    h.free()
