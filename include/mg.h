@@ -127,6 +127,7 @@ typedef struct {
   size_t bytes_device;                  /* hierarchy + workspace               */
   int64_t n_hanging;
   double omega;
+  size_t bytes_workspace;               /* one extra solve workspace (serving)   */
 } mg_info;
 
 typedef struct {
@@ -141,6 +142,9 @@ typedef struct {
 } mg_stats;
 
 const char* mg_strerror(int code);
+/* Message of the last error raised on the calling thread (static storage,
+ * valid until the next call on that thread). */
+const char* mg_last_error(void);
 void mg_default_opts(mg_opts* opts);
 
 /* Context: one device, one stream (a cudaStream_t from the caller, e.g.
@@ -148,6 +152,7 @@ void mg_default_opts(mg_opts* opts);
  * an HBM budget (bytes; 0 = no limit) that bounds every hierarchy and
  * workspace allocated through this context.  The allocator struct is copied. */
 int mg_init(int device, size_t hbm_budget_bytes, const mg_allocator* alloc, void* stream, mg_ctx** out);
+/* MG_ERR_INVALID while hierarchies of this context are still alive. */
 int mg_destroy(mg_ctx* ctx);
 
 /* Build the hierarchy (Sec. 2.2 global coarsening; level operators by
@@ -214,6 +219,11 @@ int mg_submit(mg_ctx* ctx, mg_hier* h, const double* b, double* x, double rtol, 
               uint64_t* ticket);
 int mg_poll(mg_ctx* ctx, uint64_t ticket, mg_stats* stats);
 int mg_cancel(mg_ctx* ctx, uint64_t ticket);
+/* Maximum number of solves the scheduler keeps in flight at once (default 16;
+ * each runs on its own stream with its own workspace). */
+int mg_serve_config(mg_ctx* ctx, int max_slots);
+/* Kernels the library has enqueued on behalf of this hierarchy so far. */
+int64_t mg_launch_count(const mg_hier* h);
 
 #ifdef __cplusplus
 }

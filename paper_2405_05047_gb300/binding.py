@@ -12,6 +12,8 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
+import weakref
 
 import numpy as np
 
@@ -57,7 +59,8 @@ class MgInfo(C.Structure):
     _fields_ = [("dim", C.c_int), ("nc", C.c_int), ("levels", C.c_int), ("n_nodes", C.c_int64),
                 ("n_dofs", C.c_int64), ("n_free", C.c_int64), ("level_nodes", C.c_int64 * 32),
                 ("level_nnzb", C.c_int64 * 32), ("level_rows_nnzb", C.c_int64 * 32),
-                ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double)]
+                ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double),
+                ("bytes_workspace", C.c_size_t)]
 
 
 class MgStats(C.Structure):
@@ -104,6 +107,7 @@ _SIGS = {
     "mg_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "mg_launch_count": (C.c_int64, [C.c_void_p]),
     "mg_time_op": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "mg_serve_config": (C.c_int, [C.c_void_p, C.c_int]),
 }
 
 
@@ -303,22 +307,44 @@ def mg_cancel(ctx, ticket):
     return load_library().mg_cancel(ctx, ticket)
 
 
+def mg_serve_config(ctx, max_slots):
+    return _check(load_library().mg_serve_config(ctx, max_slots))
+
+
 # ---------------------------------------------------------------- wrappers
 class Context:
     def __init__(self, device=0, hbm_budget_bytes=0, allocator="torch", stream=None):
         self.handle, self._keep = mg_init(device, hbm_budget_bytes, allocator, stream)
         self.device = device
+        self._hiers = weakref.WeakSet()
 
     @property
     def stream(self):
         return self._keep[1]
 
+    def submit(self, hier, b, x, rtol=1e-8, max_it=200, prec=MG_MIXED_FP32):
+        return mg_submit(self.handle, hier.handle, b, x, rtol, max_it, prec)
+
+    def poll(self, ticket):
+        return mg_poll(self.handle, ticket)
+
+    def cancel(self, ticket):
+        return mg_cancel(self.handle, ticket)
+
+    def serve_config(self, max_slots):
+        return mg_serve_config(self.handle, max_slots)
+
     def close(self):
+        """Free every hierarchy of this context, then the context."""
         if self.handle:
+            for h in list(self._hiers):
+                h.free()
             mg_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -330,7 +356,10 @@ class Hierarchy:
 
     def __init__(self, ctx: Context, leafmesh, problem: MgProblem, opts: MgOpts | None = None):
         self.ctx = ctx
+        if not ctx.handle:
+            raise MGError(-1, "context is closed")
         self.handle = mg_setup(ctx.handle, leafmesh, problem, opts)
+        ctx._hiers.add(self)
         self.info = mg_hier_info(self.handle)
         self.nc = self.info.nc
         self.n_nodes = self.info.n_nodes
@@ -372,6 +401,8 @@ class Hierarchy:
             self.handle = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.free()
         except Exception:

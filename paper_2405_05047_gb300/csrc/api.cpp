@@ -1,0 +1,524 @@
+// C-ABI entry points (include/mg.h) and the serving scheduler.
+//
+// Serving: requests are solves on resident hierarchies.  A scheduler thread
+// keeps up to `max_slots` solves in flight, each on its own CUDA stream with
+// its own workspace, so requests that arrive while others run are admitted as
+// soon as a slot and HBM budget for a workspace are free, and their work
+// overlaps on the device (continuous batching).  Workspaces are pooled per
+// hierarchy; the budget counts every device byte of the context.  Every solve
+// is deterministic (fixed-order reductions, fixed grids), so a request's
+// result does not depend on what else runs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "device.h"
+
+using namespace mgi;
+
+#define CU(call)                                                                                        \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return fail(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct ServeRequest {
+  uint64_t ticket = 0;
+  mg_hier* h = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double rtol = 1e-8;
+  int max_it = 100;
+  int prec = MG_MIXED_FP32;
+  int state = 0;            // 0 queued, 1 running, 2 finished
+  int status = MG_PENDING;
+  mg_stats stats{};
+  Workspace* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  std::chrono::steady_clock::time_point t_submit, t_start, t_end;
+};
+
+namespace {
+
+// A workspace for a serving request: an idle pooled one, or a new one if the
+// budget allows (nullptr otherwise).
+Workspace* acquire_ws(mg_hier* h, cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lk(h->pool_mu);
+    if (!h->pool.empty()) {
+      Workspace* w = h->pool.back();
+      h->pool.pop_back();
+      return w;
+    }
+  }
+  mg_ctx* c = h->ctx;
+  if (c->budget && c->used + h->ws_bytes > c->budget) return nullptr;
+  Workspace* w = nullptr;
+  if (ws_create(h, false, s, &w) != MG_OK) return nullptr;
+  std::lock_guard<std::mutex> lk(h->pool_mu);
+  h->all_ws.push_back(w);
+  return w;
+}
+
+void release_ws(mg_hier* h, Workspace* w) {
+  std::lock_guard<std::mutex> lk(h->pool_mu);
+  h->pool.push_back(w);
+}
+
+void finish(mg_ctx* c, const std::shared_ptr<ServeRequest>& r, int status) {
+  r->t_end = std::chrono::steady_clock::now();
+  r->stats.setup_ms = std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count();
+  r->status = status;
+  r->state = 2;
+  if (r->ws) release_ws(r->h, r->ws);
+  r->ws = nullptr;
+  if (r->stream) c->free_streams.push_back(r->stream);
+  r->stream = nullptr;
+}
+
+void serve_worker(mg_ctx* c) {
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  while (!c->stop) {
+    bool progress = false;
+    // completions
+    for (size_t i = 0; i < c->running.size();) {
+      auto r = c->running[i];
+      if (cudaEventQuery(r->ws->ev1) == cudaSuccess) {
+        int rc = solve_check(r->h, *r->ws, r->stream, &r->stats);
+        if (rc == MG_PENDING) { ++i; continue; }
+        finish(c, r, rc);
+        c->running.erase(c->running.begin() + i);
+        progress = true;
+      } else {
+        ++i;
+      }
+    }
+    // admissions: first come first served, later requests may pass one that
+    // does not fit yet
+    for (auto it = c->queue.begin(); it != c->queue.end() && (int)c->running.size() < c->max_slots;) {
+      auto r = *it;
+      if (c->free_streams.empty()) {
+        cudaStream_t s;
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        c->free_streams.push_back(s);
+      }
+      // a pooled workspace was last used on another stream: that solve has
+      // finished (its ev1 completed) before the workspace went back to the pool
+      Workspace* w = acquire_ws(r->h, c->free_streams.back());
+      if (!w) { ++it; continue; }
+      r->stream = c->free_streams.back();
+      c->free_streams.pop_back();
+      r->ws = w;
+      r->state = 1;
+      r->t_start = std::chrono::steady_clock::now();
+      int rc = solve_start(r->h, *w, r->b, false, r->x, false, r->x, false, r->rtol, r->max_it, r->prec, r->stream);
+      it = c->queue.erase(it);
+      if (rc != MG_OK) finish(c, r, rc);
+      else c->running.push_back(r);
+      progress = true;
+    }
+    if (c->running.empty() && c->queue.empty()) {
+      c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+    } else if (!progress) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mg_strerror(int code) {
+  switch (code) {
+    case MG_OK: return "ok";
+    case MG_PENDING: return "pending";
+    case MG_ERR_INVALID: return "invalid argument";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_ADMISSION: return "request exceeds the HBM budget";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_BREAKDOWN: return "Krylov breakdown";
+    case MG_ERR_NAN: return "NaN or Inf in a reduction";
+    case MG_ERR_TIMEOUT: return "device wait timed out";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_CANCELLED: return "cancelled";
+    default: return "unknown status";
+  }
+}
+
+const char* mg_last_error(void) { return last_error(); }
+
+void mg_default_opts(mg_opts* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega = 0.8;
+  o->min_level = -1;
+  o->max_levels = 0;
+  o->krylov = MG_KRYLOV_AUTO;
+  o->restart = 30;
+  o->store_fp64 = 1;
+  o->store_fp32 = 1;
+  o->launch_mode = 0;
+  o->tail_rows = 4096;
+}
+
+int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
+  if (!out) return fail(MG_ERR_INVALID, "out is NULL");
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(MG_ERR_INVALID, "no such device");
+  CU(cudaSetDevice(device));
+  mg_ctx* c = new mg_ctx();
+  c->device = device;
+  c->budget = budget;
+  if (alloc && alloc->malloc_fn && alloc->free_fn) { c->alloc = *alloc; c->has_alloc = true; }
+  if (stream) c->stream = (cudaStream_t)stream;
+  else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return fail(MG_ERR_CUDA, "stream"); }
+    c->own_stream = true;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+int mg_destroy(mg_ctx* c) {
+  if (!c) return MG_ERR_INVALID;
+  if (c->live_hiers.load() > 0) return fail(MG_ERR_INVALID, "context still has hierarchies: mg_free them first");
+  {
+    std::unique_lock<std::mutex> lk(c->mu);
+    c->stop = true;
+  }
+  c->cv.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  for (auto& r : c->running) cudaStreamSynchronize(r->stream);
+  for (cudaStream_t s : c->free_streams) cudaStreamDestroy(s);
+  for (auto& r : c->running)
+    if (r->stream) cudaStreamDestroy(r->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return MG_OK;
+}
+
+int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_opts* opts_in, mg_hier** out) {
+  if (!ctx || !mesh || !prob || !out) return fail(MG_ERR_INVALID, "NULL argument");
+  CU(cudaSetDevice(ctx->device));
+  mg_opts opts;
+  if (opts_in) opts = *opts_in;
+  else mg_default_opts(&opts);
+  if (opts.nu1 < 1 || opts.nu2 < 0 || opts.nu1 > 16 || opts.nu2 > 16) return fail(MG_ERR_INVALID, "nu1 must be >= 1");
+  if (!(opts.omega > 0.0)) return fail(MG_ERR_INVALID, "omega must be positive");
+  if (!opts.store_fp64 && !opts.store_fp32) return fail(MG_ERR_INVALID, "no precision stored");
+  HostHierarchy H;
+  Status st = build_hierarchy(*mesh, *prob, opts, &H);
+  if (!st.good()) return fail(st.code, st.msg);
+  auto h = std::make_unique<mg_hier>();
+  h->ctx = ctx;
+  h->dim = H.dim;
+  h->nc = H.nc;
+  h->nlev = (int)H.levels.size();
+  const HostLevel& F = H.levels.back();
+  h->n_nodes = F.topo.n_nodes;
+  h->n_dofs = h->n_nodes * H.nc;
+  h->n_free = H.n_free;
+  h->prob = *prob;
+  h->opts = opts;
+  h->has_fp64 = opts.store_fp64 != 0;
+  h->has_fp32 = opts.store_fp32 != 0;
+  if (method_of(h.get()) == 3) h->gmres_m = std::max(2, std::min(opts.restart > 0 ? opts.restart : 30, 64));
+  for (int64_t i = 0; i < h->n_nodes; ++i) h->n_hanging += F.topo.hanging[i];
+  h->coords.resize(h->n_nodes * H.dim);
+  for (int64_t i = 0; i < h->n_nodes; ++i) {
+    int64_t X[3];
+    F.topo.lattice_coords(i, X);
+    for (int d = 0; d < H.dim; ++d)
+      h->coords[i * H.dim + d] = H.origin[d] + (double)X[d] * (H.extent[d] / (double)F.topo.ncell[d]);
+  }
+  // admission, first a lower bound without allocating anything (stored
+  // values of the level operators); the exact check follows the upload
+  {
+    size_t lower = 0;
+    const int nb = H.nc * H.nc;
+    for (const HostLevel& lv : H.levels) {
+      if (opts.store_fp64) lower += (size_t)lv.A.nnzb() * nb * 8;
+      if (opts.store_fp32) lower += (size_t)lv.A.nnzb() * nb * 4;
+    }
+    if (ctx->budget && ctx->used + lower > ctx->budget)
+      return fail(MG_ERR_ADMISSION, "hierarchy needs more than " + std::to_string(lower) + " bytes, budget left " +
+                                        std::to_string(ctx->budget - std::min(ctx->budget, (size_t)ctx->used)));
+  }
+  mg_hier* hp = h.get();
+  int rc = upload_hierarchy(hp, H);
+  if (rc == MG_OK) {
+    hp->ws_bytes = workspace_bytes(hp);
+    rc = ws_create(hp, true, ctx->stream, &hp->ws0);
+  }
+  if (rc == MG_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (rc == MG_OK && ctx->budget && ctx->used > ctx->budget)
+    rc = fail(MG_ERR_ADMISSION, "hierarchy and its workspace need " + std::to_string(hp->bytes + hp->ws0->bytes) +
+                                    " bytes, over the HBM budget");
+  if (rc != MG_OK) {
+    free_hierarchy(hp);
+    return rc;
+  }
+  ctx->resident += hp->bytes + hp->ws0->bytes;
+  ctx->live_hiers++;
+  *out = h.release();
+  return MG_OK;
+}
+
+int mg_hier_info(const mg_hier* h, mg_info* info) {
+  if (!h || !info) return fail(MG_ERR_INVALID, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->dim = h->dim;
+  info->nc = h->nc;
+  info->levels = h->nlev;
+  info->n_nodes = h->n_nodes;
+  info->n_dofs = h->n_dofs;
+  info->n_free = h->n_free;
+  for (int l = 0; l < h->nlev && l < 32; ++l) {
+    info->level_nodes[l] = h->level_nodes[l];
+    info->level_nnzb[l] = h->level_nnzb[l];
+    info->level_rows_nnzb[l] = h->level_real_nnzb[l];
+  }
+  info->bytes_device = h->bytes + (h->ws0 ? h->ws0->bytes : 0);
+  info->bytes_workspace = h->ws_bytes;
+  info->n_hanging = h->n_hanging;
+  info->omega = h->opts.omega;
+  return MG_OK;
+}
+
+int mg_node_coords(const mg_hier* h, double* xyz) {
+  if (!h || !xyz) return fail(MG_ERR_INVALID, "NULL argument");
+  std::memcpy(xyz, h->coords.data(), h->coords.size() * sizeof(double));
+  return MG_OK;
+}
+
+int mg_free(mg_hier* h) {
+  if (!h) return MG_ERR_INVALID;
+  cudaSetDevice(h->ctx->device);
+  cudaDeviceSynchronize();
+  h->ctx->resident -= h->bytes + (h->ws0 ? h->ws0->bytes : 0);
+  h->ctx->live_hiers--;
+  free_hierarchy(h);
+  delete h;
+  return MG_OK;
+}
+
+int mg_assemble_rhs(mg_hier* h, const double* f, double* b) {
+  if (!h || !f || !b) return fail(MG_ERR_INVALID, "NULL argument");
+  cudaStream_t s = h->ctx->stream;
+  launch_rhs(h->F.v, h->nc, f, h->fixmask, b, s);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+static int solve_sync(mg_hier* h, const double* b, bool bh, double* x, bool xh, double rtol, int max_it, int prec,
+                      mg_stats* stats) {
+  if (!h || !b || !x || !(rtol > 0) || max_it < 1) return fail(MG_ERR_INVALID, "bad argument");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  CU(cudaSetDevice(h->ctx->device));
+  cudaStream_t s = h->ctx->stream;
+  Workspace& w = *h->ws0;
+  rc = solve_start(h, w, b, bh, x, xh, x, xh, rtol, max_it, prec, s);
+  while (rc == MG_OK || rc == MG_PENDING) {
+    CU(cudaEventSynchronize(w.ev1));
+    rc = solve_check(h, w, s, stats);
+    if (rc != MG_PENDING) break;
+  }
+  CU(cudaGetLastError());
+  return rc;
+}
+
+int mg_solve(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats) {
+  return solve_sync(h, b, false, x, false, rtol, max_it, prec, stats);
+}
+
+int mg_solve_host(mg_hier* h, const double* b_host, double* x_host, double rtol, int max_it, int prec,
+                  mg_stats* stats) {
+  return solve_sync(h, b_host, true, x_host, true, rtol, max_it, prec, stats);
+}
+
+int mg_vcycle(mg_hier* h, const void* r, void* z, int prec) {
+  if (!h || !r || !z) return fail(MG_ERR_INVALID, "NULL argument");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  cudaStream_t s = h->ctx->stream;
+  if (prec == MG_FP64) enqueue_vcycle<double>(h, *h->ws0, h->nlev - 1, (const double*)r, (double*)z, nullptr, s);
+  else enqueue_vcycle<float>(h, *h->ws0, h->nlev - 1, (const float*)r, (float*)z, nullptr, s);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+// one level operator on the given vectors (shared by mg_apply and mg_time_op)
+static int level_op(mg_hier* h, int level, int op, const void* in, const void* in2, void* out, int prec,
+                    cudaStream_t s) {
+  LevelMats& L = h->L[level];
+  LevelVecs& V = h->ws0->lv[level];
+  const int nc = h->nc;
+  const bool d = prec == MG_FP64;
+  switch (op) {
+    case MG_OP_MATVEC:
+      if (d) launch_matvec<double>(L.A64.v, nc, (const double*)in, (double*)out, nullptr, s);
+      else launch_matvec<float>(L.A32.v, nc, (const float*)in, (float*)out, nullptr, s);
+      return MG_OK;
+    case MG_OP_SMOOTH:
+      if (!in2) return fail(MG_ERR_INVALID, "smooth needs b");
+      if (d) launch_smooth<double>(L.A64.v, nc, (const double*)in, (const double*)in2, L.S64, (double*)out, h->opts.omega, false, nullptr, s);
+      else launch_smooth<float>(L.A32.v, nc, (const float*)in, (const float*)in2, L.S32, (float*)out, h->opts.omega, false, nullptr, s);
+      return MG_OK;
+    case MG_OP_RESTRICT:
+      if (level == 0 || !in2) return fail(MG_ERR_INVALID, "restrict needs level >= 1 and b");
+      if (d) {
+        launch_residual<double>(L.A64.v, nc, (const double*)in, (const double*)in2, V.r64, nullptr, s);
+        launch_restrict<double>(L.R.t, nc, V.r64, (double*)out, nullptr, nullptr, 0.0, nullptr, s);
+      } else {
+        launch_residual<float>(L.A32.v, nc, (const float*)in, (const float*)in2, V.r32, nullptr, s);
+        launch_restrict<float>(L.R.t, nc, V.r32, (float*)out, nullptr, nullptr, 0.0, nullptr, s);
+      }
+      return MG_OK;
+    case MG_OP_PROLONG_ADD:
+      if (level == 0 || !in2) return fail(MG_ERR_INVALID, "prolong needs level >= 1 and x");
+      if (d) launch_prolong_add<double>(L.P.t, nc, (const double*)in, (const double*)in2, (double*)out, nullptr, s);
+      else launch_prolong_add<float>(L.P.t, nc, (const float*)in, (const float*)in2, (float*)out, nullptr, s);
+      return MG_OK;
+    case MG_OP_COARSE:
+      if (level != 0) return fail(MG_ERR_INVALID, "coarse solve is on level 0");
+      if (d) launch_coarse<double>(h->coarse_inv, h->coarse_n, (const double*)in, (double*)out, nullptr, s);
+      else launch_coarse<float>(h->coarse_inv, h->coarse_n, (const float*)in, (float*)out, nullptr, s);
+      return MG_OK;
+    default:
+      return fail(MG_ERR_INVALID, "unknown op");
+  }
+}
+
+int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, void* out, int prec) {
+  if (!h || !in || !out || level < 0 || level >= h->nlev) return fail(MG_ERR_INVALID, "bad argument");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  cudaStream_t s = h->ctx->stream;
+  rc = level_op(h, level, op, in, in2, out, prec, s);
+  if (rc) return rc;
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms) {
+  if (!h || !ms || level < 0 || level >= h->nlev || reps < 1) return fail(MG_ERR_INVALID, "bad argument");
+  if (op == MG_OP_COARSE || ((op == MG_OP_RESTRICT || op == MG_OP_PROLONG_ADD) && level == 0))
+    return fail(MG_ERR_INVALID, "operator not timed on this level");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  cudaStream_t s = h->ctx->stream;
+  Workspace& w = *h->ws0;
+  LevelVecs& V = w.lv[level];
+  const bool d = prec == MG_FP64;
+  const void* x = d ? (const void*)V.o64 : (const void*)V.o32;
+  const void* b = d ? (const void*)V.b64 : (const void*)V.b32;
+  void* y = d ? (void*)V.t64 : (void*)V.t32;
+  void* yc = nullptr;
+  const void* xc = nullptr;
+  if (level > 0) {
+    yc = d ? (void*)w.lv[level - 1].b64 : (void*)w.lv[level - 1].b32;
+    xc = d ? (const void*)w.lv[level - 1].o64 : (const void*)w.lv[level - 1].o32;
+  }
+  auto once = [&]() -> int {
+    if (op == MG_OP_RESTRICT) return level_op(h, level, op, x, b, yc, prec, s);
+    if (op == MG_OP_PROLONG_ADD) return level_op(h, level, op, xc, x, y, prec, s);
+    return level_op(h, level, op, x, b, y, prec, s);
+  };
+  if ((rc = once())) return rc;
+  CU(cudaEventRecord(w.ev0, s));
+  for (int i = 0; i < reps; ++i) once();
+  CU(cudaEventRecord(w.ev1, s));
+  CU(cudaEventSynchronize(w.ev1));
+  float t = 0;
+  CU(cudaEventElapsedTime(&t, w.ev0, w.ev1));
+  *ms = (double)t / reps;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+int64_t mg_launch_count(const mg_hier* h) { return h ? (int64_t)h->launch_count : 0; }
+
+int mg_submit(mg_ctx* c, mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec,
+              uint64_t* ticket) {
+  if (!c || !h || !b || !x || !ticket || !(rtol > 0) || max_it < 1) return fail(MG_ERR_INVALID, "bad argument");
+  if (h->ctx != c) return fail(MG_ERR_INVALID, "hierarchy belongs to another context");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  // a request can never run if one more workspace does not fit next to the
+  // resident hierarchies
+  if (c->budget && (size_t)c->resident + h->ws_bytes > c->budget)
+    return fail(MG_ERR_ADMISSION, "a solve workspace of " + std::to_string(h->ws_bytes) +
+                                      " bytes never fits the HBM budget next to the resident hierarchies");
+  auto r = std::make_shared<ServeRequest>();
+  r->h = h; r->b = b; r->x = x; r->rtol = rtol; r->max_it = max_it; r->prec = prec;
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->worker_started) {
+      c->worker = std::thread(serve_worker, c);
+      c->worker_started = true;
+    }
+    r->ticket = c->next_ticket++;
+    c->tickets[r->ticket] = r;
+    c->queue.push_back(r);
+    *ticket = r->ticket;
+  }
+  c->cv.notify_one();
+  return MG_OK;
+}
+
+int mg_poll(mg_ctx* c, uint64_t ticket, mg_stats* stats) {
+  if (!c) return fail(MG_ERR_INVALID, "NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->tickets.find(ticket);
+  if (it == c->tickets.end()) return fail(MG_ERR_INVALID, "unknown ticket");
+  auto r = it->second;
+  if (r->state != 2) return MG_PENDING;
+  if (stats) {
+    *stats = r->stats;
+    stats->status = r->status;
+  }
+  int st = r->status;
+  c->tickets.erase(it);
+  return st;
+}
+
+int mg_cancel(mg_ctx* c, uint64_t ticket) {
+  if (!c) return fail(MG_ERR_INVALID, "NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->tickets.find(ticket);
+  if (it == c->tickets.end()) return fail(MG_ERR_INVALID, "unknown ticket");
+  auto r = it->second;
+  if (r->state != 0) return fail(MG_ERR_INVALID, "request already running or finished");
+  for (auto q = c->queue.begin(); q != c->queue.end(); ++q)
+    if ((*q)->ticket == ticket) { c->queue.erase(q); break; }
+  r->state = 2;
+  r->status = MG_ERR_CANCELLED;
+  return MG_OK;
+}
+
+int mg_serve_config(mg_ctx* c, int max_slots) {
+  if (!c || max_slots < 1 || max_slots > 256) return fail(MG_ERR_INVALID, "max_slots must be in [1, 256]");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->max_slots = max_slots;
+  return MG_OK;
+}
+
+}  // extern "C"

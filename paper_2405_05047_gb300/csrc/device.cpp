@@ -1,0 +1,652 @@
+// Device hierarchy (SELL packing + upload), solve workspaces, the V-cycle and
+// the Krylov loop as one CUDA graph.
+//
+// The V-cycle follows Algorithm "Geometric multigrid solver" of the paper
+// (Sec. 2.2): Step 0 coarse solve, Step 1 pre-smoothing, Step 2 restriction of
+// the residual, Step 3 recursion with zero initial guess, Step 4 prolongation
+// and correction, Step 5 post-smoothing.  It preconditions flexible CG
+// (Polak-Ribiere), BiCGStab or flexible GMRES(m) (Sec. 4.1.5: multigrid as
+// preconditioner of a Krylov method).  All Krylov scalars stay on the device;
+// one Krylov iteration is captured into the body of a CUDA-graph `while` node
+// whose condition is set by the convergence test on the device, so a whole
+// solve is one graph launch and only the final state crosses to the host.
+#include "device.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace mgi {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+const char* last_error() { return g_last_error.c_str(); }
+
+#define CU(call)                                                                                        \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return fail(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace {
+
+size_t rnd(size_t b) { return b == 0 ? 256 : ((b + 255) & ~(size_t)255); }
+
+// Device allocation through the context allocator (or cudaMalloc), recorded
+// in `list` and counted against the context.
+void* dev_alloc(mg_ctx* c, std::vector<Alloc>& list, size_t& total, size_t bytes, bool ctx_alloc) {
+  bytes = rnd(bytes);
+  void* p = nullptr;
+  const bool use_ctx = ctx_alloc && c->has_alloc;
+  if (use_ctx) p = c->alloc.malloc_fn(bytes, c->alloc.user);
+  else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  if (!p) return nullptr;
+  list.push_back({p, bytes, !use_ctx});
+  total += bytes;
+  c->used += bytes;
+  return p;
+}
+
+void free_list(mg_ctx* c, std::vector<Alloc>& list, size_t& total) {
+  for (auto& a : list) {
+    if (!a.cuda) c->alloc.free_fn(a.p, c->alloc.user);
+    else cudaFree(a.p);
+    c->used -= a.bytes;
+  }
+  list.clear();
+  total = 0;
+}
+
+// SELL-C packing of a block CSR matrix (C = kSlice block rows per slice).
+template <typename VT>
+void pack_sell(const BlockCSR& M, std::vector<int64_t>& sptr, std::vector<int32_t>& col, std::vector<VT>& val) {
+  const int nb = M.nc * M.nc;
+  const int64_t n = M.n, ns = (n + kSlice - 1) / kSlice;
+  sptr.assign(ns + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t w = 0;
+    for (int64_t r = s * kSlice; r < std::min(n, (s + 1) * kSlice); ++r) w = std::max(w, M.ptr[r + 1] - M.ptr[r]);
+    sptr[s + 1] = sptr[s] + kSlice * w;
+  }
+  const int64_t slots = sptr[ns];
+  col.assign(slots, 0);
+  val.assign(slots * nb, VT(0));
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t w = (sptr[s + 1] - sptr[s]) / kSlice;
+    for (int lane = 0; lane < kSlice; ++lane) {
+      const int64_t r = s * kSlice + lane;
+      const int64_t len = r < n ? M.ptr[r + 1] - M.ptr[r] : 0;
+      for (int64_t j = 0; j < w; ++j) {
+        const int64_t g = sptr[s] + kSlice * j, o = g + lane;
+        if (j < len) {
+          col[o] = (int32_t)M.col[M.ptr[r] + j];
+          for (int e = 0; e < nb; ++e) val[g * nb + (int64_t)e * kSlice + lane] = (VT)M.val[(M.ptr[r] + j) * nb + e];
+        } else {
+          col[o] = (int32_t)(r < n ? std::min<int64_t>(r, M.m - 1) : 0);
+        }
+      }
+    }
+  }
+}
+
+template <typename VT>
+int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out) {
+  std::vector<int64_t> sptr;
+  std::vector<int32_t> col;
+  std::vector<VT> val;
+  pack_sell<VT>(M, sptr, col, val);
+  void* dp = dev_alloc(h->ctx, h->allocs, h->bytes, sptr.size() * 8, true);
+  void* dc = dev_alloc(h->ctx, h->allocs, h->bytes, col.size() * 4, true);
+  void* dv = dev_alloc(h->ctx, h->allocs, h->bytes, val.size() * sizeof(VT), true);
+  if (!dp || !dc || !dv) return fail(MG_ERR_OOM, "device allocation failed");
+  CU(cudaMemcpy(dp, sptr.data(), sptr.size() * 8, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(dc, col.data(), col.size() * 4, cudaMemcpyHostToDevice));
+  if (!val.empty()) CU(cudaMemcpy(dv, val.data(), val.size() * sizeof(VT), cudaMemcpyHostToDevice));
+  out->v.sptr = out->t.sptr = (const int64_t*)dp;
+  out->v.col = out->t.col = (const int32_t*)dc;
+  out->v.val = dv;
+  out->t.w = (const float*)dv;
+  out->v.n = out->t.n = M.n;
+  out->v.nslices = out->t.nslices = (int64_t)sptr.size() - 1;
+  out->slots = (int64_t)col.size();
+  out->nnz_real = M.nnzb();
+  return MG_OK;
+}
+
+template <typename T>
+T* halloc(mg_hier* h, int64_t n) {
+  return (T*)dev_alloc(h->ctx, h->allocs, h->bytes, (size_t)std::max<int64_t>(n, 1) * sizeof(T), true);
+}
+
+// ---------------------------------------------------------------- precision helpers
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static const TailParams& tail(Workspace& w) { return w.tail64; }
+  static const SellView& A(LevelMats& l) { return l.A64.v; }
+  static const double* S(LevelMats& l) { return l.S64; }
+  static double* b(LevelVecs& v) { return v.b64; }
+  static double* o(LevelVecs& v) { return v.o64; }
+  static double* t(LevelVecs& v) { return v.t64; }
+  static double* r(LevelVecs& v) { return v.r64; }
+};
+template <>
+struct Prec<float> {
+  static const TailParams& tail(Workspace& w) { return w.tail32; }
+  static const SellView& A(LevelMats& l) { return l.A32.v; }
+  static const float* S(LevelMats& l) { return l.S32; }
+  static float* b(LevelVecs& v) { return v.b32; }
+  static float* o(LevelVecs& v) { return v.o32; }
+  static float* t(LevelVecs& v) { return v.t32; }
+  static float* r(LevelVecs& v) { return v.r32; }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- hierarchy
+int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
+  const int nc = H.nc, nb = nc * nc;
+  const int nlev = (int)H.levels.size();
+  const mg_opts& opts = h->opts;
+  h->L.resize(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    HostLevel& lv = H.levels[l];
+    LevelMats& B = h->L[l];
+    B.n = lv.topo.n_nodes;
+    h->level_nodes.push_back(B.n);
+    h->level_real_nnzb.push_back(lv.A.nnzb());
+    int rc;
+    if (opts.store_fp64) {
+      if ((rc = upload_sell<double>(h, lv.A, &B.A64))) return rc;
+      B.S64 = halloc<double>(h, B.n * nb);
+      if (!B.S64) return fail(MG_ERR_OOM, "alloc");
+      CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
+    }
+    if (opts.store_fp32) {
+      if ((rc = upload_sell<float>(h, lv.A, &B.A32))) return rc;
+      std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
+      B.S32 = halloc<float>(h, B.n * nb);
+      if (!B.S32) return fail(MG_ERR_OOM, "alloc");
+      CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
+    }
+    h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
+    if (l > 0) {
+      if ((rc = upload_sell<float>(h, lv.P, &B.P))) return rc;
+      if ((rc = upload_sell<float>(h, lv.R, &B.R))) return rc;
+    }
+    // release host copies of what is now on the device
+    if (l < nlev - 1) { lv.A = BlockCSR(); lv.leaves = LeafSet(); }
+    lv.P = BlockCSR();
+    lv.R = BlockCSR();
+  }
+  h->coarse_n = H.levels[0].topo.n_nodes * nc;
+  h->coarse_inv = halloc<double>(h, h->coarse_n * h->coarse_n);
+  if (!h->coarse_inv) return fail(MG_ERR_OOM, "alloc");
+  CU(cudaMemcpy(h->coarse_inv, H.coarse_inv.data(), H.coarse_inv.size() * 8, cudaMemcpyHostToDevice));
+  int rc;
+  if ((rc = upload_sell<double>(h, H.load, &h->F))) return rc;
+  const HostLevel& F = H.levels.back();
+  const int64_t nn = F.topo.n_nodes;
+  {
+    // hanging rows of H on the finest level (regular rows empty)
+    BlockCSR Hm;
+    Hm.n = Hm.m = nn;
+    Hm.nc = 1;
+    Hm.ptr.assign(nn + 1, 0);
+    for (int64_t i = 0; i < nn; ++i)
+      Hm.ptr[i + 1] = Hm.ptr[i] + (F.topo.hanging[i] ? F.topo.con_ptr[i + 1] - F.topo.con_ptr[i] : 0);
+    for (int64_t i = 0; i < nn; ++i)
+      if (F.topo.hanging[i])
+        for (int64_t o = F.topo.con_ptr[i]; o < F.topo.con_ptr[i + 1]; ++o) {
+          Hm.col.push_back(F.topo.con_node[o]);
+          Hm.val.push_back(F.topo.con_w[o]);
+        }
+    if ((rc = upload_sell<float>(h, Hm, &h->Hc))) return rc;
+  }
+  h->fixmask = (uint8_t*)dev_alloc(h->ctx, h->allocs, h->bytes, nn, true);
+  if (!h->fixmask) return fail(MG_ERR_OOM, "alloc");
+  CU(cudaMemcpy(h->fixmask, F.fixmask.data(), nn, cudaMemcpyHostToDevice));
+  // tail: the largest prefix of levels (from the coarsest) with <= tail_rows dofs
+  h->tail_top = 0;
+  if (opts.tail_rows > 0)
+    for (int l = 1; l < nlev && l < kTailMax; ++l)
+      if (h->L[l].n * nc <= opts.tail_rows) h->tail_top = l;
+      else break;
+  return MG_OK;
+}
+
+void free_hierarchy(mg_hier* h) {
+  for (Workspace* w : h->all_ws) ws_destroy(h, w);
+  h->all_ws.clear();
+  h->pool.clear();
+  if (h->ws0) ws_destroy(h, h->ws0);
+  h->ws0 = nullptr;
+  free_list(h->ctx, h->allocs, h->bytes);
+}
+
+// ---------------------------------------------------------------- workspaces
+size_t workspace_bytes(const mg_hier* h) {
+  const int nc = h->nc;
+  const int64_t n = h->n_dofs;
+  size_t b = 0;
+  for (const LevelMats& L : h->L) {
+    const int64_t m = L.n * nc;
+    if (h->has_fp64) b += 4 * rnd(m * 8);
+    if (h->has_fp32) b += 4 * rnd(m * 4);
+  }
+  b += 12 * rnd(n * 8) + 3 * rnd(n * 4) + rnd(Q_NUM * kMaxRedBlocks * 8) + rnd(sizeof(KrylovState));
+  if (h->gmres_m > 0) {
+    const int64_t m = h->gmres_m;
+    b += rnd((m + 1) * n * 8) + (h->has_fp64 ? rnd(m * n * 8) : 0) + (h->has_fp32 ? rnd(m * n * 4) : 0) +
+         rnd((m + 1) * kMaxRedBlocks * 8) + 8 * rnd((m + 1) * (m + 1) * 8);
+  }
+  return b;
+}
+
+int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
+  auto w = std::make_unique<Workspace>();
+  mg_ctx* c = h->ctx;
+  const int nc = h->nc;
+  const int64_t n = h->n_dofs;
+  auto A8 = [&](int64_t k) { return (double*)dev_alloc(c, w->allocs, w->bytes, (size_t)std::max<int64_t>(k, 1) * 8, ctx_alloc); };
+  auto A4 = [&](int64_t k) { return (float*)dev_alloc(c, w->allocs, w->bytes, (size_t)std::max<int64_t>(k, 1) * 4, ctx_alloc); };
+  bool ok = true;
+  w->lv.resize(h->nlev);
+  for (int l = 0; l < h->nlev; ++l) {
+    LevelVecs& v = w->lv[l];
+    const int64_t m = h->L[l].n * nc;
+    if (h->has_fp64) { v.b64 = A8(m); v.o64 = A8(m); v.t64 = A8(m); v.r64 = A8(m); ok &= v.b64 && v.o64 && v.t64 && v.r64; }
+    if (h->has_fp32) { v.b32 = A4(m); v.o32 = A4(m); v.t32 = A4(m); v.r32 = A4(m); ok &= v.b32 && v.o32 && v.t32 && v.r32; }
+  }
+  double** vecs[] = {&w->xi, &w->bi, &w->r, &w->p, &w->q, &w->z, &w->rhat, &w->sv, &w->t, &w->ph, &w->shat, &w->vcur};
+  for (double** v : vecs) { *v = A8(n); ok &= *v != nullptr; }
+  float** v32[] = {&w->r32, &w->ph32, &w->sh32};
+  for (float** v : v32) { *v = A4(n); ok &= *v != nullptr; }
+  w->part.p = A8(Q_NUM * kMaxRedBlocks);
+  w->st = (KrylovState*)dev_alloc(c, w->allocs, w->bytes, sizeof(KrylovState), ctx_alloc);
+  ok &= w->part.p && w->st;
+  if (h->gmres_m > 0 && ok) {
+    const int m = h->gmres_m;
+    GmresView& G = w->gm;
+    G.m = m;
+    G.H = A8((int64_t)(m + 1) * m);
+    G.cs = A8(m); G.sn = A8(m); G.g = A8(m + 1); G.hv = A8(m + 1); G.y = A8(m); G.zs = A8(m);
+    G.part = A8((int64_t)(m + 1) * kMaxRedBlocks);
+    G.V = A8((int64_t)(m + 1) * n);
+    if (h->has_fp64) G.Z64 = A8((int64_t)m * n);
+    if (h->has_fp32) G.Z32 = A4((int64_t)m * n);
+    ok &= G.H && G.cs && G.sn && G.g && G.hv && G.y && G.zs && G.part && G.V && (!h->has_fp64 || G.Z64) &&
+          (!h->has_fp32 || G.Z32);
+  }
+  if (!ok) {
+    free_list(c, w->allocs, w->bytes);
+    return fail(MG_ERR_OOM, "workspace allocation failed");
+  }
+  // initialised in stream order on the stream the solves will use
+  for (double** v : vecs) CU(cudaMemsetAsync(*v, 0, n * 8, s));
+  CU(cudaMemsetAsync(w->part.p, 0, Q_NUM * kMaxRedBlocks * 8, s));
+  CU(cudaMemsetAsync(w->st, 0, sizeof(KrylovState), s));
+  CU(cudaMallocHost(&w->st_host, sizeof(KrylovState)));
+  CU(cudaEventCreate(&w->ev0));
+  CU(cudaEventCreate(&w->ev1));
+  // tail parameters: matrices of the hierarchy, vectors of this workspace
+  for (int pi = 0; pi < 2; ++pi) {
+    TailParams& P = pi == 0 ? w->tail64 : w->tail32;
+    const bool d = pi == 0;
+    if (d ? !h->has_fp64 : !h->has_fp32) continue;
+    P.nt = h->tail_top + 1;
+    P.nu1 = h->opts.nu1;
+    P.nu2 = h->opts.nu2;
+    P.omega = h->opts.omega;
+    P.cinv = h->coarse_inv;
+    P.cn = h->coarse_n;
+    for (int l = 0; l <= h->tail_top; ++l) {
+      LevelMats& B = h->L[l];
+      LevelVecs& V = w->lv[l];
+      TailLevel& T = P.lv[l];
+      T.A = d ? B.A64.v : B.A32.v;
+      T.P = B.P.t;
+      T.R = B.R.t;
+      T.S = d ? (const void*)B.S64 : (const void*)B.S32;
+      T.b = d ? (void*)V.b64 : (void*)V.b32;
+      T.o = d ? (void*)V.o64 : (void*)V.o32;
+      T.t = d ? (void*)V.t64 : (void*)V.t32;
+      T.r = d ? (void*)V.r64 : (void*)V.r32;
+    }
+  }
+  *out = w.release();
+  return MG_OK;
+}
+
+void ws_destroy(mg_hier* h, Workspace* w) {
+  if (!w) return;
+  for (auto& g : w->graphs) cudaGraphExecDestroy(g.exec);
+  if (w->st_host) cudaFreeHost(w->st_host);
+  if (w->ev0) cudaEventDestroy(w->ev0);
+  if (w->ev1) cudaEventDestroy(w->ev1);
+  free_list(h->ctx, w->allocs, w->bytes);
+  delete w;
+}
+
+// ---------------------------------------------------------------- V-cycle
+// z = GMG(l, 0, b): the V-cycle of Algorithm "Geometric multigrid solver".
+// first_done: the first pre-smoothing sweep (from x = 0) was already written
+// into its buffer by the restriction kernel of the finer level.
+template <typename T>
+void enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
+                    bool first_done) {
+  const int nc = h->nc;
+  if (l == 0) {                                                  // Step 0
+    launch_coarse<T>(h->coarse_inv, h->coarse_n, b, out, done, s);
+    h->launch_count++;
+    return;
+  }
+  if (l <= h->tail_top) {                                        // small levels: one CTA
+    launch_tail<T>(Prec<T>::tail(w), nc, b, out, first_done, done, s);
+    h->launch_count++;
+    return;
+  }
+  LevelMats& L = h->L[l];
+  LevelVecs& V = w.lv[l];
+  LevelMats& C = h->L[l - 1];
+  LevelVecs& CV = w.lv[l - 1];
+  const int nu1 = h->opts.nu1, nu2 = h->opts.nu2, ns = nu1 + nu2;
+  auto bufof = [&](LevelVecs& X, T* o, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? o : Prec<T>::t(X); };
+  const double om = h->opts.omega;
+  T* cur = nullptr;
+  for (int k = 0; k < nu1; ++k) {                                // Step 1
+    T* dst = bufof(V, out, k);
+    if (!(k == 0 && first_done)) {
+      launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
+      h->launch_count++;
+    }
+    cur = dst;
+  }
+  launch_residual<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::r(V), done, s);   // Step 2
+  const bool fuse = l - 1 > 0;
+  T* cfirst = fuse ? bufof(CV, Prec<T>::o(CV), 0) : nullptr;
+  launch_restrict<T>(L.R.t, nc, Prec<T>::r(V), Prec<T>::b(CV), Prec<T>::S(C), cfirst, om, done, s);
+  h->launch_count += 2;
+  enqueue_vcycle<T>(h, w, l - 1, Prec<T>::b(CV), Prec<T>::o(CV), done, s, fuse);   // Step 3
+  T* pdst = nu2 == 0 ? out : cur;                                                   // Step 4
+  launch_prolong_add<T>(L.P.t, nc, Prec<T>::o(CV), cur, pdst, done, s);
+  cur = pdst;
+  h->launch_count++;
+  for (int k = nu1; k < ns; ++k) {                               // Step 5
+    T* dst = bufof(V, out, k);
+    launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, false, done, s);
+    cur = dst;
+    h->launch_count++;
+  }
+}
+template void enqueue_vcycle<double>(mg_hier*, Workspace&, int, const double*, double*, const int*, cudaStream_t,
+                                     bool);
+template void enqueue_vcycle<float>(mg_hier*, Workspace&, int, const float*, float*, const int*, cudaStream_t, bool);
+
+// ---------------------------------------------------------------- Krylov
+enum { M_CG = 1, M_BICG = 2, M_GMRES = 3 };
+
+int method_of(const mg_hier* h) {
+  int k = h->opts.krylov;
+  if (k == MG_KRYLOV_AUTO) k = (h->prob.kind == MG_TRANSPORT) ? MG_BICGSTAB : MG_CG;
+  return k == MG_BICGSTAB ? M_BICG : (k == MG_GMRES ? M_GMRES : M_CG);
+}
+
+int check_prec(const mg_hier* h, int prec) {
+  if (prec == MG_FP64 && !h->has_fp64) return fail(MG_ERR_INVALID, "hierarchy built without FP64 level matrices");
+  if (prec == MG_MIXED_FP32 && !h->has_fp32) return fail(MG_ERR_INVALID, "hierarchy built without FP32 level matrices");
+  if (prec != MG_FP64 && prec != MG_MIXED_FP32) return fail(MG_ERR_INVALID, "unsupported precision");
+  return MG_OK;
+}
+
+namespace {
+
+// One Krylov iteration (the body of the graph's while node).  The last kernel
+// of the iteration runs the convergence test and sets the while condition.
+void enqueue_iteration(mg_hier* h, Workspace& w, int method, int prec, unsigned long long cond, cudaStream_t s) {
+  const int nc = h->nc;
+  const int fine = h->nlev - 1;
+  const int64_t n = h->n_dofs;
+  const SellView& A = h->L[fine].A64.v;
+  const int* done = &w.st->done;
+  const bool mixed = prec != MG_FP64;
+  if (cond) {
+    launch_cond_reset(cond, s);
+    h->launch_count++;
+  }
+  if (method == M_CG) {
+    PVec z;
+    if (mixed) {
+      launch_to_f32(n, w.r, w.r32, w.st, s);
+      enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s);
+      z.f = w.ph32;
+      h->launch_count++;
+    } else {
+      enqueue_vcycle<double>(h, w, fine, w.r, w.z, done, s);
+      z.d = w.z;
+    }
+    launch_cg_dots(n, z, w.r, w.q, w.part, w.st, s);
+    launch_cg_update_p(n, z, w.p, w.st, s);
+    PVec pp;
+    pp.d = w.p;
+    launch_spmv_dot(A, nc, pp, nullptr, w.q, w.part, Q_PQ, w.st, s);
+    launch_cg_update_xr(n, w.p, w.q, w.xi, w.r, w.part, w.st, cond, s);
+    h->launch_count += 4;
+  } else if (method == M_GMRES) {
+    // one Arnoldi step of flexible GMRES(m); cycle end and restart are gated
+    // on the device (gm_end / gm_j).  The view carries only the preconditioned
+    // vectors of the active precision.
+    GmresView gm = w.gm;
+    if (mixed) gm.Z64 = nullptr;
+    else gm.Z32 = nullptr;
+    PVec z;
+    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s); z.f = w.ph32; }
+    else { enqueue_vcycle<double>(h, w, fine, w.vcur, w.z, done, s); z.d = w.z; }
+    launch_gm_spmv(A, nc, z, w.q, gm, w.st, s);
+    launch_gm_orth(n, w.q, gm, w.st, 0, w.part, s);
+    launch_gm_orth(n, w.q, gm, w.st, 1, w.part, s);
+    launch_gm_givens(gm, w.st, s);
+    launch_gm_next(n, w.q, mixed ? w.r32 : nullptr, mixed ? nullptr : w.vcur, gm, w.st, s);
+    launch_gm_update_x(n, w.xi, gm, w.st, s);
+    launch_gm_residual(A, nc, w.xi, w.bi, w.r, w.part, w.st, cond, s);
+    launch_gm_start(n, w.r, mixed ? w.r32 : nullptr, mixed ? nullptr : w.vcur, gm, w.st, s);
+    h->launch_count += 1 + 3 * 2 + 1 + 2 + 1 + 1 + 1;
+  } else {
+    // in mixed mode bicg_p / bicg_s also write the FP32 preconditioner input
+    launch_bicg_p(n, w.r, w.t /* v */, w.p, mixed ? w.r32 : nullptr, w.st, s);
+    PVec ph;
+    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s); ph.f = w.ph32; }
+    else { enqueue_vcycle<double>(h, w, fine, w.p, w.ph, done, s); ph.d = w.ph; }
+    launch_spmv_dot(A, nc, ph, w.rhat, w.t /* v */, w.part, Q_RHV, w.st, s);
+    launch_bicg_s(n, w.r, w.t, w.sv, mixed ? w.r32 : nullptr, w.st, s);
+    PVec sh;
+    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.sh32, done, s); sh.f = w.sh32; }
+    else { enqueue_vcycle<double>(h, w, fine, w.sv, w.shat, done, s); sh.d = w.shat; }
+    launch_spmv_2dots(A, nc, sh, w.sv, w.q /* t */, w.part, w.st, s);
+    launch_bicg_x(n, ph, sh, w.sv, w.q, w.rhat, w.xi, w.r, w.part, w.st, cond, s);
+    h->launch_count += 5;
+  }
+}
+
+int build_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph* out) {
+  cudaStream_t cs;
+  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  CU(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle handle;
+  CU(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = handle;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CU(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = h->launch_count;
+  enqueue_iteration(h, w, method, prec, (unsigned long long)handle, cs);
+  out->launches_per_iter = h->launch_count - before;
+  h->launch_count = before;
+  cudaGraph_t captured;
+  cudaError_t e = cudaStreamEndCapture(cs, &captured);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return fail(MG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&out->exec, g, 0);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  out->method = method;
+  out->prec = prec;
+  return MG_OK;
+}
+
+int get_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph** g) {
+  for (auto& x : w.graphs)
+    if (x.method == method && x.prec == prec) { *g = &x; return MG_OK; }
+  SolveGraph ng;
+  int rc = build_graph(h, w, method, prec, &ng);
+  if (rc) return rc;
+  w.graphs.push_back(ng);
+  *g = &w.graphs.back();
+  return MG_OK;
+}
+
+// One round: residual of the current iterate, the device loop (graph or
+// direct launches), the true residual, outputs and the state mirror.
+int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
+  const int nc = h->nc;
+  const int fine = h->nlev - 1;
+  const SellView& A = h->L[fine].A64.v;
+  const int method = w.method, prec = w.prec;
+  SolveGraph* g = nullptr;
+  if (h->opts.launch_mode != 1) {
+    int rc = get_graph(h, w, method, prec, &g);
+    if (rc) return rc;
+  }
+  launch_residual_norm(A, nc, w.xi, w.bi, w.r, w.part, w.st, 1, s);
+  w.launches += 1;
+  if (method == M_GMRES) {
+    GmresView gm = w.gm;
+    launch_gm_start(h->n_dofs, w.r, prec != MG_FP64 ? w.r32 : nullptr, prec != MG_FP64 ? nullptr : w.vcur, gm,
+                    w.st, s);
+    w.launches += 1;
+  } else if (method == M_BICG) {
+    // rhat = r0, (rhat, r) = (r, r)
+    CU(cudaMemcpyAsync(w.rhat, w.r, h->n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(&w.st->red[Q_RHR], &w.st->red[Q_RR], sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemsetAsync(w.t, 0, h->n_dofs * sizeof(double), s));
+  } else {
+    CU(cudaMemsetAsync(w.q, 0, h->n_dofs * sizeof(double), s));
+  }
+  if (h->opts.launch_mode == 1) {
+    // direct launches (profilers): one iteration at a time, status polled
+    const int64_t before = h->launch_count;
+    for (int it = 0; it < w.max_it + 1; ++it) {
+      CU(cudaMemcpyAsync(w.st_host, w.st, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (w.st_host->done) break;
+      enqueue_iteration(h, w, method, prec, 0ull, s);
+    }
+    w.launches += h->launch_count - before;
+    h->launch_count = before;
+  } else {
+    CU(cudaGraphLaunch(g->exec, s));
+  }
+  // true residual of the final iterate, solution with hanging values, state
+  launch_residual_norm(A, nc, w.xi, w.bi, w.r, w.part, w.st, 0, s);
+  launch_copy_fixed(h->n_nodes, nc, h->fixmask, w.bi, w.xi, w.p, s);     // p <- x (hanging/Dirichlet from b)
+  launch_fill_hanging(h->Hc.t, nc, w.p, s);
+  w.launches += 3;
+  CU(cudaMemcpyAsync(w.x_out, w.p, h->n_dofs * 8, w.x_out_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     s));
+  CU(cudaMemcpyAsync(w.st_host, w.st, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+  CU(cudaEventRecord(w.ev1, s));
+  return MG_OK;
+}
+
+}  // namespace
+
+int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const double* x0, bool x0_host,
+                double* x_out, bool x_out_host, double rtol, int max_it, int prec, cudaStream_t s) {
+  const int64_t n = h->n_dofs;
+  w.method = method_of(h);
+  w.prec = prec;
+  w.rtol = rtol;
+  w.max_it = max_it;
+  w.rounds = 0;
+  w.iter_base = 0;
+  w.launches = 0;
+  w.x_out = x_out;
+  w.x_out_host = x_out_host;
+  if (w.method == M_GMRES && !w.gm.V) return fail(MG_ERR_INVALID, "hierarchy set up without GMRES workspace");
+  CU(cudaEventRecord(w.ev0, s));
+  CU(cudaMemsetAsync(&w.st->counter, 0, sizeof(unsigned int), s));   // reduction arrival counter
+  CU(cudaMemcpyAsync(w.bi, b, n * 8, b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(w.p, x0, n * 8, x0_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  launch_copy_fixed(h->n_nodes, h->nc, h->fixmask, w.bi, w.p, w.xi, s);
+  launch_norm_init(h->n_nodes, h->nc, h->fixmask, w.bi, w.part, w.st, rtol, max_it, s);
+  w.launches += 2;
+  return enqueue_round(h, w, s);
+}
+
+int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats) {
+  const KrylovState& S = *w.st_host;
+  const double rel = std::sqrt(S.red[Q_RR]) / S.bnorm;
+  SolveGraph* g = nullptr;
+  for (auto& x : w.graphs)
+    if (x.method == w.method && x.prec == w.prec) g = &x;
+  int status;
+  if (S.status == -6) status = MG_ERR_NAN;
+  else if (S.status == -5) status = MG_ERR_BREAKDOWN;
+  else if (rel <= w.rtol) status = MG_OK;
+  else if (S.iter >= w.max_it || w.rounds >= 3) status = MG_ERR_NOT_CONVERGED;
+  else status = MG_PENDING;
+  const int iters_round = S.iter - w.iter_base;
+  if (status == MG_PENDING) {
+    // the recursive residual converged but the true one did not: restart
+    // from the true residual, keeping the iteration count
+    KrylovState fix = S;
+    fix.done = 0;
+    fix.status = 0;
+    fix.restart_pos = fix.iter;
+    fix.gm_j = 0;
+    fix.gm_end = 0;
+    *w.st_host = fix;
+    CU(cudaMemcpyAsync(w.st, w.st_host, sizeof(KrylovState), cudaMemcpyHostToDevice, s));
+    // reset hanging / Dirichlet entries of the iterate
+    launch_copy_fixed(h->n_nodes, h->nc, h->fixmask, w.bi, w.xi, w.xi, s);
+    w.launches += 1;
+    w.rounds += 1;
+    w.iter_base = S.iter;
+    if (g) w.launches += (int64_t)iters_round * g->launches_per_iter;
+    int rc = enqueue_round(h, w, s);
+    return rc ? rc : MG_PENDING;
+  }
+  if (g) w.launches += (int64_t)iters_round * g->launches_per_iter;
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, w.ev0, w.ev1);
+  if (stats) {
+    stats->status = status;
+    stats->iters = S.iter;
+    stats->vcycles = S.iter * (w.method == M_BICG ? 2 : 1);
+    stats->precision = w.prec;
+    stats->rel_res = rel;
+    stats->solve_ms = ms;
+    stats->launches = w.launches;
+  }
+  h->launch_count += w.launches;
+  return status;
+}
+
+}  // namespace mgi

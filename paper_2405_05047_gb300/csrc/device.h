@@ -1,0 +1,165 @@
+// Device-side hierarchy, solve workspaces and the asynchronous solve driver.
+#pragma once
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace mgi {
+
+struct Alloc {
+  void* p = nullptr;
+  size_t bytes = 0;
+  bool cuda = false;          // allocated with cudaMalloc (not the context allocator)
+};
+
+struct SellBuf {
+  SellView v;
+  TransferView t;
+  int64_t nnz_real = 0;
+  int64_t slots = 0;
+};
+
+// Read-only matrices of one level.
+struct LevelMats {
+  int64_t n = 0;              // nodes
+  SellBuf A64, A32, P, R;
+  double* S64 = nullptr;
+  float* S32 = nullptr;
+};
+
+// V-cycle vectors of one level in one workspace: rhs, out, ping-pong, residual.
+struct LevelVecs {
+  double *b64 = nullptr, *o64 = nullptr, *t64 = nullptr, *r64 = nullptr;
+  float *b32 = nullptr, *o32 = nullptr, *t32 = nullptr, *r32 = nullptr;
+};
+
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  int method = 0, prec = 0;
+  int64_t launches_per_iter = 0;
+};
+
+// Everything one solve writes: a hierarchy can run as many solves at once as
+// it has workspaces.
+struct Workspace {
+  std::vector<LevelVecs> lv;
+  double *xi = nullptr, *bi = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *rhat = nullptr,
+         *sv = nullptr, *t = nullptr, *ph = nullptr, *shat = nullptr, *vcur = nullptr;
+  float *r32 = nullptr, *ph32 = nullptr, *sh32 = nullptr;
+  Partials part;
+  KrylovState* st = nullptr;
+  KrylovState* st_host = nullptr;   // pinned mirror, written at the end of every round
+  GmresView gm;
+  TailParams tail64, tail32;
+  std::vector<SolveGraph> graphs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<Alloc> allocs;
+  size_t bytes = 0;
+  // the solve in flight
+  int method = 0, prec = 0, rounds = 0, max_it = 0, iter_base = 0;
+  double rtol = 0.0;
+  int64_t launches = 0;
+  double* x_out = nullptr;
+  bool x_out_host = false;
+};
+
+int fail(int code, const std::string& msg);
+const char* last_error();
+
+}  // namespace mgi
+
+struct ServeRequest;
+
+struct mg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  mg_allocator alloc{};
+  bool has_alloc = false;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};          // every device byte allocated through this context
+  std::atomic<size_t> resident{0};      // hierarchies and their default workspaces
+  std::atomic<int> live_hiers{0};       // hierarchies not yet freed
+  // serving
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+  bool worker_started = false;
+  uint64_t next_ticket = 1;
+  int max_slots = 16;
+  std::deque<std::shared_ptr<ServeRequest>> queue;
+  std::vector<std::shared_ptr<ServeRequest>> running;
+  std::map<uint64_t, std::shared_ptr<ServeRequest>> tickets;
+  std::vector<cudaStream_t> free_streams;
+};
+
+struct mg_hier {
+  mg_ctx* ctx = nullptr;
+  int dim = 2, nc = 1, nlev = 0;
+  int64_t n_nodes = 0, n_dofs = 0, n_free = 0, n_hanging = 0;
+  mg_problem prob{};
+  mg_opts opts{};
+  std::vector<double> coords;            // finest nodes, external order
+  std::vector<int64_t> level_nodes, level_nnzb, level_real_nnzb;
+  std::vector<mgi::Alloc> allocs;        // matrices
+  size_t bytes = 0;
+  std::vector<mgi::LevelMats> L;         // [0] coarsest
+  double* coarse_inv = nullptr;          // (n0 nc)^2
+  int64_t coarse_n = 0;
+  mgi::SellBuf F;                        // load matrix (finest)
+  mgi::SellBuf Hc;                       // hanging rows of H (finest)
+  uint8_t* fixmask = nullptr;            // finest, per node
+  bool has_fp64 = true, has_fp32 = true;
+  int tail_top = 0;                      // levels 0..tail_top run in the single-CTA tail kernel
+  int gmres_m = 0;                       // > 0: workspaces carry GMRES(m) arrays
+  mgi::Workspace* ws0 = nullptr;         // default workspace (mg_solve, mg_vcycle, mg_apply)
+  std::mutex solve_mu;                   // guards ws0
+  std::mutex pool_mu;
+  std::vector<mgi::Workspace*> pool;     // idle serving workspaces
+  std::vector<mgi::Workspace*> all_ws;   // every serving workspace
+  size_t ws_bytes = 0;                   // device bytes of one workspace
+  std::atomic<int64_t> launch_count{0};  // kernels enqueued (host-side count)
+};
+
+namespace mgi {
+
+int method_of(const mg_hier* h);
+int check_prec(const mg_hier* h, int prec);
+size_t workspace_bytes(const mg_hier* h);
+// New workspace; its buffers are initialised in stream order on `s`, the
+// stream its solves will run on.
+int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out);
+void ws_destroy(mg_hier* h, Workspace* ws);
+int upload_hierarchy(mg_hier* h, HostHierarchy& H);
+void free_hierarchy(mg_hier* h);
+
+template <typename T>
+void enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
+                    bool first_done = false);
+
+// Asynchronous solve: solve_start copies the inputs (device or host
+// pointers) into the workspace and enqueues the first round; a round ends
+// with the outputs written to x_out and the state mirrored to st_host, then
+// ev1 recorded.  solve_check (after ev1 completed) either returns the final
+// status or enqueues another round (true residual above rtol) and returns
+// MG_PENDING.
+int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const double* x0, bool x0_host,
+                double* x_out, bool x_out_host, double rtol, int max_it, int prec, cudaStream_t s);
+int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats);
+
+}  // namespace mgi

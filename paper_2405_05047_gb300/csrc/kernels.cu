@@ -497,6 +497,15 @@ __device__ __forceinline__ double pv(const PVec& p, int64_t i, double scale) {
   return p.f ? (double)p.f[i] * scale : p.d[i];
 }
 
+// First kernel of every loop body: the while condition is cleared here, so the
+// loop only continues if the convergence test at the end of the body sets it
+// again (a body that fails to reach its test ends the loop instead of
+// spinning).
+__global__ void k_cond_reset(unsigned long long cond) {
+  pdl_wait();
+  if (threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+}
+
 // Convergence test, thread 0 of the last block.  count: increment iter.
 __device__ void converge_step(KrylovState* st, bool count, unsigned long long cond) {
   if (count) st->iter += 1;
@@ -696,7 +705,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_update_xr(int64_t n, const dou
                                                           unsigned long long cond) {
   __shared__ double sh[40];
   pdl_wait();
-  if (st->done) return;
+  if (st->done) {   // already converged: the device loop must still end here
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
   const double pq = st->red[Q_PQ];
   const double alpha = st->rho / pq;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -840,7 +852,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_bicg_x(int64_t n, PVec ph, PVec s
                                                     KrylovState* st, unsigned long long cond) {
   __shared__ double sh[40];
   pdl_wait();
-  if (st->done) return;
+  if (st->done) {   // already converged: the device loop must still end here
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
   const double ts = st->red[Q_TS], tt = st->red[Q_TT];
   const double om = tt > 0.0 ? ts / tt : 0.0;
   const double alpha = st->alpha;
@@ -1307,6 +1322,8 @@ void launch_bicg_x(int64_t n, PVec ph, PVec sh, const double* sv, const double* 
                    double* r, Partials part, KrylovState* st, unsigned long long cond, cudaStream_t s) {
   launch(k_bicg_x, grid_vec4(n), s, n, ph, sh, sv, t, rhat, x, r, part.p, st, cond);
 }
+
+void launch_cond_reset(unsigned long long cond, cudaStream_t s) { launch(k_cond_reset, 1, s, cond); }
 
 // ---- GMRES launchers
 void launch_gm_start(int64_t n, const double* r, float* v32, double* v64, GmresView G, KrylovState* st,

@@ -125,6 +125,9 @@ struct PVec {
   const float* f = nullptr;
 };
 
+// Clears the CUDA-graph while condition (first kernel of every loop body).
+void launch_cond_reset(unsigned long long cond, cudaStream_t s);
+
 // Quantity slots of the partial arrays and of KrylovState::red
 enum { Q_RR = 0, Q_RZ = 1, Q_QZ = 2, Q_PQ = 3, Q_BB = 4, Q_RHV = 5, Q_SS = 6, Q_TS = 7, Q_TT = 8, Q_RHR = 9, Q_NUM = 10 };
 

@@ -1,0 +1,83 @@
+"""Time one level operator of a hierarchy (a profiling target).
+
+  python -m paper_2405_05047_gb300.opbench --workload td_adaptive --op smooth --prec fp32 --reps 3
+
+Sets up the hierarchy of the named workload, runs the operator `reps` times
+back to back on the finest level (or --level) through mg_time_op and prints
+one JSON line with the mean device time per launch and the algorithmic bytes
+of that launch.  Under a profiler, `-k regex:<kernel> -s <warm-up launches>
+-c <n>` selects the launches to capture.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+from . import binding as B  # noqa: E402
+from . import build as BLD  # noqa: E402
+
+OPS = {"smooth": B.MG_OP_SMOOTH, "matvec": B.MG_OP_MATVEC, "restrict": B.MG_OP_RESTRICT,
+       "prolong": B.MG_OP_PROLONG_ADD}
+
+
+def make(workload):
+    if workload == "td_adaptive":
+        return (W.td_adaptive(rounds=8, gamma=0.18),
+                B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)), {})
+    if workload.startswith("poisson"):
+        n = int(workload[len("poisson"):])
+        return W.uniform_leaves(2, (1, 1), n.bit_length() - 1), B.make_problem(kind=B.MG_POISSON), {}
+    if workload.startswith("elasticity"):
+        n = int(workload[len("elasticity"):])
+        return (W.elasticity3d(n), B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
+                {"omega": 0.5})
+    raise SystemExit(f"unknown workload {workload}")
+
+
+def alg_bytes(info, level, nc, op, vbytes):
+    """Bytes the operator must move once: stored values + 4-byte columns of
+    the level matrix, plus its vectors (x, b, S^-1 and the output for a sweep)."""
+    nnz = info.level_rows_nnzb[level] * nc * nc
+    rows = info.level_nodes[level] * nc
+    if op == "smooth":
+        return nnz * vbytes + info.level_rows_nnzb[level] * 4 + rows * vbytes * 3 + info.level_nodes[level] * nc * nc * vbytes
+    if op == "matvec":
+        return nnz * vbytes + info.level_rows_nnzb[level] * 4 + rows * vbytes * 2
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="td_adaptive")
+    ap.add_argument("--op", default="smooth", choices=sorted(OPS))
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--level", type=int, default=-1)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    BLD.build()
+    import paper_2405_05047_gb300 as G
+    lm, pb, okw = make(args.workload)
+    prec = B.MG_MIXED_FP32 if args.prec == "fp32" else B.MG_FP64
+    okw.update(store_fp64=int(prec == B.MG_FP64), store_fp32=int(prec != B.MG_FP64))
+    ctx = G.Context(0)
+    h = G.Hierarchy(ctx, lm, pb, B.make_opts(**okw))
+    level = args.level if args.level >= 0 else h.levels - 1
+    ms = h.time_op(level, OPS[args.op], prec, reps=args.reps)
+    nb = alg_bytes(h.info, level, h.nc, args.op, 4 if prec != B.MG_FP64 else 8)
+    print(json.dumps({"workload": args.workload, "op": args.op, "prec": args.prec, "level": level,
+                      "rows": int(h.info.level_nodes[level] * h.nc), "ms_per_launch": ms, "alg_bytes": nb,
+                      "achieved_gbs": (nb / (ms * 1e-3) / 1e9) if nb else None}))
+    h.free()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -51,6 +51,7 @@ CASES = {
 def ctx():
     c = G.Context(0)
     yield c
+    _cache.clear()
     c.close()
 
 
