@@ -201,6 +201,26 @@ int mg_vcycle(mg_hier* h, const void* r, void* z, int prec);
 enum { MG_OP_MATVEC = 0, MG_OP_SMOOTH = 1, MG_OP_RESTRICT = 2, MG_OP_PROLONG_ADD = 3, MG_OP_COARSE = 4 };
 int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, void* out, int prec);
 
+/* Allocation-free residual + restriction (no counterpart in the paper: it
+ * exists for callers that must not allocate device memory -- code running
+ * while a CUDA stream is being captured into a graph, where cudaMalloc is not
+ * allowed; processes whose device memory is owned by another allocator or
+ * pool; latency-bound loops that cannot afford an allocation).
+ *   d = R_l (b - A_l x) on level l >= 1, the same result as
+ *   mg_apply(h, l, MG_OP_RESTRICT, x, b, d, prec).
+ * x, b: device vectors of level l (n_l * nc entries); d: device vector of level
+ * l-1; double for MG_FP64, float for MG_MIXED_FP32.  The residual is kept in a
+ * fixed device array of 2^20 doubles (8 MiB) compiled into the library, so
+ * the level may have at most 2^20 dofs in FP64 and 2^21 in FP32; larger levels
+ * are refused with MG_ERR_INVALID before anything runs.  Every device that
+ * loads the library holds that array until the process exits.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents; calls that overlap on the GPU (other
+ * threads, other contexts) race on it.  Runs on the context's stream and
+ * returns after the work has finished; calls no allocator of any kind. */
+int mg_restrict_static(mg_hier* h, int level, const void* x, const void* b, void* d, int prec);
+
 /* Device time of one level operator: launches op (as mg_apply, on the
  * library's own level buffers, FP64 or FP32 per prec) `reps` times back to
  * back on the context's stream between two CUDA events and returns the mean

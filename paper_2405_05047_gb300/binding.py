@@ -108,6 +108,7 @@ _SIGS = {
     "mg_launch_count": (C.c_int64, [C.c_void_p]),
     "mg_time_op": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mg_serve_config": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_restrict_static": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
 }
 
 
@@ -305,6 +306,11 @@ def mg_poll(ctx, ticket):
 
 def mg_cancel(ctx, ticket):
     return load_library().mg_cancel(ctx, ticket)
+
+
+def mg_restrict_static(h, level, x, b, d, prec=MG_FP64):
+    """d = R_l (b - A_l x) without any device allocation (static scratch)."""
+    return _check(load_library().mg_restrict_static(h, level, _ptr(x), _ptr(b), _ptr(d), prec))
 
 
 def mg_serve_config(ctx, max_slots):
