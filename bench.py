@@ -450,9 +450,8 @@ def main():
     # roofline of the dominant kernel: the fused FP32 smoother sweep on the
     # finest level, cold L2 (flushed before every launch)
     fine = h.levels - 1
-    nnz = info.level_rows_nnzb[fine] * h.nc * h.nc
-    n_rows = h.n_dofs
-    alg_bytes = nnz * (4 + 4) + n_rows * (4 + 4 + 4 + 4)
+    from paper_2405_05047_gb300 import opbench
+    alg_bytes = opbench.alg_bytes(info, fine, h.nc, "smooth", 4)
     ker_ms = []
     for _ in range(10):
         flush_l2(flush)
@@ -500,7 +499,7 @@ def main():
         "gpu_launches": int(sum(s.launches for s in st_mixed)),
         "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": int(2 * 8 * h.n_dofs),
                 "d2h_bytes_per_step": int(8 * h.n_dofs), "ms_per_step": statistics.mean(e2e_ms)},
-        "roofline": {"bound": "hbm", "kernel": "k_smooth<float,1> finest level (fused residual + Jacobi sweep)",
+        "roofline": {"bound": "hbm", "kernel": f"k_smooth<float,{h.nc}> finest level (fused residual + (block-)Jacobi sweep)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": int(alg_bytes), "ms_per_launch": ker_ms_avg,
                      "ms_per_launch_l2_warm": hot_ms,
