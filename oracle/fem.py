@@ -9,7 +9,8 @@ block.  Sec. 2.2: assembled residuals and right-hand sides are multiplied by
 H^T, the solution by H.
 
 Quadrature: tensor 2-point Gauss, exact for every bilinear form below on
-axis-parallel boxes (the integrands are polynomials of degree <= 2 per axis).
+axis-parallel boxes (the integrands are polynomials of degree <= 3 per axis;
+degree 3 only for the Oseen convection term with its cell-wise bilinear beta).
 
 Bilinear forms (row = test function, column = trial function):
   Poisson            (grad u, grad v)
@@ -17,7 +18,7 @@ Bilinear forms (row = test function, column = trial function):
                      + sum_T delta_T (beta.grad u, beta.grad v)_T      (SUPG)
   elasticity (3D)    2 mu (eps(u), eps(v)) + lambda (div u, div v)     (Sec. 5.2)
                      written with the Voigt strain-displacement matrix B.
-  Oseen (2D, u,v,p)  see ``oseen_element``.
+  Oseen (2D, u,v,p)  see ``oseen_patch_matrices`` (assembled per patch).
 """
 from __future__ import annotations
 
@@ -114,6 +115,93 @@ def supg_delta(h, eps, beta, delta0=0.5):
     return delta0 * hT * hT / (6.0 * eps + float(np.linalg.norm(beta)) * hT)
 
 
+def lps_interpolation(dim=2):
+    """Pi (3^d x 3^d): values at the 3^d patch lattice points of the coarse Q1
+    interpolant i_2h built from the patch's 2^d corner values (corners
+    weight 1, edge midpoints 1/2 each, centre 1/4 each)."""
+    n = 3 ** dim
+    Pi = np.zeros((n, n))
+    for i in range(n):
+        loc = [(i // 3 ** d) % 3 for d in range(dim)]
+        for c in range(1 << dim):
+            w = 1.0
+            j = 0
+            for d in range(dim):
+                b = (c >> d) & 1
+                w *= (loc[d] / 2.0) if b else (1.0 - loc[d] / 2.0)
+                j += (2 * b) * 3 ** d
+            Pi[i, j] += w
+    return Pi
+
+
+def oseen_patch_matrices(h, beta9, nu, dt, alpha0):
+    """Patch matrices (n_p, 27, 27) of the 2D Oseen system with local
+    projection stabilisation, node-major (row 3a+i, i = u, v, p):
+
+      (1/dt)(u, v) + nu (grad u, grad v) + ((beta_h . grad) u, v)
+      - (p, div v) + (div u, q)
+      + alpha_P (grad kappa p, grad kappa q)_P
+      + alpha_P (beta_P . grad kappa u, beta_P . grad kappa v)_P   (u, v comps)
+
+    over a patch P of four child cells with edge lengths h.  beta_h is the
+    cell-wise Q1 interpolant of the nodal field beta9 (n_p, 9, 2); beta_P its
+    value at the patch centre; kappa = id - i_2h (fluctuation with respect to
+    the patch's coarse Q1 interpolant); alpha_P = alpha0 h_P^2 / (nu +
+    |beta_P| h_P) with h_P the patch diameter.  Two-point Gauss rules are
+    exact for every integrand (degree <= 3 per axis)."""
+    h = np.asarray(h, dtype=np.float64)
+    beta9 = np.asarray(beta9, dtype=np.float64)
+    n_p = beta9.shape[0]
+    vol = float(np.prod(h))
+    pts, wts = quadrature(2)
+    K = np.zeros((n_p, 27, 27))
+    G9 = np.zeros((9, 9))                       # patch stiffness (grad, grad)
+    Gij = np.zeros((2, 2, 9, 9))                # int d_i phi_A d_j phi_B over the patch
+    for cy in range(2):
+        for cx in range(2):
+            loc = np.array([(cx + (c & 1)) + 3 * (cy + (c >> 1)) for c in range(4)])
+            bc = beta9[:, loc, :]                                  # (n_p, 4, 2)
+            for xi, w in zip(pts, wts):
+                phi, dref = q1_basis(2, xi)
+                g = dref / h[None, :]
+                wv = w * vol
+                bq = np.einsum("c,pcd->pd", phi, bc)               # beta_h at the point
+                conv = wv * np.einsum("a,pb->pab", phi, bq @ g.T)  # (beta.grad phi_B) phi_A
+                mass = wv * np.outer(phi, phi) / dt
+                diff = wv * nu * (g @ g.T)
+                for i in range(2):
+                    K[:, 3 * loc[:, None] + i, 3 * loc[None, :] + i] += mass + diff + conv
+                    # -(p, div v): row velocity comp i (test phi_A), column p (phi_B)
+                    K[:, 3 * loc[:, None] + i, 3 * loc[None, :] + 2] -= wv * np.outer(g[:, i], phi)
+                    # (div u, q): row p (test phi_A), column velocity comp i
+                    K[:, 3 * loc[:, None] + 2, 3 * loc[None, :] + i] += wv * np.outer(phi, g[:, i])
+                G9[np.ix_(loc, loc)] += wv * (g @ g.T)
+                for i in range(2):
+                    for j in range(2):
+                        Gij[i, j][np.ix_(loc, loc)] += wv * np.outer(g[:, i], g[:, j])
+    kap = np.eye(9) - lps_interpolation(2)
+    bP = beta9[:, 4, :]                                            # patch centre
+    hP = 2.0 * float(np.linalg.norm(h))
+    alpha = alpha0 * hP * hP / (nu + np.linalg.norm(bP, axis=1) * hP)
+    Sp = kap.T @ G9 @ kap
+    Cb = np.einsum("pi,pj,ijab->pab", bP, bP, Gij)
+    Sc = np.einsum("ka,pkl,lb->pab", kap, Cb, kap)
+    K[:, 2::3, 2::3] += alpha[:, None, None] * Sp[None, :, :]
+    for i in range(2):
+        K[:, i::3, i::3] += alpha[:, None, None] * Sc
+    return K
+
+
+def assemble_patches(mesh, patch_nodes, Kp, nc):
+    """Sum patch matrices Kp (n_p, (3^d nc)^2) over the patches' nodes."""
+    m = patch_nodes.shape[1] * nc
+    dofs = (patch_nodes[:, :, None] * nc + np.arange(nc)[None, None, :]).reshape(-1, m)
+    rows = np.repeat(dofs, m, axis=1).ravel()
+    cols = np.tile(dofs, (1, m)).ravel()
+    n = mesh.n_nodes * nc
+    return sp.coo_matrix((Kp.reshape(-1), (rows, cols)), shape=(n, n)).tocsr()
+
+
 def assemble(mesh, element_of_size, nc=1):
     """Sum element matrices into a global (n_nodes*nc)^2 CSR matrix.
     element_of_size(h) returns the (2^d nc)^2 element matrix for a cell with
@@ -161,9 +249,15 @@ def condense(A, H, hang, dirichlet):
     return Ac
 
 
-def condense_rhs(b_all, H, hang, dirichlet, g=None):
-    """b_c = H^T b (Sec. 2.2), zero on hanging rows, g on Dirichlet rows."""
+def condense_rhs(b_all, H, hang, dirichlet, g=None, A_raw=None):
+    """b_c = H^T b (Sec. 2.2), zero on hanging rows, g on Dirichlet rows.
+    With Dirichlet data g (a dof vector; only its Dirichlet entries are used)
+    the free rows are lifted: b_c -= (H^T A H)[:, D] g_D (symmetric
+    elimination of the prescribed values)."""
     b = H.T @ b_all
+    if g is not None:
+        gd = np.where(dirichlet, np.asarray(g, dtype=np.float64), 0.0)
+        b = b - H.T @ (A_raw @ (H @ gd))
     b[hang] = 0.0
-    b[dirichlet] = 0.0 if g is None else g[dirichlet]
+    b[dirichlet] = 0.0 if g is None else np.asarray(g, dtype=np.float64)[dirichlet]
     return b

@@ -205,19 +205,25 @@ def _violations(dim, macro, level, anchor):
     return np.unique(np.concatenate(bad)) if bad else np.zeros(0, dtype=np.int64)
 
 
-def coarsen_once(dim, macro, level, anchor, min_level):
+def coarsen_once(dim, macro, level, anchor, min_level, patch=False):
     """One global coarsening step.  Returns (level, anchor) of the coarser
-    leaf set, or None if nothing can be taken back."""
+    leaf set, or None if nothing can be taken back.
+
+    patch=False: the unit taken back is a family of 2^d sibling leaves.
+    patch=True (patch meshes, where every leaf belongs to a complete family):
+    the unit is the 4^d grandchildren of one cell, all leaves, which become
+    that cell's 2^d children, so the coarser mesh is a patch mesh again."""
     macro = np.asarray(macro, dtype=np.int64)
     level = np.asarray(level, dtype=np.int64)
     anchor = np.asarray(anchor, dtype=np.int64)
-    cand = level > min_level
-    pk = np.full(level.shape[0], -1, dtype=np.int64)
-    pk[cand] = _cell_keys(dim, level[cand] - 1, anchor[cand] >> 1)
-    uniq, counts = np.unique(pk[cand], return_counts=True)
-    families = set(uniq[counts == (1 << dim)].tolist())
+    up = 2 if patch else 1
+    cand = (level > min_level) & (level >= up)
+    uk = np.full(level.shape[0], -1, dtype=np.int64)          # key of the unit's root cell
+    uk[cand] = _cell_keys(dim, level[cand] - up, anchor[cand] >> up)
+    uniq, counts = np.unique(uk[cand], return_counts=True)
+    units = set(uniq[counts == (1 << (dim * up))].tolist())
     while True:
-        take = np.array([k in families for k in pk.tolist()], dtype=bool)
+        take = np.array([k in units for k in uk.tolist()], dtype=bool)
         if not take.any():
             return None
         keep_l, keep_a = level[~take], anchor[~take]
@@ -226,22 +232,58 @@ def coarsen_once(dim, macro, level, anchor, min_level):
         pkeys, first = np.unique(_cell_keys(dim, par_l, par_a), return_index=True)
         new_l = np.concatenate([keep_l, par_l[first]])
         new_a = np.concatenate([keep_a, par_a[first]])
-        bad = set(_violations(dim, macro, new_l, new_a).tolist())
-        revert = families & bad
+        bad = _violations(dim, macro, new_l, new_a)
+        # a too-coarse new leaf reverts the unit it came from
+        bad_units = set()
+        if bad.size:
+            nk = _cell_keys(dim, par_l[first], par_a[first])
+            hit = np.isin(nk, bad)
+            if hit.any():
+                root = _cell_keys(dim, par_l[first][hit] - (up - 1), par_a[first][hit] >> (up - 1))
+                bad_units = set(root.tolist())
+        revert = units & bad_units
         if not revert:
             return new_l, new_a
-        families -= revert
+        units -= revert
 
 
-def hierarchy(dim, macro, level, anchor, min_level, max_levels=0):
+def hierarchy(dim, macro, level, anchor, min_level, max_levels=0, patch=False):
     """Leaf sets from finest (index 0) to coarsest."""
     out = [(np.asarray(level, dtype=np.int64), np.asarray(anchor, dtype=np.int64))]
     while max_levels <= 0 or len(out) < max_levels:
-        nxt = coarsen_once(dim, macro, out[-1][0], out[-1][1], min_level)
+        nxt = coarsen_once(dim, macro, out[-1][0], out[-1][1], min_level, patch)
         if nxt is None:
             break
         out.append(nxt)
     return out
+
+
+def patches(mesh):
+    """Patches of a patch mesh: the parents of the sibling families.  Returns
+    (nodes (n_p, 3^d) in lexicographic order of the patch's 3^d lattice
+    points, x fastest; level of the children (n_p,)).  Raises if a leaf is
+    not part of a complete family."""
+    dim = mesh.dim
+    if np.any(mesh.level < 1):
+        raise ValueError("patch mesh: a leaf on level 0 has no family")
+    pk = _cell_keys(dim, mesh.level - 1, mesh.anchor >> 1)
+    uniq, inv, counts = np.unique(pk, return_inverse=True, return_counts=True)
+    if np.any(counts != (1 << dim)):
+        raise ValueError("not a patch mesh: incomplete sibling family")
+    n_p = uniq.size
+    nodes = np.full((n_p, 3 ** dim), -1, dtype=np.int64)
+    lev = np.zeros(n_p, dtype=np.int64)
+    off = mesh.corners_offsets()
+    child = mesh.anchor & 1                                   # position of each leaf in its family
+    for c in range(1 << dim):
+        loc = child + off[c][None, :]                         # patch lattice point, entries in {0,1,2}
+        li = np.zeros(mesh.level.shape[0], dtype=np.int64)
+        for d in reversed(range(dim)):
+            li = li * 3 + loc[:, d]
+        nodes[inv, li] = mesh.cell_nodes[:, c]
+    lev[inv] = mesh.level
+    assert np.all(nodes >= 0)
+    return nodes, lev
 
 
 def default_min_level(macro):

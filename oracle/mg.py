@@ -67,10 +67,13 @@ def embedding(fine: M.Q1Mesh, coarse: M.Q1Mesh):
 
 
 class Level:
-    def __init__(self, leaf_level, leaf_anchor, leafmesh, prob, lattice_level=None):
+    def __init__(self, leaf_level, leaf_anchor, leafmesh, prob, lattice_level=None, fine_mesh=None):
         self.mesh = M.Q1Mesh(leafmesh.dim, leafmesh.origin, leafmesh.extent, leafmesh.macro,
                              leaf_level, leaf_anchor, lattice_level)
-        self.sys = PB.build_system(self.mesh, prob, with_load=False)
+        beta = None
+        if prob.kind == PB.OSEEN:      # nodal convection field, injected from the finest mesh
+            beta = PB.inject(fine_mesh, prob.conv, self.mesh) if fine_mesh is not None else prob.conv
+        self.sys = PB.build_system(self.mesh, prob, with_load=False, beta=beta)
         self.A = self.sys.A
         self.nc = prob.nc
         self.P = None          # prolongation from the next coarser level
@@ -95,11 +98,16 @@ class Hierarchy:
     """Levels 0 (coarsest) .. L (finest) of the global coarsening."""
 
     def __init__(self, leafmesh, prob, min_level=None, max_levels=0, omega=0.8, nu1=2, nu2=2):
+        patch = prob.kind == PB.OSEEN   # LPS patches: keep every level a patch mesh
         if min_level is None:
-            min_level = M.default_min_level(leafmesh.macro)
+            min_level = max(M.default_min_level(leafmesh.macro), 1 if patch else 0)
         sets = M.hierarchy(leafmesh.dim, leafmesh.macro, leafmesh.level, leafmesh.anchor,
-                           min_level, max_levels)[::-1]
-        self.levels = [Level(l, a, leafmesh, prob) for (l, a) in sets]
+                           min_level, max_levels, patch)[::-1]
+        fine_mesh = None
+        if patch:
+            fine_mesh = M.Q1Mesh(leafmesh.dim, leafmesh.origin, leafmesh.extent, leafmesh.macro,
+                                 sets[-1][0], sets[-1][1])
+        self.levels = [Level(l, a, leafmesh, prob, fine_mesh=fine_mesh) for (l, a) in sets]
         self.prob = prob
         self.omega, self.nu1, self.nu2 = omega, nu1, nu2
         nc = prob.nc

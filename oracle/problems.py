@@ -6,9 +6,14 @@ Poisson (-Laplace u = f) and transport-diffusion (-eps Laplace u + beta.grad u
 = f) are the scalar problems; the paper's transport-diffusion example is
 Sec. 5.1 (there with a time derivative and without stabilisation).  Linear
 elasticity, -div sigma(u) = f with sigma = lambda tr(eps(u)) I + 2 mu eps(u),
-is Sec. 5.2 (here the static operator).  Right-hand side: b = H^T (M I_h f)
-with the consistent mass matrix M and the nodal interpolant I_h f, plus the
-SUPG load term for transport-diffusion; Dirichlet data are homogeneous.
+is Sec. 5.2 (here the static operator).  The Oseen system (one linearised
+backward-Euler step of the incompressible Navier-Stokes equations, equal-order
+Q1 velocity and pressure with local projection stabilisation, the form in
+``fem.oseen_patch_matrices``) is the saddle-point problem of Sec. 5.3's flow
+example.  Right-hand side: b = H^T (M I_h f) with the consistent mass matrix M
+and the nodal interpolant I_h f, plus the SUPG load term for
+transport-diffusion; Dirichlet data g are eliminated symmetrically (lifted
+into the free rows).
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import fem
+from . import mesh as M
 
 POISSON, TRANSPORT, ELASTICITY, OSEEN = "poisson", "transport", "elasticity", "oseen"
 
@@ -31,6 +37,10 @@ class Problem:
     lam: float = 1.0
     supg_delta0: float = 0.5
     dirichlet: tuple = (0xFF,)          # face mask per component
+    nu: float = 1e-3                    # Oseen: viscosity
+    dt: float = 0.01                    # Oseen: time step of the mass term
+    lps_alpha0: float = 0.5             # Oseen: LPS parameter
+    conv: object = None                 # Oseen: nodal beta (n_nodes, 2) on the finest mesh
 
     @property
     def nc(self):
@@ -88,16 +98,45 @@ class System:
     def fixed(self):
         return self.hang | self.dirichlet
 
-    def rhs(self, f_nodal):
-        """b_c for nodal source values f (n_nodes x nc or n_nodes)."""
+    def rhs(self, f_nodal, g_nodal=None):
+        """b_c for nodal source values f (n_nodes x nc or n_nodes) and
+        optional nodal Dirichlet data g (same shape; used on Dirichlet dofs)."""
         f = np.asarray(f_nodal, dtype=np.float64).reshape(self.mesh.n_nodes, -1)
         b_all = (self.F @ f).ravel()
-        return fem.condense_rhs(b_all, self.H, self.hang, self.dirichlet)
+        g = None if g_nodal is None else np.asarray(g_nodal, dtype=np.float64).ravel()
+        return fem.condense_rhs(b_all, self.H, self.hang, self.dirichlet, g, self.A_raw)
 
 
-def build_system(mesh, prob: Problem, with_load=True) -> System:
+def inject(fine_mesh, values, mesh):
+    """Values of a nodal field of fine_mesh at the nodes of a coarser mesh of
+    the same hierarchy (every coarse node is a fine node)."""
+    X = np.asarray(mesh.X, dtype=np.int64) << (fine_mesh.L - mesh.L)
+    idx = fine_mesh.lookup(fine_mesh.key(X))
+    assert np.all(idx >= 0)
+    return np.asarray(values)[idx]
+
+
+def oseen_matrix(mesh, prob: Problem, beta):
+    """Oseen + LPS operator assembled patch by patch (before condensation)."""
+    nodes, lev = M.patches(mesh)
+    beta = np.asarray(beta, dtype=np.float64)
+    A = None
+    for l in np.unique(lev):
+        sel = np.nonzero(lev == l)[0]
+        h = mesh.extent / (mesh.macro * 2.0 ** int(l))
+        Kp = fem.oseen_patch_matrices(h, beta[nodes[sel]], prob.nu, prob.dt, prob.lps_alpha0)
+        Al = fem.assemble_patches(mesh, nodes[sel], Kp, 3)
+        A = Al if A is None else A + Al
+    return A.tocsr()
+
+
+def build_system(mesh, prob: Problem, with_load=True, beta=None) -> System:
+    """beta: nodal convection field of this mesh (Oseen only)."""
     nc = prob.nc
-    A_raw = fem.assemble(mesh, element(prob, mesh.dim), nc)
+    if prob.kind == OSEEN:
+        A_raw = oseen_matrix(mesh, prob, beta)
+    else:
+        A_raw = fem.assemble(mesh, element(prob, mesh.dim), nc)
     H = fem.expand(mesh.H(), nc)
     hang, dirichlet = fem.constrained_dofs(mesh, prob.masks(), nc)
     A = fem.condense(A_raw, H, hang, dirichlet)

@@ -401,3 +401,185 @@ def test_rhs_load_vector_integrates_constants():
     assert b_all.sum() == pytest.approx(1.0, rel=1e-13)
     # H^T keeps the total (partition of unity of the conforming basis)
     assert (s.H.T @ b_all).sum() == pytest.approx(1.0, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Oseen system with local projection stabilisation (patch meshes)
+# ---------------------------------------------------------------------------
+
+def _oseen_case(rounds=2, **kw):
+    lm = W.oseen_channel(1, rounds)
+    fm = M.Q1Mesh(2, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+    beta = W.oseen_beta(fm.coords)
+    args = dict(dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01, conv=beta)
+    args.update(kw)
+    return lm, fm, PB.Problem(PB.OSEEN, **args)
+
+
+def _leg_rule(n):
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def test_lps_interpolation_is_a_projection_onto_coarse_q1():
+    Pi = fem.lps_interpolation(2)
+    assert np.allclose(Pi @ Pi, Pi, atol=0, rtol=0)
+    # values of a bilinear function on the 3x3 patch points are reproduced
+    pts = np.array([[(i % 3) / 2.0, (i // 3) / 2.0] for i in range(9)])
+    f = 1.5 - 2.0 * pts[:, 0] + 0.25 * pts[:, 1] + 3.0 * pts[:, 0] * pts[:, 1]
+    assert np.allclose(Pi @ f, f, rtol=0, atol=1e-15)
+    # the fluctuation of the centre "bubble" is the bubble itself
+    e = np.zeros(9); e[4] = 1.0
+    assert np.array_equal((np.eye(9) - Pi) @ e, e)
+
+
+def test_oseen_patch_matrix_against_brute_force_quadrature():
+    """Every term of one patch matrix recomputed from the hat functions with a
+    5-point Gauss-Legendre rule per axis and per child cell."""
+    rng = np.random.default_rng(3)
+    h = np.array([0.1, 0.0625])
+    beta9 = rng.standard_normal((1, 9, 2))
+    nu, dt, a0 = 2e-3, 0.05, 0.5
+    K = fem.oseen_patch_matrices(h, beta9, nu, dt, a0)[0]
+    xs, ws = _leg_rule(5)
+    Kb = np.zeros((27, 27))
+    G = np.zeros((9, 9))
+    C = np.zeros((2, 2, 9, 9))
+
+    def hat(t, b):                       # 1D hat on [0,1] at local coordinate t
+        return t if b else 1.0 - t
+
+    for cy in range(2):
+        for cx in range(2):
+            for xa, wa in zip(xs, ws):
+                for ya, wb in zip(xs, ws):
+                    wv = wa * wb * h[0] * h[1]
+                    phi = np.zeros(9); gx = np.zeros(9); gy = np.zeros(9)
+                    for c in range(4):
+                        bx, by = c & 1, c >> 1
+                        n = (cx + bx) + 3 * (cy + by)
+                        phi[n] = hat(xa, bx) * hat(ya, by)
+                        gx[n] = (1 if bx else -1) / h[0] * hat(ya, by)
+                        gy[n] = hat(xa, bx) * (1 if by else -1) / h[1]
+                    bq = phi @ beta9[0]
+                    conv_t = bq[0] * gx + bq[1] * gy
+                    for a in range(9):
+                        for b in range(9):
+                            v = phi[a] * phi[b] / dt + nu * (gx[a] * gx[b] + gy[a] * gy[b]) + phi[a] * conv_t[b]
+                            Kb[3 * a, 3 * b] += wv * v
+                            Kb[3 * a + 1, 3 * b + 1] += wv * v
+                            Kb[3 * a, 3 * b + 2] -= wv * gx[a] * phi[b]
+                            Kb[3 * a + 1, 3 * b + 2] -= wv * gy[a] * phi[b]
+                            Kb[3 * a + 2, 3 * b] += wv * phi[a] * gx[b]
+                            Kb[3 * a + 2, 3 * b + 1] += wv * phi[a] * gy[b]
+                            G[a, b] += wv * (gx[a] * gx[b] + gy[a] * gy[b])
+                            gg = ((gx[a], gy[a]), (gx[b], gy[b]))
+                            for i in range(2):
+                                for j in range(2):
+                                    C[i, j, a, b] += wv * gg[0][i] * gg[1][j]
+    kap = np.eye(9)
+    for i in range(9):             # kappa from its definition: e_i minus the coarse interpolant of e_i
+        lx, ly = i % 3, i // 3
+        if lx in (0, 2) and ly in (0, 2):
+            for j in range(9):
+                jx, jy = j % 3, j // 3
+                wx = (1 - jx / 2) if lx == 0 else jx / 2
+                wy = (1 - jy / 2) if ly == 0 else jy / 2
+                kap[j, i] -= wx * wy
+    bP = beta9[0, 4]
+    hP = 2 * np.linalg.norm(h)
+    alpha = a0 * hP ** 2 / (nu + np.linalg.norm(bP) * hP)
+    Kb[2::3, 2::3] += alpha * kap.T @ G @ kap
+    Cb = sum(bP[i] * bP[j] * C[i, j] for i in range(2) for j in range(2))
+    for i in range(2):
+        Kb[i::3, i::3] += alpha * kap.T @ Cb @ kap
+    assert np.allclose(K, Kb, rtol=1e-12, atol=1e-12 * np.abs(Kb).max())
+
+
+def test_oseen_patch_matrix_closed_forms():
+    h = np.array([0.05, 0.05])
+    nu, dt, a0 = 1e-3, 0.01, 0.5
+    K = fem.oseen_patch_matrices(h, np.zeros((1, 9, 2)), nu, dt, a0)[0]
+    # pressure-velocity coupling: -(p, div v) is minus the transpose of (div u, q)
+    for i in range(2):
+        assert np.array_equal(K[i::3, 2::3], -K[2::3, i::3].T)
+    # LPS pressure term on the centre bubble of a square patch: alpha * 8/3
+    hP = 2 * math.sqrt(2) * 0.05
+    assert K[3 * 4 + 2, 3 * 4 + 2] == pytest.approx(a0 * hP * hP / nu * 8.0 / 3.0, rel=1e-14)
+    # and it annihilates coarse bilinear pressures, leaving rank 5
+    S = K[2::3, 2::3]
+    pts = np.array([[(i % 3), (i // 3)] for i in range(9)], dtype=float)
+    assert np.allclose(S @ (1 + pts[:, 0] - 2 * pts[:, 1] + pts[:, 0] * pts[:, 1]), 0, atol=1e-12)
+    assert np.linalg.matrix_rank(S, tol=1e-10 * np.abs(S).max()) == 5
+    # mass: the velocity block of a constant field integrates to |P| / dt
+    ones = np.zeros(27); ones[0::3] = 1.0
+    Kmass = fem.oseen_patch_matrices(h, np.zeros((1, 9, 2)), nu, dt, a0)[0]   # constants: no stiffness, no LPS
+    assert (ones @ Kmass @ ones) == pytest.approx(4 * 0.05 * 0.05 / dt, rel=1e-14)
+
+
+def test_oseen_operator_annihilates_divergence_free_linear_fields():
+    """Patch test of the assembled, condensed operator: with 1/dt = 0 and
+    beta = 0 a linear divergence-free velocity with zero pressure, and a
+    constant pressure with zero velocity, leave a zero residual on every row
+    that touches no boundary (hanging nodes inside)."""
+    lm, fm, prob = _oseen_case(3, dt=np.inf, conv=None)
+    beta = np.zeros((fm.n_nodes, 2))
+    A = PB.oseen_matrix(fm, prob, beta)
+    H = fem.expand(fm.H(), 3)
+    Ac = (H.T @ A @ H).tocsr()
+    x, y = fm.coords[:, 0], fm.coords[:, 1]
+    u = np.zeros((fm.n_nodes, 3))
+    u[:, 0], u[:, 1] = 2.0 * x + 0.5 * y - 1.0, -2.0 * y + 0.25 * x
+    p = np.zeros((fm.n_nodes, 3)); p[:, 2] = 1.0
+    bnd = fm.boundary_nodes(0xF)
+    touches = np.asarray((abs(fem.expand(fm.H(), 1).T @ abs(sp.csr_matrix(A[0::3, 0::3])) @ fem.expand(fm.H(), 1))
+                          @ bnd.astype(float))).ravel() > 0
+    interior = np.repeat(~touches & ~fm.hanging, 3)
+    for v in (u, p):
+        r = Ac @ v.ravel()
+        assert np.abs(r[interior]).max() < 1e-12 * np.abs(Ac).max()
+    assert interior.sum() > 300
+
+
+def test_oseen_lifting_equals_nonsymmetric_elimination():
+    """Symmetric elimination with lifted Dirichlet data gives the solution of
+    the system whose Dirichlet rows are simply replaced by x_D = g."""
+    lm, fm, prob = _oseen_case(2)
+    S = PB.build_system(fm, prob, beta=prob.conv)
+    g = W.oseen_inflow(fm.coords)
+    b = S.rhs(np.zeros((fm.n_nodes, 3)), g)
+    x = spl.spsolve(S.A.tocsc(), b)
+    Ac = (S.H.T @ S.A_raw @ S.H).tolil()
+    rhs = np.zeros(Ac.shape[0])
+    gv = g.ravel()
+    for i in np.nonzero(S.fixed)[0]:
+        Ac.rows[i] = [i]; Ac.data[i] = [1.0]
+        rhs[i] = gv[i] if S.dirichlet[i] else 0.0
+    x2 = spl.spsolve(Ac.tocsc(), rhs)
+    assert np.allclose(x, x2, rtol=0, atol=1e-11 * np.abs(x2).max())
+    assert np.abs(x[0::3]).max() == pytest.approx(0.3 * 4 * 0.205 * 0.205 / 0.41 ** 2, rel=0.05)
+
+
+def test_patch_coarsening_keeps_patch_meshes():
+    lm, fm, prob = _oseen_case(4)
+    sets = M.hierarchy(2, lm.macro, lm.level, lm.anchor, 1, patch=True)
+    assert len(sets) >= 4
+    area = float(np.prod(lm.extent))
+    for l, a in sets:
+        m = M.Q1Mesh(2, lm.origin, lm.extent, lm.macro, l, a)
+        M.patches(m)                                 # raises unless every family is complete
+        assert M._violations(2, np.asarray(lm.macro), l, a).size == 0
+        assert float(m.cell_size().prod(axis=1).sum()) == pytest.approx(area, rel=1e-13)
+    # the coarsest level is the macro grid refined once
+    assert np.all(sets[-1][0] == 1) and sets[-1][0].size == 4 * 22 * 4
+
+
+def test_oseen_mg_gmres_equals_direct_solve():
+    lm, fm, prob = _oseen_case(3)
+    h = mg.Hierarchy(lm, prob, omega=0.8)
+    S = PB.build_system(h.fine.mesh, prob, beta=prob.conv)
+    b = S.rhs(np.zeros((fm.n_nodes, 3)), W.oseen_inflow(fm.coords))
+    xd = spl.spsolve(S.A.tocsc(), b)
+    x, info = krylov.gmres(S.A, b, h.precondition, rtol=1e-11, restart=30, maxit=400)
+    assert info["true_rel"] <= 1e-11
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)

@@ -75,9 +75,23 @@ def uniform_leaves(dim, macro, level, origin=None, extent=None) -> LeafMesh:
     return LeafMesh(dim, origin, extent, macro, lev, anchor)
 
 
-def refine(mesh: LeafMesh, mask: np.ndarray) -> LeafMesh:
-    """Replace every marked leaf by its 2**dim children."""
+def family_mask(mesh: LeafMesh, mask: np.ndarray) -> np.ndarray:
+    """Extend a leaf mask to every sibling of a marked leaf (same parent)."""
     dim = mesh.dim
+    sel = mesh.level >= 1
+    pk = np.full(mesh.n_leaves, -1, dtype=np.int64)
+    pk[sel] = _keys(dim, mesh.level[sel] - 1, mesh.anchor[sel] >> 1)
+    marked = np.unique(pk[mask & sel])
+    return mask | (sel & np.isin(pk, marked))
+
+
+def refine(mesh: LeafMesh, mask: np.ndarray, families: bool = False) -> LeafMesh:
+    """Replace every marked leaf by its 2**dim children.  With families=True
+    every sibling of a marked leaf is refined too, so a mesh whose leaves all
+    come in complete sibling families (a patch mesh) stays one."""
+    dim = mesh.dim
+    if families:
+        mask = family_mask(mesh, mask)
     keep_l, keep_a = mesh.level[~mask], mesh.anchor[~mask]
     par_l, par_a = mesh.level[mask], mesh.anchor[mask]
     kids_l, kids_a = [], []
@@ -90,8 +104,9 @@ def refine(mesh: LeafMesh, mask: np.ndarray) -> LeafMesh:
     return LeafMesh(dim, mesh.origin, mesh.extent, mesh.macro, level, anchor, dict(mesh.meta))
 
 
-def balance_2to1(mesh: LeafMesh) -> LeafMesh:
-    """Refine until face-neighbouring leaves differ by at most one level."""
+def balance_2to1(mesh: LeafMesh, families: bool = False) -> LeafMesh:
+    """Refine until face-neighbouring leaves differ by at most one level
+    (refining whole sibling families when families=True)."""
     dim = mesh.dim
     while True:
         lev, anc = mesh.level, mesh.anchor
@@ -130,7 +145,7 @@ def balance_2to1(mesh: LeafMesh) -> LeafMesh:
                     cl, ca = cl[~hit], ca[~hit]
         if not mark.any():
             return mesh
-        mesh = refine(mesh, mark)
+        mesh = refine(mesh, mark, families)
 
 
 def _cell_box(mesh: LeafMesh):
@@ -192,9 +207,11 @@ def elasticity3d(n: int = 128) -> LeafMesh:
 
 
 def oseen_channel(uniform: int = 1, rounds: int = 0, band: float = 2.0) -> LeafMesh:
-    """Channel [0,2.2]x[0,0.41] on a 22x4 macro grid, refined `uniform` times
-    everywhere, then `rounds` times in the cells within band*h of the circle
-    |x - (0.2, 0.2)| = 0.05 (h the cell's diameter), 2:1 balanced."""
+    """Channel [0,2.2]x[0,0.41] on a 22x4 macro grid, refined `uniform` (>= 1)
+    times everywhere, then `rounds` times in the cells within band*h of the
+    circle |x - (0.2, 0.2)| = 0.05 (h the cell's diameter), 2:1 balanced.
+    Refinement is by whole sibling families, so every leaf belongs to a
+    complete family (the patches of the local projection stabilisation)."""
     m = uniform_leaves(2, (22, 4), uniform, origin=(0.0, 0.0), extent=(2.2, 0.41))
     c, rad = np.array([0.2, 0.2]), 0.05
     for _ in range(rounds):
@@ -205,9 +222,37 @@ def oseen_channel(uniform: int = 1, rounds: int = 0, band: float = 2.0) -> LeafM
         dmax = np.linalg.norm(far - c, axis=1)
         diam = np.linalg.norm(h, axis=1)
         dist = np.where((dmin <= rad) & (dmax >= rad), 0.0, np.minimum(np.abs(dmin - rad), np.abs(dmax - rad)))
-        m = balance_2to1(refine(m, dist <= band * diam))
+        m = balance_2to1(refine(m, dist <= band * diam, families=True), families=True)
     m.meta.update(workload=f"oseen_channel_u{uniform}_r{rounds}")
     return m
+
+
+def oseen_beta(xy: np.ndarray, seed: int = MASTER_SEED, modes: int = 4) -> np.ndarray:
+    """Divergence-free convection field beta = (d psi/dy, -d psi/dx) of the
+    seeded stream function psi = sum a_mn sin(m pi x/2.2) sin(n pi y/0.41)
+    / (m^2 + n^2), scaled so that max |beta| over the given points is 1."""
+    a = stream_coeffs(seed, modes)
+    x, y = xy[:, 0], xy[:, 1]
+    bx = np.zeros_like(x)
+    by = np.zeros_like(x)
+    for m in range(1, modes + 1):
+        for n in range(1, modes + 1):
+            km, kn = m * math.pi / 2.2, n * math.pi / 0.41
+            c = a[m - 1, n - 1] / (m * m + n * n)
+            bx += c * np.sin(km * x) * kn * np.cos(kn * y)
+            by -= c * km * np.cos(km * x) * np.sin(kn * y)
+    beta = np.stack([bx, by], axis=1)
+    return beta / np.max(np.linalg.norm(beta, axis=1))
+
+
+def oseen_inflow(xy: np.ndarray, um: float = 0.3) -> np.ndarray:
+    """Nodal Dirichlet data (u, v, p): parabolic inflow u = 4 um y (H - y)/H^2
+    at x = 0 (H = 0.41), zero elsewhere (walls); p entries are unused."""
+    g = np.zeros((xy.shape[0], 3))
+    H = 0.41
+    at_in = xy[:, 0] == 0.0
+    g[at_in, 0] = 4.0 * um * xy[at_in, 1] * (H - xy[at_in, 1]) / (H * H)
+    return g
 
 
 # ---------------------------------------------------------------------------
