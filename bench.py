@@ -380,6 +380,7 @@ def main():
     stream = ctx.stream
     t0 = time.perf_counter()
     ok["launch_mode"] = 1 if args.launch == "direct" else 0
+    ok["store_bf16"] = 1
     h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
     setup_s = time.perf_counter() - t0
     info = h.info
@@ -423,6 +424,9 @@ def main():
         barrier()
     # FP64 path of the same fused kernels (reported beside the value)
     ms64, st64 = timed_solves(B.MG_FP64, max(2, args.steps // 2), 1)
+    barrier()
+    # ablation: BF16-stored matrix values in the FP32 V-cycle
+    ms16, st16 = timed_solves(B.MG_MIXED_BF16, max(2, args.steps // 2), 1)
     barrier()
     value, t_max = whole_job_rate(n_free, args.steps, sum(ms_mixed), world, "cuda")
     assert all(s.status == 0 for s in st_mixed + st64), [s.as_dict() for s in st_mixed + st64]
@@ -471,10 +475,13 @@ def main():
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / (ker_ms_avg * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None       # DRAM bytes per launch from the ncu capture, while it matches the current kernel
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.txt")
     if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get(args.workload)
+        for line in open(tr_path):
+            if line.startswith("bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                traffic = None if v == "null" else int(v)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "td_adaptive":
@@ -490,11 +497,16 @@ def main():
         "config": {"workload": args.workload, "description": desc, "n_nodes": int(info.n_nodes),
                    "n_free_dofs": int(n_free), "levels": int(info.levels), "hanging_nodes": int(info.n_hanging),
                    "rtol": args.rtol, "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tail_levels": int(info.tail_levels),
+                   "tail_cluster": int(info.tail_cluster), "tuned_vcycle_ms": info.vcycle_ms},
         "iters": [s.iters for s in st_mixed], "rel_res": max(s.rel_res for s in st_mixed),
         "fp64": {"value": world * n_free / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
                  "iters": [s.iters for s in st64], "rel_res": max(s.rel_res for s in st64)},
         "speedup_mixed_vs_fp64": statistics.mean(ms64) / statistics.mean(ms_mixed),
+        "bf16_values_ablation": {"value": world * n_free / (statistics.mean(ms16) * 1e-3),
+                                 "ms_per_step": statistics.mean(ms16), "iters": [s.iters for s in st16],
+                                 "rel_res": max(s.rel_res for s in st16),
+                                 "converged": all(s.status == 0 for s in st16)},
         "setup_s": setup_s,
         "gpu_launches": int(sum(s.launches for s in st_mixed)),
         "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": int(2 * 8 * h.n_dofs),

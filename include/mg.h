@@ -52,8 +52,11 @@ enum {
 };
 
 typedef enum { MG_FP64 = 0, MG_MIXED_FP32 = 1, MG_MIXED_BF16 = 2 } mg_precision;
-typedef enum { MG_POISSON = 0, MG_TRANSPORT = 1, MG_ELASTICITY = 2 } mg_kind;
-typedef enum { MG_KRYLOV_AUTO = 0, MG_CG = 1, MG_BICGSTAB = 2, MG_GMRES = 3 } mg_krylov;
+typedef enum { MG_POISSON = 0, MG_TRANSPORT = 1, MG_ELASTICITY = 2, MG_OSEEN = 3 } mg_kind;
+/* MG_MGITER: the multigrid iteration itself as the solver, x <- x + GMG(0, b - A x)
+ * with the defect computed in FP64 (defect correction when the V-cycle runs
+ * in FP32). */
+typedef enum { MG_KRYLOV_AUTO = 0, MG_CG = 1, MG_BICGSTAB = 2, MG_GMRES = 3, MG_MGITER = 4 } mg_krylov;
 
 typedef struct mg_ctx mg_ctx;
 typedef struct mg_hier mg_hier;
@@ -85,12 +88,27 @@ typedef struct {
 
 /* Problem: bilinear form and Dirichlet faces.  Face bit 2d = face x_d = min,
  * bit 2d+1 = face x_d = max; dirichlet_mask[c] selects the faces on which
- * component c is fixed to 0.
+ * component c is prescribed (values from mg_assemble_rhs's g, else 0).
  *   POISSON      (grad u, grad v)                                  nc = 1
  *   TRANSPORT    eps (grad u, grad v) + (beta.grad u, v)
  *                + sum_T delta_T (beta.grad u, beta.grad v)_T,
  *                delta_T = supg_delta0 h_T^2 / (6 eps + |beta| h_T)   nc = 1
- *   ELASTICITY   2 mu (eps(u), eps(v)) + lambda (div u, div v), 3D  nc = 3 */
+ *   ELASTICITY   2 mu (eps(u), eps(v)) + lambda (div u, div v), 3D  nc = 3
+ *   OSEEN        one linearised backward-Euler step of incompressible flow
+ *                (Sec. 5.3's equations), 2D, unknowns (u, v, p), nc = 3:
+ *                (1/dt)(u, v) + nu (grad u, grad v) + ((beta_h.grad) u, v)
+ *                - (p, div v) + (div u, q)
+ *                + sum_P alpha_P [(grad kp, grad kq)_P
+ *                                 + (beta_P.grad ku, beta_P.grad kv)_P]
+ *                with local projection stabilisation on patches P (the
+ *                parents of the sibling families: the mesh must be a patch
+ *                mesh, every leaf in a complete family), k = id - i_2h the
+ *                fluctuation w.r.t. the patch's coarse Q1 interpolant,
+ *                alpha_P = lps_alpha0 h_P^2 / (nu + |beta_P| h_P), h_P the
+ *                patch diameter, beta_h the cell-wise Q1 interpolant of the
+ *                nodal field conv, beta_P its value at the patch centre.
+ *                Coarser levels inject conv at their nodes and are coarsened
+ *                so that they stay patch meshes (coarsest >= level 1). */
 typedef struct {
   int kind;
   double eps;
@@ -99,6 +117,13 @@ typedef struct {
   double lambda;
   double supg_delta0;
   uint32_t dirichlet_mask[3];
+  double nu;                   /* OSEEN: viscosity                              */
+  double dt;                   /* OSEEN: time step (INFINITY: no mass term)     */
+  double lps_alpha0;           /* OSEEN: LPS parameter (0.5 is customary)       */
+  const double* conv;          /* OSEEN: host, n_nodes * dim doubles, the nodal
+                                  convection field at the finest nodes in the
+                                  external order (see mg_mesh_nodes); read
+                                  during mg_setup only                          */
 } mg_problem;
 
 typedef struct {
@@ -116,6 +141,12 @@ typedef struct {
   int tail_rows;               /* levels with at most this many dofs (and all
                                   coarser ones) run as one single-CTA kernel
                                   per V-cycle (0: off; default 4096)          */
+  int store_bf16;              /* keep BF16 copies of the level matrices for
+                                  MG_MIXED_BF16 (FP32 vectors and arithmetic,
+                                  values rounded to BF16: an ablation)        */
+  int autotune;                /* 1 (default): at setup, time V-cycles over
+                                  tail thresholds x cluster sizes and keep the
+                                  fastest (cached per hierarchy shape)        */
 } mg_opts;
 
 typedef struct {
@@ -128,6 +159,10 @@ typedef struct {
   int64_t n_hanging;
   double omega;
   size_t bytes_workspace;               /* one extra solve workspace (serving)   */
+  int tail_levels;                      /* levels run by the cluster tail kernel  */
+  int tail_cluster;                     /* CTAs in that kernel's cluster (0: one
+                                           CTA working in shared memory)         */
+  double vcycle_ms;                     /* tuned V-cycle time (0 if not tuned)    */
 } mg_info;
 
 typedef struct {
@@ -164,21 +199,30 @@ int mg_destroy(mg_ctx* ctx);
 int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* problem, const mg_opts* opts,
              mg_hier** out);
 int mg_hier_info(const mg_hier* h, mg_info* info);
+/* Finest-level nodes of a leaf mesh before any setup: *n_nodes receives their
+ * number and, when xyz_host != NULL, their physical coordinates (host buffer
+ * of n_nodes * dim doubles, external order).  MG_ERR_INVALID for a malformed
+ * mesh.  Needs no context and no GPU. */
+int mg_mesh_nodes(const mg_mesh* mesh, int64_t* n_nodes, double* xyz_host);
 /* Physical coordinates of the finest-level nodes, external order, host
  * buffer of n_nodes * dim doubles. */
 int mg_node_coords(const mg_hier* h, double* xyz_host);
 int mg_free(mg_hier* h);
 
-/* b = H^T (M I_h f) (+ SUPG load term), zero on hanging and Dirichlet rows.
+/* b = H^T (M I_h f) (+ SUPG load term) with the Dirichlet data eliminated
+ * symmetrically: b -= (H^T A H)[:, D] g_D on the free rows, b = g on the
+ * Dirichlet rows, 0 on hanging rows (Sec. 2.2 for H, H^T).
  * f_nodal: device, n_nodes * nc doubles (nodal source values at every node,
- * hanging ones included); b: device, n_nodes * nc doubles. */
-int mg_assemble_rhs(mg_hier* h, const double* f_nodal, double* b);
+ * hanging ones included); g_nodal: device, n_nodes * nc doubles or NULL
+ * (homogeneous data), only its Dirichlet entries are read; b: device,
+ * n_nodes * nc doubles. */
+int mg_assemble_rhs(mg_hier* h, const double* f_nodal, const double* g_nodal, double* b);
 
 /* Krylov solve (CG / BiCGStab / GMRES per opts.krylov) preconditioned by one
  * V-cycle per iteration (Sec. 4.1.5).  b, x: device, n_nodes * nc doubles,
  * caller-owned.  x in: initial guess; out: solution on all nodes, hanging
- * values filled by H (Sec. 2.2) and Dirichlet values 0.  Stops when the true
- * FP64 residual satisfies ||b - A x|| <= rtol ||b_free||; prec selects the
+ * values filled by H (Sec. 2.2), Dirichlet values taken from b.  Stops when
+ * the true FP64 residual satisfies ||b - A x|| <= rtol ||b_free||; prec selects the
  * V-cycle precision (MG_FP64, or FP32 inside the FP64 Krylov loop).  Returns
  * MG_ERR_NOT_CONVERGED after max_it iterations (x and stats valid). */
 int mg_solve(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats);
@@ -200,6 +244,18 @@ int mg_vcycle(mg_hier* h, const void* r, void* z, int prec);
  *   MG_OP_COARSE       out = A_0^-1 in            (level must be 0) */
 enum { MG_OP_MATVEC = 0, MG_OP_SMOOTH = 1, MG_OP_RESTRICT = 2, MG_OP_PROLONG_ADD = 3, MG_OP_COARSE = 4 };
 int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, void* out, int prec);
+
+/* Launch shape of the smallest levels: levels with at most tail_rows dofs
+ * (and all coarser ones) run as one kernel on a cluster of `cluster` CTAs
+ * (1..8), or, for cluster == 0, on one CTA that first copies their vectors
+ * and, coarsest first, as many of their matrices as fit into 200 KB of
+ * shared memory (the threshold is lowered until the vectors fit).
+ * tail_rows < 0: time V-cycles of precision prec over a set of thresholds and
+ * launch shapes and keep the fastest (what opts.autotune does at setup).
+ * Results are bitwise identical for every choice.  Errors: MG_ERR_INVALID
+ * (cluster outside 0..8, unknown precision), MG_ERR_OOM (the shared-memory
+ * image of the tail could not be allocated). */
+int mg_tune(mg_hier* h, int prec, int tail_rows, int cluster);
 
 /* Allocation-free residual + restriction (no counterpart in the paper: it
  * exists for callers that must not allocate device memory -- code running

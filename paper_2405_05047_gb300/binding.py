@@ -20,8 +20,9 @@ import numpy as np
 MG_OK, MG_PENDING = 0, 1
 MG_ERR_NOT_CONVERGED = -4
 MG_FP64, MG_MIXED_FP32, MG_MIXED_BF16 = 0, 1, 2
-MG_POISSON, MG_TRANSPORT, MG_ELASTICITY = 0, 1, 2
-MG_KRYLOV_AUTO, MG_CG, MG_BICGSTAB, MG_GMRES = 0, 1, 2, 3
+MG_ERR_CANCELLED = -9
+MG_POISSON, MG_TRANSPORT, MG_ELASTICITY, MG_OSEEN = 0, 1, 2, 3
+MG_KRYLOV_AUTO, MG_CG, MG_BICGSTAB, MG_GMRES, MG_MGITER = 0, 1, 2, 3, 4
 MG_OP_MATVEC, MG_OP_SMOOTH, MG_OP_RESTRICT, MG_OP_PROLONG_ADD, MG_OP_COARSE = 0, 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,14 +46,15 @@ class MgMesh(C.Structure):
 
 class MgProblem(C.Structure):
     _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("beta", C.c_double * 3), ("mu", C.c_double),
-                ("lambda_", C.c_double), ("supg_delta0", C.c_double), ("dirichlet_mask", C.c_uint32 * 3)]
+                ("lambda_", C.c_double), ("supg_delta0", C.c_double), ("dirichlet_mask", C.c_uint32 * 3),
+                ("nu", C.c_double), ("dt", C.c_double), ("lps_alpha0", C.c_double), ("conv", C.c_void_p)]
 
 
 class MgOpts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("min_level", C.c_int),
                 ("max_levels", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("store_fp64", C.c_int),
                 ("store_fp32", C.c_int), ("launch_mode", C.c_int),
-                ("tail_rows", C.c_int)]
+                ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int)]
 
 
 class MgInfo(C.Structure):
@@ -60,7 +62,8 @@ class MgInfo(C.Structure):
                 ("n_dofs", C.c_int64), ("n_free", C.c_int64), ("level_nodes", C.c_int64 * 32),
                 ("level_nnzb", C.c_int64 * 32), ("level_rows_nnzb", C.c_int64 * 32),
                 ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double),
-                ("bytes_workspace", C.c_size_t)]
+                ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
+                ("vcycle_ms", C.c_double)]
 
 
 class MgStats(C.Structure):
@@ -94,7 +97,8 @@ _SIGS = {
     "mg_hier_info": (C.c_int, [C.c_void_p, C.POINTER(MgInfo)]),
     "mg_node_coords": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_free": (C.c_int, [C.c_void_p]),
-    "mg_assemble_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_assemble_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mg_mesh_nodes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
                            C.POINTER(MgStats)]),
     "mg_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
@@ -108,6 +112,7 @@ _SIGS = {
     "mg_launch_count": (C.c_int64, [C.c_void_p]),
     "mg_time_op": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mg_serve_config": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "mg_restrict_static": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
 }
 
@@ -217,7 +222,8 @@ def make_mesh(leafmesh):
 
 
 def make_problem(kind=MG_POISSON, eps=1.0, beta=(0.0, 0.0, 0.0), mu=1.0, lam=1.0, supg_delta0=0.5,
-                 dirichlet=(0xFF,)):
+                 dirichlet=(0xFF,), nu=1e-3, dt=0.01, lps_alpha0=0.5, conv=None):
+    """conv (OSEEN): nodal convection field at the finest nodes, (n_nodes, dim)."""
     p = MgProblem()
     p.kind = kind
     p.eps = eps
@@ -226,7 +232,14 @@ def make_problem(kind=MG_POISSON, eps=1.0, beta=(0.0, 0.0, 0.0), mu=1.0, lam=1.0
     p.mu = mu
     p.lambda_ = lam
     p.supg_delta0 = supg_delta0
-    nc = 3 if kind == MG_ELASTICITY else 1
+    p.nu = nu
+    p.dt = dt
+    p.lps_alpha0 = lps_alpha0
+    if conv is not None:
+        arr = np.ascontiguousarray(conv, dtype=np.float64)
+        p._conv = arr                 # kept alive with the struct
+        p.conv = arr.ctypes.data
+    nc = 3 if kind in (MG_ELASTICITY, MG_OSEEN) else 1
     masks = tuple(dirichlet) * (nc if len(dirichlet) == 1 else 1)
     for c in range(3):
         p.dirichlet_mask[c] = masks[c] if c < len(masks) else 0
@@ -250,6 +263,17 @@ def mg_setup(ctx, leafmesh, problem: MgProblem, opts: MgOpts | None = None):
     return out
 
 
+def mg_mesh_nodes(leafmesh):
+    """Physical coordinates (n_nodes, dim) of the finest nodes, external order."""
+    lib = load_library()
+    m, keep = make_mesh(leafmesh)
+    n = C.c_int64()
+    _check(lib.mg_mesh_nodes(C.byref(m), C.byref(n), None))
+    xyz = np.empty((n.value, leafmesh.dim), dtype=np.float64)
+    _check(lib.mg_mesh_nodes(C.byref(m), C.byref(n), xyz.ctypes.data))
+    return xyz
+
+
 def mg_hier_info(h) -> MgInfo:
     info = MgInfo()
     _check(load_library().mg_hier_info(h, C.byref(info)))
@@ -266,8 +290,8 @@ def mg_free(h):
     return _check(load_library().mg_free(h))
 
 
-def mg_assemble_rhs(h, f, b):
-    return _check(load_library().mg_assemble_rhs(h, _ptr(f), _ptr(b)))
+def mg_assemble_rhs(h, f, b, g=None):
+    return _check(load_library().mg_assemble_rhs(h, _ptr(f), _ptr(g) if g is not None else None, _ptr(b)))
 
 
 def mg_solve(h, b, x, rtol, max_it, prec=MG_FP64):
@@ -378,8 +402,8 @@ class Hierarchy:
     def level_nodes(self):
         return [self.info.level_nodes[l] for l in range(self.levels)]
 
-    def assemble_rhs(self, f, b):
-        return mg_assemble_rhs(self.handle, f, b)
+    def assemble_rhs(self, f, b, g=None):
+        return mg_assemble_rhs(self.handle, f, b, g)
 
     def solve(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_solve(self.handle, b, x, rtol, max_it, prec)
@@ -397,6 +421,10 @@ class Hierarchy:
         ms = C.c_double()
         _check(load_library().mg_time_op(self.handle, level, op, prec, reps, C.byref(ms)))
         return ms.value
+
+    def tune(self, prec=MG_MIXED_FP32, tail_rows=-1, cluster=1):
+        _check(load_library().mg_tune(self.handle, prec, tail_rows, cluster))
+        self.info = mg_hier_info(self.handle)
 
     def launch_count(self):
         return int(load_library().mg_launch_count(self.handle))

@@ -164,6 +164,8 @@ void mg_default_opts(mg_opts* o) {
   o->store_fp32 = 1;
   o->launch_mode = 0;
   o->tail_rows = 4096;
+  o->store_bf16 = 0;
+  o->autotune = 1;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -211,7 +213,9 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   else mg_default_opts(&opts);
   if (opts.nu1 < 1 || opts.nu2 < 0 || opts.nu1 > 16 || opts.nu2 > 16) return fail(MG_ERR_INVALID, "nu1 must be >= 1");
   if (!(opts.omega > 0.0)) return fail(MG_ERR_INVALID, "omega must be positive");
-  if (!opts.store_fp64 && !opts.store_fp32) return fail(MG_ERR_INVALID, "no precision stored");
+  if (!opts.store_fp64 && !opts.store_fp32 && !opts.store_bf16) return fail(MG_ERR_INVALID, "no precision stored");
+  if (!opts.store_fp64 && !(opts.store_fp32 || opts.store_bf16))
+    return fail(MG_ERR_INVALID, "no precision stored");
   HostHierarchy H;
   Status st = build_hierarchy(*mesh, *prob, opts, &H);
   if (!st.good()) return fail(st.code, st.msg);
@@ -225,9 +229,11 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   h->n_dofs = h->n_nodes * H.nc;
   h->n_free = H.n_free;
   h->prob = *prob;
+  h->prob.conv = nullptr;   // read during setup only
   h->opts = opts;
   h->has_fp64 = opts.store_fp64 != 0;
   h->has_fp32 = opts.store_fp32 != 0;
+  h->has_bf16 = opts.store_bf16 != 0;
   if (method_of(h.get()) == 3) h->gmres_m = std::max(2, std::min(opts.restart > 0 ? opts.restart : 30, 64));
   for (int64_t i = 0; i < h->n_nodes; ++i) h->n_hanging += F.topo.hanging[i];
   h->coords.resize(h->n_nodes * H.dim);
@@ -260,6 +266,8 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, cudaGetErrorString(e));
   }
+  if (rc == MG_OK && opts.autotune)
+    rc = autotune(hp, hp->has_fp32 ? MG_MIXED_FP32 : (hp->has_bf16 ? MG_MIXED_BF16 : MG_FP64));
   if (rc == MG_OK && ctx->budget && ctx->used > ctx->budget)
     rc = fail(MG_ERR_ADMISSION, "hierarchy and its workspace need " + std::to_string(hp->bytes + hp->ws0->bytes) +
                                     " bytes, over the HBM budget");
@@ -289,8 +297,29 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
   }
   info->bytes_device = h->bytes + (h->ws0 ? h->ws0->bytes : 0);
   info->bytes_workspace = h->ws_bytes;
+  info->tail_levels = h->tail_top > 0 ? h->tail_top + 1 : 0;
+  info->tail_cluster = h->tail_cluster;
+  info->vcycle_ms = h->tuned_vcycle_ms;
   info->n_hanging = h->n_hanging;
   info->omega = h->opts.omega;
+  return MG_OK;
+}
+
+int mg_mesh_nodes(const mg_mesh* mesh, int64_t* n_nodes, double* xyz) {
+  if (!mesh || !n_nodes) return fail(MG_ERR_INVALID, "NULL argument");
+  LeafSet s;
+  Status st = validate_mesh(*mesh, &s);
+  if (!st.good()) return fail(st.code, st.msg);
+  Topology T;
+  build_topology(s, &T);
+  *n_nodes = T.n_nodes;
+  if (xyz)
+    for (int64_t i = 0; i < T.n_nodes; ++i) {
+      int64_t X[3];
+      T.lattice_coords(i, X);
+      for (int d = 0; d < mesh->dim; ++d)
+        xyz[i * mesh->dim + d] = mesh->origin[d] + (double)X[d] * (mesh->extent[d] / (double)T.ncell[d]);
+    }
   return MG_OK;
 }
 
@@ -311,10 +340,12 @@ int mg_free(mg_hier* h) {
   return MG_OK;
 }
 
-int mg_assemble_rhs(mg_hier* h, const double* f, double* b) {
+int mg_assemble_rhs(mg_hier* h, const double* f, const double* g, double* b) {
   if (!h || !f || !b) return fail(MG_ERR_INVALID, "NULL argument");
+  CU(cudaSetDevice(h->ctx->device));
   cudaStream_t s = h->ctx->stream;
-  launch_rhs(h->F.v, h->nc, f, h->fixmask, b, s);
+  launch_rhs(h->F.v, h->nc, f, h->fixmask, h->dirmask, g, b, s);
+  if (g) launch_lift(h->Lift.v, h->nc, g, b, s);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(s));
   return MG_OK;
@@ -355,7 +386,8 @@ int mg_vcycle(mg_hier* h, const void* r, void* z, int prec) {
   std::lock_guard<std::mutex> lk(h->solve_mu);
   cudaStream_t s = h->ctx->stream;
   if (prec == MG_FP64) enqueue_vcycle<double>(h, *h->ws0, h->nlev - 1, (const double*)r, (double*)z, nullptr, s);
-  else enqueue_vcycle<float>(h, *h->ws0, h->nlev - 1, (const float*)r, (float*)z, nullptr, s);
+  else enqueue_vcycle<float>(h, *h->ws0, h->nlev - 1, (const float*)r, (float*)z, nullptr, s, false,
+                             prec == MG_MIXED_BF16);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(s));
   return MG_OK;
@@ -368,15 +400,16 @@ static int level_op(mg_hier* h, int level, int op, const void* in, const void* i
   LevelVecs& V = h->ws0->lv[level];
   const int nc = h->nc;
   const bool d = prec == MG_FP64;
+  const SellView& A32 = prec == MG_MIXED_BF16 ? L.A16.v : L.A32.v;
   switch (op) {
     case MG_OP_MATVEC:
       if (d) launch_matvec<double>(L.A64.v, nc, (const double*)in, (double*)out, nullptr, s);
-      else launch_matvec<float>(L.A32.v, nc, (const float*)in, (float*)out, nullptr, s);
+      else launch_matvec<float>(A32, nc, (const float*)in, (float*)out, nullptr, s);
       return MG_OK;
     case MG_OP_SMOOTH:
       if (!in2) return fail(MG_ERR_INVALID, "smooth needs b");
       if (d) launch_smooth<double>(L.A64.v, nc, (const double*)in, (const double*)in2, L.S64, (double*)out, h->opts.omega, false, nullptr, s);
-      else launch_smooth<float>(L.A32.v, nc, (const float*)in, (const float*)in2, L.S32, (float*)out, h->opts.omega, false, nullptr, s);
+      else launch_smooth<float>(A32, nc, (const float*)in, (const float*)in2, L.S32, (float*)out, h->opts.omega, false, nullptr, s);
       return MG_OK;
     case MG_OP_RESTRICT:
       if (level == 0 || !in2) return fail(MG_ERR_INVALID, "restrict needs level >= 1 and b");
@@ -384,7 +417,7 @@ static int level_op(mg_hier* h, int level, int op, const void* in, const void* i
         launch_residual<double>(L.A64.v, nc, (const double*)in, (const double*)in2, V.r64, nullptr, s);
         launch_restrict<double>(L.R.t, nc, V.r64, (double*)out, nullptr, nullptr, 0.0, nullptr, s);
       } else {
-        launch_residual<float>(L.A32.v, nc, (const float*)in, (const float*)in2, V.r32, nullptr, s);
+        launch_residual<float>(A32, nc, (const float*)in, (const float*)in2, V.r32, nullptr, s);
         launch_restrict<float>(L.R.t, nc, V.r32, (float*)out, nullptr, nullptr, 0.0, nullptr, s);
       }
       return MG_OK;
@@ -454,6 +487,15 @@ int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms) {
 }
 
 int64_t mg_launch_count(const mg_hier* h) { return h ? (int64_t)h->launch_count : 0; }
+
+int mg_tune(mg_hier* h, int prec, int tail_rows, int cluster) {
+  if (!h || (tail_rows >= 0 && (cluster < 0 || cluster > 8))) return fail(MG_ERR_INVALID, "bad argument");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  if (tail_rows < 0) return autotune(h, prec);
+  return set_tail(h, tail_rows, cluster);
+}
 
 int mg_submit(mg_ctx* c, mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec,
               uint64_t* ticket) {

@@ -4,7 +4,7 @@
 #include <memory>
 
 #include "../../include/mg_debug.h"
-#include "internal.h"
+#include "device.h"
 
 using namespace mgi;
 
@@ -23,7 +23,7 @@ int mg_host_build(const mg_mesh* mesh, const mg_problem* prob, const mg_opts* op
   else mg_default_opts(&opts);
   auto h = std::make_unique<mg_host_hier>();
   Status st = build_hierarchy(*mesh, *prob, opts, &h->H);
-  if (!st.good()) return st.code;
+  if (!st.good()) return fail(st.code, st.msg);
   const int nc = h->H.nc, nb = nc * nc;
   for (const HostLevel& lv : h->H.levels) {
     BlockCSR S;
@@ -62,6 +62,7 @@ int mg_host_level(const mg_host_hier* h, int level, int which, int64_t* n, int64
     case 3: M = &h->H.load; break;
     case 4: M = &h->sinv[level]; break;
     case 5: M = &h->hmat[level]; break;
+    case 6: M = &h->H.lift; break;
     default: return MG_ERR_INVALID;
   }
   *n = M->n; *m = M->m; *nc = M->nc; *nnzb = M->nnzb();

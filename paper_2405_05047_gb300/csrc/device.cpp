@@ -12,9 +12,12 @@
 // solve is one graph launch and only the final state crosses to the host.
 #include "device.h"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 
 namespace mgi {
 
@@ -63,6 +66,11 @@ void free_list(mg_ctx* c, std::vector<Alloc>& list, size_t& total) {
   total = 0;
 }
 
+template <typename VT>
+VT to_vt(double v) { return (VT)v; }
+template <>
+__nv_bfloat16 to_vt<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }   // via FP32, round to nearest even
+
 // SELL-C packing of a block CSR matrix (C = kSlice block rows per slice).
 template <typename VT>
 void pack_sell(const BlockCSR& M, std::vector<int64_t>& sptr, std::vector<int32_t>& col, std::vector<VT>& val) {
@@ -76,7 +84,7 @@ void pack_sell(const BlockCSR& M, std::vector<int64_t>& sptr, std::vector<int32_
   }
   const int64_t slots = sptr[ns];
   col.assign(slots, 0);
-  val.assign(slots * nb, VT(0));
+  val.assign(slots * nb, to_vt<VT>(0.0));
   for (int64_t s = 0; s < ns; ++s) {
     const int64_t w = (sptr[s + 1] - sptr[s]) / kSlice;
     for (int lane = 0; lane < kSlice; ++lane) {
@@ -86,7 +94,7 @@ void pack_sell(const BlockCSR& M, std::vector<int64_t>& sptr, std::vector<int32_
         const int64_t g = sptr[s] + kSlice * j, o = g + lane;
         if (j < len) {
           col[o] = (int32_t)M.col[M.ptr[r] + j];
-          for (int e = 0; e < nb; ++e) val[g * nb + (int64_t)e * kSlice + lane] = (VT)M.val[(M.ptr[r] + j) * nb + e];
+          for (int e = 0; e < nb; ++e) val[g * nb + (int64_t)e * kSlice + lane] = to_vt<VT>(M.val[(M.ptr[r] + j) * nb + e]);
         } else {
           col[o] = (int32_t)(r < n ? std::min<int64_t>(r, M.m - 1) : 0);
         }
@@ -150,6 +158,139 @@ struct Prec<float> {
 
 }  // namespace
 
+// ---------------------------------------------------------------- tail tuning
+namespace {
+int tail_top_for(const mg_hier* h, int rows) {
+  int top = 0;
+  if (rows > 0)
+    for (int l = 1; l < h->nlev && l < kTailMax; ++l)
+      if (h->L[l].n * h->nc <= rows) top = l;
+      else break;
+  return top;
+}
+uint32_t rnd16(uint64_t b) { return (uint32_t)((b + 15) & ~uint64_t(15)); }
+
+// Precision slot pi (0 FP64, 1 FP32, 2 BF16-stored values) of a hierarchy.
+bool has_slot(const mg_hier* h, int pi) { return pi == 0 ? h->has_fp64 : (pi == 1 ? h->has_fp32 : h->has_bf16); }
+const SellBuf& slot_A(const LevelMats& B, int pi) { return pi == 0 ? B.A64 : (pi == 1 ? B.A32 : B.A16); }
+uint32_t slot_tsize(int pi) { return pi == 0 ? 8 : 4; }
+uint32_t slot_vsize(int pi) { return pi == 0 ? 8 : (pi == 1 ? 4 : 2); }
+
+// Bytes of the header and the vectors of a staged tail over levels 0..top.
+uint64_t tail_vec_bytes(const mg_hier* h, int pi, int top) {
+  uint64_t b = rnd16((uint64_t)(top + 1) * sizeof(TailLevel));
+  for (int l = 0; l <= top; ++l) b += 4 * (uint64_t)rnd16((uint64_t)h->L[l].n * h->nc * slot_tsize(pi));
+  return b;
+}
+
+// Largest tail top whose staged vectors fit in shared memory, for every slot.
+int staged_top_cap(const mg_hier* h, int top) {
+  for (int pi = 0; pi < 3; ++pi)
+    if (has_slot(h, pi))
+      while (top > 0 && tail_vec_bytes(h, pi, top) > kTailSmemMax) --top;
+  return top;
+}
+
+// Shared-memory image of levels 0..top (layout in kernels.h, TailParams).
+// Matrices are staged level by level from the coarsest while they fit.
+int tail_image(mg_hier* h, int pi, int top, mg_hier::TailImage* out) {
+  auto it = h->tail_img.find({pi, top});
+  if (it != h->tail_img.end()) { *out = it->second; return MG_OK; }
+  const int nc = h->nc, nb = nc * nc, nt = top + 1;
+  const uint32_t ts = slot_tsize(pi), vs = slot_vsize(pi);
+  struct Piece { const void* src; uint64_t bytes; uint32_t off; };
+  std::vector<Piece> pieces;
+  std::vector<TailLevel> hdr(nt);
+  uint64_t off = rnd16((uint64_t)nt * sizeof(TailLevel));
+  const uint64_t vec_bytes = tail_vec_bytes(h, pi, top) - off;
+  uint32_t mask = 0;
+  bool staging = true;
+  for (int l = 0; l < nt; ++l) {
+    const LevelMats& B = h->L[l];
+    const SellBuf& A = slot_A(B, pi);
+    TailLevel& T = hdr[l];
+    T.A = A.v;
+    T.P = B.P.t;
+    T.R = B.R.t;
+    T.S = pi == 0 ? (const void*)B.S64 : (const void*)B.S32;
+    std::vector<Piece> lp;
+    uint64_t lo = off;
+    auto add = [&](const void* src, uint64_t bytes) -> const void* {
+      lp.push_back({src, bytes, (uint32_t)lo});
+      const void* o = (const void*)(uintptr_t)lo;
+      lo += rnd16(bytes);
+      return o;
+    };
+    TailLevel S = T;
+    S.A.sptr = (const int64_t*)add(A.v.sptr, (A.v.nslices + 1) * 8);
+    S.A.col = (const int32_t*)add(A.v.col, A.slots * 4);
+    S.A.val = add(A.v.val, A.slots * nb * vs);
+    S.S = add(T.S, B.n * nb * ts);
+    if (l > 0)
+      for (TransferView* V : {&S.P, &S.R}) {
+        const SellBuf& X = V == &S.P ? B.P : B.R;
+        V->sptr = (const int64_t*)add(X.t.sptr, (X.t.nslices + 1) * 8);
+        V->col = (const int32_t*)add(X.t.col, X.slots * 4);
+        V->w = (const float*)add(X.t.w, X.slots * 4);
+      }
+    if (staging && lo + vec_bytes <= kTailSmemMax) {
+      T = S;
+      mask |= 1u << l;
+      pieces.insert(pieces.end(), lp.begin(), lp.end());
+      off = lo;
+    } else {
+      staging = false;   // levels only grow: stage a prefix
+    }
+  }
+  const uint32_t image_bytes = (uint32_t)off;
+  uint64_t v = image_bytes;
+  for (int l = 0; l < nt; ++l) {
+    const uint64_t m = rnd16((uint64_t)h->L[l].n * nc * ts);
+    hdr[l].b = (void*)(uintptr_t)v; v += m;
+    hdr[l].o = (void*)(uintptr_t)v; v += m;
+    hdr[l].t = (void*)(uintptr_t)v; v += m;
+    hdr[l].r = (void*)(uintptr_t)v; v += m;
+  }
+  if (v > kTailSmemMax) return fail(MG_ERR_INVALID, "tail levels do not fit in shared memory");
+  unsigned char* img = (unsigned char*)dev_alloc(h->ctx, h->allocs, h->bytes, image_bytes, true);
+  if (!img) return fail(MG_ERR_OOM, "alloc");
+  CU(cudaMemset(img, 0, image_bytes));
+  CU(cudaMemcpy(img, hdr.data(), nt * sizeof(TailLevel), cudaMemcpyHostToDevice));
+  for (const Piece& p : pieces) CU(cudaMemcpy(img + p.off, p.src, p.bytes, cudaMemcpyDeviceToDevice));
+  mg_hier::TailImage ti;
+  ti.p = img;
+  ti.image_bytes = image_bytes;
+  ti.smem = (uint32_t)v;
+  ti.staged_mask = mask;
+  h->tail_img[{pi, top}] = ti;
+  *out = ti;
+  return MG_OK;
+}
+
+void apply_tail(mg_hier* h, Workspace* w) {
+  for (int pi = 0; pi < 3; ++pi) {
+    TailParams* P = pi == 0 ? &w->tail64 : (pi == 1 ? &w->tail32 : &w->tail16);
+    P->nt = h->tail_top + 1;
+    P->cluster = h->tail_cluster;
+    P->image = nullptr;
+    P->image_bytes = P->smem = P->staged_mask = 0;
+    if (h->tail_cluster == 0 && h->tail_top > 0 && has_slot(h, pi)) {
+      auto it = h->tail_img.find({pi, h->tail_top});
+      if (it != h->tail_img.end()) {
+        P->image = it->second.p;
+        P->image_bytes = it->second.image_bytes;
+        P->smem = it->second.smem;
+        P->staged_mask = it->second.staged_mask;
+      }
+    }
+  }
+  for (auto& g : w->graphs) cudaGraphExecDestroy(g.exec);
+  w->graphs.clear();
+}
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;   // shape -> (rows, cluster)
+}  // namespace
+
 // ---------------------------------------------------------------- hierarchy
 int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
   const int nc = H.nc, nb = nc * nc;
@@ -176,10 +317,34 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       if (!B.S32) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
     }
+    if (opts.store_bf16) {
+      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16))) return rc;
+      B.A16.v.bf16 = 1;
+      if (!B.S32) {
+        std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
+        B.S32 = halloc<float>(h, B.n * nb);
+        if (!B.S32) return fail(MG_ERR_OOM, "alloc");
+        CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
+      }
+    }
     h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
     if (l > 0) {
       if ((rc = upload_sell<float>(h, lv.P, &B.P))) return rc;
       if ((rc = upload_sell<float>(h, lv.R, &B.R))) return rc;
+      // per-component rows of partly fixed nodes (block problems)
+      auto partial_mask = [&](const HostLevel& X, const uint8_t** out) -> int {
+        const uint8_t all = (uint8_t)((1 << nc) - 1);
+        bool partial = false;
+        for (uint8_t m : X.fixmask) partial |= (m != 0 && m != all);
+        if (!partial) return MG_OK;
+        uint8_t* d = (uint8_t*)dev_alloc(h->ctx, h->allocs, h->bytes, X.fixmask.size(), true);
+        if (!d) return fail(MG_ERR_OOM, "alloc");
+        CU(cudaMemcpy(d, X.fixmask.data(), X.fixmask.size(), cudaMemcpyHostToDevice));
+        *out = d;
+        return MG_OK;
+      };
+      if ((rc = partial_mask(lv, &B.P.t.fix))) return rc;
+      if ((rc = partial_mask(H.levels[l - 1], &B.R.t.fix))) return rc;
     }
     // release host copies of what is now on the device
     if (l < nlev - 1) { lv.A = BlockCSR(); lv.leaves = LeafSet(); }
@@ -213,12 +378,17 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
   h->fixmask = (uint8_t*)dev_alloc(h->ctx, h->allocs, h->bytes, nn, true);
   if (!h->fixmask) return fail(MG_ERR_OOM, "alloc");
   CU(cudaMemcpy(h->fixmask, F.fixmask.data(), nn, cudaMemcpyHostToDevice));
+  {
+    std::vector<uint8_t> dm(nn);
+    for (int64_t i = 0; i < nn; ++i) dm[i] = F.topo.hanging[i] ? 0 : F.fixmask[i];
+    h->dirmask = (uint8_t*)dev_alloc(h->ctx, h->allocs, h->bytes, nn, true);
+    if (!h->dirmask) return fail(MG_ERR_OOM, "alloc");
+    CU(cudaMemcpy(h->dirmask, dm.data(), nn, cudaMemcpyHostToDevice));
+  }
+  if (H.lift.nnzb() > 0 && (rc = upload_sell<double>(h, H.lift, &h->Lift))) return rc;
   // tail: the largest prefix of levels (from the coarsest) with <= tail_rows dofs
-  h->tail_top = 0;
-  if (opts.tail_rows > 0)
-    for (int l = 1; l < nlev && l < kTailMax; ++l)
-      if (h->L[l].n * nc <= opts.tail_rows) h->tail_top = l;
-      else break;
+  h->tail_top = tail_top_for(h, opts.tail_rows);
+  h->tail_cluster = 1;
   return MG_OK;
 }
 
@@ -239,12 +409,12 @@ size_t workspace_bytes(const mg_hier* h) {
   for (const LevelMats& L : h->L) {
     const int64_t m = L.n * nc;
     if (h->has_fp64) b += 4 * rnd(m * 8);
-    if (h->has_fp32) b += 4 * rnd(m * 4);
+    if (h->has_fp32 || h->has_bf16) b += 4 * rnd(m * 4);
   }
   b += 12 * rnd(n * 8) + 3 * rnd(n * 4) + rnd(Q_NUM * kMaxRedBlocks * 8) + rnd(sizeof(KrylovState));
   if (h->gmres_m > 0) {
     const int64_t m = h->gmres_m;
-    b += rnd((m + 1) * n * 8) + (h->has_fp64 ? rnd(m * n * 8) : 0) + (h->has_fp32 ? rnd(m * n * 4) : 0) +
+    b += rnd((m + 1) * n * 8) + (h->has_fp64 ? rnd(m * n * 8) : 0) + (h->has_fp32 || h->has_bf16 ? rnd(m * n * 4) : 0) +
          rnd((m + 1) * kMaxRedBlocks * 8) + 8 * rnd((m + 1) * (m + 1) * 8);
   }
   return b;
@@ -263,7 +433,7 @@ int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
     LevelVecs& v = w->lv[l];
     const int64_t m = h->L[l].n * nc;
     if (h->has_fp64) { v.b64 = A8(m); v.o64 = A8(m); v.t64 = A8(m); v.r64 = A8(m); ok &= v.b64 && v.o64 && v.t64 && v.r64; }
-    if (h->has_fp32) { v.b32 = A4(m); v.o32 = A4(m); v.t32 = A4(m); v.r32 = A4(m); ok &= v.b32 && v.o32 && v.t32 && v.r32; }
+    if (h->has_fp32 || h->has_bf16) { v.b32 = A4(m); v.o32 = A4(m); v.t32 = A4(m); v.r32 = A4(m); ok &= v.b32 && v.o32 && v.t32 && v.r32; }
   }
   double** vecs[] = {&w->xi, &w->bi, &w->r, &w->p, &w->q, &w->z, &w->rhat, &w->sv, &w->t, &w->ph, &w->shat, &w->vcur};
   for (double** v : vecs) { *v = A8(n); ok &= *v != nullptr; }
@@ -281,9 +451,9 @@ int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
     G.part = A8((int64_t)(m + 1) * kMaxRedBlocks);
     G.V = A8((int64_t)(m + 1) * n);
     if (h->has_fp64) G.Z64 = A8((int64_t)m * n);
-    if (h->has_fp32) G.Z32 = A4((int64_t)m * n);
+    if (h->has_fp32 || h->has_bf16) G.Z32 = A4((int64_t)m * n);
     ok &= G.H && G.cs && G.sn && G.g && G.hv && G.y && G.zs && G.part && G.V && (!h->has_fp64 || G.Z64) &&
-          (!h->has_fp32 || G.Z32);
+          (!(h->has_fp32 || h->has_bf16) || G.Z32);
   }
   if (!ok) {
     free_list(c, w->allocs, w->bytes);
@@ -297,21 +467,20 @@ int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
   CU(cudaEventCreate(&w->ev0));
   CU(cudaEventCreate(&w->ev1));
   // tail parameters: matrices of the hierarchy, vectors of this workspace
-  for (int pi = 0; pi < 2; ++pi) {
-    TailParams& P = pi == 0 ? w->tail64 : w->tail32;
+  for (int pi = 0; pi < 3; ++pi) {
+    TailParams& P = pi == 0 ? w->tail64 : (pi == 1 ? w->tail32 : w->tail16);
     const bool d = pi == 0;
-    if (d ? !h->has_fp64 : !h->has_fp32) continue;
-    P.nt = h->tail_top + 1;
+    if (pi == 0 ? !h->has_fp64 : (pi == 1 ? !h->has_fp32 : !h->has_bf16)) continue;
     P.nu1 = h->opts.nu1;
     P.nu2 = h->opts.nu2;
     P.omega = h->opts.omega;
     P.cinv = h->coarse_inv;
     P.cn = h->coarse_n;
-    for (int l = 0; l <= h->tail_top; ++l) {
+    for (int l = 0; l < h->nlev && l < kTailMax; ++l) {
       LevelMats& B = h->L[l];
       LevelVecs& V = w->lv[l];
       TailLevel& T = P.lv[l];
-      T.A = d ? B.A64.v : B.A32.v;
+      T.A = d ? B.A64.v : (pi == 1 ? B.A32.v : B.A16.v);
       T.P = B.P.t;
       T.R = B.R.t;
       T.S = d ? (const void*)B.S64 : (const void*)B.S32;
@@ -321,6 +490,7 @@ int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
       T.r = d ? (void*)V.r64 : (void*)V.r32;
     }
   }
+  apply_tail(h, w.get());
   *out = w.release();
   return MG_OK;
 }
@@ -335,25 +505,94 @@ void ws_destroy(mg_hier* h, Workspace* w) {
   delete w;
 }
 
+int set_tail(mg_hier* h, int rows, int cluster) {
+  int top = tail_top_for(h, rows);
+  cluster = std::max(0, std::min(cluster, 8));
+  if (cluster == 0) {
+    top = staged_top_cap(h, top);
+    for (int pi = 0; pi < 3 && top > 0; ++pi) {
+      mg_hier::TailImage ti;
+      int rc;
+      if (has_slot(h, pi) && (rc = tail_image(h, pi, top, &ti))) return rc;
+    }
+  }
+  h->tail_top = top;
+  h->tail_cluster = cluster;
+  if (h->ws0) apply_tail(h, h->ws0);
+  std::lock_guard<std::mutex> lk(h->pool_mu);
+  for (Workspace* w : h->all_ws) apply_tail(h, w);
+  return MG_OK;
+}
+
+int autotune(mg_hier* h, int prec) {
+  std::vector<int64_t> key = {h->dim, h->nc, prec};
+  for (const LevelMats& L : h->L) key.push_back(L.n);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      return set_tail(h, it->second.first, it->second.second);
+    }
+  }
+  Workspace& w = *h->ws0;
+  cudaStream_t s = h->ctx->stream;
+  const int fine = h->nlev - 1;
+  const int rows_c[] = {0, 256, 1024, 4096, 16384, 65536};
+  const int cl_c[] = {1, 0, 2, 4, 8};   // 0: one CTA in shared memory
+  double best = 1e30;
+  int best_rows = 0, best_cl = 1, last_top = -1;
+  for (int rows : rows_c) {
+    const int top = tail_top_for(h, rows);
+    if (top == last_top) continue;      // same split as a smaller threshold
+    last_top = top;
+    for (int cl : cl_c) {
+      if (top == 0 && cl != 1) break;
+      int rc = set_tail(h, rows, cl);
+      if (rc) return rc;
+      auto once = [&]() {
+        if (prec == MG_FP64) enqueue_vcycle<double>(h, w, fine, w.r, w.z, nullptr, s);
+        else enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, nullptr, s, false, prec == MG_MIXED_BF16);
+      };
+      once();
+      CU(cudaEventRecord(w.ev0, s));
+      for (int i = 0; i < 8; ++i) once();
+      CU(cudaEventRecord(w.ev1, s));
+      CU(cudaEventSynchronize(w.ev1));
+      float ms = 0.0f;
+      CU(cudaEventElapsedTime(&ms, w.ev0, w.ev1));
+      CU(cudaGetLastError());
+      const double t = ms / 8.0;
+      if (t < best * 0.98) { best = t; best_rows = rows; best_cl = cl; }
+    }
+  }
+  int rc = set_tail(h, best_rows, best_cl);
+  if (rc) return rc;
+  h->tuned_vcycle_ms = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {best_rows, best_cl};
+  return MG_OK;
+}
+
 // ---------------------------------------------------------------- V-cycle
 // z = GMG(l, 0, b): the V-cycle of Algorithm "Geometric multigrid solver".
 // first_done: the first pre-smoothing sweep (from x = 0) was already written
 // into its buffer by the restriction kernel of the finer level.
 template <typename T>
-void enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
-                    bool first_done) {
+bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
+                    bool first_done, bool bf16, double* out64, const double* scale) {
   const int nc = h->nc;
   if (l == 0) {                                                  // Step 0
     launch_coarse<T>(h->coarse_inv, h->coarse_n, b, out, done, s);
     h->launch_count++;
-    return;
+    return false;
   }
-  if (l <= h->tail_top) {                                        // small levels: one CTA
-    launch_tail<T>(Prec<T>::tail(w), nc, b, out, first_done, done, s);
+  if (l <= h->tail_top) {                                        // small levels: one cluster
+    launch_tail<T>(bf16 ? w.tail16 : Prec<T>::tail(w), nc, b, out, first_done, done, s, out64, scale);
     h->launch_count++;
-    return;
+    return out64 != nullptr && h->opts.nu2 > 0;
   }
   LevelMats& L = h->L[l];
+  const SellView& AL = bf16 ? L.A16.v : Prec<T>::A(L);
   LevelVecs& V = w.lv[l];
   LevelMats& C = h->L[l - 1];
   LevelVecs& CV = w.lv[l - 1];
@@ -364,45 +603,52 @@ void enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
   for (int k = 0; k < nu1; ++k) {                                // Step 1
     T* dst = bufof(V, out, k);
     if (!(k == 0 && first_done)) {
-      launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
+      launch_smooth<T>(AL, nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
       h->launch_count++;
     }
     cur = dst;
   }
-  launch_residual<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::r(V), done, s);   // Step 2
+  launch_residual<T>(AL, nc, cur, b, Prec<T>::r(V), done, s);   // Step 2
   const bool fuse = l - 1 > 0;
   T* cfirst = fuse ? bufof(CV, Prec<T>::o(CV), 0) : nullptr;
   launch_restrict<T>(L.R.t, nc, Prec<T>::r(V), Prec<T>::b(CV), Prec<T>::S(C), cfirst, om, done, s);
   h->launch_count += 2;
-  enqueue_vcycle<T>(h, w, l - 1, Prec<T>::b(CV), Prec<T>::o(CV), done, s, fuse);   // Step 3
+  enqueue_vcycle<T>(h, w, l - 1, Prec<T>::b(CV), Prec<T>::o(CV), done, s, fuse, bf16);   // Step 3
   T* pdst = nu2 == 0 ? out : cur;                                                   // Step 4
   launch_prolong_add<T>(L.P.t, nc, Prec<T>::o(CV), cur, pdst, done, s);
   cur = pdst;
   h->launch_count++;
   for (int k = nu1; k < ns; ++k) {                               // Step 5
     T* dst = bufof(V, out, k);
-    launch_smooth<T>(Prec<T>::A(L), nc, cur, b, Prec<T>::S(L), dst, om, false, done, s);
+    const bool last = k == ns - 1;
+    launch_smooth<T>(AL, nc, cur, b, Prec<T>::S(L), dst, om, false, done, s, last ? out64 : nullptr,
+                     last ? scale : nullptr);
     cur = dst;
     h->launch_count++;
   }
+  return out64 != nullptr && nu2 > 0;
 }
-template void enqueue_vcycle<double>(mg_hier*, Workspace&, int, const double*, double*, const int*, cudaStream_t,
-                                     bool);
-template void enqueue_vcycle<float>(mg_hier*, Workspace&, int, const float*, float*, const int*, cudaStream_t, bool);
+template bool enqueue_vcycle<double>(mg_hier*, Workspace&, int, const double*, double*, const int*, cudaStream_t,
+                                     bool, bool, double*, const double*);
+template bool enqueue_vcycle<float>(mg_hier*, Workspace&, int, const float*, float*, const int*, cudaStream_t, bool,
+                                    bool, double*, const double*);
 
 // ---------------------------------------------------------------- Krylov
-enum { M_CG = 1, M_BICG = 2, M_GMRES = 3 };
+enum { M_CG = 1, M_BICG = 2, M_GMRES = 3, M_MGI = 4 };
 
 int method_of(const mg_hier* h) {
   int k = h->opts.krylov;
-  if (k == MG_KRYLOV_AUTO) k = (h->prob.kind == MG_TRANSPORT) ? MG_BICGSTAB : MG_CG;
+  if (k == MG_KRYLOV_AUTO)
+    k = h->prob.kind == MG_TRANSPORT ? MG_BICGSTAB : (h->prob.kind == MG_OSEEN ? MG_GMRES : MG_CG);
+  if (k == MG_MGITER) return M_MGI;
   return k == MG_BICGSTAB ? M_BICG : (k == MG_GMRES ? M_GMRES : M_CG);
 }
 
 int check_prec(const mg_hier* h, int prec) {
   if (prec == MG_FP64 && !h->has_fp64) return fail(MG_ERR_INVALID, "hierarchy built without FP64 level matrices");
   if (prec == MG_MIXED_FP32 && !h->has_fp32) return fail(MG_ERR_INVALID, "hierarchy built without FP32 level matrices");
-  if (prec != MG_FP64 && prec != MG_MIXED_FP32) return fail(MG_ERR_INVALID, "unsupported precision");
+  if (prec == MG_MIXED_BF16 && !h->has_bf16) return fail(MG_ERR_INVALID, "hierarchy built without BF16 level matrices");
+  if (prec != MG_FP64 && prec != MG_MIXED_FP32 && prec != MG_MIXED_BF16) return fail(MG_ERR_INVALID, "unsupported precision");
   return MG_OK;
 }
 
@@ -417,16 +663,33 @@ void enqueue_iteration(mg_hier* h, Workspace& w, int method, int prec, unsigned 
   const SellView& A = h->L[fine].A64.v;
   const int* done = &w.st->done;
   const bool mixed = prec != MG_FP64;
+  const bool bf16 = prec == MG_MIXED_BF16;
   if (cond) {
     launch_cond_reset(cond, s);
     h->launch_count++;
   }
-  if (method == M_CG) {
+  const double* scale = &w.st->scale;
+  if (method == M_MGI) {
+    // Algorithm "Geometric multigrid solver" as the solver: x <- x + GMG(0, b - A x)
     PVec z;
     if (mixed) {
       launch_to_f32(n, w.r, w.r32, w.st, s);
-      enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s);
-      z.f = w.ph32;
+      if (enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s, false, bf16, w.z, scale)) z.d = w.z;
+      else z.f = w.ph32;
+      h->launch_count++;
+    } else {
+      enqueue_vcycle<double>(h, w, fine, w.r, w.z, done, s);
+      z.d = w.z;
+    }
+    launch_mgi_update(n, z, w.xi, w.st, s);
+    launch_residual_norm(A, nc, w.xi, w.bi, w.r, w.part, w.st, 2, s, cond);
+    h->launch_count += 2;
+  } else if (method == M_CG) {
+    PVec z;
+    if (mixed) {
+      launch_to_f32(n, w.r, w.r32, w.st, s);
+      if (enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s, false, bf16, w.z, scale)) z.d = w.z;
+      else z.f = w.ph32;
       h->launch_count++;
     } else {
       enqueue_vcycle<double>(h, w, fine, w.r, w.z, done, s);
@@ -447,7 +710,7 @@ void enqueue_iteration(mg_hier* h, Workspace& w, int method, int prec, unsigned 
     if (mixed) gm.Z64 = nullptr;
     else gm.Z32 = nullptr;
     PVec z;
-    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s); z.f = w.ph32; }
+    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s, false, bf16); z.f = w.ph32; }
     else { enqueue_vcycle<double>(h, w, fine, w.vcur, w.z, done, s); z.d = w.z; }
     launch_gm_spmv(A, nc, z, w.q, gm, w.st, s);
     launch_gm_orth(n, w.q, gm, w.st, 0, w.part, s);
@@ -462,13 +725,23 @@ void enqueue_iteration(mg_hier* h, Workspace& w, int method, int prec, unsigned 
     // in mixed mode bicg_p / bicg_s also write the FP32 preconditioner input
     launch_bicg_p(n, w.r, w.t /* v */, w.p, mixed ? w.r32 : nullptr, w.st, s);
     PVec ph;
-    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s); ph.f = w.ph32; }
-    else { enqueue_vcycle<double>(h, w, fine, w.p, w.ph, done, s); ph.d = w.ph; }
+    if (mixed) {
+      if (enqueue_vcycle<float>(h, w, fine, w.r32, w.ph32, done, s, false, bf16, w.ph, scale)) ph.d = w.ph;
+      else ph.f = w.ph32;
+    } else {
+      enqueue_vcycle<double>(h, w, fine, w.p, w.ph, done, s);
+      ph.d = w.ph;
+    }
     launch_spmv_dot(A, nc, ph, w.rhat, w.t /* v */, w.part, Q_RHV, w.st, s);
     launch_bicg_s(n, w.r, w.t, w.sv, mixed ? w.r32 : nullptr, w.st, s);
     PVec sh;
-    if (mixed) { enqueue_vcycle<float>(h, w, fine, w.r32, w.sh32, done, s); sh.f = w.sh32; }
-    else { enqueue_vcycle<double>(h, w, fine, w.sv, w.shat, done, s); sh.d = w.shat; }
+    if (mixed) {
+      if (enqueue_vcycle<float>(h, w, fine, w.r32, w.sh32, done, s, false, bf16, w.shat, scale)) sh.d = w.shat;
+      else sh.f = w.sh32;
+    } else {
+      enqueue_vcycle<double>(h, w, fine, w.sv, w.shat, done, s);
+      sh.d = w.shat;
+    }
     launch_spmv_2dots(A, nc, sh, w.sv, w.q /* t */, w.part, w.st, s);
     launch_bicg_x(n, ph, sh, w.sv, w.q, w.rhat, w.xi, w.r, w.part, w.st, cond, s);
     h->launch_count += 5;

@@ -36,7 +36,7 @@ struct SellBuf {
 // Read-only matrices of one level.
 struct LevelMats {
   int64_t n = 0;              // nodes
-  SellBuf A64, A32, P, R;
+  SellBuf A64, A32, A16, P, R;   // A16: BF16-stored values
   double* S64 = nullptr;
   float* S32 = nullptr;
 };
@@ -64,7 +64,7 @@ struct Workspace {
   KrylovState* st = nullptr;
   KrylovState* st_host = nullptr;   // pinned mirror, written at the end of every round
   GmresView gm;
-  TailParams tail64, tail32;
+  TailParams tail64, tail32, tail16;
   std::vector<SolveGraph> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<Alloc> allocs;
@@ -123,9 +123,18 @@ struct mg_hier {
   int64_t coarse_n = 0;
   mgi::SellBuf F;                        // load matrix (finest)
   mgi::SellBuf Hc;                       // hanging rows of H (finest)
-  uint8_t* fixmask = nullptr;            // finest, per node
-  bool has_fp64 = true, has_fp32 = true;
-  int tail_top = 0;                      // levels 0..tail_top run in the single-CTA tail kernel
+  uint8_t* fixmask = nullptr;            // finest, per node: fixed-dof bits (hanging or Dirichlet)
+  uint8_t* dirmask = nullptr;            // finest, per node: Dirichlet bits
+  mgi::SellBuf Lift;                     // finest: free-row x Dirichlet-column couplings (n = 0: none)
+  bool has_fp64 = true, has_fp32 = true, has_bf16 = false;
+  int tail_top = 0;                      // levels 0..tail_top run in the tail kernel
+  int tail_cluster = 1;                  // 0: one CTA in shared memory, else cluster CTAs
+  struct TailImage {
+    void* p = nullptr;
+    uint32_t image_bytes = 0, smem = 0, staged_mask = 0;
+  };
+  std::map<std::pair<int, int>, TailImage> tail_img;   // (precision slot, top) -> shared-memory image
+  double tuned_vcycle_ms = 0.0;
   int gmres_m = 0;                       // > 0: workspaces carry GMRES(m) arrays
   mgi::Workspace* ws0 = nullptr;         // default workspace (mg_solve, mg_vcycle, mg_apply)
   std::mutex solve_mu;                   // guards ws0
@@ -146,11 +155,22 @@ size_t workspace_bytes(const mg_hier* h);
 int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out);
 void ws_destroy(mg_hier* h, Workspace* ws);
 int upload_hierarchy(mg_hier* h, HostHierarchy& H);
+// Tail threshold (levels <= rows dofs) and cluster size for every workspace;
+// cached solve graphs are dropped (they embed the old configuration).
+// cluster 0: one CTA with the tail in shared memory (the threshold is lowered
+// until its vectors fit).
+int set_tail(mg_hier* h, int rows, int cluster);
+// Time V-cycles over tail thresholds x cluster sizes, keep the fastest.
+int autotune(mg_hier* h, int prec);
 void free_hierarchy(mg_hier* h);
 
+// bf16 (T = float only): level operators with BF16-stored values.  out64
+// (optional): the result also in FP64 times *scale, written by the last sweep;
+// returns false when the cycle could not produce it (the caller then reads out).
 template <typename T>
-void enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
-                    bool first_done = false);
+bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
+                    bool first_done = false, bool bf16 = false, double* out64 = nullptr,
+                    const double* scale = nullptr);
 
 // Asynchronous solve: solve_start copies the inputs (device or host
 // pointers) into the workspace and enqueues the first round; a round ends

@@ -78,6 +78,7 @@ struct HostHierarchy {
   mg_opts opts{};
   std::vector<HostLevel> levels;    // [0] = coarsest
   BlockCSR load;                    // finest: b = load * f  (scalar, rows regular nodes)
+  BlockCSR lift;                    // finest: (H^T A H)[free rows, Dirichlet columns]
   std::vector<double> coarse_inv;   // dense (n0 nc)^2 inverse of A_0, row-major
   int64_t n_free = 0;
 };
@@ -85,7 +86,8 @@ struct HostHierarchy {
 Status validate_mesh(const mg_mesh& mesh, LeafSet* out);
 Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opts& opts, HostHierarchy* H);
 void build_topology(const LeafSet& leaves, Topology* T);
-bool coarsen_once(const LeafSet& fine, int min_level, LeafSet* coarse);
+bool coarsen_once(const LeafSet& fine, int min_level, bool patch, LeafSet* coarse);
+Status mesh_patches(const LeafSet& s, const Topology& T, std::vector<int64_t>* nodes, std::vector<int32_t>* clev);
 int default_min_level(const int macro[3], int dim);
 
 // ----------------------------------------------------------------- device side

@@ -10,11 +10,16 @@
 // writes one partial per block (fixed grid, fixed order inside the block),
 // the consuming kernel sums the partials in a fixed order.  No floating-point
 // atomics anywhere.
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -66,10 +71,28 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 // Vector loads: through the read-only path where the vector is constant for
 // the kernel's lifetime, plain (coherent) loads in the single-CTA tail kernel
 // that rewrites its vectors between __syncthreads().
-template <bool RO, typename T>
+// Load modes: 0 grid kernels (read-only path), 1 unstaged tail kernel (its
+// CTAs run on several SMs: vectors L2-coherent), 2 shared-memory-staged tail
+// kernel (plain generic loads, operands may sit in shared memory).
+template <int LM, typename T>
 __device__ __forceinline__ T vld(const T* p) {
-  if (RO) return __ldg(p);
+  if (LM == 0) return __ldg(p);
+  if (LM == 1) return __ldcg(p);
   return *p;
+}
+
+// Stored matrix values: float/double as they are, BF16 widened to FP32.
+// Matrix loads: read-only path in the grid kernels; plain generic loads in
+// the tail kernel, whose matrices may sit in shared memory.
+template <int LM, typename T>
+__device__ __forceinline__ T mld(const T* p) {
+  if (LM <= 1) return __ldg(p);       // matrices never change during a kernel
+  return *p;
+}
+template <typename AT, int LM = 0, typename VT>
+__device__ __forceinline__ AT ldv(const VT* p) {
+  if constexpr (std::is_same<VT, __nv_bfloat16>::value) return (AT)__bfloat162float(mld<LM>(p));
+  else return (AT)mld<LM>(p);
 }
 
 // y_row = sum_j A(row, j) x_j for a scalar SELL row (thread = row).  Slots
@@ -77,45 +100,46 @@ __device__ __forceinline__ T vld(const T* p) {
 // together, then the 4 gathers, then the FMAs in slot order); the slice width
 // is the same for the 32 threads of a warp, so the remainder switch is
 // warp-uniform.  The summation order is the plain sequential one.
-template <typename AT, bool RO = true, typename VT, typename XT>
+template <typename AT, int LM = 0, typename VT, typename XT>
 __device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                          const VT* __restrict__ val, int64_t slice, int lane,
                                          const XT* __restrict__ x) {
-  const int64_t s0 = __ldg(sptr + slice) + lane, s1 = __ldg(sptr + slice + 1);
+  const int64_t s0 = mld<LM>(sptr + slice) + lane, s1 = mld<LM>(sptr + slice + 1);
   AT acc = AT(0);
   int64_t o = s0;
   for (; o + 3 * 32 < s1; o += 4 * 32) {
-    const int c0 = __ldg(col + o), c1 = __ldg(col + o + 32), c2 = __ldg(col + o + 64), c3 = __ldg(col + o + 96);
-    const VT v0 = __ldg(val + o), v1 = __ldg(val + o + 32), v2 = __ldg(val + o + 64), v3 = __ldg(val + o + 96);
-    const XT x0 = vld<RO>(x + c0), x1 = vld<RO>(x + c1), x2 = vld<RO>(x + c2), x3 = vld<RO>(x + c3);
-    acc = fmad((AT)v0, (AT)x0, acc);
-    acc = fmad((AT)v1, (AT)x1, acc);
-    acc = fmad((AT)v2, (AT)x2, acc);
-    acc = fmad((AT)v3, (AT)x3, acc);
+    const int c0 = mld<LM>(col + o), c1 = mld<LM>(col + o + 32), c2 = mld<LM>(col + o + 64), c3 = mld<LM>(col + o + 96);
+    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32), v2 = ldv<AT, LM>(val + o + 64),
+             v3 = ldv<AT, LM>(val + o + 96);
+    const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2), x3 = vld<LM>(x + c3);
+    acc = fmad(v0, (AT)x0, acc);
+    acc = fmad(v1, (AT)x1, acc);
+    acc = fmad(v2, (AT)x2, acc);
+    acc = fmad(v3, (AT)x3, acc);
   }
   const int rem = (int)((s1 - o + 31) >> 5);   // 0..3, identical across the warp
   if (rem == 3) {
-    const int c0 = __ldg(col + o), c1 = __ldg(col + o + 32), c2 = __ldg(col + o + 64);
-    const VT v0 = __ldg(val + o), v1 = __ldg(val + o + 32), v2 = __ldg(val + o + 64);
-    const XT x0 = vld<RO>(x + c0), x1 = vld<RO>(x + c1), x2 = vld<RO>(x + c2);
-    acc = fmad((AT)v0, (AT)x0, acc);
-    acc = fmad((AT)v1, (AT)x1, acc);
-    acc = fmad((AT)v2, (AT)x2, acc);
+    const int c0 = mld<LM>(col + o), c1 = mld<LM>(col + o + 32), c2 = mld<LM>(col + o + 64);
+    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32), v2 = ldv<AT, LM>(val + o + 64);
+    const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2);
+    acc = fmad(v0, (AT)x0, acc);
+    acc = fmad(v1, (AT)x1, acc);
+    acc = fmad(v2, (AT)x2, acc);
   } else if (rem == 2) {
-    const int c0 = __ldg(col + o), c1 = __ldg(col + o + 32);
-    const VT v0 = __ldg(val + o), v1 = __ldg(val + o + 32);
-    const XT x0 = vld<RO>(x + c0), x1 = vld<RO>(x + c1);
-    acc = fmad((AT)v0, (AT)x0, acc);
-    acc = fmad((AT)v1, (AT)x1, acc);
+    const int c0 = mld<LM>(col + o), c1 = mld<LM>(col + o + 32);
+    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32);
+    const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1);
+    acc = fmad(v0, (AT)x0, acc);
+    acc = fmad(v1, (AT)x1, acc);
   } else if (rem == 1) {
-    acc = fmad((AT)__ldg(val + o), (AT)vld<RO>(x + __ldg(col + o)), acc);
+    acc = fmad(ldv<AT, LM>(val + o), (AT)vld<LM>(x + mld<LM>(col + o)), acc);
   }
   return acc;
 }
 
-template <typename T, bool RO = true>
+template <typename T, int LM = 0, typename VT = T>
 __device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x) {
-  return sell_dot1x<T, RO>(A.sptr, A.col, (const T*)A.val, slice, lane, x);
+  return sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x);
 }
 
 // acc[0..2] = sum_j A(row, j) x_j for a 3x3-block SELL row.
@@ -141,22 +165,22 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
   }
 }
 
-template <typename T, bool RO = true>
+template <typename T, int LM = 0, typename VT = T>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
                                           T acc[3]) {
-  const int64_t s0 = A.sptr[slice], s1 = A.sptr[slice + 1];
-  const T* __restrict__ val = (const T*)A.val;
+  const int64_t s0 = mld<LM>(A.sptr + slice), s1 = mld<LM>(A.sptr + slice + 1);
+  const VT* __restrict__ val = (const VT*)A.val;
   acc[0] = acc[1] = acc[2] = T(0);
   for (int64_t g = s0; g < s1; g += 32) {
-    const int c = __ldg(A.col + g + lane);
-    const T* __restrict__ v = val + g * 9 + lane;
-    const T x0 = vld<RO>(x + 3 * c), x1 = vld<RO>(x + 3 * c + 1), x2 = vld<RO>(x + 3 * c + 2);
+    const int c = mld<LM>(A.col + g + lane);
+    const VT* __restrict__ v = val + g * 9 + lane;
+    const T x0 = vld<LM>(x + 3 * c), x1 = vld<LM>(x + 3 * c + 1), x2 = vld<LM>(x + 3 * c + 2);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       T a = acc[i];
-      a = fmad(__ldg(v + (3 * i + 0) * 32), x0, a);
-      a = fmad(__ldg(v + (3 * i + 1) * 32), x1, a);
-      a = fmad(__ldg(v + (3 * i + 2) * 32), x2, a);
+      a = fmad(ldv<T, LM>(v + (3 * i + 0) * 32), x0, a);
+      a = fmad(ldv<T, LM>(v + (3 * i + 1) * 32), x1, a);
+      a = fmad(ldv<T, LM>(v + (3 * i + 2) * 32), x2, a);
       acc[i] = a;
     }
   }
@@ -164,10 +188,10 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
 
 // acc[c] += sum_j W(row, j) v[NC j + c] for a transfer matrix row: batches
 // of 4 slots (loads first), warp-uniform remainder, sequential summation.
-template <typename T, int NC, bool RO>
+template <typename T, int NC, int LM>
 __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t slice, int lane, const T* v,
                                                 T acc[NC]) {
-  const int64_t s0 = __ldg(W.sptr + slice) + lane, s1 = __ldg(W.sptr + slice + 1);
+  const int64_t s0 = mld<LM>(W.sptr + slice) + lane, s1 = mld<LM>(W.sptr + slice + 1);
   int64_t o = s0;
   for (; o < s1; o += 4 * 32) {
     const int m = (int)min((int64_t)4, (s1 - o + 31) >> 5);   // warp-uniform
@@ -175,13 +199,13 @@ __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t s
     float w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k < m) { j[k] = __ldg(W.col + o + 32 * k); w[k] = __ldg(W.w + o + 32 * k); }
+      if (k < m) { j[k] = mld<LM>(W.col + o + 32 * k); w[k] = mld<LM>(W.w + o + 32 * k); }
     T xv[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (k < m)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) xv[k][c] = vld<RO>(v + (int64_t)NC * j[k] + c);
+        for (int c = 0; c < NC; ++c) xv[k][c] = vld<LM>(v + (int64_t)NC * j[k] + c);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (k < m)
@@ -194,54 +218,54 @@ __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t s
 // One row (block row) of each level step.  The grid kernels below and the
 // single-CTA tail kernel call the same functions, so both produce bitwise
 // identical results.
-template <typename T, int NC, bool RO>
+template <typename T, int NC, int LM, typename VT = T>
 __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const T* x, const T* b, const T* Sinv,
                                            T* xo, T omega, bool from_zero) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   if (NC == 1) {
-    T r = from_zero ? T(0) : sell_dot1<T, RO>(A, slice, lane, x);
+    T r = from_zero ? T(0) : sell_dot1<T, LM, VT>(A, slice, lane, x);
     if (row < A.n) {
-      const T bi = vld<RO>(b + row);
+      const T bi = vld<LM>(b + row);
       if (from_zero) xo[row] = omega * Sinv[row] * bi;
-      else xo[row] = fmad(omega * Sinv[row], bi - r, vld<RO>(x + row));
+      else xo[row] = fmad(omega * Sinv[row], bi - r, vld<LM>(x + row));
     }
   } else {
     T acc[3] = {T(0), T(0), T(0)};
-    if (!from_zero) sell_dot3<T, RO>(A, slice, lane, x, acc);
+    if (!from_zero) sell_dot3<T, LM, VT>(A, slice, lane, x, acc);
     if (row < A.n) {
       T res[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) res[i] = vld<RO>(b + 3 * row + i) - acc[i];
+      for (int i = 0; i < 3; ++i) res[i] = vld<LM>(b + 3 * row + i) - acc[i];
       const T* S = Sinv + 9 * row;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         T c = S[3 * i] * res[0];
         c = fmad(S[3 * i + 1], res[1], c);
         c = fmad(S[3 * i + 2], res[2], c);
-        xo[3 * row + i] = from_zero ? omega * c : fmad(omega, c, vld<RO>(x + 3 * row + i));
+        xo[3 * row + i] = from_zero ? omega * c : fmad(omega, c, vld<LM>(x + 3 * row + i));
       }
     }
   }
 }
 
-template <typename T, int NC, bool RO>
+template <typename T, int NC, int LM, typename VT = T>
 __device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   if (NC == 1) {
-    T r = sell_dot1<T, RO>(A, slice, lane, x);
-    if (row < A.n) y[row] = vld<RO>(b + row) - r;
+    T r = sell_dot1<T, LM, VT>(A, slice, lane, x);
+    if (row < A.n) y[row] = vld<LM>(b + row) - r;
   } else {
     T acc[3];
-    sell_dot3<T, RO>(A, slice, lane, x, acc);
+    sell_dot3<T, LM, VT>(A, slice, lane, x, acc);
     if (row < A.n)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) y[3 * row + i] = vld<RO>(b + 3 * row + i) - acc[i];
+      for (int i = 0; i < 3; ++i) y[3 * row + i] = vld<LM>(b + 3 * row + i) - acc[i];
   }
 }
 
-template <typename T, int NC, bool RO>
+template <typename T, int NC, int LM>
 __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row, const T* r, T* d, const T* Sinv,
                                              T* x0, T omega) {
   const int64_t slice = row >> 5;
@@ -249,8 +273,15 @@ __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row,
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
-  transfer_gather<T, NC, RO>(R, slice, lane, r, acc);
+  transfer_gather<T, NC, LM>(R, slice, lane, r, acc);
   if (row < R.n) {
+    if constexpr (NC > 1)
+      if (R.fix) {
+        const unsigned m = mld<LM>(R.fix + row);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if ((m >> c) & 1u) acc[c] = T(0);
+      }
 #pragma unroll
     for (int c = 0; c < NC; ++c) d[NC * row + c] = acc[c];
     if (x0) {
@@ -270,33 +301,49 @@ __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row,
   }
 }
 
-template <typename T, int NC, bool RO>
+template <typename T, int NC, int LM>
 __device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, const T* y, const T* xin, T* xo) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
-  transfer_gather<T, NC, RO>(P, slice, lane, y, acc);
-  if (row < P.n)
+  transfer_gather<T, NC, LM>(P, slice, lane, y, acc);
+  if (row < P.n) {
+    if constexpr (NC > 1)
+      if (P.fix) {
+        const unsigned m = mld<LM>(P.fix + row);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) xo[NC * row + c] = vld<RO>(xin + NC * row + c) + acc[c];
+        for (int c = 0; c < NC; ++c)
+          if ((m >> c) & 1u) acc[c] = T(0);
+      }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) xo[NC * row + c] = vld<LM>(xin + NC * row + c) + acc[c];
+  }
 }
 
 // ------------------------------------------------------------------ level ops
 // x_out = x + omega S (b - A x)  (Sec. 4.1.4), S = inverse diagonal block.
-template <typename T, int NC, bool FROM_ZERO>
+// xo64 (optional): the sweep's output also written in FP64 times *scale (the
+// last sweep of an FP32 V-cycle hands the FP64 Krylov loop its result).
+template <typename T, typename VT, int NC, bool FROM_ZERO>
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, const T* __restrict__ x, const T* __restrict__ b,
                                                     const T* __restrict__ Sinv, T* __restrict__ xo, T omega,
-                                                    const int* done) {
+                                                    const int* done, double* __restrict__ xo64,
+                                                    const double* scale) {
   pdl_wait();
   if (stopped(done)) return;
+  const double sc = xo64 ? *scale : 1.0;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads)
-    row_smooth<T, NC, true>(A, row, x, b, Sinv, xo, omega, FROM_ZERO);
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
+    row_smooth<T, NC, 0, VT>(A, row, x, b, Sinv, xo, omega, FROM_ZERO);
+    if (xo64 && row < A.n)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xo64[NC * row + c] = (double)xo[NC * row + c] * sc;
+  }
 }
 
-template <typename T, int NC, int MODE>   // MODE 0: y = A x; 1: y = b - A x
+template <typename T, typename VT, int NC, int MODE>   // MODE 0: y = A x; 1: y = b - A x
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ y, const int* done) {
   pdl_wait();
@@ -304,17 +351,17 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, c
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     if (MODE == 1) {
-      row_residual<T, NC, true>(A, row, x, b, y);
+      row_residual<T, NC, 0, VT>(A, row, x, b, y);
       continue;
     }
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
     if (NC == 1) {
-      T r = sell_dot1<T>(A, slice, lane, x);
+      T r = sell_dot1<T, 0, VT>(A, slice, lane, x);
       if (row < A.n) y[row] = r;
     } else {
       T acc[3];
-      sell_dot3<T>(A, slice, lane, x, acc);
+      sell_dot3<T, 0, VT>(A, slice, lane, x, acc);
       if (row < A.n)
 #pragma unroll
         for (int i = 0; i < 3; ++i) y[3 * row + i] = acc[i];
@@ -333,7 +380,7 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_restrict(TransferVi
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < R.nslices * 32; row += nthreads)
-    row_restrict<T, NC, true>(R, row, r, d, Sinv, S0 ? x0 : nullptr, omega);
+    row_restrict<T, NC, 0>(R, row, r, d, Sinv, S0 ? x0 : nullptr, omega);
 }
 
 // x_out_i = x_in_i + sum_j P(i,j) y_j   (Algorithm "Geometric multigrid solver", Step 4)
@@ -344,76 +391,137 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_prolong(TransferVie
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < P.nslices * 32; row += nthreads)
-    row_prolong<T, NC, true>(P, row, y, xin, xo);
+    row_prolong<T, NC, 0>(P, row, y, xin, xo);
 }
 
-// The V-cycle below (and including) level `nt - 1` in one CTA: every step of
-// Algorithm "Geometric multigrid solver" for the small levels, separated by
-// __syncthreads() instead of kernel boundaries.  Same row functions as the
-// grid kernels, so the result is bitwise identical to the multi-kernel cycle.
-template <typename T, int NC>
+// The V-cycle below (and including) level `nt - 1` in one launch: every step
+// of Algorithm "Geometric multigrid solver" for the small levels, separated
+// by block or cluster barriers instead of kernel boundaries.  Same row
+// functions as the grid kernels, so the result is bitwise identical to the
+// multi-kernel cycle.
+//   TLM 1: one thread-block cluster of gridDim.x CTAs over the device arrays;
+//          barriers are hardware cluster barriers (release/acquire at cluster
+//          scope) and vectors are read with L2-coherent loads.
+//   TLM 2: one CTA whose vectors (and the matrices of the staged levels) live
+//          in dynamic shared memory, copied from the tail image at start; each
+//          step then runs at shared-memory latency instead of L2 latency.
+__device__ __forceinline__ void tail_sync() {
+  if (gridDim.x > 1) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void block_copy(T* dst, const T* src, int64_t n) {
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+template <typename T, typename VT, int NC, int TLM>
 __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* btop, T* otop, int first_done,
-                                                        const int* done) {
+                                                        const int* done, double* o64, const double* scale) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  const int top = P.nt - 1, ns = P.nu1 + P.nu2;
+  const TailLevel* LV = P.lv;
+  if constexpr (TLM == 2) {
+    // the image holds only matrices and offsets: copy it before waiting on
+    // the preceding kernel
+    const uint4* src = (const uint4*)P.image;
+    uint4* dst = (uint4*)tail_smem;
+    for (uint32_t i = threadIdx.x; i < P.image_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    TailLevel* hdr = (TailLevel*)tail_smem;
+    for (int l = threadIdx.x; l < P.nt; l += blockDim.x) {
+      TailLevel& L = hdr[l];
+      auto at = [&](const void* off) -> unsigned char* { return tail_smem + (uintptr_t)off; };
+      L.b = at(L.b); L.o = at(L.o); L.t = at(L.t); L.r = at(L.r);
+      if ((P.staged_mask >> l) & 1u) {
+        L.A.sptr = (const int64_t*)at(L.A.sptr);
+        L.A.col = (const int32_t*)at(L.A.col);
+        L.A.val = at(L.A.val);
+        L.S = at(L.S);
+        if (l > 0) {
+          L.P.sptr = (const int64_t*)at(L.P.sptr); L.P.col = (const int32_t*)at(L.P.col); L.P.w = (const float*)at(L.P.w);
+          L.R.sptr = (const int64_t*)at(L.R.sptr); L.R.col = (const int32_t*)at(L.R.col); L.R.w = (const float*)at(L.R.w);
+        }
+      }
+    }
+    LV = hdr;
+  }
   pdl_wait();
   if (stopped(done)) return;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int top = P.nt - 1, ns = P.nu1 + P.nu2;
+  if constexpr (TLM == 2) {
+    __syncthreads();
+    const int64_t m = LV[top].A.n * NC;
+    block_copy((T*)LV[top].b, btop, m);
+    if (first_done && P.nu1 > 0) {   // first pre-smoothing sweep, written by the finer level's restriction
+      const bool in_o = (ns - 1) % 2 == 0;
+      block_copy((T*)(in_o ? LV[top].o : LV[top].t), in_o ? (const T*)otop : (const T*)P.lv[top].t, m);
+    }
+    __syncthreads();
+  }
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   const T om = (T)P.omega;
   T* cur_of[kTailMax];
-  auto bvec = [&](int l) -> T* { return l == top ? const_cast<T*>(btop) : (T*)P.lv[l].b; };
-  auto ovec = [&](int l) -> T* { return l == top ? otop : (T*)P.lv[l].o; };
-  auto bufof = [&](int l, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? ovec(l) : (T*)P.lv[l].t; };
+  auto bvec = [&](int l) -> T* { return (TLM == 1 && l == top) ? const_cast<T*>(btop) : (T*)LV[l].b; };
+  auto ovec = [&](int l) -> T* { return (TLM == 1 && l == top) ? otop : (T*)LV[l].o; };
+  auto bufof = [&](int l, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? ovec(l) : (T*)LV[l].t; };
   int fdone = first_done;
   for (int l = top; l >= 1; --l) {
-    const TailLevel& L = P.lv[l];
+    const TailLevel& L = LV[l];
     const T* S = (const T*)L.S;
     T* cur = nullptr;
     for (int k = 0; k < P.nu1; ++k) {
       T* dst = bufof(l, k);
       if (!(k == 0 && fdone)) {
         for (int64_t row = tid; row < L.A.nslices * 32; row += nth)
-          row_smooth<T, NC, false>(L.A, row, cur, bvec(l), S, dst, om, k == 0);
-        __syncthreads();
+          row_smooth<T, NC, TLM, VT>(L.A, row, cur, bvec(l), S, dst, om, k == 0);
+        tail_sync();
       }
       cur = dst;
     }
-    for (int64_t row = tid; row < L.A.nslices * 32; row += nth) row_residual<T, NC, false>(L.A, row, cur, bvec(l), (T*)L.r);
-    __syncthreads();
+    for (int64_t row = tid; row < L.A.nslices * 32; row += nth) row_residual<T, NC, TLM, VT>(L.A, row, cur, bvec(l), (T*)L.r);
+    tail_sync();
     T* x0 = l - 1 > 0 ? bufof(l - 1, 0) : nullptr;
     for (int64_t row = tid; row < L.R.nslices * 32; row += nth)
-      row_restrict<T, NC, false>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)P.lv[l - 1].S, x0, om);
-    __syncthreads();
+      row_restrict<T, NC, TLM>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)LV[l - 1].S, x0, om);
+    tail_sync();
     fdone = l - 1 > 0;
     cur_of[l] = cur;
   }
   {   // coarse direct solve, one warp per row
-    const int lane = tid & 31;
+    const int lane = threadIdx.x & 31;
     const T* d = bvec(0);
     T* z = ovec(0);
     for (int64_t row = tid >> 5; row < P.cn; row += nth >> 5) {
       double acc = 0.0;
-      for (int64_t j = lane; j < P.cn; j += 32) acc = fma(P.cinv[row * P.cn + j], (double)d[j], acc);
+      for (int64_t j = lane; j < P.cn; j += 32) acc = fma(P.cinv[row * P.cn + j], (double)vld<TLM>(d + j), acc);
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) z[row] = (T)acc;
     }
-    __syncthreads();
+    tail_sync();
   }
   for (int l = 1; l <= top; ++l) {
-    const TailLevel& L = P.lv[l];
+    const TailLevel& L = LV[l];
     T* cur = cur_of[l];
     T* pdst = P.nu2 == 0 ? ovec(l) : cur;
     for (int64_t row = tid; row < L.P.nslices * 32; row += nth)
-      row_prolong<T, NC, false>(L.P, row, ovec(l - 1), cur, pdst);
-    __syncthreads();
+      row_prolong<T, NC, TLM>(L.P, row, ovec(l - 1), cur, pdst);
+    tail_sync();
     cur = pdst;
     for (int k = P.nu1; k < ns; ++k) {
       T* dst = bufof(l, k);
-      for (int64_t row = tid; row < L.A.nslices * 32; row += nth)
-        row_smooth<T, NC, false>(L.A, row, cur, bvec(l), (const T*)L.S, dst, om, false);
-      __syncthreads();
+      const bool out64 = o64 && l == top && k == ns - 1;   // last sweep: also the FP64 copy times *scale
+      const double sc = out64 ? *scale : 1.0;
+      for (int64_t row = tid; row < L.A.nslices * 32; row += nth) {
+        row_smooth<T, NC, TLM, VT>(L.A, row, cur, bvec(l), (const T*)L.S, dst, om, false);
+        if (out64 && row < L.A.n)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) o64[NC * row + c] = (double)dst[NC * row + c] * sc;
+      }
+      tail_sync();
       cur = dst;
     }
   }
+  if constexpr (TLM == 2) block_copy(otop, (const T*)LV[top].o, LV[top].A.n * NC);
 }
 
 // z = A_0^{-1} d with the FP64 inverse of the coarse matrix; one warp per row.
@@ -433,8 +541,10 @@ __global__ void __launch_bounds__(kBlock) k_coarse(const double* __restrict__ Ai
 }
 
 // ------------------------------------------------------------------ vectors
+// b = H^T (F f) on free dofs; Dirichlet dofs take g (0 without g), hanging
+// dofs 0.  fix: fixed-dof bits per node, dir: Dirichlet bits per node.
 __global__ void k_rhs(SellView F, int nc, const double* __restrict__ f, const uint8_t* __restrict__ fix,
-                      double* __restrict__ b) {
+                      const uint8_t* __restrict__ dir, const double* __restrict__ g, double* __restrict__ b) {
   pdl_wait();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < F.nslices * 32; row += nthreads) {
@@ -448,7 +558,39 @@ __global__ void k_rhs(SellView F, int nc, const double* __restrict__ f, const ui
       for (int c = 0; c < nc; ++c) acc[c] = fma(w, f[(int64_t)nc * j + c], acc[c]);
     }
     if (row < F.n)
-      for (int c = 0; c < nc; ++c) b[nc * row + c] = ((fix[row] >> c) & 1) ? 0.0 : acc[c];
+      for (int c = 0; c < nc; ++c) {
+        double v = acc[c];
+        if ((dir[row] >> c) & 1) v = g ? g[nc * row + c] : 0.0;
+        else if ((fix[row] >> c) & 1) v = 0.0;
+        b[nc * row + c] = v;
+      }
+  }
+}
+
+// b -= Lift g on the free dofs: Lift holds the couplings of free rows to
+// Dirichlet columns of the condensed operator (symmetric elimination).
+template <int NC>
+__global__ void k_lift(SellView L, const double* __restrict__ g, double* __restrict__ b) {
+  pdl_wait();
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < L.nslices * 32; row += nthreads) {
+    const int64_t slice = row >> 5;
+    const int lane = (int)(row & 31);
+    const double* val = (const double*)L.val;
+    double acc[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) acc[i] = 0.0;
+    for (int64_t o = L.sptr[slice] + lane; o < L.sptr[slice + 1]; o += 32) {
+      const int64_t j = L.col[o];
+      const int64_t vb = (o - lane) * NC * NC + lane;
+#pragma unroll
+      for (int i = 0; i < NC; ++i)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[i] = fma(val[vb + (int64_t)(i * NC + k) * 32], g[NC * j + k], acc[i]);
+    }
+    if (row < L.n)
+#pragma unroll
+      for (int i = 0; i < NC; ++i) b[NC * row + i] -= acc[i];
   }
 }
 
@@ -548,13 +690,19 @@ __device__ bool reduce_partials(double* part, int nq, const int* q, const double
   return true;
 }
 
-// r = b - A x and ||r||^2; with test != 0 the initial convergence test runs
+// r = b - A x and ||r||^2; test 1: initial convergence test; test 2: end of
+// an iteration of the multigrid solver (counts it, sets the loop condition)
 template <int NC>
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_residual_norm(SellView A, const double* __restrict__ x,
                                                            const double* __restrict__ b, double* __restrict__ r,
-                                                           double* part, KrylovState* st, int test) {
+                                                           double* part, KrylovState* st, int test,
+                                                           unsigned long long cond) {
   __shared__ double sh[40];
   pdl_wait();
+  if (test == 2 && st->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
@@ -571,7 +719,28 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_residual_norm(SellV
     }
   }
   const int q[1] = {Q_RR};
-  if (reduce_partials(part, 1, q, &acc, st, sh) && test && threadIdx.x == 0) converge_step(st, false, 0ull);
+  if (reduce_partials(part, 1, q, &acc, st, sh) && test && threadIdx.x == 0) converge_step(st, test == 2, cond);
+}
+
+// x += z (z = preconditioner output, FP64 or FP32 times st->scale)
+__global__ void __launch_bounds__(kBlock) k_mgi_update(int64_t n, PVec z, double* __restrict__ x, KrylovState* st) {
+  pdl_wait();
+  if (st->done) return;
+  const double sc = st->scale;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
+    double zi[4], xi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) { zi[k] = pv(z, j, sc); xi[k] = x[j]; }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = i + k * nthreads;
+      if (j < n) x[j] = xi[k] + zi[k];
+    }
+  }
 }
 
 // ||b_free||^2 and the initial state of the Krylov loop
@@ -1164,29 +1333,59 @@ static int grid_sell(int64_t nslices) { return grid_for_rows(nslices * 32); }
 
 template <typename T>
 void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* Sinv, T* xo, double omega,
-                   bool from_zero, const int* done, cudaStream_t s) {
+                   bool from_zero, const int* done, cudaStream_t s, double* xo64, const double* scale) {
   const int g = grid_sell(A.nslices);
+  const T om = (T)omega;
+  if constexpr (std::is_same<T, float>::value) {
+    if (A.bf16) {
+      using V = __nv_bfloat16;
+      if (nc == 1) {
+        if (from_zero) launch(k_smooth<T, V, 1, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+        else launch(k_smooth<T, V, 1, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+      } else {
+        if (from_zero) launch(k_smooth<T, V, 3, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+        else launch(k_smooth<T, V, 3, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+      }
+      return;
+    }
+  }
   if (nc == 1) {
-    if (from_zero) launch(k_smooth<T, 1, true>, g, s, A, x, b, Sinv, xo, (T)omega, done);
-    else launch(k_smooth<T, 1, false>, g, s, A, x, b, Sinv, xo, (T)omega, done);
+    if (from_zero) launch(k_smooth<T, T, 1, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+    else launch(k_smooth<T, T, 1, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
   } else {
-    if (from_zero) launch(k_smooth<T, 3, true>, g, s, A, x, b, Sinv, xo, (T)omega, done);
-    else launch(k_smooth<T, 3, false>, g, s, A, x, b, Sinv, xo, (T)omega, done);
+    if (from_zero) launch(k_smooth<T, T, 3, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+    else launch(k_smooth<T, T, 3, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
   }
 }
 
 template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s) {
   const int g = grid_sell(A.nslices);
-  if (nc == 1) launch(k_apply<T, 1, 1>, g, s, A, x, b, r, done);
-  else launch(k_apply<T, 3, 1>, g, s, A, x, b, r, done);
+  if constexpr (std::is_same<T, float>::value) {
+    if (A.bf16) {
+      using V = __nv_bfloat16;
+      if (nc == 1) launch(k_apply<T, V, 1, 1>, g, s, A, x, b, r, done);
+      else launch(k_apply<T, V, 3, 1>, g, s, A, x, b, r, done);
+      return;
+    }
+  }
+  if (nc == 1) launch(k_apply<T, T, 1, 1>, g, s, A, x, b, r, done);
+  else launch(k_apply<T, T, 3, 1>, g, s, A, x, b, r, done);
 }
 
 template <typename T>
 void launch_matvec(const SellView& A, int nc, const T* x, T* y, const int* done, cudaStream_t s) {
   const int g = grid_sell(A.nslices);
-  if (nc == 1) launch(k_apply<T, 1, 0>, g, s, A, x, nullptr, y, done);
-  else launch(k_apply<T, 3, 0>, g, s, A, x, nullptr, y, done);
+  if constexpr (std::is_same<T, float>::value) {
+    if (A.bf16) {
+      using V = __nv_bfloat16;
+      if (nc == 1) launch(k_apply<T, V, 1, 0>, g, s, A, x, (const T*)nullptr, y, done);
+      else launch(k_apply<T, V, 3, 0>, g, s, A, x, (const T*)nullptr, y, done);
+      return;
+    }
+  }
+  if (nc == 1) launch(k_apply<T, T, 1, 0>, g, s, A, x, (const T*)nullptr, y, done);
+  else launch(k_apply<T, T, 3, 0>, g, s, A, x, (const T*)nullptr, y, done);
 }
 
 template <typename T>
@@ -1220,7 +1419,7 @@ void launch_coarse(const double* Ainv, int64_t n, const T* d, T* z, const int* d
 
 #define MGI_INST(T)                                                                                                \
   template void launch_smooth<T>(const SellView&, int, const T*, const T*, const T*, T*, double, bool, const int*, \
-                                 cudaStream_t);                                                                    \
+                                 cudaStream_t, double*, const double*);                                            \
   template void launch_residual<T>(const SellView&, int, const T*, const T*, T*, const int*, cudaStream_t);        \
   template void launch_matvec<T>(const SellView&, int, const T*, T*, const int*, cudaStream_t);                    \
   template void launch_restrict<T>(const TransferView&, int, const T*, T*, const T*, T*, double, const int*,       \
@@ -1231,26 +1430,79 @@ MGI_INST(double)
 MGI_INST(float)
 #undef MGI_INST
 
-template <typename T>
-void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(1);
-  cfg.blockDim = dim3(kTailThreads);
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = g_pdl ? 1 : 0;
-  const int fd = first_done ? 1 : 0;
-  if (nc == 1) cudaLaunchKernelEx(&cfg, k_tail<T, 1>, P, b, out, fd, done);
-  else cudaLaunchKernelEx(&cfg, k_tail<T, 3>, P, b, out, fd, done);
+template <typename T, typename V, int NC, int TLM>
+void launch_tail_k(cudaLaunchConfig_t& cfg, const TailParams& P, const T* b, T* out, int fd, const int* done,
+                   double* o64, const double* scale) {
+  if constexpr (TLM == 2) {
+    static std::once_flag once;   // opt in to the large dynamic shared memory, once per instantiation
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(k_tail<T, V, NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    });
+  }
+  cudaLaunchKernelEx(&cfg, k_tail<T, V, NC, TLM>, P, b, out, fd, done, o64, scale);
 }
-template void launch_tail<double>(const TailParams&, int, const double*, double*, bool, const int*, cudaStream_t);
-template void launch_tail<float>(const TailParams&, int, const float*, float*, bool, const int*, cudaStream_t);
 
-void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, double* b, cudaStream_t s) {
-  launch(k_rhs, grid_sell(F.nslices), s, F, nc, f, fixmask, b);
+template <typename T, typename V>
+void launch_tail_v(cudaLaunchConfig_t& cfg, const TailParams& P, int nc, const T* b, T* out, int fd, const int* done,
+                   double* o64, const double* scale) {
+  const bool staged = P.cluster == 0;
+  if (nc == 1) {
+    if (staged) launch_tail_k<T, V, 1, 2>(cfg, P, b, out, fd, done, o64, scale);
+    else launch_tail_k<T, V, 1, 1>(cfg, P, b, out, fd, done, o64, scale);
+  } else {
+    if (staged) launch_tail_k<T, V, 3, 2>(cfg, P, b, out, fd, done, o64, scale);
+    else launch_tail_k<T, V, 3, 1>(cfg, P, b, out, fd, done, o64, scale);
+  }
+}
+
+template <typename T>
+void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s,
+                 double* o64, const double* scale) {
+  const bool staged = P.cluster == 0;
+  const int cl = staged ? 1 : P.cluster;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cl);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = staged ? P.smem : 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (!staged) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = (unsigned)cl;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (g_pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  const int fd = first_done ? 1 : 0;
+  if constexpr (std::is_same<T, float>::value) {
+    if (P.lv[0].A.bf16) {
+      launch_tail_v<T, __nv_bfloat16>(cfg, P, nc, b, out, fd, done, o64, scale);
+      return;
+    }
+  }
+  launch_tail_v<T, T>(cfg, P, nc, b, out, fd, done, o64, scale);
+}
+template void launch_tail<double>(const TailParams&, int, const double*, double*, bool, const int*, cudaStream_t,
+                                  double*, const double*);
+template void launch_tail<float>(const TailParams&, int, const float*, float*, bool, const int*, cudaStream_t,
+                                 double*, const double*);
+
+void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, const uint8_t* dirmask,
+                const double* g, double* b, cudaStream_t s) {
+  launch(k_rhs, grid_sell(F.nslices), s, F, nc, f, fixmask, dirmask, g, b);
+}
+void launch_lift(const SellView& L, int nc, const double* g, double* b, cudaStream_t s) {
+  if (L.n == 0) return;
+  if (nc == 1) launch(k_lift<1>, grid_sell(L.nslices), s, L, g, b);
+  else launch(k_lift<3>, grid_sell(L.nslices), s, L, g, b);
 }
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s) {
   launch(k_fill_hanging, grid_sell(Hc.nslices), s, Hc, nc, x);
@@ -1260,11 +1512,12 @@ void launch_copy_fixed(int64_t n, int nc, const uint8_t* fixmask, const double* 
   launch(k_copy_fixed, grid_for_rows(n), s, n, nc, fixmask, b, xin, x);
 }
 void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
-                          KrylovState* st, int test, cudaStream_t s) {
+                          KrylovState* st, int test, cudaStream_t s, unsigned long long cond) {
   const int g = grid_sell(A64.nslices);
-  if (nc == 1) launch(k_residual_norm<1>, g, s, A64, x, b, r, part.p, st, test);
-  else launch(k_residual_norm<3>, g, s, A64, x, b, r, part.p, st, test);
+  if (nc == 1) launch(k_residual_norm<1>, g, s, A64, x, b, r, part.p, st, test, cond);
+  else launch(k_residual_norm<3>, g, s, A64, x, b, r, part.p, st, test, cond);
 }
+
 void launch_norm_init(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, Partials part,
                       KrylovState* st, double rtol, int max_it, cudaStream_t s) {
   launch(k_norm_init, grid_for_rows(n_nodes), s, n_nodes, nc, fixmask, b, part.p, st, rtol, max_it);
@@ -1272,6 +1525,9 @@ void launch_norm_init(int64_t n_nodes, int nc, const uint8_t* fixmask, const dou
 static int grid_vec4(int64_t n) {  // 4 entries per thread (k_bicg_x: 2, capped grid)
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
+}
+void launch_mgi_update(int64_t n, PVec z, double* x, KrylovState* st, cudaStream_t s) {
+  launch(k_mgi_update, grid_vec4(n), s, n, z, x, st);
 }
 void launch_to_f32(int64_t n, const double* v, float* v32, const KrylovState* st, cudaStream_t s) {
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);

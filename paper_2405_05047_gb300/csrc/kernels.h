@@ -21,15 +21,20 @@ struct SellView {
   const void* val = nullptr;
   int64_t n = 0;          // block rows
   int64_t nslices = 0;
+  int bf16 = 0;           // values stored as BF16 (read by the FP32 kernels, widened to FP32)
 };
 
-// Transfer matrices (P, R) are scalar SELL with float weights.
+// Transfer matrices (P, R) are scalar SELL with float weights, applied to
+// every component.  fix (block problems with partly fixed nodes, else NULL):
+// per row node the bits of the components whose output stays untouched (P)
+// or zero (R) -- the per-component rows of the constrained dofs.
 struct TransferView {
   const int64_t* sptr = nullptr;
   const int32_t* col = nullptr;
   const float* w = nullptr;
   int64_t n = 0;
   int64_t nslices = 0;
+  const uint8_t* fix = nullptr;
 };
 
 // Scalars of the Krylov loop, resident in device memory.
@@ -71,9 +76,11 @@ int grid_for_rows(int64_t rows);       // blocks for one thread per row, capped 
 int grid_for_vec(int64_t n);
 
 // ---- level operators (T = double or float; nc = 1 or 3) --------------------
+// xo64 (optional): FP64 copy of the output times *scale
 template <typename T>
 void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* Sinv, T* xo, double omega,
-                   bool from_zero, const int* done, cudaStream_t s);
+                   bool from_zero, const int* done, cudaStream_t s, double* xo64 = nullptr,
+                   const double* scale = nullptr);
 template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s);
 template <typename T>
@@ -108,12 +115,30 @@ struct TailParams {
   double omega = 0.8;
   const double* cinv = nullptr;   // coarse inverse
   int64_t cn = 0;
+  int cluster = 1;            // CTAs of the one thread-block cluster that runs the tail (1..8);
+                              // 0: one CTA working in shared memory (below)
+  // Shared-memory image of the tail (cluster == 0).  image[0, image_bytes) is
+  // copied into dynamic shared memory at kernel start: TailLevel hdr[nt] whose
+  // pointers are byte offsets into that memory (the vectors b, o, t, r of every
+  // level, and the matrices A, S, P, R of the levels whose bit is set in
+  // staged_mask; the other levels keep device pointers), followed by the
+  // staged matrix arrays.  The vectors occupy [image_bytes, smem).
+  const void* image = nullptr;
+  uint32_t image_bytes = 0;
+  uint32_t smem = 0;
+  uint32_t staged_mask = 0;
 };
+constexpr uint32_t kTailSmemMax = 200 * 1024;   // dynamic shared memory of the staged tail
 template <typename T>
-void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s);
+// o64 (optional): FP64 copy of the output times *scale, written by the last
+// post-smoothing sweep (nothing when nu2 == 0)
+void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s,
+                 double* o64 = nullptr, const double* scale = nullptr);
 
 // ---- vector kernels --------------------------------------------------------
-void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, double* b, cudaStream_t s);
+void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, const uint8_t* dirmask,
+                const double* g, double* b, cudaStream_t s);
+void launch_lift(const SellView& L, int nc, const double* g, double* b, cudaStream_t s);
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s);
 void launch_copy_fixed(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, const double* xin,
                        double* x, cudaStream_t s);
@@ -131,9 +156,12 @@ void launch_cond_reset(unsigned long long cond, cudaStream_t s);
 // Quantity slots of the partial arrays and of KrylovState::red
 enum { Q_RR = 0, Q_RZ = 1, Q_QZ = 2, Q_PQ = 3, Q_BB = 4, Q_RHV = 5, Q_SS = 6, Q_TS = 7, Q_TT = 8, Q_RHR = 9, Q_NUM = 10 };
 
-// r = b - A x and ||r||^2 -> red[Q_RR]; test: run the initial convergence test
+// r = b - A x and ||r||^2 -> red[Q_RR]; test 1: initial convergence test; test 2:
+// end of a multigrid-solver iteration (counts it and sets the while condition)
 void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
-                          KrylovState* st, int test, cudaStream_t s);
+                          KrylovState* st, int test, cudaStream_t s, unsigned long long cond = 0ull);
+// x += z for the multigrid iteration
+void launch_mgi_update(int64_t n, PVec z, double* x, KrylovState* st, cudaStream_t s);
 // ||b_free||^2 -> bnorm, and the initial Krylov state
 void launch_norm_init(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, Partials part,
                       KrylovState* st, double rtol, int max_it, cudaStream_t s);

@@ -65,7 +65,8 @@ extern "C" int mg_restrict_static(mg_hier* h, int level, const void* x, const vo
     launch_residual<double>(L.A64.v, nc, (const double*)x, (const double*)b, (double*)scratch, nullptr, s);
     launch_restrict<double>(L.R.t, nc, (const double*)scratch, (double*)d, nullptr, nullptr, 0.0, nullptr, s);
   } else {
-    launch_residual<float>(L.A32.v, nc, (const float*)x, (const float*)b, (float*)scratch, nullptr, s);
+    launch_residual<float>(prec == MG_MIXED_BF16 ? L.A16.v : L.A32.v, nc, (const float*)x, (const float*)b,
+                           (float*)scratch, nullptr, s);
     launch_restrict<float>(L.R.t, nc, (const float*)scratch, (float*)d, nullptr, nullptr, 0.0, nullptr, s);
   }
   cudaError_t e = cudaGetLastError();

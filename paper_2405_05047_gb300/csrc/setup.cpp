@@ -212,59 +212,63 @@ Status validate_mesh(const mg_mesh& mesh, LeafSet* out) {
 // Sec. 2.2: take back every family of 2^d sibling leaves (above min_level);
 // families whose parent would be two levels coarser than a face neighbour are
 // kept refined; repeat that check until the coarser mesh is 1-irregular.
-bool coarsen_once(const LeafSet& fine, int min_level, LeafSet* coarse) {
-  const int dim = fine.dim, nkids = 1 << dim;
-  KeyMap count(fine.size());
-  std::vector<uint64_t> pkey(fine.size(), ~0ull);
-  std::vector<uint64_t> fams;
+// patch = true (patch meshes of the LPS-stabilised Oseen problem): the unit
+// taken back is all 4^d grandchildren of one cell, which become its 2^d
+// children, so every coarser level is again a patch mesh.
+bool coarsen_once(const LeafSet& fine, int min_level, bool patch, LeafSet* coarse) {
+  const int dim = fine.dim, up = patch ? 2 : 1, nunit = 1 << (dim * up);
+  std::vector<uint64_t> ukey(fine.size(), ~0ull);
+  std::vector<uint64_t> units;
   int64_t a[3];
   {
-    // count leaf children per parent
+    // count leaves per unit root (parent, or grandparent for patch meshes)
     std::vector<std::pair<uint64_t, int>> tally;
     KeyMap slot(fine.size());
     for (size_t k = 0; k < fine.size(); ++k) {
-      if (fine.lev[k] <= min_level) continue;
-      for (int d = 0; d < dim; ++d) a[d] = fine.anc[k * dim + d] >> 1;
-      uint64_t pk = cell_key(dim, fine.lev[k] - 1, a);
-      pkey[k] = pk;
-      int64_t s = slot.get(pk);
-      if (s < 0) { slot.insert(pk, (int64_t)tally.size()); tally.push_back({pk, 1}); }
+      if (fine.lev[k] <= min_level || fine.lev[k] < up) continue;
+      for (int d = 0; d < dim; ++d) a[d] = fine.anc[k * dim + d] >> up;
+      uint64_t uk = cell_key(dim, fine.lev[k] - up, a);
+      ukey[k] = uk;
+      int64_t s = slot.get(uk);
+      if (s < 0) { slot.insert(uk, (int64_t)tally.size()); tally.push_back({uk, 1}); }
       else tally[s].second++;
     }
     for (auto& t : tally)
-      if (t.second == nkids) fams.push_back(t.first);
+      if (t.second == nunit) units.push_back(t.first);
   }
-  if (fams.empty()) return false;
-  std::sort(fams.begin(), fams.end());
-  std::vector<char> active(fams.size(), 1);
-  auto fam_index = [&](uint64_t k) -> int64_t {
-    auto it = std::lower_bound(fams.begin(), fams.end(), k);
-    return (it != fams.end() && *it == k) ? (int64_t)(it - fams.begin()) : -1;
+  if (units.empty()) return false;
+  std::sort(units.begin(), units.end());
+  std::vector<char> active(units.size(), 1);
+  auto unit_index = [&](uint64_t k) -> int64_t {
+    auto it = std::lower_bound(units.begin(), units.end(), k);
+    return (it != units.end() && *it == k) ? (int64_t)(it - units.begin()) : -1;
   };
   while (true) {
     LeafSet c;
     c.dim = dim;
     std::copy(fine.macro, fine.macro + 3, c.macro);
-    std::vector<char> done(fams.size(), 0);
-    std::vector<int64_t> parent_of_leaf;   // index into fams for new parent leaves, -1 otherwise
+    KeyMap made(units.size() * 4 + 16);       // new leaves already emitted
+    std::vector<int64_t> unit_of_leaf;        // unit a new (coarsened) leaf came from, -1 otherwise
     for (size_t k = 0; k < fine.size(); ++k) {
-      int64_t f = pkey[k] == ~0ull ? -1 : fam_index(pkey[k]);
-      if (f >= 0 && active[f]) {
-        if (done[f]) continue;
-        done[f] = 1;
+      int64_t u = ukey[k] == ~0ull ? -1 : unit_index(ukey[k]);
+      if (u >= 0 && active[u]) {
+        for (int d = 0; d < dim; ++d) a[d] = fine.anc[k * dim + d] >> 1;
+        uint64_t pk = cell_key(dim, fine.lev[k] - 1, a);
+        if (made.has(pk)) continue;
+        made.insert(pk, 1);
         c.lev.push_back(fine.lev[k] - 1);
-        for (int d = 0; d < dim; ++d) c.anc.push_back(fine.anc[k * dim + d] >> 1);
-        parent_of_leaf.push_back(f);
+        for (int d = 0; d < dim; ++d) c.anc.push_back((int32_t)a[d]);
+        unit_of_leaf.push_back(u);
       } else {
         c.lev.push_back(fine.lev[k]);
         for (int d = 0; d < dim; ++d) c.anc.push_back(fine.anc[k * dim + d]);
-        parent_of_leaf.push_back(-1);
+        unit_of_leaf.push_back(-1);
       }
     }
     std::vector<int64_t> bad = too_coarse_leaves(c);
     bool reverted = false;
     for (int64_t b : bad)
-      if (parent_of_leaf[b] >= 0) { active[parent_of_leaf[b]] = 0; reverted = true; }
+      if (unit_of_leaf[b] >= 0) { active[unit_of_leaf[b]] = 0; reverted = true; }
     if (!reverted) {
       bool any = false;
       for (char x : active) any |= (x != 0);
@@ -273,6 +277,41 @@ bool coarsen_once(const LeafSet& fine, int min_level, LeafSet* coarse) {
       return true;
     }
   }
+}
+
+// Patches of a patch mesh: the parents of its sibling families, each with
+// its 3^d lattice points (x fastest) as node indices of T.  Fails when a leaf
+// lies on level 0 or its family is incomplete.
+Status mesh_patches(const LeafSet& s, const Topology& T, std::vector<int64_t>* nodes, std::vector<int32_t>* clev) {
+  const int dim = s.dim, nv = 1 << dim, np3 = dim == 2 ? 9 : 27;
+  KeyMap pidx(s.size() / nv + 16);
+  std::vector<int> count;
+  int64_t a[3];
+  for (size_t k = 0; k < s.size(); ++k) {
+    if (s.lev[k] < 1) return Status::err(MG_ERR_INVALID, "patch mesh: a leaf on level 0 has no sibling family");
+    for (int d = 0; d < dim; ++d) a[d] = s.anc[k * dim + d] >> 1;
+    uint64_t pk = cell_key(dim, s.lev[k] - 1, a);
+    int64_t p = pidx.get(pk);
+    if (p < 0) {
+      p = (int64_t)count.size();
+      pidx.insert(pk, p);
+      count.push_back(0);
+      clev->push_back(s.lev[k]);
+      nodes->insert(nodes->end(), np3, -1);
+    }
+    count[p]++;
+    for (int c = 0; c < nv; ++c) {
+      int li = 0, m = 1;
+      for (int d = 0; d < dim; ++d) {
+        li += (int)(((s.anc[k * dim + d] & 1) + ((c >> d) & 1)) * m);
+        m *= 3;
+      }
+      (*nodes)[p * np3 + li] = T.cell_node[k * nv + c];
+    }
+  }
+  for (int c : count)
+    if (c != nv) return Status::err(MG_ERR_INVALID, "not a patch mesh: a sibling family is incomplete");
+  return Status::ok();
 }
 
 // ------------------------------------------------------------------ topology
@@ -465,6 +504,105 @@ std::vector<double> element_matrix(const mg_problem& P, int dim, const double* h
   return K;
 }
 
+// Triple 1D integrals over [0, h] for the cell-wise bilinear convection field:
+// t[0][c][a][b] = int phi_c phi_a phi_b, t[1][c][a][b] = int phi_c phi_a phi_b'.
+struct Line3 {
+  double t[2][2][2][2];
+  explicit Line3(double h) {
+    for (int c = 0; c < 2; ++c)
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const double sb = b ? 1.0 : -1.0;
+          t[0][c][a][b] = h / 12.0 * ((a == b && b == c) ? 3.0 : 1.0);
+          t[1][c][a][b] = sb / 6.0 * (c == a ? 2.0 : 1.0);
+        }
+  }
+};
+
+// Patch matrix (27 x 27, node-major (A*3 + i)*27 + B*3 + j, i = u, v, p) of
+// the 2D Oseen form with local projection stabilisation on a patch of four
+// child cells of edge lengths h; beta9: nodal convection at the patch's 3x3
+// lattice points (x fastest), 9 x 2.  Integrals are exact tensor products of
+// 1D integrals (the convection field is bilinear on every child).
+void oseen_patch_matrix(const mg_problem& P, const double* h, const double* beta9, double* K) {
+  std::fill(K, K + 27 * 27, 0.0);
+  BoxIntegrals I(2, h);
+  Line3 L3x(h[0]), L3y(h[1]);
+  const double inv_dt = std::isinf(P.dt) ? 0.0 : 1.0 / P.dt;
+  double G9[9][9] = {}, Gij[2][2][9][9] = {};
+  for (int cy = 0; cy < 2; ++cy)
+    for (int cx = 0; cx < 2; ++cx) {
+      int loc[4];
+      for (int c = 0; c < 4; ++c) loc[c] = (cx + (c & 1)) + 3 * (cy + (c >> 1));
+      for (int A = 0; A < 4; ++A)
+        for (int B = 0; B < 4; ++B) {
+          const int ax = A & 1, ay = A >> 1, bx = B & 1, by = B >> 1;
+          const double mass = I.G(-1, -1, A, B);
+          const double lap = I.G(0, 0, A, B) + I.G(1, 1, A, B);
+          double conv = 0.0;    // int phi_A (beta_h . grad phi_B)
+          for (int C = 0; C < 4; ++C) {
+            const int cxx = C & 1, cyy = C >> 1;
+            const double* bC = beta9 + 2 * loc[C];
+            conv += bC[0] * L3x.t[1][cxx][ax][bx] * L3y.t[0][cyy][ay][by];
+            conv += bC[1] * L3x.t[0][cxx][ax][bx] * L3y.t[1][cyy][ay][by];
+          }
+          const double vv = inv_dt * mass + P.nu * lap + conv;
+          const int r = loc[A], c = loc[B];
+          for (int i = 0; i < 2; ++i) {
+            K[(r * 3 + i) * 27 + c * 3 + i] += vv;
+            K[(r * 3 + i) * 27 + c * 3 + 2] -= I.G(i, -1, A, B);   // -(p, div v)
+            K[(r * 3 + 2) * 27 + c * 3 + i] += I.G(-1, i, A, B);   // (div u, q)
+          }
+          G9[r][c] += lap;
+          for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) Gij[i][j][r][c] += I.G(i, j, A, B);
+        }
+    }
+  // kappa = id - Pi, Pi the coarse Q1 interpolant from the patch corners
+  double kap[9][9];
+  for (int n = 0; n < 9; ++n)
+    for (int m = 0; m < 9; ++m) {
+      double pi = 0.0;
+      const int mx = m % 3, my = m / 3;
+      if ((mx == 0 || mx == 2) && (my == 0 || my == 2)) {
+        const double tx = (n % 3) / 2.0, ty = (n / 3) / 2.0;
+        pi = (mx ? tx : 1.0 - tx) * (my ? ty : 1.0 - ty);
+      }
+      kap[n][m] = (n == m ? 1.0 : 0.0) - pi;
+    }
+  const double* bP = beta9 + 2 * 4;
+  const double hP = 2.0 * std::sqrt(h[0] * h[0] + h[1] * h[1]);
+  const double alpha = P.lps_alpha0 * hP * hP / (P.nu + std::sqrt(bP[0] * bP[0] + bP[1] * bP[1]) * hP);
+  double Cb[9][9];
+  for (int a = 0; a < 9; ++a)
+    for (int b = 0; b < 9; ++b) {
+      double v = 0.0;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) v += bP[i] * bP[j] * Gij[i][j][a][b];
+      Cb[a][b] = v;
+    }
+  // S = kappa^T M kappa for M = G9 (pressure) and Cb (velocity components)
+  for (int which = 0; which < 2; ++which) {
+    double (*M)[9] = which == 0 ? G9 : Cb;
+    double Mk[9][9];
+    for (int a = 0; a < 9; ++a)
+      for (int b = 0; b < 9; ++b) {
+        double v = 0.0;
+        for (int k = 0; k < 9; ++k) v += M[a][k] * kap[k][b];
+        Mk[a][b] = v;
+      }
+    for (int a = 0; a < 9; ++a)
+      for (int b = 0; b < 9; ++b) {
+        double v = 0.0;
+        for (int k = 0; k < 9; ++k) v += kap[k][a] * Mk[k][b];
+        v *= alpha;
+        if (which == 0) K[(a * 3 + 2) * 27 + b * 3 + 2] += v;
+        else
+          for (int i = 0; i < 2; ++i) K[(a * 3 + i) * 27 + b * 3 + i] += v;
+      }
+  }
+}
+
 // Load element F[A][B]: b_A = sum_B F[A][B] f_B for nodal f (mass matrix,
 // plus the SUPG term delta_T (f_h, beta.grad phi_A) for transport).
 std::vector<double> load_element(const mg_problem& P, int dim, const double* h) {
@@ -492,22 +630,21 @@ void cell_size(const HostHierarchy& H, int lev, double* h) {
   for (int d = 0; d < H.dim; ++d) h[d] = H.extent[d] / ((double)H.macro[d] * std::ldexp(1.0, lev));
 }
 
-// node -> list of (cell, corner) incidences through the constraints:
-// entry for every regular node p that receives a share of corner A of cell k.
+// node -> list of (element, local node) incidences through the constraints:
+// entry for every regular node p that receives a share of local node A of
+// element k.  Elements are cells (m = 2^d corners) or LPS patches (m = 3^d).
 struct Incidence {
   std::vector<int64_t> ptr, cell;
   std::vector<int8_t> corner;
   std::vector<double> w;
 };
 
-Incidence expanded_incidence(const LeafSet& s, const Topology& T) {
-  const int nv = 1 << s.dim;
-  const int64_t n = (int64_t)s.size();
+Incidence expanded_incidence(int64_t n_elem, int m, const std::vector<int64_t>& elem_node, const Topology& T) {
   Incidence inc;
   inc.ptr.assign(T.n_nodes + 1, 0);
-  for (int64_t k = 0; k < n; ++k)
-    for (int A = 0; A < nv; ++A) {
-      int64_t v = T.cell_node[k * nv + A];
+  for (int64_t k = 0; k < n_elem; ++k)
+    for (int A = 0; A < m; ++A) {
+      int64_t v = elem_node[k * m + A];
       for (int64_t o = T.con_ptr[v]; o < T.con_ptr[v + 1]; ++o) inc.ptr[T.con_node[o] + 1]++;
     }
   for (int64_t i = 0; i < T.n_nodes; ++i) inc.ptr[i + 1] += inc.ptr[i];
@@ -515,9 +652,9 @@ Incidence expanded_incidence(const LeafSet& s, const Topology& T) {
   inc.corner.resize(inc.ptr.back());
   inc.w.resize(inc.ptr.back());
   std::vector<int64_t> fill(inc.ptr.begin(), inc.ptr.end() - 1);
-  for (int64_t k = 0; k < n; ++k)
-    for (int A = 0; A < nv; ++A) {
-      int64_t v = T.cell_node[k * nv + A];
+  for (int64_t k = 0; k < n_elem; ++k)
+    for (int A = 0; A < m; ++A) {
+      int64_t v = elem_node[k * m + A];
       for (int64_t o = T.con_ptr[v]; o < T.con_ptr[v + 1]; ++o) {
         int64_t p = T.con_node[o];
         int64_t at = fill[p]++;
@@ -527,6 +664,10 @@ Incidence expanded_incidence(const LeafSet& s, const Topology& T) {
       }
     }
   return inc;
+}
+
+Incidence expanded_incidence(const LeafSet& s, const Topology& T) {
+  return expanded_incidence((int64_t)s.size(), 1 << s.dim, T.cell_node, T);
 }
 
 uint8_t dirichlet_bits(const HostHierarchy& H, const Topology& T, int64_t node) {
@@ -544,22 +685,20 @@ uint8_t dirichlet_bits(const HostHierarchy& H, const Topology& T, int64_t node) 
 }
 
 // Condensed operator H^T A H with identity rows/columns on fixed dofs,
-// assembled row by row (each row gathers the cells whose constrained corner
-// shares reach it).
-void assemble_level(const HostHierarchy& H, HostLevel& lv) {
-  const LeafSet& s = lv.leaves;
+// assembled row by row (each row gathers the elements whose constrained node
+// shares reach it).  Elements have m nodes (elem_node[k*m + a]); Kof(k)
+// returns element k's (m nc)^2 matrix, node-major.  With lift != nullptr the
+// entries of H^T A H that couple free dofs (rows) to Dirichlet dofs (columns)
+// are also kept there before the elimination (lifting of Dirichlet data).
+void assemble_condensed(const HostHierarchy& H, HostLevel& lv, int64_t n_elem, int m,
+                        const std::vector<int64_t>& elem_node, const std::function<const double*(int64_t)>& Kof,
+                        BlockCSR* lift) {
   const Topology& T = lv.topo;
-  const int dim = s.dim, nv = 1 << dim, nc = H.nc, nb = nc * nc;
+  const int nc = H.nc, nb = nc * nc;
   const uint8_t all = (uint8_t)((1 << nc) - 1);
   lv.fixmask.assign(T.n_nodes, 0);
   for (int64_t i = 0; i < T.n_nodes; ++i) lv.fixmask[i] = T.hanging[i] ? all : dirichlet_bits(H, T, i);
-  // element matrices per cell level
-  std::vector<std::vector<double>> Ke(32);
-  for (size_t k = 0; k < s.size(); ++k) {
-    int l = s.lev[k];
-    if (Ke[l].empty()) { double h[3]; cell_size(H, l, h); Ke[l] = element_matrix(H.prob, dim, h); }
-  }
-  Incidence inc = expanded_incidence(s, T);
+  Incidence inc = expanded_incidence(n_elem, m, elem_node, T);
   BlockCSR& A = lv.A;
   A.n = A.m = T.n_nodes;
   A.nc = nc;
@@ -570,8 +709,8 @@ void assemble_level(const HostHierarchy& H, HostLevel& lv) {
     if (T.hanging[p]) return;
     for (int64_t o = inc.ptr[p]; o < inc.ptr[p + 1]; ++o) {
       int64_t k = inc.cell[o];
-      for (int B = 0; B < nv; ++B) {
-        int64_t v = T.cell_node[k * nv + B];
+      for (int B = 0; B < m; ++B) {
+        int64_t v = elem_node[k * m + B];
         for (int64_t q = T.con_ptr[v]; q < T.con_ptr[v + 1]; ++q) cols.push_back(T.con_node[q]);
       }
     }
@@ -587,6 +726,9 @@ void assemble_level(const HostHierarchy& H, HostLevel& lv) {
   for (int64_t p = 0; p < T.n_nodes; ++p) A.ptr[p + 1] += A.ptr[p];
   A.col.resize(A.ptr.back());
   A.val.assign(A.ptr.back() * nb, 0.0);
+  std::vector<std::vector<int64_t>> lcol(lift ? T.n_nodes : 0);
+  std::vector<std::vector<double>> lval(lift ? T.n_nodes : 0);
+  const int w = m * nc;
 #pragma omp parallel
   {
     std::vector<int64_t> cols;
@@ -602,24 +744,34 @@ void assemble_level(const HostHierarchy& H, HostLevel& lv) {
           int64_t k = inc.cell[o];
           int Acorner = inc.corner[o];
           double wa = inc.w[o];
-          const std::vector<double>& K = Ke[s.lev[k]];
-          for (int B = 0; B < nv; ++B) {
-            int64_t v = T.cell_node[k * nv + B];
+          const double* K = Kof(k);
+          for (int B = 0; B < m; ++B) {
+            int64_t v = elem_node[k * m + B];
             for (int64_t q = T.con_ptr[v]; q < T.con_ptr[v + 1]; ++q) {
               int64_t c = T.con_node[q];
-              double w = wa * T.con_w[q];
+              double wq = wa * T.con_w[q];
               int64_t pos = std::lower_bound(cols.begin(), cols.end(), c) - cols.begin();
               double* blk = rv + pos * nb;
               for (int i = 0; i < nc; ++i)
-                for (int j = 0; j < nc; ++j)
-                  blk[i * nc + j] += w * K[(Acorner * nc + i) * (nv * nc) + B * nc + j];
+                for (int j = 0; j < nc; ++j) blk[i * nc + j] += wq * K[(Acorner * nc + i) * w + B * nc + j];
             }
           }
         }
       }
+      uint8_t fp = lv.fixmask[p];
+      if (lift && fp != all)
+        for (int64_t e = 0; e < len; ++e) {
+          uint8_t fq = lv.fixmask[cols[e]];     // columns are regular nodes: Dirichlet bits only
+          if (!fq) continue;
+          std::vector<double> blk(nb, 0.0);
+          bool any = false;
+          for (int i = 0; i < nc; ++i)
+            for (int j = 0; j < nc; ++j)
+              if (!((fp >> i) & 1) && ((fq >> j) & 1)) { blk[i * nc + j] = rv[e * nb + i * nc + j]; any = true; }
+          if (any) { lcol[p].push_back(cols[e]); lval[p].insert(lval[p].end(), blk.begin(), blk.end()); }
+        }
       // symmetric elimination of fixed dofs: zero their rows and columns,
       // identity on their diagonal
-      uint8_t fp = lv.fixmask[p];
       for (int64_t e = 0; e < len; ++e) {
         uint8_t fq = lv.fixmask[cols[e]];
         double* blk = rv + e * nb;
@@ -632,6 +784,53 @@ void assemble_level(const HostHierarchy& H, HostLevel& lv) {
       }
     }
   }
+  if (lift) {
+    lift->n = lift->m = T.n_nodes;
+    lift->nc = nc;
+    lift->ptr.assign(T.n_nodes + 1, 0);
+    for (int64_t p = 0; p < T.n_nodes; ++p) lift->ptr[p + 1] = lift->ptr[p] + (int64_t)lcol[p].size();
+    lift->col.clear();
+    lift->val.clear();
+    for (int64_t p = 0; p < T.n_nodes; ++p) {
+      lift->col.insert(lift->col.end(), lcol[p].begin(), lcol[p].end());
+      lift->val.insert(lift->val.end(), lval[p].begin(), lval[p].end());
+    }
+  }
+}
+
+// Level operator by rediscretisation: cell element matrices (constant
+// coefficients, one matrix per cell level), or for OSEEN the patch matrices
+// with the level's nodal convection field beta (n_nodes x 2).
+Status assemble_level(const HostHierarchy& H, HostLevel& lv, const std::vector<double>& beta, BlockCSR* lift) {
+  const LeafSet& s = lv.leaves;
+  const Topology& T = lv.topo;
+  const int dim = s.dim, nv = 1 << dim;
+  if (H.prob.kind == MG_OSEEN) {
+    std::vector<int64_t> pn;
+    std::vector<int32_t> clev;
+    Status st = mesh_patches(s, T, &pn, &clev);
+    if (!st.good()) return st;
+    const int64_t np = (int64_t)clev.size();
+    std::vector<double> Kp((size_t)np * 27 * 27);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < np; ++k) {
+      double h[3], b9[18];
+      cell_size(H, clev[k], h);
+      for (int a = 0; a < 9; ++a)
+        for (int d = 0; d < 2; ++d) b9[2 * a + d] = beta[2 * pn[k * 9 + a] + d];
+      oseen_patch_matrix(H.prob, h, b9, &Kp[(size_t)k * 729]);
+    }
+    assemble_condensed(H, lv, np, 9, pn, [&](int64_t k) { return &Kp[(size_t)k * 729]; }, lift);
+    return Status::ok();
+  }
+  std::vector<std::vector<double>> Ke(32);
+  for (size_t k = 0; k < s.size(); ++k) {
+    int l = s.lev[k];
+    if (Ke[l].empty()) { double h[3]; cell_size(H, l, h); Ke[l] = element_matrix(H.prob, dim, h); }
+  }
+  assemble_condensed(H, lv, (int64_t)s.size(), nv, T.cell_node, [&](int64_t k) { return Ke[s.lev[k]].data(); },
+                     lift);
+  return Status::ok();
 }
 
 // b = H^T (F f): rows are the nodes receiving constrained shares, columns are
@@ -794,11 +993,18 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
   LeafSet fine;
   Status st = validate_mesh(mesh, &fine);
   if (!st.good()) return st;
-  if (prob.kind < MG_POISSON || prob.kind > MG_ELASTICITY) return Status::err(MG_ERR_INVALID, "unknown problem kind");
+  if (prob.kind < MG_POISSON || prob.kind > MG_OSEEN) return Status::err(MG_ERR_INVALID, "unknown problem kind");
   if (prob.kind == MG_ELASTICITY && mesh.dim != 3) return Status::err(MG_ERR_INVALID, "elasticity needs dim = 3");
   if (prob.kind == MG_TRANSPORT && !(prob.eps > 0)) return Status::err(MG_ERR_INVALID, "transport needs eps > 0");
+  const bool oseen = prob.kind == MG_OSEEN;
+  if (oseen) {
+    if (mesh.dim != 2) return Status::err(MG_ERR_INVALID, "oseen needs dim = 2");
+    if (!prob.conv) return Status::err(MG_ERR_INVALID, "oseen needs the nodal convection field conv");
+    if (!(prob.nu > 0) || !(prob.dt > 0) || !(prob.lps_alpha0 >= 0))
+      return Status::err(MG_ERR_INVALID, "oseen needs nu > 0, dt > 0, lps_alpha0 >= 0");
+  }
   H->dim = mesh.dim;
-  H->nc = prob.kind == MG_ELASTICITY ? 3 : 1;
+  H->nc = (prob.kind == MG_ELASTICITY || oseen) ? 3 : 1;
   for (int d = 0; d < 3; ++d) {
     H->origin[d] = d < mesh.dim ? mesh.origin[d] : 0.0;
     H->extent[d] = d < mesh.dim ? mesh.extent[d] : 1.0;
@@ -807,22 +1013,44 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
   H->prob = prob;
   H->opts = opts;
   int min_level = opts.min_level >= 0 ? opts.min_level : default_min_level(H->macro, H->dim);
+  if (oseen) min_level = std::max(min_level, 1);   // patches need a parent cell
   // leaf sets from fine to coarse, then reversed so that [0] is the coarsest
   std::vector<LeafSet> sets;
   sets.push_back(std::move(fine));
   while (opts.max_levels <= 0 || (int)sets.size() < opts.max_levels) {
     LeafSet c;
-    if (!coarsen_once(sets.back(), min_level, &c)) break;
+    if (!coarsen_once(sets.back(), min_level, oseen, &c)) break;
     sets.push_back(std::move(c));
     if ((int)sets.size() >= kMaxLevels) break;
   }
   std::reverse(sets.begin(), sets.end());
-  H->levels.resize(sets.size());
-  for (size_t l = 0; l < sets.size(); ++l) {
+  const int nlev = (int)sets.size();
+  H->levels.resize(nlev);
+  for (int l = 0; l < nlev; ++l) {
     HostLevel& lv = H->levels[l];
     lv.leaves = std::move(sets[l]);
     build_topology(lv.leaves, &lv.topo);
-    assemble_level(*H, lv);
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    HostLevel& lv = H->levels[l];
+    std::vector<double> beta;
+    if (oseen) {
+      // nodal convection field of this level: injected from the finest nodes
+      const Topology& Tf = H->levels[nlev - 1].topo;
+      const Topology& T = lv.topo;
+      beta.resize(T.n_nodes * 2);
+      for (int64_t i = 0; i < T.n_nodes; ++i) {
+        int64_t X[3];
+        T.lattice_coords(i, X);
+        const int64_t k = (X[0] << (Tf.L - T.L)) + (X[1] << (Tf.L - T.L)) * (Tf.ncell[0] + 1);
+        const int64_t f = Tf.find(k);
+        if (f < 0) return Status::err(MG_ERR_INVALID, "internal: coarse node missing on the finest level");
+        beta[2 * i] = prob.conv[2 * f];
+        beta[2 * i + 1] = prob.conv[2 * f + 1];
+      }
+    }
+    Status st = assemble_level(*H, lv, beta, l == nlev - 1 ? &H->lift : nullptr);
+    if (!st.good()) return st;
   }
   for (size_t l = 1; l < H->levels.size(); ++l) build_transfer(*H, H->levels[l - 1], H->levels[l]);
   // smoother: inverse of the nc x nc diagonal block of every node

@@ -24,7 +24,7 @@ _SIGS = {
     "mg_host_free": (C.c_int, [C.c_void_p]),
 }
 
-A, P, R, LOAD, SMOOTHER, HMAT = 0, 1, 2, 3, 4, 5
+A, P, R, LOAD, SMOOTHER, HMAT, LIFT = 0, 1, 2, 3, 4, 5, 6
 
 
 def _lib():

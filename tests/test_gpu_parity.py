@@ -251,25 +251,58 @@ def test_not_converged_status(ctx):
 
 @pytest.mark.parametrize("name", ["td_adaptive", "elasticity16"])
 def test_tail_kernel_bitwise_equals_level_kernels(ctx, name):
-    """The single-CTA tail V-cycle runs the same row steps as the grid
-    kernels: identical bits with and without it, FP64 and FP32."""
+    """The tail V-cycle runs the same row steps as the grid kernels: identical
+    bits without it, with it on a cluster of 1, 2, 4 or 8 CTAs, and on one CTA
+    working in shared memory (cluster 0: all vectors staged, matrices staged
+    coarsest first while they fit), in FP64, FP32 and with BF16 values."""
     mk, prob, pkw, okw = CASES[name]
     lm = mk()
-    hs = [G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(tail_rows=t, **okw)) for t in (0, 1 << 20)]
-    n = hs[0].n_dofs
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(autotune=0, store_bf16=1, **okw))
+    n = h.n_dofs
     rng = np.random.default_rng(9)
     r = rng.standard_normal(n)
     oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
     r[oh.fine.sys.fixed] = 0.0
-    for prec, dt in ((B.MG_FP64, torch.float64), (B.MG_MIXED_FP32, torch.float32)):
-        outs = []
-        for hh in hs:
+    shapes = ((0, 1), (1 << 20, 1), (1 << 20, 2), (1 << 20, 4), (1 << 20, 8), (1024, 4),
+              (1 << 20, 0), (4096, 0), (256, 0))
+    for prec, dt in ((B.MG_FP64, torch.float64), (B.MG_MIXED_FP32, torch.float32),
+                     (B.MG_MIXED_BF16, torch.float32)):
+        outs, staged_levels = [], []
+        for rows, cl in shapes:
+            h.tune(prec, rows, cl)
+            if cl == 0:
+                staged_levels.append(h.info.tail_levels)
             z = torch.empty(n, device="cuda", dtype=dt)
-            hh.vcycle(dev(r, dt), z, prec)
+            h.vcycle(dev(r, dt), z, prec)
             outs.append(z.cpu().numpy())
-        assert np.array_equal(outs[0], outs[1])
-    for hh in hs:
-        hh.free()
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o)
+        assert max(staged_levels) >= 2      # the shared-memory tail really ran
+    # the autotuner picks one of these shapes and the solve still matches
+    h.tune(B.MG_MIXED_FP32, -1)
+    assert 0 <= h.info.tail_cluster <= 8
+    h.free()
+
+
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+def test_shared_memory_tail_solve_identical(ctx, prec):
+    """A whole solve (CUDA-graph while loop) with the shared-memory tail gives
+    the same iterates, bit for bit, as the multi-kernel V-cycle."""
+    lm = W.td_adaptive(rounds=4, gamma=1.0)
+    h = G.Hierarchy(ctx, lm, B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)), B.make_opts(autotune=0))
+    f = dev(W.f_transport(h.coords(), 1e-3, (1.0, 0.5)))
+    b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(f, b)
+    xs, its = [], []
+    for rows, cl in ((0, 1), (1 << 20, 0)):
+        h.tune(prec, rows, cl)
+        x = torch.zeros_like(b)
+        st = h.solve(b, x, rtol=1e-10, max_it=100, prec=prec)
+        assert st.status == B.MG_OK
+        xs.append(x.cpu().numpy())
+        its.append(st.iters)
+    assert its[0] == its[1] and np.array_equal(xs[0], xs[1])
+    h.free()
 
 
 def test_direct_launch_mode_equals_graph(ctx):
@@ -315,4 +348,85 @@ def test_gmres_matches_direct(ctx, prec, restart):
     _, info = __import__("oracle.krylov", fromlist=["gmres"]).gmres(oh.fine.A, bref, oh.precondition, rtol=1e-10,
                                                                     restart=restart, maxit=300)
     assert abs(info["iters"] - st.iters) <= max(3, info["iters"] // 3), (info["iters"], st.iters)
+    h.free()
+
+
+def _bf16_round(a):
+    """Round-to-nearest-even of FP64 values to BF16 through FP32 (the
+    library's stored-value rounding), returned as FP64."""
+    f = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["poisson64", "elasticity16"])
+def test_bf16_values_smoother_parity(ctx, name):
+    """BF16-stored values (ablation): one smoothing sweep equals an FP64
+    evaluation with the BF16-rounded operator, FP32 vectors."""
+    mk, prob, pkw, okw = CASES[name]
+    lm = mk()
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(store_bf16=1, **okw))
+    lv = oh.fine
+    A16 = lv.A.copy()
+    A16.data = _bf16_round(A16.data)
+    rng = np.random.default_rng(13)
+    n = lv.A.shape[0]
+    x = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    bvec = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    x[lv.sys.fixed] = 0.0
+    bvec[lv.sys.fixed] = 0.0
+    out = torch.empty(n, device="cuda", dtype=torch.float32)
+    h.apply(h.levels - 1, B.MG_OP_MATVEC, dev(x, torch.float32), None, out, B.MG_MIXED_BF16)
+    ref = A16 @ x
+    assert np.abs(out.cpu().double().numpy() - ref).max() <= 2e-5 * bound(A16, x)
+    h.free()
+
+
+@pytest.mark.parametrize("name", ["td_adaptive", "elasticity16"])
+def test_bf16_values_solve_reaches_tolerance(ctx, name):
+    lm, prob, oh, _ = setup_case(ctx, name)
+    mk, prob, pkw, okw = CASES[name]
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(store_bf16=1, **okw))
+    s = PB.build_system(oh.fine.mesh, prob)
+    bref = s.rhs(rhs_for(name, oh.fine.mesh.coords, prob.nc))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(dev(bref), x, rtol=1e-10, max_it=300, prec=B.MG_MIXED_BF16)
+    assert st.status == 0 and st.rel_res <= 1e-10
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= 1e-8
+    h.free()
+
+
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+@pytest.mark.parametrize("name", ["poisson64", "elasticity16"])
+def test_multigrid_iteration_solver(ctx, name, prec):
+    """The V-cycle iterated as the solver (Algorithm "Geometric multigrid
+    solver"), defect b - A x in FP64: reaches the tolerance, equals the
+    direct solve, and contracts at least as fast as the oracle's iteration."""
+    lm, prob, oh, _ = setup_case(ctx, name)
+    mk, prob, pkw, okw = CASES[name]
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(krylov=B.MG_MGITER, **okw))
+    s = PB.build_system(oh.fine.mesh, prob)
+    bref = s.rhs(rhs_for(name, oh.fine.mesh.coords, prob.nc))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(dev(bref), x, rtol=1e-10, max_it=300, prec=prec)
+    assert st.status == 0 and st.rel_res <= 1e-10, st.as_dict()
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= (1e-9 if prec == B.MG_FP64 else 1e-8)
+    # the oracle's multigrid iteration needs the same number of cycles (FP64)
+    xo = np.zeros_like(bref)
+    its = 0
+    nb = np.linalg.norm(bref[~s.fixed])
+    while np.linalg.norm(bref - oh.fine.A @ xo) > 1e-10 * nb and its < 300:
+        xo = xo + oh.precondition(bref - oh.fine.A @ xo)
+        its += 1
+    if prec == B.MG_FP64:
+        assert st.iters == its
+    else:
+        assert abs(st.iters - its) <= 2
     h.free()

@@ -10,6 +10,7 @@ import pytest
 import scipy.sparse as sp
 
 import workloads as W
+from oracle import mesh as M
 from oracle import mg
 from oracle import problems as PB
 from paper_2405_05047_gb300 import binding as B
@@ -47,30 +48,71 @@ def test_host_hierarchy_matches_oracle(name):
     lm = mk()
     oh = mg.Hierarchy(lm, prob)
     hh = HV.HostHierarchy(lm, B.make_problem(**pkw))
+    _compare(oh, hh, prob)
+
+
+@pytest.mark.parametrize("rounds", [2, 4])
+def test_host_hierarchy_oseen_matches_oracle(rounds):
+    """Oseen + LPS on a patch mesh: per-level operators (patch-preserving
+    coarsening, injected convection field), transfers, 3x3 point blocks, the
+    load matrix and the lifting couplings of the Dirichlet data."""
+    lm = W.oseen_channel(1, rounds)
+    xy = B.mg_mesh_nodes(lm)
+    fm = M.Q1Mesh(2, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+    assert np.array_equal(xy, fm.coords)
+    beta = W.oseen_beta(xy)
+    kw = dict(dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01)
+    prob = PB.Problem(PB.OSEEN, conv=beta, **kw)
+    oh = mg.Hierarchy(lm, prob)
+    hh = HV.HostHierarchy(lm, B.make_problem(kind=B.MG_OSEEN, conv=beta, **kw))
+    _compare(oh, hh, prob, tol=1e-12)
+    # lifting: the free-row x Dirichlet-column part of H^T A H
+    S = PB.build_system(oh.fine.mesh, prob, beta=beta)
+    Ac = (S.H.T @ S.A_raw @ S.H).tocsr()
+    free = (~S.fixed).astype(float)
+    Lo = sp.diags(free) @ Ac @ sp.diags(S.dirichlet.astype(float))
+    assert close(hh.matrix(hh.levels - 1, HV.LIFT), Lo, 1e-12)
+
+
+def test_oseen_rejects_non_patch_mesh():
+    lm = W.oseen_channel(1, 0)
+    lm = W.refine(lm, np.arange(lm.n_leaves) == 5)       # one leaf refined alone: its family is incomplete
+    beta = np.zeros((B.mg_mesh_nodes(lm).shape[0], 2))
+    with pytest.raises(B.MGError, match="patch mesh"):
+        HV.HostHierarchy(lm, B.make_problem(kind=B.MG_OSEEN, conv=beta, dirichlet=(0xD, 0xD, 0)))
+
+
+def _compare(oh, hh, prob, tol=1e-13):
     assert hh.levels == len(oh.levels)
     nc = prob.nc
     for l, lv in enumerate(oh.levels):
         A = hh.matrix(l, HV.A)
         assert A.shape == lv.A.shape
-        assert close(A, lv.A), f"A level {l}"
+        assert close(A, lv.A, tol), f"A level {l}"
         fm = hh.fixmask(l)
         fixed = np.zeros(lv.mesh.n_nodes * nc, dtype=bool)
         for c in range(nc):
             fixed[c::nc] = (fm >> c) & 1
         assert np.array_equal(fixed, lv.sys.fixed)
         S = hh.matrix(l, HV.SMOOTHER)
-        assert close(S, lv.S, 1e-12), f"smoother level {l}"
+        assert close(S, lv.S, max(tol, 1e-12)), f"smoother level {l}"
         if l > 0:
+            # the library's scalar P, with the per-component rows of partly
+            # fixed nodes masked (as its kernels do), is each component block
+            # of the oracle's P_eff
             Pl = hh.matrix(l, HV.P)
-            Po = lv.P if nc == 1 else lv.P[::nc, ::nc]
-            assert close(Pl, Po, 0.0), f"P level {l}"
+            fc = hh.fixmask(l - 1)
+            for c in range(nc):
+                keep_f = sp.diags(((fm >> c) & 1 == 0).astype(float))
+                keep_c = sp.diags(((fc >> c) & 1 == 0).astype(float))
+                assert close(keep_f @ Pl @ keep_c, lv.P[c::nc, c::nc], 0.0), f"P level {l} comp {c}"
             Rl = hh.matrix(l, HV.R)
             assert (abs(Rl - Pl.T) > 0).nnz == 0
     inv = hh.coarse_inverse()
     A0 = oh.levels[0].A.toarray()
     assert np.abs(inv @ A0 - np.eye(A0.shape[0])).max() < 1e-11
     # load matrix: b = H^T F f on the finest level
-    sysf = PB.build_system(oh.fine.mesh, prob)
+    sysf = PB.build_system(oh.fine.mesh, prob, beta=prob.conv)
     F = hh.matrix(hh.levels - 1, HV.LOAD)
     Fo = (oh.fine.mesh.H().T @ sysf.F).tocsr()
     hang = oh.fine.mesh.hanging
