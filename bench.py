@@ -40,19 +40,33 @@ METRIC = "DoF/s to 1e-8 rel. residual (FP32-MG + FP64 Krylov)"
 GAMMA_TD = 0.18          # radius decay chosen so that the mesh has ~1.2 M nodes
 
 
+OSEEN_ROUNDS = 12       # refinement rounds towards the circle: ~658 k nodes, ~1.97 M DoFs
+
+
 def workload(name):
-    """(leaf mesh, problem kwargs, opts kwargs, rhs function, description)."""
+    """(leaf mesh, problem kwargs, opts kwargs, rhs function, description,
+    Dirichlet data function or None)."""
     from paper_2405_05047_gb300 import binding as B
+    if name == "oseen":
+        lm = W.oseen_channel(1, OSEEN_ROUNDS)
+        xy = B.mg_mesh_nodes(lm)
+        pk = dict(kind=B.MG_OSEEN, dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01, conv=W.oseen_beta(xy))
+        return lm, pk, dict(krylov=B.MG_GMRES, restart=30), (lambda c: np.zeros(c.shape[0] * 3)), (
+            "2D Oseen (one backward-Euler step, nu=1e-3, dt=0.01) equal-order Q1 (u,v,p) + LPS on the channel "
+            f"[0,2.2]x[0,0.41], 22x4 macro cells refined once, then {OSEEN_ROUNDS} rounds towards the circle "
+            "|x-(0.2,0.2)|=0.05 by sibling families, 2:1; seeded divergence-free convection field, parabolic "
+            "inflow (lifted), no-slip walls, do-nothing outflow; GMRES(30) + V(2,2) point-block (Vanka) "
+            "Jacobi w=0.8"), W.oseen_inflow
     if name == "td_adaptive":
         lm = W.td_adaptive(rounds=8, gamma=GAMMA_TD)
         pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
         return lm, pk, dict(krylov=B.MG_BICGSTAB), (lambda xy: W.f_transport(xy, 1e-3, (1.0, 0.5))), (
             "2D transport-diffusion eps=1e-3 beta=(1,0.5) Q1+SUPG, 32x32 start + 8 rounds refined within "
-            f"r_k=0.05*2^(-{GAMMA_TD}k) of 16 seeded points, 2:1, hanging nodes; BiCGStab + V(2,2) Jacobi w=0.8")
+            f"r_k=0.05*2^(-{GAMMA_TD}k) of 16 seeded points, 2:1, hanging nodes; BiCGStab + V(2,2) Jacobi w=0.8"), None
     if name == "poisson64":
         lm = W.poisson64(64)
         return lm, dict(kind=B.MG_POISSON), dict(krylov=B.MG_CG), W.f_poisson, (
-            "2D Poisson 64x64 Q1, CG + V(2,2) Jacobi w=0.8, 5 levels")
+            "2D Poisson 64x64 Q1, CG + V(2,2) Jacobi w=0.8, 5 levels"), None
     if name.startswith("elasticity"):
         n = int(name[len("elasticity"):] or 128)
         lm = W.elasticity3d(n)
@@ -60,7 +74,7 @@ def workload(name):
         return lm, pk, dict(krylov=B.MG_CG, omega=0.5), (
             lambda xyz: np.tile([0.0, 0.0, -1.0], (xyz.shape[0], 1)).ravel()), (
             f"3D linear elasticity {n}^3 Q1 hexes, mu=1 lambda=10, clamped x=0, f=(0,0,-1); "
-            "CG + V(2,2) point-block Jacobi w=0.5")
+            "CG + V(2,2) point-block Jacobi w=0.5"), None
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -375,7 +389,7 @@ def main():
     BLD.build()
     torch.cuda.set_device(local)
 
-    lm, pk, ok, ffun, desc = workload(args.workload)
+    lm, pk, ok, ffun, desc, gfun = workload(args.workload)
     ctx = G.Context(local)
     stream = ctx.stream
     t0 = time.perf_counter()
@@ -388,7 +402,10 @@ def main():
     coords = h.coords()
     f = torch.from_numpy(np.ascontiguousarray(ffun(coords), dtype=np.float64)).cuda()
     b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
-    h.assemble_rhs(f, b)
+    g = None
+    if gfun is not None:
+        g = torch.from_numpy(np.ascontiguousarray(gfun(coords), dtype=np.float64).ravel()).cuda()
+    h.assemble_rhs(f, b, g)
     x = torch.zeros_like(b)
     flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MB > L2
 

@@ -23,6 +23,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
 import workloads as W
+from oracle import mesh as M
 from oracle import mg
 from oracle import problems as PB
 
@@ -45,6 +46,27 @@ CASES = {
                             PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
                             dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), dict(omega=0.5)),
 }
+
+
+def _oseen_entry(rounds=3):
+    """Oseen + LPS on the channel patch mesh: GMRES(30), point-block smoother."""
+    lm = W.oseen_channel(1, rounds)
+    fm = M.Q1Mesh(2, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+    beta = W.oseen_beta(fm.coords)
+    kw = dict(dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01)
+    return (lambda: lm, PB.Problem(PB.OSEEN, conv=beta, **kw), dict(kind=B.MG_OSEEN, conv=beta, **kw), {})
+
+
+CASES["oseen"] = _oseen_entry()
+
+
+def system_for(oh, prob):
+    return PB.build_system(oh.fine.mesh, prob, beta=prob.conv)
+
+
+def g_for(name, coords):
+    """Nodal Dirichlet data: the parabolic inflow for the channel, else none."""
+    return W.oseen_inflow(coords).ravel() if name == "oseen" else None
 
 
 @pytest.fixture(scope="module")
@@ -168,6 +190,8 @@ def test_vcycle_fp32_close_to_fp64(ctx):
 
 
 def rhs_for(name, coords, nc):
+    if name == "oseen":
+        return np.zeros(coords.shape[0] * 3)
     if name.startswith("poisson"):
         return W.f_poisson(coords)
     if name.startswith("td"):
@@ -178,16 +202,37 @@ def rhs_for(name, coords, nc):
 @pytest.mark.parametrize("name", list(CASES))
 def test_rhs_assembly(ctx, name):
     lm, prob, oh, h = setup_case(ctx, name)
-    s = PB.build_system(oh.fine.mesh, prob)
+    s = system_for(oh, prob)
     f = rhs_for(name, oh.fine.mesh.coords, prob.nc)
+    g = g_for(name, oh.fine.mesh.coords)
     b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
-    h.assemble_rhs(dev(f), b)
-    ref = s.rhs(f)
+    h.assemble_rhs(dev(f), b, dev(g) if g is not None else None)
+    ref = s.rhs(f, g)
     assert np.abs(b.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
+def test_rhs_lifting_with_dirichlet_data(ctx):
+    """Nonhomogeneous Dirichlet data on a scalar problem: b = g on Dirichlet
+    rows, the couplings lifted into the free rows."""
+    lm, prob, oh, h = setup_case(ctx, "td_adaptive")
+    s = system_for(oh, prob)
+    xy = oh.fine.mesh.coords
+    f = rhs_for("td", xy, 1)
+    g = 1.0 + xy[:, 0] ** 2 - 0.5 * xy[:, 1]
+    b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(dev(f), b, dev(g))
+    ref = s.rhs(f, g)
+    assert np.abs(b.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(b, x, rtol=1e-10, max_it=200)
+    xstar = s.H @ spl.spsolve(s.A.tocsc(), ref)
+    assert st.status == 0
+    assert np.abs(x.cpu().numpy() - xstar).max() <= 1e-8 * np.abs(xstar).max()
+    assert np.array_equal(x.cpu().numpy()[s.dirichlet], g[s.dirichlet])
+
+
 def lumped_weights(oh, prob):
-    s = PB.build_system(oh.fine.mesh, prob)
+    s = system_for(oh, prob)
     m = np.asarray(s.F.sum(axis=1)).ravel()
     return np.repeat(m, prob.nc)
 
@@ -196,13 +241,13 @@ def lumped_weights(oh, prob):
 @pytest.mark.parametrize("name", list(CASES))
 def test_solve_matches_direct(ctx, name, prec):
     lm, prob, oh, h = setup_case(ctx, name)
-    s = PB.build_system(oh.fine.mesh, prob)
+    s = system_for(oh, prob)
     f = rhs_for(name, oh.fine.mesh.coords, prob.nc)
-    bref = s.rhs(f)
+    bref = s.rhs(f, g_for(name, oh.fine.mesh.coords))
     xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
     b = dev(bref)
     x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
-    st = h.solve(b, x, rtol=1e-10, max_it=200, prec=prec)
+    st = h.solve(b, x, rtol=1e-10, max_it=600, prec=prec)
     assert st.status == 0, st.as_dict()
     assert st.rel_res <= 1e-10
     xg = x.cpu().numpy()
