@@ -398,6 +398,8 @@ def main():
     h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
     setup_s = time.perf_counter() - t0
     info = h.info
+    # kernels launched by setup (autotuner V-cycles): a profiler skips these to reach the solves
+    print(f"launches after setup: {h.launch_count()}", file=sys.stderr, flush=True)
     n_free = info.n_free
     coords = h.coords()
     f = torch.from_numpy(np.ascontiguousarray(ffun(coords), dtype=np.float64)).cuda()

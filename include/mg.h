@@ -147,6 +147,16 @@ typedef struct {
   int autotune;                /* 1 (default): at setup, time V-cycles over
                                   tail thresholds x cluster sizes and keep the
                                   fastest (cached per hierarchy shape)        */
+  double inner_rtol;           /* > 0: defect correction -- every round runs
+                                  the Krylov method until its residual fell by
+                                  this factor (or reached rtol), then the FP64
+                                  defect b - A x is recomputed and the next
+                                  round solves for the correction (0: off)    */
+  int sell_sigma;              /* SELL-C-sigma window: rows of each window of
+                                  sigma rows sorted by length before slicing
+                                  (-1: automatic, 256 on levels of >= 32768
+                                  rows; 0: never; > 0: this window on every
+                                  level, a multiple of 32)                    */
 } mg_opts;
 
 typedef struct {

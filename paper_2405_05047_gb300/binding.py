@@ -54,7 +54,8 @@ class MgOpts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("min_level", C.c_int),
                 ("max_levels", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("store_fp64", C.c_int),
                 ("store_fp32", C.c_int), ("launch_mode", C.c_int),
-                ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int)]
+                ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int),
+                ("inner_rtol", C.c_double), ("sell_sigma", C.c_int)]
 
 
 class MgInfo(C.Structure):

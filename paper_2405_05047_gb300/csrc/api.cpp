@@ -166,6 +166,8 @@ void mg_default_opts(mg_opts* o) {
   o->tail_rows = 4096;
   o->store_bf16 = 0;
   o->autotune = 1;
+  o->inner_rtol = 0.0;
+  o->sell_sigma = -1;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -213,6 +215,9 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   else mg_default_opts(&opts);
   if (opts.nu1 < 1 || opts.nu2 < 0 || opts.nu1 > 16 || opts.nu2 > 16) return fail(MG_ERR_INVALID, "nu1 must be >= 1");
   if (!(opts.omega > 0.0)) return fail(MG_ERR_INVALID, "omega must be positive");
+  if (!(opts.inner_rtol >= 0.0 && opts.inner_rtol < 1.0)) return fail(MG_ERR_INVALID, "inner_rtol must be in [0, 1)");
+  if (opts.sell_sigma < -1 || (opts.sell_sigma > 0 && opts.sell_sigma % 32 != 0))
+    return fail(MG_ERR_INVALID, "sell_sigma must be -1, 0 or a positive multiple of 32");
   if (!opts.store_fp64 && !opts.store_fp32 && !opts.store_bf16) return fail(MG_ERR_INVALID, "no precision stored");
   if (!opts.store_fp64 && !(opts.store_fp32 || opts.store_bf16))
     return fail(MG_ERR_INVALID, "no precision stored");

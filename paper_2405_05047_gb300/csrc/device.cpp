@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <numeric>
 
 namespace mgi {
 
@@ -71,15 +72,39 @@ VT to_vt(double v) { return (VT)v; }
 template <>
 __nv_bfloat16 to_vt<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }   // via FP32, round to nearest even
 
-// SELL-C packing of a block CSR matrix (C = kSlice block rows per slice).
+// SELL-C-sigma packing of a block CSR matrix (C = kSlice block rows per
+// slice).  With sigma > 0 the rows of every window of sigma consecutive rows
+// are ordered by decreasing length before slicing, so rows of similar length
+// share a slice (less padding); perm[sell row] = matrix row.  A window is one
+// thread block of the kernels (kBlock rows), so the permuted vector accesses
+// stay within one block's rows.
 template <typename VT>
-void pack_sell(const BlockCSR& M, std::vector<int64_t>& sptr, std::vector<int32_t>& col, std::vector<VT>& val) {
+void pack_sell(const BlockCSR& M, int64_t sigma, std::vector<int64_t>& sptr, std::vector<int32_t>& col,
+               std::vector<VT>& val, std::vector<int32_t>& perm) {
   const int nb = M.nc * M.nc;
   const int64_t n = M.n, ns = (n + kSlice - 1) / kSlice;
+  perm.clear();
+  if (sigma > 0) {
+    perm.resize(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    for (int64_t w0 = 0; w0 < n; w0 += sigma) {
+      const int64_t w1 = std::min(n, w0 + sigma);
+      std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int32_t a, int32_t b) {
+        return M.ptr[a + 1] - M.ptr[a] > M.ptr[b + 1] - M.ptr[b];
+      });
+    }
+    bool identity = true;
+    for (int64_t r = 0; r < n && identity; ++r) identity = perm[r] == r;
+    if (identity) perm.clear();
+  }
+  auto mrow = [&](int64_t r) -> int64_t { return perm.empty() ? r : perm[r]; };
   sptr.assign(ns + 1, 0);
   for (int64_t s = 0; s < ns; ++s) {
     int64_t w = 0;
-    for (int64_t r = s * kSlice; r < std::min(n, (s + 1) * kSlice); ++r) w = std::max(w, M.ptr[r + 1] - M.ptr[r]);
+    for (int64_t r = s * kSlice; r < std::min(n, (s + 1) * kSlice); ++r) {
+      const int64_t q = mrow(r);
+      w = std::max(w, M.ptr[q + 1] - M.ptr[q]);
+    }
     sptr[s + 1] = sptr[s] + kSlice * w;
   }
   const int64_t slots = sptr[ns];
@@ -89,26 +114,29 @@ void pack_sell(const BlockCSR& M, std::vector<int64_t>& sptr, std::vector<int32_
     const int64_t w = (sptr[s + 1] - sptr[s]) / kSlice;
     for (int lane = 0; lane < kSlice; ++lane) {
       const int64_t r = s * kSlice + lane;
-      const int64_t len = r < n ? M.ptr[r + 1] - M.ptr[r] : 0;
+      const int64_t q = r < n ? mrow(r) : -1;
+      const int64_t len = q >= 0 ? M.ptr[q + 1] - M.ptr[q] : 0;
       for (int64_t j = 0; j < w; ++j) {
         const int64_t g = sptr[s] + kSlice * j, o = g + lane;
         if (j < len) {
-          col[o] = (int32_t)M.col[M.ptr[r] + j];
-          for (int e = 0; e < nb; ++e) val[g * nb + (int64_t)e * kSlice + lane] = to_vt<VT>(M.val[(M.ptr[r] + j) * nb + e]);
+          col[o] = (int32_t)M.col[M.ptr[q] + j];
+          for (int e = 0; e < nb; ++e) val[g * nb + (int64_t)e * kSlice + lane] = to_vt<VT>(M.val[(M.ptr[q] + j) * nb + e]);
         } else {
-          col[o] = (int32_t)(r < n ? std::min<int64_t>(r, M.m - 1) : 0);
+          col[o] = (int32_t)(q >= 0 ? std::min<int64_t>(q, M.m - 1) : 0);
         }
       }
     }
   }
 }
 
+// sigma: SELL-C-sigma window (0: rows in matrix order)
 template <typename VT>
-int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out) {
+int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0) {
   std::vector<int64_t> sptr;
   std::vector<int32_t> col;
   std::vector<VT> val;
-  pack_sell<VT>(M, sptr, col, val);
+  std::vector<int32_t> perm;
+  pack_sell<VT>(M, sigma, sptr, col, val, perm);
   void* dp = dev_alloc(h->ctx, h->allocs, h->bytes, sptr.size() * 8, true);
   void* dc = dev_alloc(h->ctx, h->allocs, h->bytes, col.size() * 4, true);
   void* dv = dev_alloc(h->ctx, h->allocs, h->bytes, val.size() * sizeof(VT), true);
@@ -116,6 +144,13 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out) {
   CU(cudaMemcpy(dp, sptr.data(), sptr.size() * 8, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(dc, col.data(), col.size() * 4, cudaMemcpyHostToDevice));
   if (!val.empty()) CU(cudaMemcpy(dv, val.data(), val.size() * sizeof(VT), cudaMemcpyHostToDevice));
+  out->v.perm = out->t.perm = nullptr;
+  if (!perm.empty()) {
+    void* dq = dev_alloc(h->ctx, h->allocs, h->bytes, perm.size() * 4, true);
+    if (!dq) return fail(MG_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpy(dq, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
+    out->v.perm = out->t.perm = (const int32_t*)dq;
+  }
   out->v.sptr = out->t.sptr = (const int64_t*)dp;
   out->v.col = out->t.col = (const int32_t*)dc;
   out->v.val = dv;
@@ -130,6 +165,18 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out) {
 template <typename T>
 T* halloc(mg_hier* h, int64_t n) {
   return (T*)dev_alloc(h->ctx, h->allocs, h->bytes, (size_t)std::max<int64_t>(n, 1) * sizeof(T), true);
+}
+
+// SELL-C-sigma window of the level operators and transfers, used on levels
+// with at least kSigmaMinRows rows: there the padding costs bandwidth, while
+// on the small, latency-bound levels the extra permutation load would cost
+// more than it saves.
+constexpr int64_t kSigma = kBlock;
+constexpr int64_t kSigmaMinRows = 32768;
+int64_t sigma_for(const mg_hier* h, int64_t rows) {
+  const int o = h->opts.sell_sigma;
+  if (o >= 0) return o;
+  return rows >= kSigmaMinRows ? kSigma : 0;
 }
 
 // ---------------------------------------------------------------- precision helpers
@@ -305,20 +352,20 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     h->level_real_nnzb.push_back(lv.A.nnzb());
     int rc;
     if (opts.store_fp64) {
-      if ((rc = upload_sell<double>(h, lv.A, &B.A64))) return rc;
+      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n)))) return rc;
       B.S64 = halloc<double>(h, B.n * nb);
       if (!B.S64) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
     }
     if (opts.store_fp32) {
-      if ((rc = upload_sell<float>(h, lv.A, &B.A32))) return rc;
+      if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n)))) return rc;
       std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
       B.S32 = halloc<float>(h, B.n * nb);
       if (!B.S32) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
     }
     if (opts.store_bf16) {
-      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16))) return rc;
+      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n)))) return rc;
       B.A16.v.bf16 = 1;
       if (!B.S32) {
         std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
@@ -329,8 +376,8 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     }
     h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
     if (l > 0) {
-      if ((rc = upload_sell<float>(h, lv.P, &B.P))) return rc;
-      if ((rc = upload_sell<float>(h, lv.R, &B.R))) return rc;
+      if ((rc = upload_sell<float>(h, lv.P, &B.P, sigma_for(h, lv.P.n)))) return rc;
+      if ((rc = upload_sell<float>(h, lv.R, &B.R, sigma_for(h, lv.R.n)))) return rc;
       // per-component rows of partly fixed nodes (block problems)
       auto partial_mask = [&](const HostLevel& X, const uint8_t** out) -> int {
         const uint8_t all = (uint8_t)((1 << nc) - 1);
@@ -868,7 +915,11 @@ int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const do
   CU(cudaMemcpyAsync(w.bi, b, n * 8, b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   CU(cudaMemcpyAsync(w.p, x0, n * 8, x0_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   launch_copy_fixed(h->n_nodes, h->nc, h->fixmask, w.bi, w.p, w.xi, s);
-  launch_norm_init(h->n_nodes, h->nc, h->fixmask, w.bi, w.part, w.st, rtol, max_it, s);
+  // defect correction: the first round stops at inner_rtol (relative to b; x0
+  // contributes through the recomputed defect of the next round)
+  const double inner = h->opts.inner_rtol;
+  launch_norm_init(h->n_nodes, h->nc, h->fixmask, w.bi, w.part, w.st, inner > 0 ? std::max(rtol, inner) : rtol,
+                   max_it, s);
   w.launches += 2;
   return enqueue_round(h, w, s);
 }
@@ -883,7 +934,7 @@ int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats) {
   if (S.status == -6) status = MG_ERR_NAN;
   else if (S.status == -5) status = MG_ERR_BREAKDOWN;
   else if (rel <= w.rtol) status = MG_OK;
-  else if (S.iter >= w.max_it || w.rounds >= 3) status = MG_ERR_NOT_CONVERGED;
+  else if (S.iter >= w.max_it || w.rounds >= (h->opts.inner_rtol > 0 ? 200 : 3)) status = MG_ERR_NOT_CONVERGED;
   else status = MG_PENDING;
   const int iters_round = S.iter - w.iter_base;
   if (status == MG_PENDING) {
@@ -895,6 +946,8 @@ int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats) {
     fix.restart_pos = fix.iter;
     fix.gm_j = 0;
     fix.gm_end = 0;
+    // defect correction: this round reduces the current true defect by inner_rtol
+    if (h->opts.inner_rtol > 0) fix.rtol = std::max(w.rtol, h->opts.inner_rtol * rel);
     *w.st_host = fix;
     CU(cudaMemcpyAsync(w.st, w.st_host, sizeof(KrylovState), cudaMemcpyHostToDevice, s));
     // reset hanging / Dirichlet entries of the iterate

@@ -95,6 +95,14 @@ __device__ __forceinline__ AT ldv(const VT* p) {
   else return (AT)mld<LM>(p);
 }
 
+// Output row of SELL row `row` (< A.n): rows may be sorted by length within
+// windows (SELL-C-sigma); perm maps them back to node order.
+template <int LM = 0, typename V>
+__device__ __forceinline__ int64_t srow(const V& A, int64_t row) {
+  if (A.perm && row < A.n) return (int64_t)mld<LM>(A.perm + row);
+  return row;
+}
+
 // y_row = sum_j A(row, j) x_j for a scalar SELL row (thread = row).  Slots
 // are processed in batches of 4 (column and value loads of a batch issued
 // together, then the 4 gathers, then the FMAs in slot order); the slice width
@@ -165,13 +173,43 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
   }
 }
 
+// Slot groups are processed two at a time (both column loads, then both
+// blocks' values and gathers, then the FMAs in slot order), so a thread keeps
+// two dependent load chains in flight; the group count is warp-uniform.
 template <typename T, int LM = 0, typename VT = T>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
                                           T acc[3]) {
   const int64_t s0 = mld<LM>(A.sptr + slice), s1 = mld<LM>(A.sptr + slice + 1);
   const VT* __restrict__ val = (const VT*)A.val;
   acc[0] = acc[1] = acc[2] = T(0);
-  for (int64_t g = s0; g < s1; g += 32) {
+  int64_t g = s0;
+  for (; g + 32 < s1; g += 64) {
+    const int ca = mld<LM>(A.col + g + lane), cb = mld<LM>(A.col + g + 32 + lane);
+    const VT* __restrict__ va = val + g * 9 + lane;
+    const VT* __restrict__ vb = va + 32 * 9;
+    T ma[9], mb[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) { ma[e] = ldv<T, LM>(va + e * 32); mb[e] = ldv<T, LM>(vb + e * 32); }
+    const T xa0 = vld<LM>(x + 3 * ca), xa1 = vld<LM>(x + 3 * ca + 1), xa2 = vld<LM>(x + 3 * ca + 2);
+    const T xb0 = vld<LM>(x + 3 * cb), xb1 = vld<LM>(x + 3 * cb + 1), xb2 = vld<LM>(x + 3 * cb + 2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T a = acc[i];
+      a = fmad(ma[3 * i + 0], xa0, a);
+      a = fmad(ma[3 * i + 1], xa1, a);
+      a = fmad(ma[3 * i + 2], xa2, a);
+      acc[i] = a;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T a = acc[i];
+      a = fmad(mb[3 * i + 0], xb0, a);
+      a = fmad(mb[3 * i + 1], xb1, a);
+      a = fmad(mb[3 * i + 2], xb2, a);
+      acc[i] = a;
+    }
+  }
+  if (g < s1) {
     const int c = mld<LM>(A.col + g + lane);
     const VT* __restrict__ v = val + g * 9 + lane;
     const T x0 = vld<LM>(x + 3 * c), x1 = vld<LM>(x + 3 * c + 1), x2 = vld<LM>(x + 3 * c + 2);
@@ -223,12 +261,13 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
                                            T* xo, T omega, bool from_zero) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
+  const int64_t orow = srow<LM>(A, row);
   if (NC == 1) {
     T r = from_zero ? T(0) : sell_dot1<T, LM, VT>(A, slice, lane, x);
     if (row < A.n) {
-      const T bi = vld<LM>(b + row);
-      if (from_zero) xo[row] = omega * Sinv[row] * bi;
-      else xo[row] = fmad(omega * Sinv[row], bi - r, vld<LM>(x + row));
+      const T bi = vld<LM>(b + orow);
+      if (from_zero) xo[orow] = omega * Sinv[orow] * bi;
+      else xo[orow] = fmad(omega * Sinv[orow], bi - r, vld<LM>(x + orow));
     }
   } else {
     T acc[3] = {T(0), T(0), T(0)};
@@ -236,14 +275,14 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
     if (row < A.n) {
       T res[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) res[i] = vld<LM>(b + 3 * row + i) - acc[i];
-      const T* S = Sinv + 9 * row;
+      for (int i = 0; i < 3; ++i) res[i] = vld<LM>(b + 3 * orow + i) - acc[i];
+      const T* S = Sinv + 9 * orow;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         T c = S[3 * i] * res[0];
         c = fmad(S[3 * i + 1], res[1], c);
         c = fmad(S[3 * i + 2], res[2], c);
-        xo[3 * row + i] = from_zero ? omega * c : fmad(omega, c, vld<LM>(x + 3 * row + i));
+        xo[3 * orow + i] = from_zero ? omega * c : fmad(omega, c, vld<LM>(x + 3 * orow + i));
       }
     }
   }
@@ -253,15 +292,16 @@ template <typename T, int NC, int LM, typename VT = T>
 __device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
+  const int64_t orow = srow<LM>(A, row);
   if (NC == 1) {
     T r = sell_dot1<T, LM, VT>(A, slice, lane, x);
-    if (row < A.n) y[row] = vld<LM>(b + row) - r;
+    if (row < A.n) y[orow] = vld<LM>(b + orow) - r;
   } else {
     T acc[3];
     sell_dot3<T, LM, VT>(A, slice, lane, x, acc);
     if (row < A.n)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) y[3 * row + i] = vld<LM>(b + 3 * row + i) - acc[i];
+      for (int i = 0; i < 3; ++i) y[3 * orow + i] = vld<LM>(b + 3 * orow + i) - acc[i];
   }
 }
 
@@ -270,6 +310,7 @@ __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row,
                                              T* x0, T omega) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
+  const int64_t orow = srow<LM>(R, row);
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
@@ -277,24 +318,24 @@ __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row,
   if (row < R.n) {
     if constexpr (NC > 1)
       if (R.fix) {
-        const unsigned m = mld<LM>(R.fix + row);
+        const unsigned m = mld<LM>(R.fix + orow);
 #pragma unroll
         for (int c = 0; c < NC; ++c)
           if ((m >> c) & 1u) acc[c] = T(0);
       }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) d[NC * row + c] = acc[c];
+    for (int c = 0; c < NC; ++c) d[NC * orow + c] = acc[c];
     if (x0) {
       if (NC == 1) {
-        x0[row] = omega * Sinv[row] * acc[0];
+        x0[orow] = omega * Sinv[orow] * acc[0];
       } else {
-        const T* S = Sinv + NC * NC * row;
+        const T* S = Sinv + NC * NC * orow;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
           T c = S[NC * i] * acc[0];
 #pragma unroll
           for (int k = 1; k < NC; ++k) c = fmad(S[NC * i + k], acc[k], c);
-          x0[NC * row + i] = omega * c;
+          x0[NC * orow + i] = omega * c;
         }
       }
     }
@@ -305,6 +346,7 @@ template <typename T, int NC, int LM>
 __device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, const T* y, const T* xin, T* xo) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
+  const int64_t orow = srow<LM>(P, row);
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
@@ -312,13 +354,13 @@ __device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, 
   if (row < P.n) {
     if constexpr (NC > 1)
       if (P.fix) {
-        const unsigned m = mld<LM>(P.fix + row);
+        const unsigned m = mld<LM>(P.fix + orow);
 #pragma unroll
         for (int c = 0; c < NC; ++c)
           if ((m >> c) & 1u) acc[c] = T(0);
       }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) xo[NC * row + c] = vld<LM>(xin + NC * row + c) + acc[c];
+    for (int c = 0; c < NC; ++c) xo[NC * orow + c] = vld<LM>(xin + NC * orow + c) + acc[c];
   }
 }
 
@@ -337,9 +379,11 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, 
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     row_smooth<T, NC, 0, VT>(A, row, x, b, Sinv, xo, omega, FROM_ZERO);
-    if (xo64 && row < A.n)
+    if (xo64 && row < A.n) {
+      const int64_t orow = srow<0>(A, row);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) xo64[NC * row + c] = (double)xo[NC * row + c] * sc;
+      for (int c = 0; c < NC; ++c) xo64[NC * orow + c] = (double)xo[NC * orow + c] * sc;
+    }
   }
 }
 
@@ -356,15 +400,16 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, c
     }
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
+  const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       T r = sell_dot1<T, 0, VT>(A, slice, lane, x);
-      if (row < A.n) y[row] = r;
+      if (row < A.n) y[orow] = r;
     } else {
       T acc[3];
       sell_dot3<T, 0, VT>(A, slice, lane, x, acc);
       if (row < A.n)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) y[3 * row + i] = acc[i];
+        for (int i = 0; i < 3; ++i) y[3 * orow + i] = acc[i];
     }
   }
 }
@@ -513,9 +558,11 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
       const double sc = out64 ? *scale : 1.0;
       for (int64_t row = tid; row < L.A.nslices * 32; row += nth) {
         row_smooth<T, NC, TLM, VT>(L.A, row, cur, bvec(l), (const T*)L.S, dst, om, false);
-        if (out64 && row < L.A.n)
+        if (out64 && row < L.A.n) {
+          const int64_t orow = srow<TLM>(L.A, row);
 #pragma unroll
-          for (int c = 0; c < NC; ++c) o64[NC * row + c] = (double)dst[NC * row + c] * sc;
+          for (int c = 0; c < NC; ++c) o64[NC * orow + c] = (double)dst[NC * orow + c] * sc;
+        }
       }
       tail_sync();
       cur = dst;
@@ -708,14 +755,15 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_residual_norm(SellV
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
+  const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       double ax = sell_dot1<double>(A, slice, lane, x);
-      if (row < A.n) { double ri = b[row] - ax; r[row] = ri; acc = fma(ri, ri, acc); }
+      if (row < A.n) { double ri = b[orow] - ax; r[orow] = ri; acc = fma(ri, ri, acc); }
     } else {
       double a3[3];
       sell_dot3<double>(A, slice, lane, x, a3);
       if (row < A.n)
-        for (int i = 0; i < 3; ++i) { double ri = b[3 * row + i] - a3[i]; r[3 * row + i] = ri; acc = fma(ri, ri, acc); }
+        for (int i = 0; i < 3; ++i) { double ri = b[3 * orow + i] - a3[i]; r[3 * orow + i] = ri; acc = fma(ri, ri, acc); }
     }
   }
   const int q[1] = {Q_RR};
@@ -844,12 +892,13 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_dot(SellView A
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
+  const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, p.f) * sc
                             : sell_dot1<double>(A, slice, lane, p.d);
       if (row < A.n) {
-        out[row] = ax;
-        acc = fma(w ? w[row] : (F32 ? (double)p.f[row] * sc : p.d[row]), ax, acc);
+        out[orow] = ax;
+        acc = fma(w ? w[orow] : (F32 ? (double)p.f[orow] * sc : p.d[orow]), ax, acc);
       }
     } else {
       double a3[3];
@@ -858,8 +907,8 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_dot(SellView A
       if (row < A.n)
         for (int i = 0; i < 3; ++i) {
           const double y = F32 ? a3[i] * sc : a3[i];
-          out[3 * row + i] = y;
-          acc = fma(w ? w[3 * row + i] : (F32 ? (double)p.f[3 * row + i] * sc : p.d[3 * row + i]), y, acc);
+          out[3 * orow + i] = y;
+          acc = fma(w ? w[3 * orow + i] : (F32 ? (double)p.f[3 * orow + i] * sc : p.d[3 * orow + i]), y, acc);
         }
     }
   }
@@ -992,10 +1041,11 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_2dots(SellView
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
+  const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, shv.f) * sc
                             : sell_dot1<double>(A, slice, lane, shv.d);
-      if (row < A.n) { t[row] = ax; a = fma(ax, sv[row], a); c = fma(ax, ax, c); }
+      if (row < A.n) { t[orow] = ax; a = fma(ax, sv[orow], a); c = fma(ax, ax, c); }
     } else {
       double a3[3];
       if (F32) sell_dot3<double, float>(A, slice, lane, shv.f, 1.0, a3);
@@ -1003,8 +1053,8 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_2dots(SellView
       if (row < A.n)
         for (int i = 0; i < 3; ++i) {
           const double y = F32 ? a3[i] * sc : a3[i];
-          t[3 * row + i] = y;
-          a = fma(y, sv[3 * row + i], a);
+          t[3 * orow + i] = y;
+          a = fma(y, sv[3 * orow + i], a);
           c = fma(y, y, c);
         }
     }
@@ -1098,13 +1148,14 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_spmv(SellView A,
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
+  const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, z.f)
                             : sell_dot1<double>(A, slice, lane, z.d);
       if (row < A.n) {
-        w[row] = ax;
-        if (F32) G.Z32[(int64_t)j * n + row] = z.f[row];
-        else G.Z64[(int64_t)j * n + row] = z.d[row];
+        w[orow] = ax;
+        if (F32) G.Z32[(int64_t)j * n + orow] = z.f[orow];
+        else G.Z64[(int64_t)j * n + orow] = z.d[orow];
       }
     } else {
       double a3[3];
@@ -1112,9 +1163,9 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_spmv(SellView A,
       else sell_dot3<double>(A, slice, lane, z.d, a3);
       if (row < A.n)
         for (int i = 0; i < 3; ++i) {
-          w[3 * row + i] = a3[i];
-          if (F32) G.Z32[(int64_t)j * n + 3 * row + i] = z.f[3 * row + i];
-          else G.Z64[(int64_t)j * n + 3 * row + i] = z.d[3 * row + i];
+          w[3 * orow + i] = a3[i];
+          if (F32) G.Z32[(int64_t)j * n + 3 * orow + i] = z.f[3 * orow + i];
+          else G.Z64[(int64_t)j * n + 3 * orow + i] = z.d[3 * orow + i];
         }
     }
   }
@@ -1281,14 +1332,15 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_residual(SellVie
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
+  const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       double ax = sell_dot1<double>(A, slice, lane, x);
-      if (row < A.n) { double ri = b[row] - ax; r[row] = ri; acc = fma(ri, ri, acc); }
+      if (row < A.n) { double ri = b[orow] - ax; r[orow] = ri; acc = fma(ri, ri, acc); }
     } else {
       double a3[3];
       sell_dot3<double>(A, slice, lane, x, a3);
       if (row < A.n)
-        for (int i = 0; i < 3; ++i) { double ri = b[3 * row + i] - a3[i]; r[3 * row + i] = ri; acc = fma(ri, ri, acc); }
+        for (int i = 0; i < 3; ++i) { double ri = b[3 * orow + i] - a3[i]; r[3 * orow + i] = ri; acc = fma(ri, ri, acc); }
     }
   }
   const int q[1] = {Q_RR};

@@ -22,6 +22,7 @@ struct SellView {
   int64_t n = 0;          // block rows
   int64_t nslices = 0;
   int bf16 = 0;           // values stored as BF16 (read by the FP32 kernels, widened to FP32)
+  const int32_t* perm = nullptr;   // SELL row -> node row (rows sorted by length within windows), or NULL
 };
 
 // Transfer matrices (P, R) are scalar SELL with float weights, applied to
@@ -34,7 +35,8 @@ struct TransferView {
   const float* w = nullptr;
   int64_t n = 0;
   int64_t nslices = 0;
-  const uint8_t* fix = nullptr;
+  const uint8_t* fix = nullptr;    // indexed by node row
+  const int32_t* perm = nullptr;   // SELL row -> node row, or NULL
 };
 
 // Scalars of the Krylov loop, resident in device memory.

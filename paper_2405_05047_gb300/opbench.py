@@ -39,6 +39,12 @@ def make(workload):
         n = int(workload[len("elasticity"):])
         return (W.elasticity3d(n), B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
                 {"omega": 0.5})
+    if workload.startswith("oseen"):
+        rounds = int(workload[len("oseen"):] or 12)
+        lm = W.oseen_channel(1, rounds)
+        beta = W.oseen_beta(B.mg_mesh_nodes(lm))
+        return (lm, B.make_problem(kind=B.MG_OSEEN, dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01, conv=beta),
+                {"krylov": B.MG_GMRES})
     raise SystemExit(f"unknown workload {workload}")
 
 

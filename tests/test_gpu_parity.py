@@ -260,6 +260,26 @@ def test_solve_matches_direct(ctx, name, prec):
     assert np.linalg.norm(bref - oh.fine.A @ xr) <= 1.01e-10 * np.linalg.norm(bref[~s.fixed])
 
 
+@pytest.mark.parametrize("name", ["poisson64", "elasticity16", "oseen"])
+def test_defect_correction_rounds(ctx, name):
+    """Defect correction (inner_rtol): rounds of the mixed-precision Krylov
+    solve, each on the recomputed FP64 defect, reach the outer tolerance and
+    the direct solution."""
+    lm, prob, oh, h0 = setup_case(ctx, name)
+    mk, _, pkw, okw = CASES[name]
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(inner_rtol=1e-2, autotune=0, **okw))
+    s = system_for(oh, prob)
+    bref = s.rhs(rhs_for(name, oh.fine.mesh.coords, prob.nc), g_for(name, oh.fine.mesh.coords))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(dev(bref), x, rtol=1e-10, max_it=2000, prec=B.MG_MIXED_FP32)
+    assert st.status == 0 and st.rel_res <= 1e-10, st.as_dict()
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= 1e-8
+    h.free()
+
+
 def test_solve_host_equals_device(ctx):
     lm, prob, oh, h = setup_case(ctx, "td_adaptive")
     s = PB.build_system(oh.fine.mesh, prob)
@@ -348,6 +368,40 @@ def test_shared_memory_tail_solve_identical(ctx, prec):
         its.append(st.iters)
     assert its[0] == its[1] and np.array_equal(xs[0], xs[1])
     h.free()
+
+
+@pytest.mark.parametrize("name", ["td_adaptive", "oseen", "elasticity16"])
+def test_sell_sigma_sorting_is_bitwise_neutral(ctx, name):
+    """Rows sorted by length within windows (SELL-C-sigma) give the same V-cycle
+    bits as rows in node order (each row's sum keeps its order), and a solve
+    with sorted rows still matches the direct solution."""
+    lm, prob, oh, _ = setup_case(ctx, name)
+    mk, _, pkw, okw = CASES[name]
+    hs = [G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(sell_sigma=sg, autotune=0, **okw))
+          for sg in (0, 256)]
+    rng = np.random.default_rng(8)
+    n = oh.fine.A.shape[0]
+    r = rng.standard_normal(n)
+    r[oh.fine.sys.fixed] = 0.0
+    for prec, dt in ((B.MG_FP64, torch.float64), (B.MG_MIXED_FP32, torch.float32)):
+        outs = []
+        for hh in hs:
+            hh.tune(prec, 0, 1)
+            z = torch.empty(n, device="cuda", dtype=dt)
+            hh.vcycle(dev(r, dt), z, prec)
+            outs.append(z.cpu().numpy())
+        assert np.array_equal(outs[0], outs[1])
+    s = system_for(oh, prob)
+    bref = s.rhs(rhs_for(name, oh.fine.mesh.coords, prob.nc), g_for(name, oh.fine.mesh.coords))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(n, device="cuda", dtype=torch.float64)
+    st = hs[1].solve(dev(bref), x, rtol=1e-10, max_it=600, prec=B.MG_MIXED_FP32)
+    assert st.status == 0
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= 1e-8
+    for hh in hs:
+        hh.free()
 
 
 def test_direct_launch_mode_equals_graph(ctx):
