@@ -517,7 +517,8 @@ def main():
                    "n_free_dofs": int(n_free), "levels": int(info.levels), "hanging_nodes": int(info.n_hanging),
                    "rtol": args.rtol, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}", "tail_levels": int(info.tail_levels),
-                   "tail_cluster": int(info.tail_cluster), "tuned_vcycle_ms": info.vcycle_ms},
+                   "tail_cluster": int(info.tail_cluster), "tuned_vcycle_ms": info.vcycle_ms,
+                   "col16_slices": int(info.col16_slices), "col32_slices": int(info.col32_slices)},
         "iters": [s.iters for s in st_mixed], "rel_res": max(s.rel_res for s in st_mixed),
         "fp64": {"value": world * n_free / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
                  "iters": [s.iters for s in st64], "rel_res": max(s.rel_res for s in st64)},

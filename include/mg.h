@@ -157,6 +157,9 @@ typedef struct {
                                   (-1: automatic, 256 on levels of >= 32768
                                   rows; 0: never; > 0: this window on every
                                   level, a multiple of 32)                    */
+  int col16;                   /* 16-bit column offsets in the FP32/BF16 level
+                                  matrices (-1: automatic, levels of >= 32768
+                                  rows; 0: never; 1: every level)            */
 } mg_opts;
 
 typedef struct {
@@ -173,6 +176,9 @@ typedef struct {
   int tail_cluster;                     /* CTAs in that kernel's cluster (0: one
                                            CTA working in shared memory)         */
   double vcycle_ms;                     /* tuned V-cycle time (0 if not tuned)    */
+  int64_t col16_slices;                 /* slices read with 16-bit columns        */
+  int64_t col32_slices;                 /* slices of those matrices that keep
+                                           32-bit columns (offsets outside int16) */
 } mg_info;
 
 typedef struct {
@@ -290,7 +296,12 @@ int mg_restrict_static(mg_hier* h, int level, const void* x, const void* b, void
 /* Device time of one level operator: launches op (as mg_apply, on the
  * library's own level buffers, FP64 or FP32 per prec) `reps` times back to
  * back on the context's stream between two CUDA events and returns the mean
- * milliseconds per launch in *ms.  For measurement only. */
+ * milliseconds per launch in *ms.  Two more ops time whole V-cycles started on
+ * `level` (levels below it included, current tail configuration):
+ * MG_TIME_VCYCLE launches their kernels directly, MG_TIME_VCYCLE_GRAPH
+ * captures `reps` cycles into one CUDA graph and times its launch (the form
+ * the solves use).  For measurement only. */
+enum { MG_TIME_VCYCLE = 5, MG_TIME_VCYCLE_GRAPH = 6 };
 int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms);
 
 /* Serving: continuous batching of solves on resident hierarchies.

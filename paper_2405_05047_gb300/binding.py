@@ -24,6 +24,7 @@ MG_ERR_CANCELLED = -9
 MG_POISSON, MG_TRANSPORT, MG_ELASTICITY, MG_OSEEN = 0, 1, 2, 3
 MG_KRYLOV_AUTO, MG_CG, MG_BICGSTAB, MG_GMRES, MG_MGITER = 0, 1, 2, 3, 4
 MG_OP_MATVEC, MG_OP_SMOOTH, MG_OP_RESTRICT, MG_OP_PROLONG_ADD, MG_OP_COARSE = 0, 1, 2, 3, 4
+MG_TIME_VCYCLE, MG_TIME_VCYCLE_GRAPH = 5, 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -55,7 +56,7 @@ class MgOpts(C.Structure):
                 ("max_levels", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("store_fp64", C.c_int),
                 ("store_fp32", C.c_int), ("launch_mode", C.c_int),
                 ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int),
-                ("inner_rtol", C.c_double), ("sell_sigma", C.c_int)]
+                ("inner_rtol", C.c_double), ("sell_sigma", C.c_int), ("col16", C.c_int)]
 
 
 class MgInfo(C.Structure):
@@ -64,7 +65,7 @@ class MgInfo(C.Structure):
                 ("level_nnzb", C.c_int64 * 32), ("level_rows_nnzb", C.c_int64 * 32),
                 ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double),
                 ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
-                ("vcycle_ms", C.c_double)]
+                ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64)]
 
 
 class MgStats(C.Structure):

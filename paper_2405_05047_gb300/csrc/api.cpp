@@ -168,6 +168,7 @@ void mg_default_opts(mg_opts* o) {
   o->autotune = 1;
   o->inner_rtol = 0.0;
   o->sell_sigma = -1;
+  o->col16 = -1;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -305,6 +306,8 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
   info->tail_levels = h->tail_top > 0 ? h->tail_top + 1 : 0;
   info->tail_cluster = h->tail_cluster;
   info->vcycle_ms = h->tuned_vcycle_ms;
+  info->col16_slices = h->col16_slices;
+  info->col32_slices = h->col32_slices;
   info->n_hanging = h->n_hanging;
   info->omega = h->opts.omega;
   return MG_OK;
@@ -463,6 +466,42 @@ int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms) {
   std::lock_guard<std::mutex> lk(h->solve_mu);
   cudaStream_t s = h->ctx->stream;
   Workspace& w = *h->ws0;
+  if (op == MG_TIME_VCYCLE || op == MG_TIME_VCYCLE_GRAPH) {
+    LevelVecs& V = w.lv[level];
+    const bool bf = prec == MG_MIXED_BF16;
+    auto cycle = [&]() {
+      if (prec == MG_FP64) enqueue_vcycle<double>(h, w, level, V.b64, V.t64, nullptr, s);
+      else enqueue_vcycle<float>(h, w, level, V.b32, V.t32, nullptr, s, false, bf);
+    };
+    cycle();                          // warm (also the first-use setup of every kernel)
+    CU(cudaStreamSynchronize(s));
+    float t = 0;
+    if (op == MG_TIME_VCYCLE) {
+      CU(cudaEventRecord(w.ev0, s));
+      for (int i = 0; i < reps; ++i) cycle();
+      CU(cudaEventRecord(w.ev1, s));
+    } else {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      for (int i = 0; i < reps; ++i) cycle();
+      CU(cudaStreamEndCapture(s, &g));
+      cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(e));
+      CU(cudaGraphLaunch(ge, s));     // warm
+      CU(cudaEventRecord(w.ev0, s));
+      CU(cudaGraphLaunch(ge, s));
+      CU(cudaEventRecord(w.ev1, s));
+      CU(cudaEventSynchronize(w.ev1));
+      cudaGraphExecDestroy(ge);
+    }
+    CU(cudaEventSynchronize(w.ev1));
+    CU(cudaEventElapsedTime(&t, w.ev0, w.ev1));
+    *ms = (double)t / reps;
+    CU(cudaGetLastError());
+    return MG_OK;
+  }
   LevelVecs& V = w.lv[level];
   const bool d = prec == MG_FP64;
   const void* x = d ? (const void*)V.o64 : (const void*)V.o32;

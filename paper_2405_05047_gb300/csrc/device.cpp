@@ -129,32 +129,66 @@ void pack_sell(const BlockCSR& M, int64_t sigma, std::vector<int64_t>& sptr, std
   }
 }
 
-// sigma: SELL-C-sigma window (0: rows in matrix order)
+// 16-bit column offsets relative to each slice's 256-row window base;
+// slices with an offset outside int16 are flagged in bit 0 of sptr[slice]
+// and keep using the 32-bit columns.
+void pack_col16(const std::vector<int64_t>& sptr, const std::vector<int32_t>& col, std::vector<int64_t>& sptr_out,
+                std::vector<int16_t>& col16) {
+  const int64_t ns = (int64_t)sptr.size() - 1;
+  sptr_out = sptr;
+  col16.assign(col.size(), 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t base = (s / (kCol16Window / kSlice)) * kCol16Window;
+    bool fits = true;
+    for (int64_t o = sptr[s]; o < sptr[s + 1] && fits; ++o) {
+      const int64_t rel = (int64_t)col[o] - base;
+      fits = rel >= -32768 && rel <= 32767;
+    }
+    if (!fits) { sptr_out[s] |= 1; continue; }
+    for (int64_t o = sptr[s]; o < sptr[s + 1]; ++o) col16[o] = (int16_t)((int64_t)col[o] - base);
+  }
+}
+
+// Upload a matrix as SELL-C-sigma in one device allocation (sptr, col,
+// optional 16-bit columns, values, optional permutation; each 256-byte
+// aligned).  sigma: window of the row sort (0: rows in matrix order); idx16:
+// also store 16-bit column offsets.
 template <typename VT>
-int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0) {
+int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, bool idx16 = false) {
   std::vector<int64_t> sptr;
   std::vector<int32_t> col;
   std::vector<VT> val;
   std::vector<int32_t> perm;
+  std::vector<int16_t> col16;
   pack_sell<VT>(M, sigma, sptr, col, val, perm);
-  void* dp = dev_alloc(h->ctx, h->allocs, h->bytes, sptr.size() * 8, true);
-  void* dc = dev_alloc(h->ctx, h->allocs, h->bytes, col.size() * 4, true);
-  void* dv = dev_alloc(h->ctx, h->allocs, h->bytes, val.size() * sizeof(VT), true);
-  if (!dp || !dc || !dv) return fail(MG_ERR_OOM, "device allocation failed");
-  CU(cudaMemcpy(dp, sptr.data(), sptr.size() * 8, cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(dc, col.data(), col.size() * 4, cudaMemcpyHostToDevice));
-  if (!val.empty()) CU(cudaMemcpy(dv, val.data(), val.size() * sizeof(VT), cudaMemcpyHostToDevice));
-  out->v.perm = out->t.perm = nullptr;
-  if (!perm.empty()) {
-    void* dq = dev_alloc(h->ctx, h->allocs, h->bytes, perm.size() * 4, true);
-    if (!dq) return fail(MG_ERR_OOM, "device allocation failed");
-    CU(cudaMemcpy(dq, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
-    out->v.perm = out->t.perm = (const int32_t*)dq;
+  if (idx16) {
+    std::vector<int64_t> flagged;
+    pack_col16(sptr, col, flagged, col16);
+    sptr.swap(flagged);
+    for (size_t k = 0; k + 1 < sptr.size(); ++k) {
+      if (sptr[k] & 1) h->col32_slices++;
+      else h->col16_slices++;
+    }
   }
-  out->v.sptr = out->t.sptr = (const int64_t*)dp;
-  out->v.col = out->t.col = (const int32_t*)dc;
-  out->v.val = dv;
-  out->t.w = (const float*)dv;
+  auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_sptr = sptr.size() * 8, b_col = col.size() * 4, b_c16 = col16.size() * 2,
+               b_val = val.size() * sizeof(VT), b_perm = perm.size() * 4;
+  // 16-bit columns and values adjacent: the part a sweep streams
+  const size_t o_c16 = 0, o_val = r256(b_c16), o_col = o_val + r256(b_val), o_sptr = o_col + r256(b_col),
+               o_perm = o_sptr + r256(b_sptr), total = o_perm + r256(b_perm);
+  unsigned char* base = (unsigned char*)dev_alloc(h->ctx, h->allocs, h->bytes, std::max<size_t>(total, 256), true);
+  if (!base) return fail(MG_ERR_OOM, "device allocation failed");
+  CU(cudaMemcpy(base + o_sptr, sptr.data(), b_sptr, cudaMemcpyHostToDevice));
+  if (b_col) CU(cudaMemcpy(base + o_col, col.data(), b_col, cudaMemcpyHostToDevice));
+  if (b_c16) CU(cudaMemcpy(base + o_c16, col16.data(), b_c16, cudaMemcpyHostToDevice));
+  if (b_val) CU(cudaMemcpy(base + o_val, val.data(), b_val, cudaMemcpyHostToDevice));
+  if (b_perm) CU(cudaMemcpy(base + o_perm, perm.data(), b_perm, cudaMemcpyHostToDevice));
+  out->v.perm = out->t.perm = b_perm ? (const int32_t*)(base + o_perm) : nullptr;
+  out->v.col16 = b_c16 ? (const int16_t*)(base + o_c16) : nullptr;
+  out->v.sptr = out->t.sptr = (const int64_t*)(base + o_sptr);
+  out->v.col = out->t.col = (const int32_t*)(base + o_col);
+  out->v.val = base + o_val;
+  out->t.w = (const float*)(base + o_val);
   out->v.n = out->t.n = M.n;
   out->v.nslices = out->t.nslices = (int64_t)sptr.size() - 1;
   out->slots = (int64_t)col.size();
@@ -173,6 +207,12 @@ T* halloc(mg_hier* h, int64_t n) {
 // more than it saves.
 constexpr int64_t kSigma = kBlock;
 constexpr int64_t kSigmaMinRows = 32768;
+// 16-bit column offsets for the FP32/BF16 copies of the large levels (the
+// streamed bytes per scalar entry drop from 8 to 6).
+bool idx16_for(const mg_hier* h, int64_t rows) {
+  const int o = h->opts.col16;
+  return o >= 0 ? o != 0 : rows >= kSigmaMinRows;
+}
 int64_t sigma_for(const mg_hier* h, int64_t rows) {
   const int o = h->opts.sell_sigma;
   if (o >= 0) return o;
@@ -358,14 +398,14 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
     }
     if (opts.store_fp32) {
-      if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n)))) return rc;
+      if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n)))) return rc;
       std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
       B.S32 = halloc<float>(h, B.n * nb);
       if (!B.S32) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
     }
     if (opts.store_bf16) {
-      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n)))) return rc;
+      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n)))) return rc;
       B.A16.v.bf16 = 1;
       if (!B.S32) {
         std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
@@ -634,7 +674,16 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
     return false;
   }
   if (l <= h->tail_top) {                                        // small levels: one cluster
-    launch_tail<T>(bf16 ? w.tail16 : Prec<T>::tail(w), nc, b, out, first_done, done, s, out64, scale);
+    const TailParams& TP = bf16 ? w.tail16 : Prec<T>::tail(w);
+    if (l < h->tail_top) {
+      // a cycle started below the tail's top level (measurement only): the
+      // kernel's top must be level l, whose vectors b and out are given
+      TailParams sub = TP;
+      sub.nt = l + 1;
+      launch_tail<T>(sub, nc, b, out, first_done, done, s, out64, scale);
+    } else {
+      launch_tail<T>(TP, nc, b, out, first_done, done, s, out64, scale);
+    }
     h->launch_count++;
     return out64 != nullptr && h->opts.nu2 > 0;
   }

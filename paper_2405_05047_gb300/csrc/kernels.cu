@@ -30,6 +30,10 @@ namespace {
 // Programmatic dependent launch: kernels are launched while their predecessor
 // drains; every kernel waits here before it reads anything the predecessor
 // wrote.
+// Programmatic dependent launch: wait until the preceding kernel of the
+// stream has completed and its writes are visible.  (Triggering the next
+// launch early was measured slower: the waiting blocks of the next kernel
+// take SM slots from the running one.)
 __device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
 
 __device__ __forceinline__ bool stopped(const int* done) { return done != nullptr && *(volatile const int*)done; }
@@ -108,15 +112,12 @@ __device__ __forceinline__ int64_t srow(const V& A, int64_t row) {
 // together, then the 4 gathers, then the FMAs in slot order); the slice width
 // is the same for the 32 threads of a warp, so the remainder switch is
 // warp-uniform.  The summation order is the plain sequential one.
-template <typename AT, int LM = 0, typename VT, typename XT>
-__device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
-                                         const VT* __restrict__ val, int64_t slice, int lane,
-                                         const XT* __restrict__ x) {
-  const int64_t s0 = mld<LM>(sptr + slice) + lane, s1 = mld<LM>(sptr + slice + 1);
+template <typename AT, int LM, typename VT, typename XT, typename CF>
+__device__ __forceinline__ AT sell_dot1x_loop(int64_t o, int64_t s1, const VT* __restrict__ val, const XT* __restrict__ x,
+                                              CF colat) {
   AT acc = AT(0);
-  int64_t o = s0;
   for (; o + 3 * 32 < s1; o += 4 * 32) {
-    const int c0 = mld<LM>(col + o), c1 = mld<LM>(col + o + 32), c2 = mld<LM>(col + o + 64), c3 = mld<LM>(col + o + 96);
+    const int c0 = colat(o), c1 = colat(o + 32), c2 = colat(o + 64), c3 = colat(o + 96);
     const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32), v2 = ldv<AT, LM>(val + o + 64),
              v3 = ldv<AT, LM>(val + o + 96);
     const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2), x3 = vld<LM>(x + c3);
@@ -127,34 +128,53 @@ __device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const
   }
   const int rem = (int)((s1 - o + 31) >> 5);   // 0..3, identical across the warp
   if (rem == 3) {
-    const int c0 = mld<LM>(col + o), c1 = mld<LM>(col + o + 32), c2 = mld<LM>(col + o + 64);
+    const int c0 = colat(o), c1 = colat(o + 32), c2 = colat(o + 64);
     const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32), v2 = ldv<AT, LM>(val + o + 64);
     const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
     acc = fmad(v2, (AT)x2, acc);
   } else if (rem == 2) {
-    const int c0 = mld<LM>(col + o), c1 = mld<LM>(col + o + 32);
+    const int c0 = colat(o), c1 = colat(o + 32);
     const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32);
     const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
   } else if (rem == 1) {
-    acc = fmad(ldv<AT, LM>(val + o), (AT)vld<LM>(x + mld<LM>(col + o)), acc);
+    acc = fmad(ldv<AT, LM>(val + o), (AT)vld<LM>(x + colat(o)), acc);
   }
   return acc;
 }
 
+// y_row = sum_j A(row, j) x_j for a scalar SELL row (thread = row).  Slots
+// are processed in batches of 4 (column and value loads of a batch issued
+// together, then the 4 gathers, then the FMAs in slot order); the slice width
+// is the same for the 32 threads of a warp, so the remainder switch is
+// warp-uniform.  The summation order is the plain sequential one.  Columns
+// come from the 16-bit offsets when the view has them and the slice fits.
+template <typename AT, int LM = 0, typename VT, typename XT>
+__device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                                         const VT* __restrict__ val, int64_t slice, int lane,
+                                         const XT* __restrict__ x, const int16_t* __restrict__ col16 = nullptr) {
+  const int64_t r0 = mld<LM>(sptr + slice), r1 = mld<LM>(sptr + slice + 1);
+  const int64_t s0 = (r0 & kSptrMask) + lane, s1 = r1 & kSptrMask;
+  if (col16 && !(r0 & 1)) {
+    const int base = (int)((slice >> 3) * kCol16Window);
+    return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return base + (int)mld<LM>(col16 + o); });
+  }
+  return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return (int)mld<LM>(col + o); });
+}
+
 template <typename T, int LM = 0, typename VT = T>
 __device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x) {
-  return sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x);
+  return sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x, A.col16);
 }
 
 // acc[0..2] = sum_j A(row, j) x_j for a 3x3-block SELL row.
 template <typename T, typename XT>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const XT* __restrict__ x,
                                           double xs, T acc[3]) {
-  const int64_t s0 = A.sptr[slice], s1 = A.sptr[slice + 1];
+  const int64_t s0 = A.sptr[slice] & kSptrMask, s1 = A.sptr[slice + 1] & kSptrMask;
   const T* __restrict__ val = (const T*)A.val;
   acc[0] = acc[1] = acc[2] = T(0);
   for (int64_t g = s0; g < s1; g += 32) {
@@ -173,18 +193,12 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
   }
 }
 
-// Slot groups are processed two at a time (both column loads, then both
-// blocks' values and gathers, then the FMAs in slot order), so a thread keeps
-// two dependent load chains in flight; the group count is warp-uniform.
-template <typename T, int LM = 0, typename VT = T>
-__device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
-                                          T acc[3]) {
-  const int64_t s0 = mld<LM>(A.sptr + slice), s1 = mld<LM>(A.sptr + slice + 1);
-  const VT* __restrict__ val = (const VT*)A.val;
+template <typename T, int LM, typename VT, typename CF>
+__device__ __forceinline__ void sell_dot3_loop(int64_t g, int64_t s1, int lane, const VT* __restrict__ val,
+                                               const T* __restrict__ x, T acc[3], CF colat) {
   acc[0] = acc[1] = acc[2] = T(0);
-  int64_t g = s0;
   for (; g + 32 < s1; g += 64) {
-    const int ca = mld<LM>(A.col + g + lane), cb = mld<LM>(A.col + g + 32 + lane);
+    const int ca = colat(g + lane), cb = colat(g + 32 + lane);
     const VT* __restrict__ va = val + g * 9 + lane;
     const VT* __restrict__ vb = va + 32 * 9;
     T ma[9], mb[9];
@@ -210,7 +224,7 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
     }
   }
   if (g < s1) {
-    const int c = mld<LM>(A.col + g + lane);
+    const int c = colat(g + lane);
     const VT* __restrict__ v = val + g * 9 + lane;
     const T x0 = vld<LM>(x + 3 * c), x1 = vld<LM>(x + 3 * c + 1), x2 = vld<LM>(x + 3 * c + 2);
 #pragma unroll
@@ -221,6 +235,26 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
       a = fmad(ldv<T, LM>(v + (3 * i + 2) * 32), x2, a);
       acc[i] = a;
     }
+  }
+}
+
+// acc[0..2] = sum_j A(row, j) x_j for a 3x3-block SELL row (same types).
+// Slot groups are processed two at a time (both column loads, then both
+// blocks' values and gathers, then the FMAs in slot order), so a thread keeps
+// two dependent load chains in flight; the group count is warp-uniform.
+template <typename T, int LM = 0, typename VT = T>
+__device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
+                                          T acc[3]) {
+  const int64_t r0 = mld<LM>(A.sptr + slice), r1 = mld<LM>(A.sptr + slice + 1);
+  const int64_t s0 = r0 & kSptrMask, s1 = r1 & kSptrMask;
+  const VT* __restrict__ val = (const VT*)A.val;
+  if (A.col16 && !(r0 & 1)) {
+    const int base = (int)((slice >> 3) * kCol16Window);
+    const int16_t* c16 = A.col16;
+    sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return base + (int)mld<LM>(c16 + o); });
+  } else {
+    const int32_t* c32 = A.col;
+    sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return (int)mld<LM>(c32 + o); });
   }
 }
 
@@ -1359,6 +1393,8 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_residual(SellVie
 static bool g_pdl = true;
 void set_pdl(bool on) { g_pdl = on; }
 
+
+
 template <typename... KArgs, typename... Args>
 static void launch(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
@@ -1367,10 +1403,14 @@ static void launch(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... a
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  int na = 0;
+  if (g_pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = g_pdl ? 1 : 0;
+  cfg.numAttrs = na;
   cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
 }
 

@@ -23,7 +23,14 @@ struct SellView {
   int64_t nslices = 0;
   int bf16 = 0;           // values stored as BF16 (read by the FP32 kernels, widened to FP32)
   const int32_t* perm = nullptr;   // SELL row -> node row (rows sorted by length within windows), or NULL
+  // 16-bit column indices (FP32/BF16 copies of large levels): column =
+  // (slice / 8) * 256 + col16[o].  A slice whose columns do not fit has bit 0
+  // of sptr[slice] set and uses col[] instead; slot offsets are multiples of
+  // 32, so readers mask sptr with kSptrMask.
+  const int16_t* col16 = nullptr;
 };
+constexpr int64_t kSptrMask = ~int64_t(31);
+constexpr int kCol16Window = 256;       // rows per base of the 16-bit column offsets
 
 // Transfer matrices (P, R) are scalar SELL with float weights, applied to
 // every component.  fix (block problems with partly fixed nodes, else NULL):

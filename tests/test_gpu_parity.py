@@ -372,13 +372,14 @@ def test_shared_memory_tail_solve_identical(ctx, prec):
 
 @pytest.mark.parametrize("name", ["td_adaptive", "oseen", "elasticity16"])
 def test_sell_sigma_sorting_is_bitwise_neutral(ctx, name):
-    """Rows sorted by length within windows (SELL-C-sigma) give the same V-cycle
-    bits as rows in node order (each row's sum keeps its order), and a solve
-    with sorted rows still matches the direct solution."""
+    """Rows sorted by length within windows (SELL-C-sigma) with 16-bit column
+    offsets give the same V-cycle bits as rows in node order with 32-bit
+    columns (each row's sum keeps its order), and a solve with that layout
+    still matches the direct solution."""
     lm, prob, oh, _ = setup_case(ctx, name)
     mk, _, pkw, okw = CASES[name]
-    hs = [G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(sell_sigma=sg, autotune=0, **okw))
-          for sg in (0, 256)]
+    hs = [G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(sell_sigma=sg, col16=c16, autotune=0, **okw))
+          for sg, c16 in ((0, 0), (256, 1))]
     rng = np.random.default_rng(8)
     n = oh.fine.A.shape[0]
     r = rng.standard_normal(n)
@@ -402,6 +403,30 @@ def test_sell_sigma_sorting_is_bitwise_neutral(ctx, name):
     assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= 1e-8
     for hh in hs:
         hh.free()
+
+
+@pytest.mark.slow
+def test_col16_fallback_slices_bitwise(ctx):
+    """On the 1.2 M-node adaptive mesh some slices have column offsets outside
+    int16 and keep 32-bit columns; V-cycles with the mixed layout equal the
+    plain 32-bit layout bit for bit (FP32 and BF16 values)."""
+    lm = W.td_adaptive(rounds=8, gamma=0.18)
+    pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    h0 = G.Hierarchy(ctx, lm, pb, B.make_opts(col16=0, sell_sigma=0, autotune=0, store_fp64=0, store_bf16=1))
+    h1 = G.Hierarchy(ctx, lm, pb, B.make_opts(col16=-1, sell_sigma=-1, autotune=0, store_fp64=0, store_bf16=1))
+    assert h1.info.col16_slices > 0 and h1.info.col32_slices > 0 and h0.info.col16_slices == 0
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal(h0.n_dofs).astype(np.float32)
+    for prec in (B.MG_MIXED_FP32, B.MG_MIXED_BF16):
+        outs = []
+        for hh in (h0, h1):
+            hh.tune(prec, 0, 1)
+            z = torch.empty(hh.n_dofs, device="cuda", dtype=torch.float32)
+            hh.vcycle(dev(r, torch.float32), z, prec)
+            outs.append(z.cpu().numpy())
+        assert np.array_equal(outs[0], outs[1])
+    h0.free()
+    h1.free()
 
 
 def test_direct_launch_mode_equals_graph(ctx):
