@@ -152,12 +152,12 @@ def measured_peaks():
 ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
-def cpu_baseline(steps=4, rounds=7, rtol=1e-8):
+def cpu_baseline(steps=4, rounds=7, rtol=1e-8, threads=1):
     """The oracle (numpy/scipy FP64, as it stands) on a bounded sample of the
     same workload (the adaptive TD mesh with `rounds` refinement rounds), run
-    in a child process pinned to one BLAS/OpenMP thread."""
-    env = dict(os.environ, **ONE_THREAD)
-    code = (f"import json, bench; print(json.dumps(bench._cpu_baseline_inproc({steps}, {rounds}, {rtol})))")
+    in a child process with `threads` BLAS/OpenMP threads."""
+    env = dict(os.environ, **{k: str(threads) for k in ONE_THREAD})
+    code = (f"import json, bench; print(json.dumps(bench._cpu_baseline_inproc({steps}, {rounds}, {rtol}, {threads})))")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     if r.returncode != 0:
@@ -165,7 +165,7 @@ def cpu_baseline(steps=4, rounds=7, rtol=1e-8):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def _cpu_baseline_inproc(steps, rounds, rtol):
+def _cpu_baseline_inproc(steps, rounds, rtol, threads=1):
     from oracle import krylov, mg
     from oracle import problems as PB
     if True:
@@ -184,10 +184,10 @@ def _cpu_baseline_inproc(steps, rounds, rtol):
             times.append(time.perf_counter() - t0)
             iters.append(info["iters"])
     t = statistics.mean(times)
-    return {"value": n_free / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+    return {"value": n_free / t, "unit": "DoF/s", "cores": threads, "kind": "oracle",
             "sample": f"oracle BiCGStab+V(2,2) FP64 solve to {rtol:g} of the same TD workload with {rounds} "
                       f"refinement rounds ({n_free} free DoFs, {len(Hh.levels)} levels), mean of {steps} solves, "
-                      f"1 thread (setup {t_setup:.1f}s untimed)",
+                      f"{threads} thread(s) (setup {t_setup:.1f}s untimed)",
             "iters": iters, "sec_per_solve": t}
 
 
@@ -368,6 +368,9 @@ def main():
     ap.add_argument("--sweep", type=float, nargs="*", default=[10.0, 100.0], help="serving: rate multipliers")
     ap.add_argument("--launch", default="graph", choices=["graph", "direct"],
                     help="direct: per-kernel launches (for profilers that cannot see inside graphs)")
+    ap.add_argument("--tail", default=None,
+                    help="ROWS,CLUSTER: fixed tail shape instead of the setup autotuner (profiling runs, "
+                         "where the autotuner's timings would be distorted)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -395,7 +398,13 @@ def main():
     t0 = time.perf_counter()
     ok["launch_mode"] = 1 if args.launch == "direct" else 0
     ok["store_bf16"] = 1
+    if args.tail:
+        ok["autotune"] = 0
     h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
+    if args.tail:
+        rows, cl = (int(v) for v in args.tail.split(","))
+        for p in (B.MG_MIXED_FP32, B.MG_FP64, B.MG_MIXED_BF16):
+            h.tune(p, rows, cl)
     setup_s = time.perf_counter() - t0
     info = h.info
     # kernels launched by setup (autotuner V-cycles): a profiler skips these to reach the solves
@@ -506,6 +515,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "td_adaptive":
         try:
             cpu = cpu_baseline()
+            allc = cpu_baseline(steps=2, threads=os.cpu_count() or 1)
+            if "value" in allc:
+                # the oracle's sparse kernels are single-threaded scipy; more BLAS threads barely matter
+                cpu["all_cores"] = {"cores": allc["cores"], "value": allc["value"]}
         except Exception as e:       # the baseline is reported, never required
             cpu = {"error": str(e)}
 
