@@ -179,6 +179,8 @@ typedef struct {
   int64_t col16_slices;                 /* slices read with 16-bit columns        */
   int64_t col32_slices;                 /* slices of those matrices that keep
                                            32-bit columns (offsets outside int16) */
+  int level_col16[32];                  /* 1: the level's FP32/BF16 copy stores
+                                           16-bit column offsets                 */
 } mg_info;
 
 typedef struct {

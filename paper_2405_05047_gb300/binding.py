@@ -65,7 +65,8 @@ class MgInfo(C.Structure):
                 ("level_nnzb", C.c_int64 * 32), ("level_rows_nnzb", C.c_int64 * 32),
                 ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double),
                 ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
-                ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64)]
+                ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64),
+                ("level_col16", C.c_int * 32)]
 
 
 class MgStats(C.Structure):

@@ -300,6 +300,7 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
     info->level_nodes[l] = h->level_nodes[l];
     info->level_nnzb[l] = h->level_nnzb[l];
     info->level_rows_nnzb[l] = h->level_real_nnzb[l];
+    info->level_col16[l] = h->level_col16[l];
   }
   info->bytes_device = h->bytes + (h->ws0 ? h->ws0->bytes : 0);
   info->bytes_workspace = h->ws_bytes;

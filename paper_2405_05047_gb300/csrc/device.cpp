@@ -415,6 +415,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       }
     }
     h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
+    h->level_col16.push_back(idx16_for(h, lv.A.n) ? 1 : 0);
     if (l > 0) {
       if ((rc = upload_sell<float>(h, lv.P, &B.P, sigma_for(h, lv.P.n)))) return rc;
       if ((rc = upload_sell<float>(h, lv.R, &B.R, sigma_for(h, lv.R.n)))) return rc;

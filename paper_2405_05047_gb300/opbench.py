@@ -49,14 +49,16 @@ def make(workload):
 
 
 def alg_bytes(info, level, nc, op, vbytes):
-    """Bytes the operator must move once: stored values + 4-byte columns of
-    the level matrix, plus its vectors (x, b, S^-1 and the output for a sweep)."""
+    """Bytes the operator must move once: stored values + column indices of
+    the level matrix (2 bytes where the FP32/BF16 copy stores 16-bit column
+    offsets, else 4), plus its vectors (x, b, S^-1 and the output for a sweep)."""
     nnz = info.level_rows_nnzb[level] * nc * nc
     rows = info.level_nodes[level] * nc
+    ib = 2 if (vbytes < 8 and info.level_col16[level]) else 4
     if op == "smooth":
-        return nnz * vbytes + info.level_rows_nnzb[level] * 4 + rows * vbytes * 3 + info.level_nodes[level] * nc * nc * vbytes
+        return nnz * vbytes + info.level_rows_nnzb[level] * ib + rows * vbytes * 3 + info.level_nodes[level] * nc * nc * vbytes
     if op == "matvec":
-        return nnz * vbytes + info.level_rows_nnzb[level] * 4 + rows * vbytes * 2
+        return nnz * vbytes + info.level_rows_nnzb[level] * ib + rows * vbytes * 2
     return None
 
 

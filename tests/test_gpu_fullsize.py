@@ -1,0 +1,165 @@
+"""CUDA path against the oracle at the benchmark sizes (GB300 only).
+
+The workloads and launch configuration are the ones bench.py times (graph
+mode, autotuned tail, sorted rows and 16-bit columns on the large levels):
+
+* adaptive transport-diffusion, 1,212,011 nodes: the oracle assembles the
+  whole finest system; the library's right-hand side equals the oracle's
+  entry by entry, the FP32 level operator equals the oracle's on a random
+  vector, and the library's mixed-precision solution has a true residual
+  <= 1e-8 in the oracle's own matrix.
+* Oseen/LPS channel, 657,975 nodes: the same three checks (with the lifted
+  inflow data), GMRES(30).
+* elasticity 128^3 (2,146,689 nodes): the oracle's matrix does not fit a
+  Python process, so rows are sampled: on 300 seeded free nodes the oracle
+  forms (A x)_i and b_i from the element matrices of the surrounding cells;
+  the library's FP64 operator and right-hand side match them and the
+  solution's residual entries are below the solve tolerance.
+
+Tolerances as in test_gpu_parity.py; the residual bound is the stopping test
+itself (||b - A x|| <= 1e-8 ||b_free||, 1 % slack for the summation order).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem
+from oracle import mesh as M
+from oracle import problems as PB
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow, pytest.mark.timeout(900, method="thread")]
+
+import paper_2405_05047_gb300 as G  # noqa: E402
+from paper_2405_05047_gb300 import binding as B  # noqa: E402
+
+RTOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _check_system(ctx, lm, pb_lib, opts, prob, f, g, prec_tol=2e-5):
+    h = G.Hierarchy(ctx, lm, pb_lib, opts)
+    fm = M.Q1Mesh(lm.dim, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+    assert np.array_equal(h.coords(), fm.coords)
+    S = PB.build_system(fm, prob, beta=prob.conv)
+    bref = S.rhs(f, g)
+    # right-hand side (with lifting) at full size
+    b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(dev(f), b, dev(g) if g is not None else None)
+    bl = b.cpu().numpy()
+    assert np.abs(bl - bref).max() <= 1e-13 * np.abs(bref).max()
+    # finest FP32 operator (sorted rows, 16-bit columns) on a random vector
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(h.n_dofs).astype(np.float32).astype(np.float64)
+    x[S.fixed] = 0.0
+    y = torch.empty(h.n_dofs, device="cuda", dtype=torch.float32)
+    h.apply(h.levels - 1, B.MG_OP_MATVEC, dev(x, torch.float32), None, y, B.MG_MIXED_FP32)
+    ref = S.A @ x
+    scale = float((abs(S.A) @ np.abs(x)).max())
+    assert np.abs(y.cpu().double().numpy() - ref).max() <= prec_tol * scale
+    # mixed-precision solve: true residual in the oracle's matrix
+    xs = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(b, xs, rtol=RTOL, max_it=500, prec=B.MG_MIXED_FP32)
+    assert st.status == 0, st.as_dict()
+    xg = xs.cpu().numpy()
+    xr = xg.copy()
+    xr[S.hang] = 0.0
+    res = np.linalg.norm(bref - S.A @ xr) / np.linalg.norm(bref[~S.fixed])
+    assert res <= 1.01 * RTOL, res
+    # hanging values are H applied to the regular ones; Dirichlet values are b's
+    assert np.abs(xg - S.H @ xr).max() <= 1e-13 * max(np.abs(xg).max(), 1.0)
+    assert np.array_equal(xg[S.dirichlet], bref[S.dirichlet])
+    h.free()
+
+
+def test_td_adaptive_fullsize(ctx):
+    lm = W.td_adaptive(rounds=8, gamma=0.18)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    xy = B.mg_mesh_nodes(lm)
+    _check_system(ctx, lm, pb, B.make_opts(krylov=B.MG_BICGSTAB), prob,
+                  W.f_transport(xy, 1e-3, (1.0, 0.5)), None)
+
+
+def test_oseen_fullsize(ctx):
+    lm = W.oseen_channel(1, 12)
+    xy = B.mg_mesh_nodes(lm)
+    beta = W.oseen_beta(xy)
+    kw = dict(dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01)
+    prob = PB.Problem(PB.OSEEN, conv=beta, **kw)
+    pb = B.make_problem(kind=B.MG_OSEEN, conv=beta, **kw)
+    _check_system(ctx, lm, pb, B.make_opts(krylov=B.MG_GMRES, restart=30), prob,
+                  np.zeros(xy.shape[0] * 3), W.oseen_inflow(xy).ravel())
+
+
+def _elasticity_rows(n, nodes, x, f, mu=1.0, lam=10.0):
+    """(A x)_i and b_i (3 components each) of the clamped n^3 elasticity
+    system for the given free nodes, from the element matrices of the cells
+    around each node (uniform mesh: no hanging nodes; x is 0 on the clamped
+    face, so the eliminated columns contribute nothing)."""
+    h = np.full(3, 1.0 / n)
+    Ke = fem.elasticity_element(h, mu, lam)
+    Me = fem.scalar_element(3, h, "mass")
+    m = n + 1
+    ax = np.zeros((len(nodes), 3))
+    bb = np.zeros((len(nodes), 3))
+    for t, node in enumerate(nodes):
+        i, j, k = node % m, (node // m) % m, node // (m * m)
+        for ck in (k - 1, k):
+            for cj in (j - 1, j):
+                for ci in (i - 1, i):
+                    if min(ci, cj, ck) < 0 or max(ci, cj, ck) >= n:
+                        continue
+                    a = (i - ci) + 2 * (j - cj) + 4 * (k - ck)
+                    corners = [(ci + (c & 1)) + m * (cj + ((c >> 1) & 1)) + m * m * (ck + ((c >> 2) & 1))
+                               for c in range(8)]
+                    xc = np.concatenate([x[3 * q:3 * q + 3] for q in corners])
+                    ax[t] += Ke[3 * a:3 * a + 3] @ xc
+                    for c, q in enumerate(corners):
+                        bb[t] += Me[a, c] * f[3 * q:3 * q + 3]
+    return ax, bb
+
+
+def test_elasticity128_fullsize_sampled_rows(ctx):
+    n = 128
+    lm = W.elasticity3d(n)
+    pb = B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))
+    h = G.Hierarchy(ctx, lm, pb, B.make_opts(krylov=B.MG_CG, omega=0.5))
+    m = n + 1
+    N = m ** 3
+    f = np.tile([0.0, 0.0, -1.0], N)
+    rng = np.random.default_rng(33)
+    nodes = rng.choice(np.arange(N)[np.arange(N) % m > 0], size=300, replace=False)   # free: x index > 0
+    fixed = np.repeat(np.arange(N) % m == 0, 3)
+    # FP64 operator on a random vector, sampled rows
+    x = rng.standard_normal(3 * N)
+    x[fixed] = 0.0
+    y = torch.empty(3 * N, device="cuda", dtype=torch.float64)
+    h.apply(h.levels - 1, B.MG_OP_MATVEC, dev(x), None, y, B.MG_FP64)
+    ax, _ = _elasticity_rows(n, nodes, x, f)
+    yl = y.cpu().numpy().reshape(-1, 3)[nodes]
+    assert np.abs(yl - ax).max() <= 1e-12 * np.abs(ax).max()
+    # right-hand side and the solution's residual, sampled rows
+    b = torch.empty(3 * N, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(dev(f), b)
+    bl = b.cpu().numpy()
+    xs = torch.zeros(3 * N, device="cuda", dtype=torch.float64)
+    st = h.solve(b, xs, rtol=RTOL, max_it=500, prec=B.MG_MIXED_FP32)
+    assert st.status == 0, st.as_dict()
+    xg = xs.cpu().numpy()
+    axs, bref = _elasticity_rows(n, nodes, xg, f)
+    assert np.abs(bl.reshape(-1, 3)[nodes] - bref).max() <= 1e-13 * np.abs(bref).max()
+    bnorm = np.linalg.norm(bl[~fixed])
+    assert np.abs(bref - axs).max() <= 1.01 * RTOL * bnorm
+    assert np.all(xg[fixed] == 0.0)
+    h.free()
