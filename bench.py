@@ -56,7 +56,7 @@ def workload(name):
             f"[0,2.2]x[0,0.41], 22x4 macro cells refined once, then {OSEEN_ROUNDS} rounds towards the circle "
             "|x-(0.2,0.2)|=0.05 by sibling families, 2:1; seeded divergence-free convection field, parabolic "
             "inflow (lifted), no-slip walls, do-nothing outflow; GMRES(30) + V(2,2) point-block (Vanka) "
-            "Jacobi w=0.8"), W.oseen_inflow
+            "Jacobi, w_l = 1.2/lambda_max(S_l A_l) per level"), W.oseen_inflow
     if name == "td_adaptive":
         lm = W.td_adaptive(rounds=8, gamma=GAMMA_TD)
         pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
@@ -71,10 +71,10 @@ def workload(name):
         n = int(name[len("elasticity"):] or 128)
         lm = W.elasticity3d(n)
         pk = dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))
-        return lm, pk, dict(krylov=B.MG_CG, omega=0.5), (
+        return lm, pk, dict(krylov=B.MG_CG), (
             lambda xyz: np.tile([0.0, 0.0, -1.0], (xyz.shape[0], 1)).ravel()), (
             f"3D linear elasticity {n}^3 Q1 hexes, mu=1 lambda=10, clamped x=0, f=(0,0,-1); "
-            "CG + V(2,2) point-block Jacobi w=0.5"), None
+            "CG + V(2,2) point-block Jacobi, w_l = 1.2/lambda_max(S_l A_l) per level"), None
     raise SystemExit(f"unknown workload {name}")
 
 

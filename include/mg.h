@@ -128,7 +128,11 @@ typedef struct {
 
 typedef struct {
   int nu1, nu2;                /* pre/post smoothing sweeps (default 2, 2)    */
-  double omega;                /* damping of the (block-)Jacobi smoother      */
+  double omega;                /* damping of the (block-)Jacobi smoother: > 0
+                                  on every level; <= 0 (default -1): 0.8 for
+                                  scalar problems, 1.2 / lambda_max(S_l A_l)
+                                  per level for the point-block smoothers
+                                  (20 power iterations at setup)             */
   int min_level;               /* coarsest level allowed (-1: automatic)      */
   int max_levels;              /* cap on the number of levels (0: no cap)     */
   int krylov;                  /* mg_krylov                                   */
@@ -181,6 +185,7 @@ typedef struct {
                                            32-bit columns (offsets outside int16) */
   int level_col16[32];                  /* 1: the level's FP32/BF16 copy stores
                                            16-bit column offsets                 */
+  double level_omega[32];               /* smoother damping per level            */
 } mg_info;
 
 typedef struct {

@@ -39,6 +39,8 @@ int mg_host_level(const mg_host_hier* h, int level, int which, int64_t* n, int64
  * Dirichlet) and lattice coordinates (n_nodes * dim int64, finest lattice of
  * that level). */
 int mg_host_nodes(const mg_host_hier* h, int level, const uint8_t** fixmask, int64_t* n_nodes);
+/* Smoother damping of a level (opts.omega, or the automatic per-level rule). */
+int mg_host_omega(const mg_host_hier* h, int level, double* omega);
 /* Dense inverse of the coarse operator, (n0 nc)^2 row-major. */
 int mg_host_coarse_inverse(const mg_host_hier* h, int64_t* n, const double** inv);
 int mg_host_free(mg_host_hier* h);

@@ -94,10 +94,30 @@ class Level:
                              shape=self.A.shape).tocsr()
 
 
-class Hierarchy:
-    """Levels 0 (coarsest) .. L (finest) of the global coarsening."""
+def lambda_max_power(S, A, fixed, iters=20):
+    """Largest eigenvalue magnitude of S A by `iters` power iterations
+    w = S A v, lambda = |w| / |v|, v = w / |w|, from the start vector
+    v_i = frac(i * 2654435761 / 2^32) - 1/2 on free dofs, 0 on fixed ones."""
+    n = A.shape[0]
+    v = ((np.arange(n, dtype=np.uint64) * np.uint64(2654435761)) % np.uint64(2 ** 32)).astype(np.float64) / 2.0 ** 32 - 0.5
+    v[fixed] = 0.0
+    lam = 0.0
+    for _ in range(iters):
+        w = S @ (A @ v)
+        lam = np.linalg.norm(w) / np.linalg.norm(v)
+        v = w / np.linalg.norm(w)
+    return lam
 
-    def __init__(self, leafmesh, prob, min_level=None, max_levels=0, omega=0.8, nu1=2, nu2=2):
+
+class Hierarchy:
+    """Levels 0 (coarsest) .. L (finest) of the global coarsening.
+
+    omega: smoother damping on every level; None: 0.8 for scalar problems and
+    1.2 / lambda_max(S_l A_l) per level for point-block smoothers (20 power
+    iterations; lambda_max(D^-1 A) = 1.5 for the Q1 Laplacian, where this
+    rule gives 0.8 as well)."""
+
+    def __init__(self, leafmesh, prob, min_level=None, max_levels=0, omega=None, nu1=2, nu2=2):
         patch = prob.kind == PB.OSEEN   # LPS patches: keep every level a patch mesh
         if min_level is None:
             min_level = max(M.default_min_level(leafmesh.macro), 1 if patch else 0)
@@ -109,7 +129,7 @@ class Hierarchy:
                                  sets[-1][0], sets[-1][1])
         self.levels = [Level(l, a, leafmesh, prob, fine_mesh=fine_mesh) for (l, a) in sets]
         self.prob = prob
-        self.omega, self.nu1, self.nu2 = omega, nu1, nu2
+        self.nu1, self.nu2 = nu1, nu2
         nc = prob.nc
         for lc, lf in zip(self.levels[:-1], self.levels[1:]):
             E = mesh_E = embedding(lf.mesh, lc.mesh)
@@ -123,6 +143,12 @@ class Hierarchy:
             del E
         for lv in self.levels:
             lv.S = lv.smoother_matrix()
+            if omega is not None:
+                lv.omega = float(omega)
+            elif nc == 1:
+                lv.omega = 0.8
+            else:
+                lv.omega = 1.2 / lambda_max_power(lv.S, lv.A, lv.sys.fixed)
         A0 = self.levels[0].A.toarray()
         self.coarse_lu = sla.lu_factor(A0)
 
@@ -130,10 +156,15 @@ class Hierarchy:
     def fine(self):
         return self.levels[-1]
 
+    @property
+    def omega(self):
+        """Damping of the finest level."""
+        return self.levels[-1].omega
+
     def smooth(self, l, x, b, sweeps):
         lv = self.levels[l]
         for _ in range(sweeps):
-            x = x + self.omega * (lv.S @ (b - lv.A @ x))
+            x = x + lv.omega * (lv.S @ (b - lv.A @ x))
         return x
 
     def gmg(self, l, x, b):

@@ -66,7 +66,7 @@ class MgInfo(C.Structure):
                 ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double),
                 ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
                 ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64),
-                ("level_col16", C.c_int * 32)]
+                ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32)]
 
 
 class MgStats(C.Structure):

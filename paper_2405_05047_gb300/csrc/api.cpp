@@ -155,7 +155,7 @@ void mg_default_opts(mg_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->nu1 = 2;
   o->nu2 = 2;
-  o->omega = 0.8;
+  o->omega = -1.0;
   o->min_level = -1;
   o->max_levels = 0;
   o->krylov = MG_KRYLOV_AUTO;
@@ -215,7 +215,7 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   if (opts_in) opts = *opts_in;
   else mg_default_opts(&opts);
   if (opts.nu1 < 1 || opts.nu2 < 0 || opts.nu1 > 16 || opts.nu2 > 16) return fail(MG_ERR_INVALID, "nu1 must be >= 1");
-  if (!(opts.omega > 0.0)) return fail(MG_ERR_INVALID, "omega must be positive");
+  if (std::isnan(opts.omega)) return fail(MG_ERR_INVALID, "omega is NaN");
   if (!(opts.inner_rtol >= 0.0 && opts.inner_rtol < 1.0)) return fail(MG_ERR_INVALID, "inner_rtol must be in [0, 1)");
   if (opts.sell_sigma < -1 || (opts.sell_sigma > 0 && opts.sell_sigma % 32 != 0))
     return fail(MG_ERR_INVALID, "sell_sigma must be -1, 0 or a positive multiple of 32");
@@ -310,7 +310,8 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
   info->col16_slices = h->col16_slices;
   info->col32_slices = h->col32_slices;
   info->n_hanging = h->n_hanging;
-  info->omega = h->opts.omega;
+  info->omega = h->L.back().omega;
+  for (int l = 0; l < h->nlev && l < 32; ++l) info->level_omega[l] = h->L[l].omega;
   return MG_OK;
 }
 
@@ -417,8 +418,8 @@ static int level_op(mg_hier* h, int level, int op, const void* in, const void* i
       return MG_OK;
     case MG_OP_SMOOTH:
       if (!in2) return fail(MG_ERR_INVALID, "smooth needs b");
-      if (d) launch_smooth<double>(L.A64.v, nc, (const double*)in, (const double*)in2, L.S64, (double*)out, h->opts.omega, false, nullptr, s);
-      else launch_smooth<float>(A32, nc, (const float*)in, (const float*)in2, L.S32, (float*)out, h->opts.omega, false, nullptr, s);
+      if (d) launch_smooth<double>(L.A64.v, nc, (const double*)in, (const double*)in2, L.S64, (double*)out, L.omega, false, nullptr, s);
+      else launch_smooth<float>(A32, nc, (const float*)in, (const float*)in2, L.S32, (float*)out, L.omega, false, nullptr, s);
       return MG_OK;
     case MG_OP_RESTRICT:
       if (level == 0 || !in2) return fail(MG_ERR_INVALID, "restrict needs level >= 1 and b");

@@ -77,6 +77,12 @@ int mg_host_nodes(const mg_host_hier* h, int level, const uint8_t** fixmask, int
   return MG_OK;
 }
 
+int mg_host_omega(const mg_host_hier* h, int level, double* omega) {
+  if (!h || !omega || level < 0 || level >= (int)h->H.levels.size()) return MG_ERR_INVALID;
+  *omega = h->H.levels[level].omega;
+  return MG_OK;
+}
+
 int mg_host_coarse_inverse(const mg_host_hier* h, int64_t* n, const double** inv) {
   if (!h) return MG_ERR_INVALID;
   *n = h->H.levels[0].topo.n_nodes * h->H.nc;

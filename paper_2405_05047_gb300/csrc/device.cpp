@@ -297,6 +297,7 @@ int tail_image(mg_hier* h, int pi, int top, mg_hier::TailImage* out) {
     const SellBuf& A = slot_A(B, pi);
     TailLevel& T = hdr[l];
     T.A = A.v;
+    T.omega = B.omega;
     T.P = B.P.t;
     T.R = B.R.t;
     T.S = pi == 0 ? (const void*)B.S64 : (const void*)B.S32;
@@ -388,6 +389,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     HostLevel& lv = H.levels[l];
     LevelMats& B = h->L[l];
     B.n = lv.topo.n_nodes;
+    B.omega = lv.omega;
     h->level_nodes.push_back(B.n);
     h->level_real_nnzb.push_back(lv.A.nnzb());
     int rc;
@@ -561,7 +563,7 @@ int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
     if (pi == 0 ? !h->has_fp64 : (pi == 1 ? !h->has_fp32 : !h->has_bf16)) continue;
     P.nu1 = h->opts.nu1;
     P.nu2 = h->opts.nu2;
-    P.omega = h->opts.omega;
+
     P.cinv = h->coarse_inv;
     P.cn = h->coarse_n;
     for (int l = 0; l < h->nlev && l < kTailMax; ++l) {
@@ -569,6 +571,7 @@ int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out) {
       LevelVecs& V = w->lv[l];
       TailLevel& T = P.lv[l];
       T.A = d ? B.A64.v : (pi == 1 ? B.A32.v : B.A16.v);
+      T.omega = B.omega;
       T.P = B.P.t;
       T.R = B.R.t;
       T.S = d ? (const void*)B.S64 : (const void*)B.S32;
@@ -695,7 +698,7 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
   LevelVecs& CV = w.lv[l - 1];
   const int nu1 = h->opts.nu1, nu2 = h->opts.nu2, ns = nu1 + nu2;
   auto bufof = [&](LevelVecs& X, T* o, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? o : Prec<T>::t(X); };
-  const double om = h->opts.omega;
+  const double om = L.omega, omc = C.omega;
   T* cur = nullptr;
   for (int k = 0; k < nu1; ++k) {                                // Step 1
     T* dst = bufof(V, out, k);
@@ -708,7 +711,7 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
   launch_residual<T>(AL, nc, cur, b, Prec<T>::r(V), done, s);   // Step 2
   const bool fuse = l - 1 > 0;
   T* cfirst = fuse ? bufof(CV, Prec<T>::o(CV), 0) : nullptr;
-  launch_restrict<T>(L.R.t, nc, Prec<T>::r(V), Prec<T>::b(CV), Prec<T>::S(C), cfirst, om, done, s);
+  launch_restrict<T>(L.R.t, nc, Prec<T>::r(V), Prec<T>::b(CV), Prec<T>::S(C), cfirst, omc, done, s);
   h->launch_count += 2;
   enqueue_vcycle<T>(h, w, l - 1, Prec<T>::b(CV), Prec<T>::o(CV), done, s, fuse, bf16);   // Step 3
   T* pdst = nu2 == 0 ? out : cur;                                                   // Step 4

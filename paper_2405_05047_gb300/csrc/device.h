@@ -36,6 +36,7 @@ struct SellBuf {
 // Read-only matrices of one level.
 struct LevelMats {
   int64_t n = 0;              // nodes
+  double omega = 0.8;         // smoother damping of this level
   SellBuf A64, A32, A16, P, R;   // A16: BF16-stored values
   double* S64 = nullptr;
   float* S32 = nullptr;

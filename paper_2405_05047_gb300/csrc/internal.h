@@ -68,6 +68,7 @@ struct HostLevel {
   BlockCSR P;                       // scalar (nc=1): prolongation from level-1 (rows: this level)
   BlockCSR R;                       // scalar: restriction to level-1 (rows: coarse nodes)
   std::vector<double> Sinv;         // n * nc * nc smoother blocks (inverse diagonal blocks)
+  double omega = 0.8;               // damping of the smoother on this level
 };
 
 struct HostHierarchy {

@@ -538,7 +538,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
     __syncthreads();
   }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  const T om = (T)P.omega;
   T* cur_of[kTailMax];
   auto bvec = [&](int l) -> T* { return (TLM == 1 && l == top) ? const_cast<T*>(btop) : (T*)LV[l].b; };
   auto ovec = [&](int l) -> T* { return (TLM == 1 && l == top) ? otop : (T*)LV[l].o; };
@@ -547,6 +546,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   for (int l = top; l >= 1; --l) {
     const TailLevel& L = LV[l];
     const T* S = (const T*)L.S;
+    const T om = (T)L.omega;
     T* cur = nullptr;
     for (int k = 0; k < P.nu1; ++k) {
       T* dst = bufof(l, k);
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
     tail_sync();
     T* x0 = l - 1 > 0 ? bufof(l - 1, 0) : nullptr;
     for (int64_t row = tid; row < L.R.nslices * 32; row += nth)
-      row_restrict<T, NC, TLM>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)LV[l - 1].S, x0, om);
+      row_restrict<T, NC, TLM>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)LV[l - 1].S, x0, (T)LV[l - 1].omega);
     tail_sync();
     fdone = l - 1 > 0;
     cur_of[l] = cur;
@@ -580,6 +580,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   }
   for (int l = 1; l <= top; ++l) {
     const TailLevel& L = LV[l];
+    const T om = (T)L.omega;
     T* cur = cur_of[l];
     T* pdst = P.nu2 == 0 ? ovec(l) : cur;
     for (int64_t row = tid; row < L.P.nslices * 32; row += nth)

@@ -116,12 +116,12 @@ struct TailLevel {
   void* o = nullptr;          // output
   void* t = nullptr;          // ping-pong buffer
   void* r = nullptr;          // residual
+  double omega = 0.8;         // smoother damping of this level
 };
 struct TailParams {
   TailLevel lv[kTailMax];     // [0] = coarsest level of the hierarchy
   int nt = 0;                 // levels in the tail (top = nt - 1)
   int nu1 = 2, nu2 = 2;
-  double omega = 0.8;
   const double* cinv = nullptr;   // coarse inverse
   int64_t cn = 0;
   int cluster = 1;            // CTAs of the one thread-block cluster that runs the tail (1..8);

@@ -987,6 +987,50 @@ bool invert_dense(int64_t n, std::vector<double>& M, std::vector<double>& Inv) {
   return true;
 }
 
+// Largest eigenvalue magnitude of S A (S the smoother blocks) by `iters`
+// power iterations: w = S A v, lambda = |w| / |v|, v = w / |w|.  Start vector:
+// v_i = frac(i * 2654435761 / 2^32) - 1/2 on the free dofs (a fixed
+// integer hash, so every implementation starts from the same vector), 0 on
+// the fixed ones.
+double smoothed_operator_lambda_max(const HostLevel& lv, int nc, int iters) {
+  const int nb = nc * nc;
+  const int64_t nn = lv.topo.n_nodes, n = nn * nc;
+  std::vector<double> v(n), w(n);
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t hsh = ((uint64_t)i * 2654435761ull) & 0xffffffffull;
+    const bool fixed = (lv.fixmask[i / nc] >> (i % nc)) & 1;
+    v[i] = fixed ? 0.0 : (double)hsh / 4294967296.0 - 0.5;
+  }
+  auto norm = [&](const std::vector<double>& x) {
+    double s2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) s2 += x[i] * x[i];
+    return std::sqrt(s2);
+  };
+  double lam = 0.0, nv = norm(v);
+  for (int it = 0; it < iters; ++it) {
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < nn; ++p) {
+      double acc[3] = {0.0, 0.0, 0.0};
+      for (int64_t e = lv.A.ptr[p]; e < lv.A.ptr[p + 1]; ++e) {
+        const int64_t q = lv.A.col[e];
+        for (int i = 0; i < nc; ++i)
+          for (int j = 0; j < nc; ++j) acc[i] += lv.A.val[e * nb + i * nc + j] * v[q * nc + j];
+      }
+      for (int i = 0; i < nc; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < nc; ++j) t += lv.Sinv[p * nb + i * nc + j] * acc[j];
+        w[p * nc + i] = t;
+      }
+    }
+    const double nw = norm(w);
+    if (!(nw > 0.0) || !(nv > 0.0)) return 1.0;
+    lam = nw / nv;
+    for (int64_t i = 0; i < n; ++i) v[i] = w[i] / nw;
+    nv = 1.0;
+  }
+  return lam;
+}
+
 }  // namespace
 
 Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opts& opts, HostHierarchy* H) {
@@ -1065,6 +1109,14 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
       if (!invert_dense(nc, blk, inv)) return Status::err(MG_ERR_INVALID, "singular diagonal block");
       std::copy(inv.begin(), inv.end(), lv.Sinv.begin() + p * nb);
     }
+  }
+  // damping per level: opts.omega when positive; otherwise 0.8 for scalar
+  // problems and 1.2 / lambda_max(S_l A_l) for the point-block smoothers
+  for (HostLevel& lv : H->levels) {
+    if (opts.omega > 0) lv.omega = opts.omega;
+    else if (nc == 1) lv.omega = 0.8;
+    else lv.omega = 1.2 / smoothed_operator_lambda_max(lv, nc, 20);
+    if (!(lv.omega > 0) || !std::isfinite(lv.omega)) return Status::err(MG_ERR_INVALID, "smoother damping estimate failed");
   }
   // coarse level: explicit inverse of A_0 (LU / Gauss-Jordan with pivoting)
   {

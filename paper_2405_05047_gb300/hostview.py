@@ -21,6 +21,7 @@ _SIGS = {
                                 C.POINTER(C.POINTER(C.c_int64)), C.POINTER(C.POINTER(C.c_double))]),
     "mg_host_nodes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.POINTER(C.c_uint8)), C.POINTER(C.c_int64)]),
     "mg_host_coarse_inverse": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.POINTER(C.c_double))]),
+    "mg_host_omega": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "mg_host_free": (C.c_int, [C.c_void_p]),
 }
 
@@ -66,6 +67,11 @@ class HostHierarchy:
         fm, n = C.POINTER(C.c_uint8)(), C.c_int64()
         self.lib.mg_host_nodes(self.h, level, C.byref(fm), C.byref(n))
         return np.ctypeslib.as_array(fm, shape=(n.value,)).copy()
+
+    def omega(self, level):
+        w = C.c_double()
+        self.lib.mg_host_omega(self.h, level, C.byref(w))
+        return w.value
 
     def coarse_inverse(self):
         n, inv = C.c_int64(), C.POINTER(C.c_double)()

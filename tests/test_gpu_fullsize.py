@@ -134,7 +134,7 @@ def test_elasticity128_fullsize_sampled_rows(ctx):
     n = 128
     lm = W.elasticity3d(n)
     pb = B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))
-    h = G.Hierarchy(ctx, lm, pb, B.make_opts(krylov=B.MG_CG, omega=0.5))
+    h = G.Hierarchy(ctx, lm, pb, B.make_opts(krylov=B.MG_CG))
     m = n + 1
     N = m ** 3
     f = np.tile([0.0, 0.0, -1.0], N)

@@ -44,7 +44,7 @@ CASES = {
     "elasticity_adaptive": (lambda: W.refine(W.uniform_leaves(3, (1, 1, 1), 3),
                                              W._cell_box(W.uniform_leaves(3, (1, 1, 1), 3))[1][:, 0] <= 0.25 + 1e-12),
                             PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
-                            dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), dict(omega=0.5)),
+                            dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), {}),
 }
 
 
@@ -85,7 +85,7 @@ def setup_case(ctx, name):
         return _cache[name]
     mk, prob, pkw, okw = CASES[name]
     lm = mk()
-    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
     h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(**okw))
     _cache[name] = (lm, prob, oh, h)
     return _cache[name]
@@ -133,7 +133,8 @@ def test_level_operators(ctx, name, prec):
         ref = lv.A @ x
         assert np.abs(out.cpu().double().numpy() - ref).max() <= tol * bound(lv.A, x), f"matvec level {l}"
         h.apply(l, B.MG_OP_SMOOTH, dev(x, tdt), dev(bvec, tdt), out, prec)
-        ref = x + oh.omega * (lv.S @ (bvec - lv.A @ x))
+        assert h.info.level_omega[l] == pytest.approx(lv.omega, rel=1e-12)
+        ref = x + lv.omega * (lv.S @ (bvec - lv.A @ x))
         sc = bound(abs(lv.S) @ abs(lv.A), x) + float((abs(lv.S) @ np.abs(bvec)).max()) + np.abs(x).max()
         assert np.abs(out.cpu().double().numpy() - ref).max() <= tol * sc, f"smooth level {l}"
         if l > 0:
@@ -326,7 +327,7 @@ def test_tail_kernel_bitwise_equals_level_kernels(ctx, name):
     n = h.n_dofs
     rng = np.random.default_rng(9)
     r = rng.standard_normal(n)
-    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
     r[oh.fine.sys.fixed] = 0.0
     shapes = ((0, 1), (1 << 20, 1), (1 << 20, 2), (1 << 20, 4), (1 << 20, 8), (1024, 4),
               (1 << 20, 0), (4096, 0), (256, 0))
@@ -489,7 +490,7 @@ def test_bf16_values_smoother_parity(ctx, name):
     evaluation with the BF16-rounded operator, FP32 vectors."""
     mk, prob, pkw, okw = CASES[name]
     lm = mk()
-    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega", 0.8))
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
     h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(store_bf16=1, **okw))
     lv = oh.fine
     A16 = lv.A.copy()

@@ -94,6 +94,7 @@ def _compare(oh, hh, prob, tol=1e-13):
         for c in range(nc):
             fixed[c::nc] = (fm >> c) & 1
         assert np.array_equal(fixed, lv.sys.fixed)
+        assert hh.omega(l) == pytest.approx(lv.omega, rel=1e-12), f"omega level {l}"
         S = hh.matrix(l, HV.SMOOTHER)
         assert close(S, lv.S, max(tol, 1e-12)), f"smoother level {l}"
         if l > 0:
