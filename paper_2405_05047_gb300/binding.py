@@ -18,7 +18,10 @@ import weakref
 import numpy as np
 
 MG_OK, MG_PENDING = 0, 1
-MG_ERR_NOT_CONVERGED = -4
+MG_ERR_INVALID, MG_ERR_OOM, MG_ERR_ADMISSION = -1, -2, -3
+MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_NAN, MG_ERR_TIMEOUT, MG_ERR_CUDA = -4, -5, -6, -7, -8
+# solve outcomes that still come with valid statistics (and x)
+SOLVE_OUTCOMES = (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_NAN)
 MG_FP64, MG_MIXED_FP32, MG_MIXED_BF16 = 0, 1, 2
 MG_ERR_CANCELLED = -9
 MG_POISSON, MG_TRANSPORT, MG_ELASTICITY, MG_OSEEN = 0, 1, 2, 3
@@ -300,14 +303,14 @@ def mg_assemble_rhs(h, f, b, g=None):
 def mg_solve(h, b, x, rtol, max_it, prec=MG_FP64):
     st = MgStats()
     rc = load_library().mg_solve(h, _ptr(b), _ptr(x), rtol, max_it, prec, C.byref(st))
-    _check(rc, allow=(MG_OK, MG_ERR_NOT_CONVERGED))
+    _check(rc, allow=SOLVE_OUTCOMES)
     return st
 
 
 def mg_solve_host(h, b: np.ndarray, x: np.ndarray, rtol, max_it, prec=MG_FP64):
     st = MgStats()
     rc = load_library().mg_solve_host(h, _host_ptr(b), _host_ptr(x), rtol, max_it, prec, C.byref(st))
-    _check(rc, allow=(MG_OK, MG_ERR_NOT_CONVERGED))
+    _check(rc, allow=SOLVE_OUTCOMES)
     return st
 
 

@@ -281,6 +281,24 @@ def test_defect_correction_rounds(ctx, name):
     h.free()
 
 
+@pytest.mark.parametrize("name", ["poisson64", "td_adaptive", "oseen"])
+def test_zero_and_nan_right_hand_sides(ctx, name):
+    """b = 0 returns x = 0 at once (the tolerance is absolute when b_free = 0);
+    a NaN in b ends the device loop with MG_ERR_NAN instead of iterating on."""
+    lm, prob, oh, h = setup_case(ctx, name)
+    n = h.n_dofs
+    x = torch.zeros(n, device="cuda", dtype=torch.float64)
+    st = h.solve(torch.zeros(n, device="cuda", dtype=torch.float64), x, rtol=1e-10, max_it=50,
+                 prec=B.MG_MIXED_FP32)
+    assert st.status == 0 and st.iters == 0 and not x.any()
+    b = np.zeros(n)
+    free = np.nonzero(~oh.fine.sys.fixed)[0]
+    b[free[len(free) // 2]] = np.nan
+    x.zero_()
+    st = h.solve(dev(b), x, rtol=1e-10, max_it=50, prec=B.MG_MIXED_FP32)
+    assert st.status == B.MG_ERR_NAN, st.as_dict()
+
+
 def test_solve_host_equals_device(ctx):
     lm, prob, oh, h = setup_case(ctx, "td_adaptive")
     s = PB.build_system(oh.fine.mesh, prob)
