@@ -502,10 +502,17 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   const TailLevel* LV = P.lv;
   if constexpr (TLM == 2) {
     // the image holds only matrices and offsets: copy it before waiting on
-    // the preceding kernel
+    // the preceding kernel, four 16-byte loads in flight per thread
     const uint4* src = (const uint4*)P.image;
     uint4* dst = (uint4*)tail_smem;
-    for (uint32_t i = threadIdx.x; i < P.image_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    const uint32_t n16 = P.image_bytes / 16, step = blockDim.x;
+    uint32_t i = threadIdx.x;
+    for (; i + 3 * step < n16; i += 4 * step) {
+      const uint4 a = __ldg(src + i), b = __ldg(src + i + step), c = __ldg(src + i + 2 * step),
+                  d = __ldg(src + i + 3 * step);
+      dst[i] = a; dst[i + step] = b; dst[i + 2 * step] = c; dst[i + 3 * step] = d;
+    }
+    for (; i < n16; i += step) dst[i] = __ldg(src + i);
     __syncthreads();
     TailLevel* hdr = (TailLevel*)tail_smem;
     for (int l = threadIdx.x; l < P.nt; l += blockDim.x) {
@@ -538,7 +545,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
     __syncthreads();
   }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  T* cur_of[kTailMax];
   auto bvec = [&](int l) -> T* { return (TLM == 1 && l == top) ? const_cast<T*>(btop) : (T*)LV[l].b; };
   auto ovec = [&](int l) -> T* { return (TLM == 1 && l == top) ? otop : (T*)LV[l].o; };
   auto bufof = [&](int l, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? ovec(l) : (T*)LV[l].t; };
@@ -564,7 +570,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
       row_restrict<T, NC, TLM>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)LV[l - 1].S, x0, (T)LV[l - 1].omega);
     tail_sync();
     fdone = l - 1 > 0;
-    cur_of[l] = cur;
   }
   {   // coarse direct solve, one warp per row
     const int lane = threadIdx.x & 31;
@@ -581,7 +586,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   for (int l = 1; l <= top; ++l) {
     const TailLevel& L = LV[l];
     const T om = (T)L.omega;
-    T* cur = cur_of[l];
+    T* cur = bufof(l, P.nu1 - 1);       // output of the last pre-smoothing sweep (nu1 >= 1)
     T* pdst = P.nu2 == 0 ? ovec(l) : cur;
     for (int64_t row = tid; row < L.P.nslices * 32; row += nth)
       row_prolong<T, NC, TLM>(L.P, row, ovec(l - 1), cur, pdst);
@@ -1529,7 +1534,7 @@ void launch_tail_k(cudaLaunchConfig_t& cfg, const TailParams& P, const T* b, T* 
   if constexpr (TLM == 2) {
     static std::once_flag once;   // opt in to the large dynamic shared memory, once per instantiation
     std::call_once(once, [] {
-      cudaFuncSetAttribute(k_tail<T, V, NC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+      cudaFuncSetAttribute(k_tail<T, V, NC, TLM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
     });
   }
   cudaLaunchKernelEx(&cfg, k_tail<T, V, NC, TLM>, P, b, out, fd, done, o64, scale);
