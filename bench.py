@@ -12,6 +12,12 @@ beta = (1, 0.5), SUPG) on a 1-irregular mesh refined around 16 seeded points
 Jacobi.  Inputs are synthetic and seeded; L2 is flushed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload td_adaptive|poisson64|elasticity128|oseen|serving]
+
+Other workloads (same JSON line): poisson64 (64x64 Poisson, CG), elasticityN
+(N^3 elasticity, CG), oseen (Oseen/LPS channel, 658 k nodes, GMRES(30)),
+serving (a Poisson(200/s) stream of mixed requests through mg_submit/mg_poll:
+p50/p99 latency and aggregate DoF/s, plus a rate sweep).
 
 Under torchrun each rank solves its own copy of the workload on its own GPU
 (replicas: the solve does not shard); value = all ranks' DoFs / max time.
