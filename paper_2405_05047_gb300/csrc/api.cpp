@@ -217,6 +217,7 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   if (opts.nu1 < 1 || opts.nu2 < 0 || opts.nu1 > 16 || opts.nu2 > 16) return fail(MG_ERR_INVALID, "nu1 must be >= 1");
   if (std::isnan(opts.omega)) return fail(MG_ERR_INVALID, "omega is NaN");
   if (!(opts.inner_rtol >= 0.0 && opts.inner_rtol < 1.0)) return fail(MG_ERR_INVALID, "inner_rtol must be in [0, 1)");
+  if (opts.col16 < -1 || opts.col16 > 1) return fail(MG_ERR_INVALID, "col16 must be -1, 0 or 1");
   if (opts.sell_sigma < -1 || (opts.sell_sigma > 0 && opts.sell_sigma % 32 != 0))
     return fail(MG_ERR_INVALID, "sell_sigma must be -1, 0 or a positive multiple of 32");
   if (!opts.store_fp64 && !opts.store_fp32 && !opts.store_bf16) return fail(MG_ERR_INVALID, "no precision stored");
