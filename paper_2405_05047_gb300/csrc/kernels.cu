@@ -195,12 +195,12 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
 
 template <typename T, int LM, typename VT, typename CF>
 __device__ __forceinline__ void sell_dot3_loop(int64_t g, int64_t s1, int lane, const VT* __restrict__ val,
-                                               const T* __restrict__ x, T acc[3], CF colat) {
+                                               const T* __restrict__ x, T acc[3], CF colat, int64_t stride = 32) {
   acc[0] = acc[1] = acc[2] = T(0);
-  for (; g + 32 < s1; g += 64) {
-    const int ca = colat(g + lane), cb = colat(g + 32 + lane);
+  for (; g + stride < s1; g += 2 * stride) {
+    const int ca = colat(g + lane), cb = colat(g + stride + lane);
     const VT* __restrict__ va = val + g * 9 + lane;
-    const VT* __restrict__ vb = va + 32 * 9;
+    const VT* __restrict__ vb = va + stride * 9;
     T ma[9], mb[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) { ma[e] = ldv<T, LM>(va + e * 32); mb[e] = ldv<T, LM>(vb + e * 32); }
@@ -242,20 +242,28 @@ __device__ __forceinline__ void sell_dot3_loop(int64_t g, int64_t s1, int lane, 
 // Slot groups are processed two at a time (both column loads, then both
 // blocks' values and gathers, then the FMAs in slot order), so a thread keeps
 // two dependent load chains in flight; the group count is warp-uniform.
+// With tpr > 1 (small FP32 block levels) the tpr consecutive lanes of a row
+// share its slot groups (lane sub takes groups sub, sub + tpr, ...), and a
+// butterfly over those lanes adds the partial sums; every lane of the group
+// ends with the same bits (the pairwise additions commute).
 template <typename T, int LM = 0, typename VT = T>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
-                                          T acc[3]) {
+                                          T acc[3], int sub = 0, int tpr = 1) {
   const int64_t r0 = mld<LM>(A.sptr + slice), r1 = mld<LM>(A.sptr + slice + 1);
-  const int64_t s0 = r0 & kSptrMask, s1 = r1 & kSptrMask;
+  const int64_t s0 = (r0 & kSptrMask) + 32 * sub, s1 = r1 & kSptrMask;
   const VT* __restrict__ val = (const VT*)A.val;
+  const int64_t stride = 32 * (int64_t)tpr;
   if (A.col16 && !(r0 & 1)) {
     const int base = (int)((slice >> 3) * kCol16Window);
     const int16_t* c16 = A.col16;
-    sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return base + (int)mld<LM>(c16 + o); });
+    sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return base + (int)mld<LM>(c16 + o); }, stride);
   } else {
     const int32_t* c32 = A.col;
-    sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return (int)mld<LM>(c32 + o); });
+    sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return (int)mld<LM>(c32 + o); }, stride);
   }
+  for (int o = 1; o < tpr; o <<= 1)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
 }
 
 // acc[c] += sum_j W(row, j) v[NC j + c] for a transfer matrix row: batches
@@ -290,9 +298,12 @@ __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t s
 // One row (block row) of each level step.  The grid kernels below and the
 // single-CTA tail kernel call the same functions, so both produce bitwise
 // identical results.
+// sub: lane of the row's lane group (A.tpr lanes per row, block levels);
+// xo64 (optional): also write the output in FP64 times sc.
 template <typename T, int NC, int LM, typename VT = T>
 __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const T* x, const T* b, const T* Sinv,
-                                           T* xo, T omega, bool from_zero) {
+                                           T* xo, T omega, bool from_zero, int sub = 0, double* xo64 = nullptr,
+                                           double sc = 1.0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(A, row);
@@ -300,30 +311,36 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
     T r = from_zero ? T(0) : sell_dot1<T, LM, VT>(A, slice, lane, x);
     if (row < A.n) {
       const T bi = vld<LM>(b + orow);
-      if (from_zero) xo[orow] = omega * Sinv[orow] * bi;
-      else xo[orow] = fmad(omega * Sinv[orow], bi - r, vld<LM>(x + orow));
+      const T v = from_zero ? omega * Sinv[orow] * bi : fmad(omega * Sinv[orow], bi - r, vld<LM>(x + orow));
+      xo[orow] = v;
+      if (xo64) xo64[orow] = (double)v * sc;
     }
   } else {
+    const int tpr = A.tpr;
     T acc[3] = {T(0), T(0), T(0)};
-    if (!from_zero) sell_dot3<T, LM, VT>(A, slice, lane, x, acc);
+    if (!from_zero) sell_dot3<T, LM, VT>(A, slice, lane, x, acc, sub, tpr);
     if (row < A.n) {
       T res[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) res[i] = vld<LM>(b + 3 * orow + i) - acc[i];
       const T* S = Sinv + 9 * orow;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
+      // one lane per component when the row has several lanes
+      const int i0 = tpr > 1 ? sub : 0, i1 = tpr > 1 ? sub + 1 : 3;
+      for (int i = i0; i < i1 && i < 3; ++i) {
         T c = S[3 * i] * res[0];
         c = fmad(S[3 * i + 1], res[1], c);
         c = fmad(S[3 * i + 2], res[2], c);
-        xo[3 * orow + i] = from_zero ? omega * c : fmad(omega, c, vld<LM>(x + 3 * orow + i));
+        const T v = from_zero ? omega * c : fmad(omega, c, vld<LM>(x + 3 * orow + i));
+        xo[3 * orow + i] = v;
+        if (xo64) xo64[3 * orow + i] = (double)v * sc;
       }
     }
   }
 }
 
 template <typename T, int NC, int LM, typename VT = T>
-__device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y) {
+__device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y,
+                                             int sub = 0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(A, row);
@@ -331,11 +348,13 @@ __device__ __forceinline__ void row_residual(const SellView& A, int64_t row, con
     T r = sell_dot1<T, LM, VT>(A, slice, lane, x);
     if (row < A.n) y[orow] = vld<LM>(b + orow) - r;
   } else {
+    const int tpr = A.tpr;
     T acc[3];
-    sell_dot3<T, LM, VT>(A, slice, lane, x, acc);
-    if (row < A.n)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) y[3 * orow + i] = vld<LM>(b + 3 * orow + i) - acc[i];
+    sell_dot3<T, LM, VT>(A, slice, lane, x, acc, sub, tpr);
+    if (row < A.n) {
+      const int i0 = tpr > 1 ? sub : 0, i1 = tpr > 1 ? sub + 1 : 3;
+      for (int i = i0; i < i1 && i < 3; ++i) y[3 * orow + i] = vld<LM>(b + 3 * orow + i) - acc[i];
+    }
   }
 }
 
@@ -411,14 +430,10 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, 
   if (stopped(done)) return;
   const double sc = xo64 ? *scale : 1.0;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
-    row_smooth<T, NC, 0, VT>(A, row, x, b, Sinv, xo, omega, FROM_ZERO);
-    if (xo64 && row < A.n) {
-      const int64_t orow = srow<0>(A, row);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) xo64[NC * orow + c] = (double)xo[NC * orow + c] * sc;
-    }
-  }
+  const int tpr = NC == 1 ? 1 : A.tpr;          // lanes per row (a power of two <= 4)
+  const int64_t total = A.nslices * 32 * tpr;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthreads)
+    row_smooth<T, NC, 0, VT>(A, t / tpr, x, b, Sinv, xo, omega, FROM_ZERO, (int)(t % tpr), xo64, sc);
 }
 
 template <typename T, typename VT, int NC, int MODE>   // MODE 0: y = A x; 1: y = b - A x
@@ -427,23 +442,28 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, c
   pdl_wait();
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.nslices * 32; row += nthreads) {
+  const int tpr = NC == 1 ? 1 : A.tpr;
+  const int64_t total = A.nslices * 32 * tpr;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthreads) {
+    const int64_t row = t / tpr;
+    const int sub = (int)(t % tpr);
     if (MODE == 1) {
-      row_residual<T, NC, 0, VT>(A, row, x, b, y);
+      row_residual<T, NC, 0, VT>(A, row, x, b, y, sub);
       continue;
     }
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
-  const int64_t orow = srow<0>(A, row);
+    const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
       T r = sell_dot1<T, 0, VT>(A, slice, lane, x);
       if (row < A.n) y[orow] = r;
     } else {
       T acc[3];
-      sell_dot3<T, 0, VT>(A, slice, lane, x, acc);
-      if (row < A.n)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) y[3 * orow + i] = acc[i];
+      sell_dot3<T, 0, VT>(A, slice, lane, x, acc, sub, tpr);
+      if (row < A.n) {
+        const int i0 = tpr > 1 ? sub : 0, i1 = tpr > 1 ? sub + 1 : 3;
+        for (int i = i0; i < i1 && i < 3; ++i) y[3 * orow + i] = acc[i];
+      }
     }
   }
 }
@@ -553,17 +573,19 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
     const TailLevel& L = LV[l];
     const T* S = (const T*)L.S;
     const T om = (T)L.omega;
+    const int tpr = NC == 1 ? 1 : L.A.tpr;
     T* cur = nullptr;
     for (int k = 0; k < P.nu1; ++k) {
       T* dst = bufof(l, k);
       if (!(k == 0 && fdone)) {
-        for (int64_t row = tid; row < L.A.nslices * 32; row += nth)
-          row_smooth<T, NC, TLM, VT>(L.A, row, cur, bvec(l), S, dst, om, k == 0);
+        for (int64_t t = tid; t < L.A.nslices * 32 * tpr; t += nth)
+          row_smooth<T, NC, TLM, VT>(L.A, t / tpr, cur, bvec(l), S, dst, om, k == 0, (int)(t % tpr));
         tail_sync();
       }
       cur = dst;
     }
-    for (int64_t row = tid; row < L.A.nslices * 32; row += nth) row_residual<T, NC, TLM, VT>(L.A, row, cur, bvec(l), (T*)L.r);
+    for (int64_t t = tid; t < L.A.nslices * 32 * tpr; t += nth)
+      row_residual<T, NC, TLM, VT>(L.A, t / tpr, cur, bvec(l), (T*)L.r, (int)(t % tpr));
     tail_sync();
     T* x0 = l - 1 > 0 ? bufof(l - 1, 0) : nullptr;
     for (int64_t row = tid; row < L.R.nslices * 32; row += nth)
@@ -586,6 +608,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   for (int l = 1; l <= top; ++l) {
     const TailLevel& L = LV[l];
     const T om = (T)L.omega;
+    const int tpr = NC == 1 ? 1 : L.A.tpr;
     T* cur = bufof(l, P.nu1 - 1);       // output of the last pre-smoothing sweep (nu1 >= 1)
     T* pdst = P.nu2 == 0 ? ovec(l) : cur;
     for (int64_t row = tid; row < L.P.nslices * 32; row += nth)
@@ -596,14 +619,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
       T* dst = bufof(l, k);
       const bool out64 = o64 && l == top && k == ns - 1;   // last sweep: also the FP64 copy times *scale
       const double sc = out64 ? *scale : 1.0;
-      for (int64_t row = tid; row < L.A.nslices * 32; row += nth) {
-        row_smooth<T, NC, TLM, VT>(L.A, row, cur, bvec(l), (const T*)L.S, dst, om, false);
-        if (out64 && row < L.A.n) {
-          const int64_t orow = srow<TLM>(L.A, row);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) o64[NC * orow + c] = (double)dst[NC * orow + c] * sc;
-        }
-      }
+      for (int64_t t = tid; t < L.A.nslices * 32 * tpr; t += nth)
+        row_smooth<T, NC, TLM, VT>(L.A, t / tpr, cur, bvec(l), (const T*)L.S, dst, om, false, (int)(t % tpr),
+                                   out64 ? o64 : nullptr, sc);
       tail_sync();
       cur = dst;
     }
@@ -1432,7 +1450,7 @@ static int grid_sell(int64_t nslices) { return grid_for_rows(nslices * 32); }
 template <typename T>
 void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* Sinv, T* xo, double omega,
                    bool from_zero, const int* done, cudaStream_t s, double* xo64, const double* scale) {
-  const int g = grid_sell(A.nslices);
+  const int g = grid_for_rows(A.nslices * 32 * (nc == 1 ? 1 : A.tpr));
   const T om = (T)omega;
   if constexpr (std::is_same<T, float>::value) {
     if (A.bf16) {
@@ -1458,7 +1476,7 @@ void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* S
 
 template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s) {
-  const int g = grid_sell(A.nslices);
+  const int g = grid_for_rows(A.nslices * 32 * (nc == 1 ? 1 : A.tpr));
   if constexpr (std::is_same<T, float>::value) {
     if (A.bf16) {
       using V = __nv_bfloat16;
@@ -1473,7 +1491,7 @@ void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, co
 
 template <typename T>
 void launch_matvec(const SellView& A, int nc, const T* x, T* y, const int* done, cudaStream_t s) {
-  const int g = grid_sell(A.nslices);
+  const int g = grid_for_rows(A.nslices * 32 * (nc == 1 ? 1 : A.tpr));
   if constexpr (std::is_same<T, float>::value) {
     if (A.bf16) {
       using V = __nv_bfloat16;

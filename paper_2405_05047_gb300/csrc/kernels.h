@@ -28,6 +28,7 @@ struct SellView {
   // of sptr[slice] set and uses col[] instead; slot offsets are multiples of
   // 32, so readers mask sptr with kSptrMask.
   const int16_t* col16 = nullptr;
+  int tpr = 1;                // lanes per block row (1 or 4; small FP32/BF16 block levels use 4)
 };
 constexpr int64_t kSptrMask = ~int64_t(31);
 constexpr int kCol16Window = 256;       // rows per base of the 16-bit column offsets
