@@ -164,6 +164,9 @@ typedef struct {
   int col16;                   /* 16-bit column offsets in the FP32/BF16 level
                                   matrices (-1: automatic, levels of >= 32768
                                   rows; 0: never; 1: every level)            */
+  int row_lanes;               /* lanes per row of the FP32/BF16 level matrices
+                                  (-1: automatic, 4 on the small latency-bound
+                                  levels; 1: one lane per row everywhere)     */
 } mg_opts;
 
 typedef struct {

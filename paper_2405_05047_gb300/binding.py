@@ -59,7 +59,8 @@ class MgOpts(C.Structure):
                 ("max_levels", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("store_fp64", C.c_int),
                 ("store_fp32", C.c_int), ("launch_mode", C.c_int),
                 ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int),
-                ("inner_rtol", C.c_double), ("sell_sigma", C.c_int), ("col16", C.c_int)]
+                ("inner_rtol", C.c_double), ("sell_sigma", C.c_int), ("col16", C.c_int),
+                ("row_lanes", C.c_int)]
 
 
 class MgInfo(C.Structure):

@@ -169,6 +169,7 @@ void mg_default_opts(mg_opts* o) {
   o->inner_rtol = 0.0;
   o->sell_sigma = -1;
   o->col16 = -1;
+  o->row_lanes = -1;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -218,6 +219,7 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   if (std::isnan(opts.omega)) return fail(MG_ERR_INVALID, "omega is NaN");
   if (!(opts.inner_rtol >= 0.0 && opts.inner_rtol < 1.0)) return fail(MG_ERR_INVALID, "inner_rtol must be in [0, 1)");
   if (opts.col16 < -1 || opts.col16 > 1) return fail(MG_ERR_INVALID, "col16 must be -1, 0 or 1");
+  if (opts.row_lanes != -1 && opts.row_lanes != 1) return fail(MG_ERR_INVALID, "row_lanes must be -1 or 1");
   if (opts.sell_sigma < -1 || (opts.sell_sigma > 0 && opts.sell_sigma % 32 != 0))
     return fail(MG_ERR_INVALID, "sell_sigma must be -1, 0 or a positive multiple of 32");
   if (!opts.store_fp64 && !opts.store_fp32 && !opts.store_bf16) return fail(MG_ERR_INVALID, "no precision stored");

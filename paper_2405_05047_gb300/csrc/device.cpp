@@ -213,10 +213,16 @@ bool idx16_for(const mg_hier* h, int64_t rows) {
   const int o = h->opts.col16;
   return o >= 0 ? o != 0 : rows >= kSigmaMinRows;
 }
-// Lanes per block row of the FP32/BF16 level operators: the small block
-// levels are latency-bound (one thread walks ~16 block slots), so four lanes
-// share a row there.
-int tpr_for(int nc, int64_t rows) { return (nc == 3 && rows < 65536) ? 4 : 1; }
+// Lanes per row of the FP32/BF16 level operators: the small levels are
+// latency-bound (one thread walks all slots of its row one dependent batch
+// after another), so four lanes share a row there.
+int tpr_for(const mg_hier* h, int nc, int64_t rows) {
+  if (h->opts.row_lanes == 1) return 1;
+  if (nc == 3) return rows < 65536 ? 4 : 1;
+  // scalar rows are short: the smallest levels (the shared-memory tail's,
+  // where threads are few) keep one lane per row
+  return (rows >= 1024 && rows < 32768) ? 4 : 1;
+}
 int64_t sigma_for(const mg_hier* h, int64_t rows) {
   const int o = h->opts.sell_sigma;
   if (o >= 0) return o;
@@ -405,7 +411,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     }
     if (opts.store_fp32) {
       if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n)))) return rc;
-      B.A32.v.tpr = tpr_for(nc, lv.A.n);
+      B.A32.v.tpr = tpr_for(h, nc, lv.A.n);
       std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
       B.S32 = halloc<float>(h, B.n * nb);
       if (!B.S32) return fail(MG_ERR_OOM, "alloc");
@@ -414,7 +420,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     if (opts.store_bf16) {
       if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n)))) return rc;
       B.A16.v.bf16 = 1;
-      B.A16.v.tpr = tpr_for(nc, lv.A.n);
+      B.A16.v.tpr = tpr_for(h, nc, lv.A.n);
       if (!B.S32) {
         std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
         B.S32 = halloc<float>(h, B.n * nb);

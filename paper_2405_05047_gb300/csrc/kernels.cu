@@ -114,29 +114,29 @@ __device__ __forceinline__ int64_t srow(const V& A, int64_t row) {
 // warp-uniform.  The summation order is the plain sequential one.
 template <typename AT, int LM, typename VT, typename XT, typename CF>
 __device__ __forceinline__ AT sell_dot1x_loop(int64_t o, int64_t s1, const VT* __restrict__ val, const XT* __restrict__ x,
-                                              CF colat) {
+                                              CF colat, int64_t S = 32) {
   AT acc = AT(0);
-  for (; o + 3 * 32 < s1; o += 4 * 32) {
-    const int c0 = colat(o), c1 = colat(o + 32), c2 = colat(o + 64), c3 = colat(o + 96);
-    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32), v2 = ldv<AT, LM>(val + o + 64),
-             v3 = ldv<AT, LM>(val + o + 96);
+  for (; o + 3 * S < s1; o += 4 * S) {
+    const int c0 = colat(o), c1 = colat(o + S), c2 = colat(o + 2 * S), c3 = colat(o + 3 * S);
+    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + S), v2 = ldv<AT, LM>(val + o + 2 * S),
+             v3 = ldv<AT, LM>(val + o + 3 * S);
     const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2), x3 = vld<LM>(x + c3);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
     acc = fmad(v2, (AT)x2, acc);
     acc = fmad(v3, (AT)x3, acc);
   }
-  const int rem = (int)((s1 - o + 31) >> 5);   // 0..3, identical across the warp
+  const int rem = (int)((s1 - o + S - 1) / S);   // 0..3 (identical across a warp when S = 32)
   if (rem == 3) {
-    const int c0 = colat(o), c1 = colat(o + 32), c2 = colat(o + 64);
-    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32), v2 = ldv<AT, LM>(val + o + 64);
+    const int c0 = colat(o), c1 = colat(o + S), c2 = colat(o + 2 * S);
+    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + S), v2 = ldv<AT, LM>(val + o + 2 * S);
     const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
     acc = fmad(v2, (AT)x2, acc);
   } else if (rem == 2) {
-    const int c0 = colat(o), c1 = colat(o + 32);
-    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + 32);
+    const int c0 = colat(o), c1 = colat(o + S);
+    const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + S);
     const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
@@ -155,19 +155,28 @@ __device__ __forceinline__ AT sell_dot1x_loop(int64_t o, int64_t s1, const VT* _
 template <typename AT, int LM = 0, typename VT, typename XT>
 __device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                          const VT* __restrict__ val, int64_t slice, int lane,
-                                         const XT* __restrict__ x, const int16_t* __restrict__ col16 = nullptr) {
+                                         const XT* __restrict__ x, const int16_t* __restrict__ col16 = nullptr,
+                                         int sub = 0, int tpr = 1) {
   const int64_t r0 = mld<LM>(sptr + slice), r1 = mld<LM>(sptr + slice + 1);
-  const int64_t s0 = (r0 & kSptrMask) + lane, s1 = r1 & kSptrMask;
+  const int64_t s0 = (r0 & kSptrMask) + lane + 32 * sub, s1 = r1 & kSptrMask;
+  const int64_t S = 32 * (int64_t)tpr;
   if (col16 && !(r0 & 1)) {
     const int base = (int)((slice >> 3) * kCol16Window);
-    return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return base + (int)mld<LM>(col16 + o); });
+    return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return base + (int)mld<LM>(col16 + o); }, S);
   }
-  return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return (int)mld<LM>(col + o); });
+  return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return (int)mld<LM>(col + o); }, S);
 }
 
-template <typename T, int LM = 0, typename VT = T>
-__device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x) {
-  return sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x, A.col16);
+// Scalar row sum; with tpr > 1 lane sub of the row's group takes slot groups
+// sub, sub + tpr, ... and a butterfly adds the partial sums (same bits on
+// every lane of the group).
+template <typename T, int LM = 0, typename VT = T, int TPR = 1>
+__device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
+                                       int sub = 0) {
+  T acc = sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x, A.col16, sub, TPR);
+#pragma unroll
+  for (int o = 1; o < TPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
 }
 
 // acc[0..2] = sum_j A(row, j) x_j for a 3x3-block SELL row.
@@ -246,9 +255,10 @@ __device__ __forceinline__ void sell_dot3_loop(int64_t g, int64_t s1, int lane, 
 // share its slot groups (lane sub takes groups sub, sub + tpr, ...), and a
 // butterfly over those lanes adds the partial sums; every lane of the group
 // ends with the same bits (the pairwise additions commute).
-template <typename T, int LM = 0, typename VT = T>
+template <typename T, int LM = 0, typename VT = T, int TPR = 1>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
-                                          T acc[3], int sub = 0, int tpr = 1) {
+                                          T acc[3], int sub = 0) {
+  constexpr int tpr = TPR;
   const int64_t r0 = mld<LM>(A.sptr + slice), r1 = mld<LM>(A.sptr + slice + 1);
   const int64_t s0 = (r0 & kSptrMask) + 32 * sub, s1 = r1 & kSptrMask;
   const VT* __restrict__ val = (const VT*)A.val;
@@ -261,6 +271,7 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
     const int32_t* c32 = A.col;
     sell_dot3_loop<T, LM>(s0, s1, lane, val, x, acc, [&](int64_t o) { return (int)mld<LM>(c32 + o); }, stride);
   }
+#pragma unroll
   for (int o = 1; o < tpr; o <<= 1)
 #pragma unroll
     for (int i = 0; i < 3; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
@@ -300,7 +311,7 @@ __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t s
 // identical results.
 // sub: lane of the row's lane group (A.tpr lanes per row, block levels);
 // xo64 (optional): also write the output in FP64 times sc.
-template <typename T, int NC, int LM, typename VT = T>
+template <typename T, int NC, int LM, typename VT = T, int TPR = 1>
 __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const T* x, const T* b, const T* Sinv,
                                            T* xo, T omega, bool from_zero, int sub = 0, double* xo64 = nullptr,
                                            double sc = 1.0) {
@@ -308,17 +319,17 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(A, row);
   if (NC == 1) {
-    T r = from_zero ? T(0) : sell_dot1<T, LM, VT>(A, slice, lane, x);
-    if (row < A.n) {
+    T r = from_zero ? T(0) : sell_dot1<T, LM, VT, TPR>(A, slice, lane, x, sub);
+    if (row < A.n && sub == 0) {
       const T bi = vld<LM>(b + orow);
       const T v = from_zero ? omega * Sinv[orow] * bi : fmad(omega * Sinv[orow], bi - r, vld<LM>(x + orow));
       xo[orow] = v;
       if (xo64) xo64[orow] = (double)v * sc;
     }
   } else {
-    const int tpr = A.tpr;
+    constexpr int tpr = TPR;
     T acc[3] = {T(0), T(0), T(0)};
-    if (!from_zero) sell_dot3<T, LM, VT>(A, slice, lane, x, acc, sub, tpr);
+    if (!from_zero) sell_dot3<T, LM, VT, TPR>(A, slice, lane, x, acc, sub);
     if (row < A.n) {
       T res[3];
 #pragma unroll
@@ -326,7 +337,9 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
       const T* S = Sinv + 9 * orow;
       // one lane per component when the row has several lanes
       const int i0 = tpr > 1 ? sub : 0, i1 = tpr > 1 ? sub + 1 : 3;
-      for (int i = i0; i < i1 && i < 3; ++i) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i < i0 || i >= i1) continue;
         T c = S[3 * i] * res[0];
         c = fmad(S[3 * i + 1], res[1], c);
         c = fmad(S[3 * i + 2], res[2], c);
@@ -338,22 +351,24 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
   }
 }
 
-template <typename T, int NC, int LM, typename VT = T>
+template <typename T, int NC, int LM, typename VT = T, int TPR = 1>
 __device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y,
                                              int sub = 0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(A, row);
   if (NC == 1) {
-    T r = sell_dot1<T, LM, VT>(A, slice, lane, x);
-    if (row < A.n) y[orow] = vld<LM>(b + orow) - r;
+    T r = sell_dot1<T, LM, VT, TPR>(A, slice, lane, x, sub);
+    if (row < A.n && sub == 0) y[orow] = vld<LM>(b + orow) - r;
   } else {
-    const int tpr = A.tpr;
+    constexpr int tpr = TPR;
     T acc[3];
-    sell_dot3<T, LM, VT>(A, slice, lane, x, acc, sub, tpr);
+    sell_dot3<T, LM, VT, TPR>(A, slice, lane, x, acc, sub);
     if (row < A.n) {
       const int i0 = tpr > 1 ? sub : 0, i1 = tpr > 1 ? sub + 1 : 3;
-      for (int i = i0; i < i1 && i < 3; ++i) y[3 * orow + i] = vld<LM>(b + 3 * orow + i) - acc[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i >= i0 && i < i1) y[3 * orow + i] = vld<LM>(b + 3 * orow + i) - acc[i];
     }
   }
 }
@@ -421,7 +436,7 @@ __device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, 
 // x_out = x + omega S (b - A x)  (Sec. 4.1.4), S = inverse diagonal block.
 // xo64 (optional): the sweep's output also written in FP64 times *scale (the
 // last sweep of an FP32 V-cycle hands the FP64 Krylov loop its result).
-template <typename T, typename VT, int NC, bool FROM_ZERO>
+template <typename T, typename VT, int NC, bool FROM_ZERO, int TPR>
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, const T* __restrict__ x, const T* __restrict__ b,
                                                     const T* __restrict__ Sinv, T* __restrict__ xo, T omega,
                                                     const int* done, double* __restrict__ xo64,
@@ -430,39 +445,40 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, 
   if (stopped(done)) return;
   const double sc = xo64 ? *scale : 1.0;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int tpr = NC == 1 ? 1 : A.tpr;          // lanes per row (a power of two <= 4)
-  const int64_t total = A.nslices * 32 * tpr;
+  const int64_t total = A.nslices * 32 * TPR;   // TPR lanes per row (1 or 4)
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthreads)
-    row_smooth<T, NC, 0, VT>(A, t / tpr, x, b, Sinv, xo, omega, FROM_ZERO, (int)(t % tpr), xo64, sc);
+    row_smooth<T, NC, 0, VT, TPR>(A, t / TPR, x, b, Sinv, xo, omega, FROM_ZERO, (int)(t % TPR), xo64, sc);
 }
 
-template <typename T, typename VT, int NC, int MODE>   // MODE 0: y = A x; 1: y = b - A x
+template <typename T, typename VT, int NC, int MODE, int TPR>   // MODE 0: y = A x; 1: y = b - A x
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ y, const int* done) {
   pdl_wait();
   if (stopped(done)) return;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int tpr = NC == 1 ? 1 : A.tpr;
+  constexpr int tpr = TPR;
   const int64_t total = A.nslices * 32 * tpr;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthreads) {
     const int64_t row = t / tpr;
     const int sub = (int)(t % tpr);
     if (MODE == 1) {
-      row_residual<T, NC, 0, VT>(A, row, x, b, y, sub);
+      row_residual<T, NC, 0, VT, TPR>(A, row, x, b, y, sub);
       continue;
     }
     const int64_t slice = row >> 5;
     const int lane = (int)(row & 31);
     const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
-      T r = sell_dot1<T, 0, VT>(A, slice, lane, x);
-      if (row < A.n) y[orow] = r;
+      T r = sell_dot1<T, 0, VT, TPR>(A, slice, lane, x, sub);
+      if (row < A.n && sub == 0) y[orow] = r;
     } else {
       T acc[3];
-      sell_dot3<T, 0, VT>(A, slice, lane, x, acc, sub, tpr);
+      sell_dot3<T, 0, VT, TPR>(A, slice, lane, x, acc, sub);
       if (row < A.n) {
         const int i0 = tpr > 1 ? sub : 0, i1 = tpr > 1 ? sub + 1 : 3;
-        for (int i = i0; i < i1 && i < 3; ++i) y[3 * orow + i] = acc[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i >= i0 && i < i1) y[3 * orow + i] = acc[i];
       }
     }
   }
@@ -573,19 +589,26 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
     const TailLevel& L = LV[l];
     const T* S = (const T*)L.S;
     const T om = (T)L.omega;
-    const int tpr = NC == 1 ? 1 : L.A.tpr;
+    const int tpr = L.A.tpr;
     T* cur = nullptr;
     for (int k = 0; k < P.nu1; ++k) {
       T* dst = bufof(l, k);
       if (!(k == 0 && fdone)) {
-        for (int64_t t = tid; t < L.A.nslices * 32 * tpr; t += nth)
-          row_smooth<T, NC, TLM, VT>(L.A, t / tpr, cur, bvec(l), S, dst, om, k == 0, (int)(t % tpr));
+        if (tpr == 4)
+          for (int64_t t = tid; t < L.A.nslices * 32 * 4; t += nth)
+            row_smooth<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), S, dst, om, k == 0, (int)(t % 4));
+        else
+          for (int64_t t = tid; t < L.A.nslices * 32; t += nth)
+            row_smooth<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), S, dst, om, k == 0);
         tail_sync();
       }
       cur = dst;
     }
-    for (int64_t t = tid; t < L.A.nslices * 32 * tpr; t += nth)
-      row_residual<T, NC, TLM, VT>(L.A, t / tpr, cur, bvec(l), (T*)L.r, (int)(t % tpr));
+    if (tpr == 4)
+      for (int64_t t = tid; t < L.A.nslices * 32 * 4; t += nth)
+        row_residual<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), (T*)L.r, (int)(t % 4));
+    else
+      for (int64_t t = tid; t < L.A.nslices * 32; t += nth) row_residual<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), (T*)L.r);
     tail_sync();
     T* x0 = l - 1 > 0 ? bufof(l - 1, 0) : nullptr;
     for (int64_t row = tid; row < L.R.nslices * 32; row += nth)
@@ -608,7 +631,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   for (int l = 1; l <= top; ++l) {
     const TailLevel& L = LV[l];
     const T om = (T)L.omega;
-    const int tpr = NC == 1 ? 1 : L.A.tpr;
+    const int tpr = L.A.tpr;
     T* cur = bufof(l, P.nu1 - 1);       // output of the last pre-smoothing sweep (nu1 >= 1)
     T* pdst = P.nu2 == 0 ? ovec(l) : cur;
     for (int64_t row = tid; row < L.P.nslices * 32; row += nth)
@@ -619,9 +642,14 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
       T* dst = bufof(l, k);
       const bool out64 = o64 && l == top && k == ns - 1;   // last sweep: also the FP64 copy times *scale
       const double sc = out64 ? *scale : 1.0;
-      for (int64_t t = tid; t < L.A.nslices * 32 * tpr; t += nth)
-        row_smooth<T, NC, TLM, VT>(L.A, t / tpr, cur, bvec(l), (const T*)L.S, dst, om, false, (int)(t % tpr),
-                                   out64 ? o64 : nullptr, sc);
+      if (tpr == 4)
+        for (int64_t t = tid; t < L.A.nslices * 32 * 4; t += nth)
+          row_smooth<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), (const T*)L.S, dst, om, false, (int)(t % 4),
+                                        out64 ? o64 : nullptr, sc);
+      else
+        for (int64_t t = tid; t < L.A.nslices * 32; t += nth)
+          row_smooth<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), (const T*)L.S, dst, om, false, 0,
+                                        out64 ? o64 : nullptr, sc);
       tail_sync();
       cur = dst;
     }
@@ -1447,61 +1475,74 @@ int grid_for_vec(int64_t n) { return grid_for_rows(n); }
 
 static int grid_sell(int64_t nslices) { return grid_for_rows(nslices * 32); }
 
+template <typename T, typename V, int NC, int TPR>
+void launch_smooth_k(const SellView& A, int g, cudaStream_t s, const T* x, const T* b, const T* Sinv, T* xo, T om,
+                     bool from_zero, const int* done, double* xo64, const double* scale) {
+  if (from_zero) launch(k_smooth<T, V, NC, true, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+  else launch(k_smooth<T, V, NC, false, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+}
+
+template <typename T, typename V>
+void launch_smooth_v(const SellView& A, int nc, int g, cudaStream_t s, const T* x, const T* b, const T* Sinv, T* xo,
+                     T om, bool from_zero, const int* done, double* xo64, const double* scale) {
+  const bool four = A.tpr == 4;
+  if (nc == 1) {
+    if (four) launch_smooth_k<T, V, 1, 4>(A, g, s, x, b, Sinv, xo, om, from_zero, done, xo64, scale);
+    else launch_smooth_k<T, V, 1, 1>(A, g, s, x, b, Sinv, xo, om, from_zero, done, xo64, scale);
+  } else {
+    if (four) launch_smooth_k<T, V, 3, 4>(A, g, s, x, b, Sinv, xo, om, from_zero, done, xo64, scale);
+    else launch_smooth_k<T, V, 3, 1>(A, g, s, x, b, Sinv, xo, om, from_zero, done, xo64, scale);
+  }
+}
+
 template <typename T>
 void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* Sinv, T* xo, double omega,
                    bool from_zero, const int* done, cudaStream_t s, double* xo64, const double* scale) {
-  const int g = grid_for_rows(A.nslices * 32 * (nc == 1 ? 1 : A.tpr));
+  const int g = grid_for_rows(A.nslices * 32 * A.tpr);
   const T om = (T)omega;
   if constexpr (std::is_same<T, float>::value) {
     if (A.bf16) {
-      using V = __nv_bfloat16;
-      if (nc == 1) {
-        if (from_zero) launch(k_smooth<T, V, 1, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-        else launch(k_smooth<T, V, 1, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-      } else {
-        if (from_zero) launch(k_smooth<T, V, 3, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-        else launch(k_smooth<T, V, 3, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-      }
+      launch_smooth_v<T, __nv_bfloat16>(A, nc, g, s, x, b, Sinv, xo, om, from_zero, done, xo64, scale);
       return;
     }
   }
+  launch_smooth_v<T, T>(A, nc, g, s, x, b, Sinv, xo, om, from_zero, done, xo64, scale);
+}
+
+template <typename T, typename V, int MODE>
+void launch_apply_v(const SellView& A, int nc, int g, cudaStream_t s, const T* x, const T* b, T* y, const int* done) {
+  const bool four = A.tpr == 4;
   if (nc == 1) {
-    if (from_zero) launch(k_smooth<T, T, 1, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-    else launch(k_smooth<T, T, 1, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+    if (four) launch(k_apply<T, V, 1, MODE, 4>, g, s, A, x, b, y, done);
+    else launch(k_apply<T, V, 1, MODE, 1>, g, s, A, x, b, y, done);
   } else {
-    if (from_zero) launch(k_smooth<T, T, 3, true>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-    else launch(k_smooth<T, T, 3, false>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+    if (four) launch(k_apply<T, V, 3, MODE, 4>, g, s, A, x, b, y, done);
+    else launch(k_apply<T, V, 3, MODE, 1>, g, s, A, x, b, y, done);
   }
 }
 
 template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s) {
-  const int g = grid_for_rows(A.nslices * 32 * (nc == 1 ? 1 : A.tpr));
+  const int g = grid_for_rows(A.nslices * 32 * A.tpr);
   if constexpr (std::is_same<T, float>::value) {
     if (A.bf16) {
-      using V = __nv_bfloat16;
-      if (nc == 1) launch(k_apply<T, V, 1, 1>, g, s, A, x, b, r, done);
-      else launch(k_apply<T, V, 3, 1>, g, s, A, x, b, r, done);
+      launch_apply_v<T, __nv_bfloat16, 1>(A, nc, g, s, x, b, r, done);
       return;
     }
   }
-  if (nc == 1) launch(k_apply<T, T, 1, 1>, g, s, A, x, b, r, done);
-  else launch(k_apply<T, T, 3, 1>, g, s, A, x, b, r, done);
+  launch_apply_v<T, T, 1>(A, nc, g, s, x, b, r, done);
 }
 
 template <typename T>
 void launch_matvec(const SellView& A, int nc, const T* x, T* y, const int* done, cudaStream_t s) {
-  const int g = grid_for_rows(A.nslices * 32 * (nc == 1 ? 1 : A.tpr));
+  const int g = grid_for_rows(A.nslices * 32 * A.tpr);
   if constexpr (std::is_same<T, float>::value) {
     if (A.bf16) {
-      using V = __nv_bfloat16;
-      if (nc == 1) launch(k_apply<T, V, 1, 0>, g, s, A, x, (const T*)nullptr, y, done);
-      else launch(k_apply<T, V, 3, 0>, g, s, A, x, (const T*)nullptr, y, done);
+      launch_apply_v<T, __nv_bfloat16, 0>(A, nc, g, s, x, (const T*)nullptr, y, done);
       return;
     }
   }
-  if (nc == 1) launch(k_apply<T, T, 1, 0>, g, s, A, x, (const T*)nullptr, y, done);
-  else launch(k_apply<T, T, 3, 0>, g, s, A, x, (const T*)nullptr, y, done);
+  launch_apply_v<T, T, 0>(A, nc, g, s, x, (const T*)nullptr, y, done);
 }
 
 template <typename T>
