@@ -189,6 +189,10 @@ typedef struct {
   int level_col16[32];                  /* 1: the level's FP32/BF16 copy stores
                                            16-bit column offsets                 */
   double level_omega[32];               /* smoother damping per level            */
+  int level_block_values[32];           /* values stored per block of the level
+                                           operator: nc*nc, or 6 for 3x3 blocks of
+                                           the velocity-pressure pattern
+                                           [[a,0,g1],[0,a,g2],[d1,d2,c]]          */
 } mg_info;
 
 typedef struct {
@@ -313,6 +317,39 @@ int mg_restrict_static(mg_hier* h, int level, const void* x, const void* b, void
  * the solves use).  For measurement only. */
 enum { MG_TIME_VCYCLE = 5, MG_TIME_VCYCLE_GRAPH = 6 };
 int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms);
+
+/* Per-kernel device time of one solve.  Runs the solve of mg_solve (same
+ * kernels in the same order, so x and stats are bitwise the same) but issues
+ * one Krylov iteration at a time as a plain CUDA graph with a CUDA
+ * event-record node after every kernel (and one before the first): a
+ * kernel's interval runs from the end of the previous kernel to its own end,
+ * so the intervals of an iteration add up to its device time.  The graph
+ * starts with an empty kernel (`k_prof_empty`, level -2, not part of the
+ * solve and not counted in stats->launches) whose interval is the floor of
+ * any interval: launch latency plus event overhead, which the chained kernels
+ * of mg_solve partly hide.  Launches outside the iterations are bracketed by
+ * two events on the context's stream.  Intervals are summed per
+ * (kernel, level):
+ *   kernel:   the kernel's name with its template arguments (truncated to 127
+ *             characters, NUL-terminated);
+ *   level:    the multigrid level whose V-cycle step launched it (restriction
+ *             and the fused first sweep below count for the finer level; the
+ *             small-level kernel for the top level it covers), -1 for Krylov
+ *             and bookkeeping kernels, -2 for the empty kernel;
+ *   launches, ms: launches and summed milliseconds.
+ * Entries are sorted by ms, largest first; at most `cap` are written and
+ * *n_entries receives the number of distinct pairs.  Launches beyond 8190 per
+ * iteration are not timed.  For measurement: the solve itself runs slower
+ * than mg_solve (host round trip per iteration, no overlap of neighbouring
+ * kernels). */
+typedef struct {
+  char kernel[128];
+  int level;
+  int64_t launches;
+  double ms;
+} mg_prof_entry;
+int mg_solve_profiled(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats,
+                      mg_prof_entry* entries, int cap, int* n_entries);
 
 /* Serving: continuous batching of solves on resident hierarchies.
  * mg_submit queues a solve of h (b, x device buffers, caller-owned, not to be

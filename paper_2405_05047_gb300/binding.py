@@ -70,7 +70,8 @@ class MgInfo(C.Structure):
                 ("bytes_device", C.c_size_t), ("n_hanging", C.c_int64), ("omega", C.c_double),
                 ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
                 ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64),
-                ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32)]
+                ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32),
+                ("level_block_values", C.c_int * 32)]
 
 
 class MgStats(C.Structure):
@@ -80,6 +81,10 @@ class MgStats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MgProfEntry(C.Structure):
+    _fields_ = [("kernel", C.c_char * 128), ("level", C.c_int), ("launches", C.c_int64), ("ms", C.c_double)]
 
 
 _MALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -110,6 +115,8 @@ _SIGS = {
                            C.POINTER(MgStats)]),
     "mg_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(MgStats)]),
+    "mg_solve_profiled": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
+                                    C.POINTER(MgStats), C.POINTER(MgProfEntry), C.c_int, C.POINTER(C.c_int)]),
     "mg_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
@@ -308,6 +315,20 @@ def mg_solve(h, b, x, rtol, max_it, prec=MG_FP64):
     return st
 
 
+def mg_solve_profiled(h, b, x, rtol, max_it, prec=MG_FP64, cap=256):
+    """mg_solve with per-kernel event timing: (stats, [{kernel, level,
+    launches, ms}, ...] sorted by ms, largest first)."""
+    st = MgStats()
+    ents = (MgProfEntry * cap)()
+    n = C.c_int(0)
+    rc = load_library().mg_solve_profiled(h, _ptr(b), _ptr(x), rtol, max_it, prec, C.byref(st), ents, cap,
+                                          C.byref(n))
+    _check(rc, allow=SOLVE_OUTCOMES)
+    out = [{"kernel": e.kernel.decode(), "level": e.level, "launches": e.launches, "ms": e.ms}
+           for e in ents[:min(n.value, cap)]]
+    return st, out
+
+
 def mg_solve_host(h, b: np.ndarray, x: np.ndarray, rtol, max_it, prec=MG_FP64):
     st = MgStats()
     rc = load_library().mg_solve_host(h, _host_ptr(b), _host_ptr(x), rtol, max_it, prec, C.byref(st))
@@ -414,6 +435,9 @@ class Hierarchy:
 
     def solve(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_solve(self.handle, b, x, rtol, max_it, prec)
+
+    def solve_profiled(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
+        return mg_solve_profiled(self.handle, b, x, rtol, max_it, prec)
 
     def solve_host(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_solve_host(self.handle, b, x, rtol, max_it, prec)

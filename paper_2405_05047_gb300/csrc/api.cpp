@@ -8,8 +8,11 @@
 // hierarchy; the budget counts every device byte of the context.  Every solve
 // is deterministic (fixed-order reductions, fixed grids), so a request's
 // result does not depend on what else runs.
+#include <cxxabi.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "device.h"
@@ -314,7 +317,10 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
   info->col32_slices = h->col32_slices;
   info->n_hanging = h->n_hanging;
   info->omega = h->L.back().omega;
-  for (int l = 0; l < h->nlev && l < 32; ++l) info->level_omega[l] = h->L[l].omega;
+  for (int l = 0; l < h->nlev && l < 32; ++l) {
+    info->level_omega[l] = h->L[l].omega;
+    info->level_block_values[l] = h->level_block_values[l];
+  }
   return MG_OK;
 }
 
@@ -380,6 +386,59 @@ static int solve_sync(mg_hier* h, const double* b, bool bh, double* x, bool xh, 
     if (rc != MG_PENDING) break;
   }
   CU(cudaGetLastError());
+  return rc;
+}
+
+// "k_smooth<float, float, 1, false, 1>" from the kernel's symbol: demangled,
+// without the return type, namespace and parameter list.
+static void kernel_label(const void* fn, char* out, size_t cap) {
+  const char* mangled = nullptr;
+  std::string name = "?";
+  if (cudaFuncGetName(&mangled, fn) == cudaSuccess && mangled) {
+    int st = 0;
+    char* dem = abi::__cxa_demangle(mangled, nullptr, nullptr, &st);
+    name = (st == 0 && dem) ? dem : mangled;
+    std::free(dem);
+  }
+  const std::string anon = "(anonymous namespace)::";
+  for (size_t p; (p = name.find(anon)) != std::string::npos;) name.erase(p, anon.size());
+  if (name.compare(0, 5, "void ") == 0) name.erase(0, 5);
+  int depth = 0;
+  for (size_t i = 0; i < name.size(); ++i) {   // cut at the parameter list
+    if (name[i] == '<') ++depth;
+    else if (name[i] == '>') --depth;
+    else if (name[i] == '(' && depth == 0) {
+      name.resize(i);
+      break;
+    }
+  }
+  const size_t ns = name.rfind("::", name.find('<'));   // namespace qualifiers
+  if (ns != std::string::npos) name.erase(0, ns + 2);
+  std::snprintf(out, cap, "%s", name.c_str());
+}
+
+int mg_solve_profiled(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats,
+                      mg_prof_entry* entries, int cap, int* n_entries) {
+  if (!h || !n_entries || cap < 0 || (cap > 0 && !entries)) return fail(MG_ERR_INVALID, "bad argument");
+  EventProfiler prof;
+  int rc = prof.init(2 * 4096);
+  if (rc) return rc;
+  LaunchProfiler* prev = t_prof;
+  t_prof = &prof;
+  rc = solve_sync(h, b, false, x, false, rtol, max_it, prec, stats);
+  t_prof = prev;
+  if (rc != MG_OK && rc != MG_ERR_NOT_CONVERGED && rc != MG_ERR_BREAKDOWN && rc != MG_ERR_NAN) return rc;
+  CU(cudaStreamSynchronize(h->ctx->stream));
+  prof.collect_direct();
+  std::vector<std::pair<std::pair<const void*, int>, std::pair<int64_t, double>>> v(prof.acc.begin(), prof.acc.end());
+  std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.second.second > b.second.second; });
+  *n_entries = (int)v.size();
+  for (int i = 0; i < cap && i < (int)v.size(); ++i) {
+    kernel_label(v[i].first.first, entries[i].kernel, sizeof(entries[i].kernel));
+    entries[i].level = v[i].first.second;
+    entries[i].launches = v[i].second.first;
+    entries[i].ms = v[i].second.second;
+  }
   return rc;
 }
 

@@ -78,10 +78,15 @@ __nv_bfloat16 to_vt<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float
 // share a slice (less padding); perm[sell row] = matrix row.  A window is one
 // thread block of the kernels (kBlock rows), so the permuted vector accesses
 // stay within one block's rows.
+// pat6: 3x3 blocks in the velocity-pressure pattern, stored as the 6 values
+// (a, g1, g2, d1, d2, c) of [[a, 0, g1], [0, a, g2], [d1, d2, c]]
+// (block entries 0, 2, 5, 6, 7, 8).
+constexpr int kPat6Entries[6] = {0, 2, 5, 6, 7, 8};
+
 template <typename VT>
 void pack_sell(const BlockCSR& M, int64_t sigma, std::vector<int64_t>& sptr, std::vector<int32_t>& col,
-               std::vector<VT>& val, std::vector<int32_t>& perm) {
-  const int nb = M.nc * M.nc;
+               std::vector<VT>& val, std::vector<int32_t>& perm, bool pat6 = false) {
+  const int nbm = M.nc * M.nc, nb = pat6 ? 6 : nbm;
   const int64_t n = M.n, ns = (n + kSlice - 1) / kSlice;
   perm.clear();
   if (sigma > 0) {
@@ -120,7 +125,9 @@ void pack_sell(const BlockCSR& M, int64_t sigma, std::vector<int64_t>& sptr, std
         const int64_t g = sptr[s] + kSlice * j, o = g + lane;
         if (j < len) {
           col[o] = (int32_t)M.col[M.ptr[q] + j];
-          for (int e = 0; e < nb; ++e) val[g * nb + (int64_t)e * kSlice + lane] = to_vt<VT>(M.val[(M.ptr[q] + j) * nb + e]);
+          const double* blk = &M.val[(M.ptr[q] + j) * nbm];
+          for (int e = 0; e < nb; ++e)
+            val[g * nb + (int64_t)e * kSlice + lane] = to_vt<VT>(blk[pat6 ? kPat6Entries[e] : e]);
         } else {
           col[o] = (int32_t)(q >= 0 ? std::min<int64_t>(q, M.m - 1) : 0);
         }
@@ -149,18 +156,32 @@ void pack_col16(const std::vector<int64_t>& sptr, const std::vector<int32_t>& co
   }
 }
 
+// Every 3x3 block of M has the velocity-pressure pattern (exact zeros at
+// (0,1) and (1,0), equal entries at (0,0) and (1,1)): the 2D Oseen operator,
+// whose two velocity components share one convection-diffusion operator.
+bool velocity_pressure_pattern(const BlockCSR& M) {
+  if (M.nc != 3) return false;
+  const int64_t nb = M.nnzb();
+  for (int64_t k = 0; k < nb; ++k) {
+    const double* b = &M.val[k * 9];
+    if (b[1] != 0.0 || b[3] != 0.0 || b[0] != b[4]) return false;
+  }
+  return true;
+}
+
 // Upload a matrix as SELL-C-sigma in one device allocation (sptr, col,
 // optional 16-bit columns, values, optional permutation; each 256-byte
 // aligned).  sigma: window of the row sort (0: rows in matrix order); idx16:
 // also store 16-bit column offsets.
 template <typename VT>
-int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, bool idx16 = false) {
+int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, bool idx16 = false,
+                bool pat6 = false) {
   std::vector<int64_t> sptr;
   std::vector<int32_t> col;
   std::vector<VT> val;
   std::vector<int32_t> perm;
   std::vector<int16_t> col16;
-  pack_sell<VT>(M, sigma, sptr, col, val, perm);
+  pack_sell<VT>(M, sigma, sptr, col, val, perm, pat6);
   if (idx16) {
     std::vector<int64_t> flagged;
     pack_col16(sptr, col, flagged, col16);
@@ -188,6 +209,7 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, 
   out->v.sptr = out->t.sptr = (const int64_t*)(base + o_sptr);
   out->v.col = out->t.col = (const int32_t*)(base + o_col);
   out->v.val = base + o_val;
+  out->v.bpat = pat6 ? 1 : 0;
   out->t.w = (const float*)(base + o_val);
   out->v.n = out->t.n = M.n;
   out->v.nslices = out->t.nslices = (int64_t)sptr.size() - 1;
@@ -322,7 +344,7 @@ int tail_image(mg_hier* h, int pi, int top, mg_hier::TailImage* out) {
     TailLevel S = T;
     S.A.sptr = (const int64_t*)add(A.v.sptr, (A.v.nslices + 1) * 8);
     S.A.col = (const int32_t*)add(A.v.col, A.slots * 4);
-    S.A.val = add(A.v.val, A.slots * nb * vs);
+    S.A.val = add(A.v.val, A.slots * block_values(A.v, nc) * vs);
     S.S = add(T.S, B.n * nb * ts);
     if (l > 0)
       for (TransferView* V : {&S.P, &S.R}) {
@@ -403,14 +425,16 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     h->level_nodes.push_back(B.n);
     h->level_real_nnzb.push_back(lv.A.nnzb());
     int rc;
+    const bool pat6 = velocity_pressure_pattern(lv.A);
+    h->level_block_values.push_back(pat6 ? 6 : nb);
     if (opts.store_fp64) {
-      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n)))) return rc;
+      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n), false, pat6))) return rc;
       B.S64 = halloc<double>(h, B.n * nb);
       if (!B.S64) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
     }
     if (opts.store_fp32) {
-      if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n)))) return rc;
+      if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6))) return rc;
       B.A32.v.tpr = tpr_for(h, nc, lv.A.n);
       std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
       B.S32 = halloc<float>(h, B.n * nb);
@@ -418,7 +442,8 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
     }
     if (opts.store_bf16) {
-      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n)))) return rc;
+      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6)))
+        return rc;
       B.A16.v.bf16 = 1;
       B.A16.v.tpr = tpr_for(h, nc, lv.A.n);
       if (!B.S32) {
@@ -684,6 +709,11 @@ template <typename T>
 bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const int* done, cudaStream_t s,
                     bool first_done, bool bf16, double* out64, const double* scale) {
   const int nc = h->nc;
+  struct LevelTag {          // launches below belong to level l (per-kernel timing)
+    int prev;
+    explicit LevelTag(int l) : prev(t_prof_level) { t_prof_level = l; }
+    ~LevelTag() { t_prof_level = prev; }
+  } tag(l);
   if (l == 0) {                                                  // Step 0
     launch_coarse<T>(h->coarse_inv, h->coarse_n, b, out, done, s);
     h->launch_count++;
@@ -915,10 +945,14 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
   const SellView& A = h->L[fine].A64.v;
   const int method = w.method, prec = w.prec;
   SolveGraph* g = nullptr;
-  if (h->opts.launch_mode != 1) {
+  // a profiled solve captures its own graph: the cached one must not pick up
+  // the profiler's event nodes
+  EventProfiler* prof = dynamic_cast<EventProfiler*>(t_prof);
+  if (h->opts.launch_mode != 1 && !prof) {
     int rc = get_graph(h, w, method, prec, &g);
     if (rc) return rc;
   }
+  w.graph_round = g != nullptr;
   launch_residual_norm(A, nc, w.xi, w.bi, w.r, w.part, w.st, 1, s);
   w.launches += 1;
   if (method == M_GMRES) {
@@ -934,7 +968,48 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
   } else {
     CU(cudaMemsetAsync(w.q, 0, h->n_dofs * sizeof(double), s));
   }
-  if (h->opts.launch_mode == 1) {
+  if (prof) {
+    // per-kernel timing: one iteration captured as a plain graph (every kernel
+    // between two event-record nodes), run once per iteration, status polled
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    prof->begin_capture();
+    cudaGraph_t g1 = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int64_t before = h->launch_count;
+    if (e == cudaSuccess) {
+      const int lv = t_prof_level;
+      t_prof_level = -2;             // the floor of an interval: an empty kernel
+      launch_prof_empty(cs);
+      t_prof_level = lv;
+      before = h->launch_count;
+      enqueue_iteration(h, w, method, prec, 0ull, cs);
+      e = cudaStreamEndCapture(cs, &g1);
+    }
+    const int64_t per_iter = h->launch_count - before;
+    h->launch_count = before;
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g1, 0);
+    if (g1) cudaGraphDestroy(g1);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("profiled iteration graph: ") + cudaGetErrorString(e));
+    bool ran = false;
+    for (int it = 0; it < w.max_it + 1; ++it) {
+      CU(cudaMemcpyAsync(w.st_host, w.st, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (ran) prof->collect_graph();
+      ran = false;
+      if (w.st_host->done) break;
+      CU(cudaGraphLaunch(ex, s));
+      w.launches += per_iter;
+      ran = true;
+    }
+    if (ran) {
+      CU(cudaStreamSynchronize(s));
+      prof->collect_graph();
+    }
+    cudaGraphExecDestroy(ex);
+  } else if (h->opts.launch_mode == 1) {
     // direct launches (profilers): one iteration at a time, status polled
     const int64_t before = h->launch_count;
     for (int it = 0; it < w.max_it + 1; ++it) {
@@ -961,6 +1036,79 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------ EventProfiler
+int EventProfiler::init(size_t graph_events) {
+  graph_pool.resize(graph_events);
+  for (auto& e : graph_pool) CU(cudaEventCreate(&e));
+  return MG_OK;
+}
+
+void EventProfiler::before(const void* fn, cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  pending = false;
+  if (cap == cudaStreamCaptureStatusActive) {
+    const bool first = graph_recs.empty();
+    if (graph_used + (first ? 2 : 1) > graph_pool.size()) {
+      ++dropped;
+      return;
+    }
+    Rec r{fn, t_prof_level, nullptr, nullptr};
+    if (first) {
+      r.e0 = graph_pool[graph_used++];
+      cudaEventRecordWithFlags(r.e0, s, cudaEventRecordExternal);
+    } else {
+      r.e0 = graph_recs.back().e1;
+    }
+    r.e1 = graph_pool[graph_used++];
+    graph_recs.push_back(r);
+  } else {
+    Rec r{fn, t_prof_level, nullptr, nullptr};
+    if (cudaEventCreate(&r.e0) != cudaSuccess) return;
+    if (cudaEventCreate(&r.e1) != cudaSuccess) {
+      cudaEventDestroy(r.e0);
+      return;
+    }
+    direct_pool.push_back(r.e0);
+    direct_pool.push_back(r.e1);
+    cudaEventRecord(r.e0, s);
+    direct_recs.push_back(r);
+  }
+  pending = true;
+}
+
+void EventProfiler::after(cudaStream_t s) {
+  if (!pending) return;
+  pending = false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(graph_recs.back().e1, s, cudaEventRecordExternal);
+  else cudaEventRecord(direct_recs.back().e1, s);
+}
+
+static void add_recs(std::map<std::pair<const void*, int>, std::pair<int64_t, double>>& acc,
+                     const std::vector<EventProfiler::Rec>& recs) {
+  for (const auto& r : recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) continue;
+    auto& a = acc[{r.fn, r.level}];
+    a.first += 1;
+    a.second += ms;
+  }
+}
+
+void EventProfiler::collect_graph() { add_recs(acc, graph_recs); }
+
+void EventProfiler::collect_direct() {
+  add_recs(acc, direct_recs);
+  direct_recs.clear();
+}
+
+EventProfiler::~EventProfiler() {
+  for (auto e : graph_pool) cudaEventDestroy(e);
+  for (auto e : direct_pool) cudaEventDestroy(e);
+}
 
 int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const double* x0, bool x0_host,
                 double* x_out, bool x_out_host, double rtol, int max_it, int prec, cudaStream_t s) {
@@ -992,9 +1140,10 @@ int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const do
 int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats) {
   const KrylovState& S = *w.st_host;
   const double rel = std::sqrt(S.red[Q_RR]) / S.bnorm;
-  SolveGraph* g = nullptr;
-  for (auto& x : w.graphs)
-    if (x.method == w.method && x.prec == w.prec) g = &x;
+  SolveGraph* g = nullptr;   // the round's device loop ran as this graph (launches counted per iteration)
+  if (w.graph_round)
+    for (auto& x : w.graphs)
+      if (x.method == w.method && x.prec == w.prec) g = &x;
   int status;
   if (S.status == -6) status = MG_ERR_NAN;
   else if (S.status == -5) status = MG_ERR_BREAKDOWN;

@@ -74,8 +74,41 @@ struct Workspace {
   int method = 0, prec = 0, rounds = 0, max_it = 0, iter_base = 0;
   double rtol = 0.0;
   int64_t launches = 0;
+  bool graph_round = false;       // the current round's iterations run as the cached solve graph
   double* x_out = nullptr;
   bool x_out_host = false;
+};
+
+// Per-kernel timing of a solve (mg_solve_profiled).  Launches made while a
+// stream is being captured use a fixed pool of events and are timed as a
+// chain: one event after every kernel (and one before the first), so a
+// kernel's interval runs from the end of the previous kernel to its own end
+// and the intervals add up to the captured iteration.  The graph re-records
+// the same events on every run (collect_graph after each).  Other launches
+// are bracketed by events of their own, read once at the end.  Results are
+// summed per (kernel, multigrid level).
+struct EventProfiler : LaunchProfiler {
+  struct Rec {
+    const void* fn;
+    int level;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<cudaEvent_t> graph_pool, direct_pool;
+  size_t graph_used = 0;
+  std::vector<Rec> graph_recs, direct_recs;
+  bool pending = false;          // the last before() recorded a start event
+  int64_t dropped = 0;           // launches beyond the graph pool
+  std::map<std::pair<const void*, int>, std::pair<int64_t, double>> acc;   // launches, ms
+  int init(size_t graph_events);
+  void before(const void* fn, cudaStream_t s) override;
+  void after(cudaStream_t s) override;
+  void begin_capture() {
+    graph_used = 0;
+    graph_recs.clear();
+  }
+  void collect_graph();          // after the graph's run completed
+  void collect_direct();         // after every direct launch completed
+  ~EventProfiler() override;
 };
 
 int fail(int code, const std::string& msg);
@@ -117,6 +150,7 @@ struct mg_hier {
   mg_opts opts{};
   std::vector<double> coords;            // finest nodes, external order
   std::vector<int64_t> level_nodes, level_nnzb, level_real_nnzb;
+  std::vector<int> level_block_values;   // values stored per slot (nc*nc, or 6: velocity-pressure pattern)
   std::vector<mgi::Alloc> allocs;        // matrices
   size_t bytes = 0;
   std::vector<mgi::LevelMats> L;         // [0] coarsest

@@ -29,7 +29,14 @@ struct SellView {
   // 32, so readers mask sptr with kSptrMask.
   const int16_t* col16 = nullptr;
   int tpr = 1;                // lanes per block row (1 or 4; small FP32/BF16 block levels use 4)
+  // 3x3 blocks of the velocity-pressure pattern [[a, 0, g1], [0, a, g2],
+  // [d1, d2, c]] (both velocity components share one operator, no coupling
+  // between them) are stored as the 6 values (a, g1, g2, d1, d2, c) per slot;
+  // 0: nc x nc values per slot
+  int bpat = 0;
 };
+// values stored per slot of a block matrix
+inline int block_values(const SellView& A, int nc) { return A.bpat ? 6 : nc * nc; }
 constexpr int64_t kSptrMask = ~int64_t(31);
 constexpr int kCol16Window = 256;       // rows per base of the 16-bit column offsets
 
@@ -100,6 +107,17 @@ template <typename T>
 void launch_restrict(const TransferView& R, int nc, const T* r, T* d, const T* Sinv, T* x0, double omega,
                      const int* done, cudaStream_t s);
 void set_pdl(bool on);
+// Launch timing: while a profiler is installed on the calling thread, every
+// kernel launch is bracketed by two CUDA events on its stream and recorded
+// with the multigrid level the caller set (-1 outside a V-cycle).
+struct LaunchProfiler {
+  virtual void before(const void* fn, cudaStream_t s) = 0;
+  virtual void after(cudaStream_t s) = 0;
+  virtual ~LaunchProfiler() = default;
+};
+extern thread_local LaunchProfiler* t_prof;
+extern thread_local int t_prof_level;
+void launch_prof_empty(cudaStream_t s);
 template <typename T>
 void launch_prolong_add(const TransferView& P, int nc, const T* y, const T* xin, T* xo, const int* done,
                         cudaStream_t s);

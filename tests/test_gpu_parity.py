@@ -109,6 +109,17 @@ def test_structure_and_coords(ctx, name):
     assert h.level_nodes() == [lv.mesh.n_nodes for lv in oh.levels]
     assert np.array_equal(h.coords(), oh.fine.mesh.coords)
     assert h.info.n_hanging == int(oh.fine.mesh.hanging.sum())
+    # storage per block: the Oseen blocks [[a, 0, g1], [0, a, g2], [d1, d2, c]]
+    # (the oracle's matrices have that pattern on every level) keep 6 values
+    vals = [h.info.level_block_values[l] for l in range(h.levels)]
+    if name == "oseen":
+        for lv in oh.levels:
+            C = lv.A.tocoo()
+            ru, cu = C.row % 3, C.col % 3
+            assert not np.any(C.data[(ru == 0) & (cu == 1)]) and not np.any(C.data[(ru == 1) & (cu == 0)])
+        assert vals == [6] * h.levels
+    else:
+        assert vals == [prob.nc * prob.nc] * h.levels
 
 
 @pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
@@ -467,6 +478,37 @@ def test_direct_launch_mode_equals_graph(ctx):
         hh.free()
 
 
+@pytest.mark.parametrize("name", ["td_adaptive", "oseen"])
+def test_profiled_solve_equals_solve(ctx, name):
+    """mg_solve_profiled runs the kernels of mg_solve in the same order (one
+    graph per iteration, event nodes between the kernels): the same bits and
+    iterations; every launch of the solve is in its table, and the finest
+    level's sweeps appear with three launches per V-cycle (V(2,2), the first
+    sweep from zero being a kernel of its own)."""
+    lm, prob, oh, h = setup_case(ctx, name)
+    b = dev(system_for(oh, prob).rhs(rhs_for(name, oh.fine.mesh.coords, prob.nc),
+                                     g_for(name, oh.fine.mesh.coords)))
+    x0 = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st0 = h.solve(b, x0, rtol=1e-10, max_it=500, prec=B.MG_MIXED_FP32)
+    x1 = torch.zeros_like(x0)
+    st1, ents = h.solve_profiled(b, x1, rtol=1e-10, max_it=500, prec=B.MG_MIXED_FP32)
+    assert st0.status == 0 and st1.status == 0
+    assert st1.iters == st0.iters and st1.vcycles == st0.vcycles and torch.equal(x0, x1)
+    assert all(e["launches"] > 0 and e["ms"] > 0 for e in ents)
+    assert sum(e["launches"] for e in ents if e["level"] != -2) == st1.launches
+    floor = [e for e in ents if e["level"] == -2]
+    assert len(floor) == 1 and floor[0]["kernel"] == "k_prof_empty"
+    assert [e["ms"] for e in ents] == sorted((e["ms"] for e in ents), reverse=True)
+    fine = h.levels - 1
+    sweeps = [e for e in ents if e["kernel"].startswith("k_smooth<float") and ", false," in e["kernel"]
+              and e["level"] == fine]
+    if h.info.tail_levels < h.levels:        # the finest level is not inside the small-level kernel
+        assert len(sweeps) == 1, [e["kernel"] for e in ents]
+        assert sweeps[0]["launches"] % 3 == 0 and sweeps[0]["launches"] >= 3 * st1.vcycles
+    else:
+        assert any(e["kernel"].startswith("k_tail") for e in ents)
+
+
 @pytest.mark.parametrize("restart", [30, 4])
 @pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
 def test_gmres_matches_direct(ctx, prec, restart):
@@ -491,6 +533,28 @@ def test_gmres_matches_direct(ctx, prec, restart):
     _, info = __import__("oracle.krylov", fromlist=["gmres"]).gmres(oh.fine.A, bref, oh.precondition, rtol=1e-10,
                                                                     restart=restart, maxit=300)
     assert abs(info["iters"] - st.iters) <= max(3, info["iters"] // 3), (info["iters"], st.iters)
+    h.free()
+
+
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+def test_gmres_long_cycle_two_chunks(ctx, prec):
+    """GMRES(40) on the Oseen channel with a weak smoother (V(1,1)): more
+    than 32 Arnoldi steps in one cycle, so the orthogonalisation kernels run
+    their second chunk of 32 basis vectors; the solution matches the direct
+    solve."""
+    lm, prob, oh, _ = setup_case(ctx, "oseen")
+    _, _, pkw, _ = CASES["oseen"]
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(krylov=B.MG_GMRES, restart=40, nu1=1, nu2=1))
+    s = system_for(oh, prob)
+    bref = s.rhs(rhs_for("oseen", oh.fine.mesh.coords, prob.nc), g_for("oseen", oh.fine.mesh.coords))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(dev(bref), x, rtol=1e-11, max_it=400, prec=prec)
+    assert st.status == 0 and st.rel_res <= 1e-11, st.as_dict()
+    assert st.iters > 32, st.iters
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= 1e-8
     h.free()
 
 
