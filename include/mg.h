@@ -161,9 +161,10 @@ typedef struct {
                                   (-1: automatic, 256 on levels of >= 32768
                                   rows; 0: never; > 0: this window on every
                                   level, a multiple of 32)                    */
-  int col16;                   /* 16-bit column offsets in the FP32/BF16 level
-                                  matrices (-1: automatic, levels of >= 32768
-                                  rows; 0: never; 1: every level)            */
+  int col16;                   /* 16-bit column offsets in the level matrices,
+                                  every stored precision (-1: automatic,
+                                  levels of >= 32768 rows; 0: never; 1: every
+                                  level)                                      */
   int row_lanes;               /* lanes per row of the FP32/BF16 level matrices
                                   (-1: automatic, 4 on the small latency-bound
                                   levels; 1: one lane per row everywhere)     */
@@ -186,7 +187,7 @@ typedef struct {
   int64_t col16_slices;                 /* slices read with 16-bit columns        */
   int64_t col32_slices;                 /* slices of those matrices that keep
                                            32-bit columns (offsets outside int16) */
-  int level_col16[32];                  /* 1: the level's FP32/BF16 copy stores
+  int level_col16[32];                  /* 1: the level's operator copies store
                                            16-bit column offsets                 */
   double level_omega[32];               /* smoother damping per level            */
   int level_block_values[32];           /* values stored per block of the level

@@ -229,8 +229,8 @@ T* halloc(mg_hier* h, int64_t n) {
 // more than it saves.
 constexpr int64_t kSigma = kBlock;
 constexpr int64_t kSigmaMinRows = 32768;
-// 16-bit column offsets for the FP32/BF16 copies of the large levels (the
-// streamed bytes per scalar entry drop from 8 to 6).
+// 16-bit column offsets for the level operators of the large levels, every
+// precision (streamed bytes per scalar entry: FP32 8 -> 6, FP64 12 -> 10).
 bool idx16_for(const mg_hier* h, int64_t rows) {
   const int o = h->opts.col16;
   return o >= 0 ? o != 0 : rows >= kSigmaMinRows;
@@ -428,7 +428,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     const bool pat6 = velocity_pressure_pattern(lv.A);
     h->level_block_values.push_back(pat6 ? 6 : nb);
     if (opts.store_fp64) {
-      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n), false, pat6))) return rc;
+      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6))) return rc;
       B.S64 = halloc<double>(h, B.n * nb);
       if (!B.S64) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));

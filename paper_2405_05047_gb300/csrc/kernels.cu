@@ -197,12 +197,16 @@ __device__ __forceinline__ void block_fma_p6(const M& m, T x0, T x1, T x2, T acc
 template <typename T, typename XT>
 __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int lane, const XT* __restrict__ x,
                                           double xs, T acc[3]) {
-  const int64_t s0 = A.sptr[slice] & kSptrMask, s1 = A.sptr[slice + 1] & kSptrMask;
+  const int64_t r0 = A.sptr[slice];
+  const int64_t s0 = r0 & kSptrMask, s1 = A.sptr[slice + 1] & kSptrMask;
   const T* __restrict__ val = (const T*)A.val;
+  const bool narrow = A.col16 && !(r0 & 1);
+  const int base = (int)((slice >> 3) * kCol16Window);
+  auto colat = [&](int64_t o) { return narrow ? base + (int)__ldg(A.col16 + o) : __ldg(A.col + o); };
   acc[0] = acc[1] = acc[2] = T(0);
   if (A.bpat) {
     for (int64_t g = s0; g < s1; g += 32) {
-      const int c = __ldg(A.col + g + lane);
+      const int c = colat(g + lane);
       const T* __restrict__ v = val + g * 6 + lane;
       const T x0 = (T)((double)__ldg(x + 3 * c) * xs), x1 = (T)((double)__ldg(x + 3 * c + 1) * xs),
               x2 = (T)((double)__ldg(x + 3 * c + 2) * xs);
@@ -214,7 +218,7 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
     return;
   }
   for (int64_t g = s0; g < s1; g += 32) {
-    const int c = __ldg(A.col + g + lane);
+    const int c = colat(g + lane);
     const T* __restrict__ v = val + g * 9 + lane;
     const T x0 = (T)((double)__ldg(x + 3 * c) * xs), x1 = (T)((double)__ldg(x + 3 * c + 1) * xs),
             x2 = (T)((double)__ldg(x + 3 * c + 2) * xs);
@@ -1040,7 +1044,7 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_dot(SellView A
     const int lane = (int)(row & 31);
   const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
-      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, p.f) * sc
+      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, p.f, A.col16) * sc
                             : sell_dot1<double>(A, slice, lane, p.d);
       if (row < A.n) {
         out[orow] = ax;
@@ -1189,7 +1193,7 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_2dots(SellView
     const int lane = (int)(row & 31);
   const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
-      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, shv.f) * sc
+      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, shv.f, A.col16) * sc
                             : sell_dot1<double>(A, slice, lane, shv.d);
       if (row < A.n) { t[orow] = ax; a = fma(ax, sv[orow], a); c = fma(ax, ax, c); }
     } else {
@@ -1296,7 +1300,7 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_gm_spmv(SellView A,
     const int lane = (int)(row & 31);
   const int64_t orow = srow<0>(A, row);
     if (NC == 1) {
-      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, z.f)
+      const double ax = F32 ? sell_dot1x<double>(A.sptr, A.col, (const double*)A.val, slice, lane, z.f, A.col16)
                             : sell_dot1<double>(A, slice, lane, z.d);
       if (row < A.n) {
         w[orow] = ax;

@@ -50,13 +50,13 @@ def make(workload):
 
 def alg_bytes(info, level, nc, op, vbytes):
     """Bytes the operator must move once: stored values + column indices of
-    the level matrix (2 bytes where the FP32/BF16 copy stores 16-bit column
-    offsets, else 4; 6 values per 3x3 block where the level stores the
+    the level matrix (2 bytes where the level stores 16-bit column offsets,
+    else 4; 6 values per 3x3 block where the level stores the
     velocity-pressure pattern, else nc*nc), plus its vectors (x, b, S^-1 and
     the output for a sweep)."""
     nnz = info.level_rows_nnzb[level] * info.level_block_values[level]
     rows = info.level_nodes[level] * nc
-    ib = 2 if (vbytes < 8 and info.level_col16[level]) else 4
+    ib = 2 if info.level_col16[level] else 4
     if op == "smooth":
         return nnz * vbytes + info.level_rows_nnzb[level] * ib + rows * vbytes * 3 + info.level_nodes[level] * nc * nc * vbytes
     if op == "matvec":
