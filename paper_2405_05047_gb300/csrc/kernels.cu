@@ -851,6 +851,7 @@ __device__ void converge_step(KrylovState* st, bool count, unsigned long long co
   const double rn = sqrt(st->red[Q_RR]);
   st->rnorm = rn;
   st->scale = rn > 0.0 ? rn : 1.0;
+  st->inv_scale = 1.0 / st->scale;
   int done = 0, status = st->status;
   if (!isfinite(rn)) { done = 1; status = status ? status : -6; }
   else if (status != 0) done = 1;
@@ -958,6 +959,7 @@ __global__ void k_norm_init(int64_t n, int nc, const uint8_t* __restrict__ fix, 
     st->bnorm = st->red[Q_BB] > 0.0 ? sqrt(st->red[Q_BB]) : 1.0;
     st->rtol = rtol; st->max_it = max_it; st->iter = 0; st->done = 0; st->status = 0;
     st->rho = st->rho_prev = st->alpha = st->omega = 1.0; st->beta = 0.0; st->scale = 1.0; st->restart_pos = 0;
+    st->inv_scale = 1.0; st->beta_next = 0.0; st->gm_inv = 0.0;
     st->gm_j = 0; st->gm_end = 0;
   }
 }
@@ -965,7 +967,7 @@ __global__ void k_norm_init(int64_t n, int nc, const uint8_t* __restrict__ fix, 
 __global__ void k_to_f32(int64_t n, const double* __restrict__ v, float* __restrict__ v32, const KrylovState* st) {
   pdl_wait();
   if (st->done) return;
-  const double inv = 1.0 / st->scale;
+  const double inv = st->inv_scale;
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 + 3 < n) {
     const double2 a = *reinterpret_cast<const double2*>(v + i0), b = *reinterpret_cast<const double2*>(v + i0 + 2);
@@ -1000,16 +1002,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_dots(int64_t n, PVec z, const 
   }
   const int qs[2] = {Q_RZ, Q_QZ};
   const double v[2] = {a, c};
-  reduce_partials(part, 2, qs, v, st, sh);
+  // Polak-Ribiere: beta = (z_new, r_new - r_old) / rho_old, r_new - r_old = -alpha q
+  if (reduce_partials(part, 2, qs, v, st, sh) && threadIdx.x == 0)
+    st->beta_next = -st->alpha * st->red[Q_QZ] / st->rho_prev;
 }
 
 __global__ void __launch_bounds__(kBlock) k_cg_update_p(int64_t n, PVec z, double* __restrict__ p, KrylovState* st) {
   pdl_wait();
   if (st->done) return;
-  const double rz = st->red[Q_RZ], qz = st->red[Q_QZ];
+  const double rz = st->red[Q_RZ];
   const bool first = st->iter == st->restart_pos;
-  // Polak-Ribiere: beta = (z_new, r_new - r_old) / rho_old, r_new - r_old = -alpha q
-  const double beta = first ? 0.0 : -st->alpha * qz / st->rho_prev;
+  const double beta = first ? 0.0 : st->beta_next;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
@@ -1063,7 +1066,8 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_dot(SellView A
     }
   }
   const int qs[1] = {qk};
-  reduce_partials(part, 1, qs, &acc, st, sh);
+  // CG: alpha = (r, z) / (p, A p); BiCGStab: alpha = rho / (r^, A p^)
+  if (reduce_partials(part, 1, qs, &acc, st, sh) && threadIdx.x == 0) st->alpha = st->rho / st->red[qk];
 }
 
 // x += alpha p, r -= alpha q, ||r||^2, then (last block) the convergence test
@@ -1078,7 +1082,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_update_xr(int64_t n, const dou
     return;
   }
   const double pq = st->red[Q_PQ];
-  const double alpha = st->rho / pq;
+  const double alpha = st->alpha;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
@@ -1101,7 +1105,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_update_xr(int64_t n, const dou
   }
   const int qs[1] = {Q_RR};
   if (reduce_partials(part, 1, qs, &acc, st, sh) && threadIdx.x == 0) {
-    st->alpha = alpha;
     st->rho_prev = st->rho;
     if (pq == 0.0) st->status = -5;
     converge_step(st, true, cond);
@@ -1117,9 +1120,9 @@ __global__ void __launch_bounds__(kBlock) k_bicg_p(int64_t n, const double* __re
   if (st->done) return;
   const double rho = st->red[Q_RHR];
   const bool first = st->iter == st->restart_pos;
-  const double beta = first ? 0.0 : (rho / st->rho_prev) * (st->alpha / st->omega);
+  const double beta = first ? 0.0 : st->beta_next;   // (rho / rho_prev) (alpha / omega)
   const double om = st->omega;
-  const double inv = 1.0 / st->scale;
+  const double inv = st->inv_scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
     double ri[4], vi[4], pi[4];
@@ -1152,8 +1155,8 @@ __global__ void __launch_bounds__(kBlock) k_bicg_s(int64_t n, const double* __re
   pdl_wait();
   if (st->done) return;
   const double rhv = st->red[Q_RHV];
-  const double alpha = st->rho / rhv;
-  const double inv = 1.0 / st->scale;
+  const double alpha = st->alpha;     // rho / rhv
+  const double inv = st->inv_scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * nthreads) {
     double ri[4], vi[4];
@@ -1172,10 +1175,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_s(int64_t n, const double* __re
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->alpha = alpha;
-    if (rhv == 0.0) st->status = -5;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && rhv == 0.0) st->status = -5;
 }
 
 // t = A sh, partials (t, s) and (t, t)
@@ -1211,7 +1211,10 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 4) k_spmv_2dots(SellView
   }
   const int qs[2] = {Q_TS, Q_TT};
   const double v[2] = {a, c};
-  reduce_partials(part, 2, qs, v, st, sh);
+  if (reduce_partials(part, 2, qs, v, st, sh) && threadIdx.x == 0) {
+    const double ts = st->red[Q_TS], tt = st->red[Q_TT];
+    st->omega = tt > 0.0 ? ts / tt : 0.0;
+  }
 }
 
 // omega = (t,s)/(t,t); x += alpha ph + omega sh; r = s - omega t; (r,r), (rhat,r)
@@ -1225,8 +1228,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_bicg_x(int64_t n, PVec ph, PVec s
     if (blockIdx.x == 0 && threadIdx.x == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
     return;
   }
-  const double ts = st->red[Q_TS], tt = st->red[Q_TT];
-  const double om = tt > 0.0 ? ts / tt : 0.0;
+  const double tt = st->red[Q_TT];
+  const double om = st->omega;        // (t, s) / (t, t)
   const double alpha = st->alpha;
   const double sc = st->scale;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -1255,7 +1258,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bicg_x(int64_t n, PVec ph, PVec s
   const int qs[2] = {Q_RR, Q_RHR};
   const double v[2] = {a, c};
   if (reduce_partials(part, 2, qs, v, st, sh) && threadIdx.x == 0) {
-    st->omega = om;
+    st->beta_next = (st->red[Q_RHR] / st->rho) * (alpha / om);
     st->rho_prev = st->rho;
     if (!(tt > 0.0) || om == 0.0) st->status = -5;
     converge_step(st, true, cond);
@@ -1275,8 +1278,8 @@ __global__ void __launch_bounds__(kBlock) k_gm_start(int64_t n, const double* __
                                                      double* __restrict__ v64, GmresView G, KrylovState* st) {
   pdl_wait();
   if (st->done || st->gm_j != 0) return;
-  const double rn = sqrt(st->red[Q_RR]);
-  const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+  const double rn = st->rnorm;                        // sqrt(red[Q_RR]), set with inv_scale = 1 / rn
+  const double inv = rn > 0.0 ? st->inv_scale : 0.0;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
     const double v = r[i] * inv;
@@ -1418,6 +1421,7 @@ __global__ void k_gm_givens(GmresView G, KrylovState* st) {
   G.cs[j] = c;
   G.sn[j] = sn;
   st->red[Q_TT] = Hc[j + 1];           // h_{j+1,j} before the rotation: norm of the new basis vector
+  st->gm_inv = 1.0 / Hc[j + 1];
   Hc[j] = den;
   Hc[j + 1] = 0.0;
   G.g[j + 1] = -sn * G.g[j];
@@ -1443,7 +1447,7 @@ __global__ void __launch_bounds__(kBlock) k_gm_next(int64_t n, const double* __r
   pdl_wait();
   if (st->done || st->gm_end) return;
   const int j = st->gm_j;
-  const double inv = 1.0 / st->red[Q_TT];
+  const double inv = st->gm_inv;      // 1 / h_{j+1,j}
   double* vn = G.V + (int64_t)(j + 1) * n;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += nthreads) {

@@ -58,6 +58,12 @@ struct TransferView {
 struct KrylovState {
   double rho, rho_prev, alpha, omega, beta;
   double rnorm, bnorm, rtol, scale;  // scale: factor of the FP32 preconditioner input
+  // step scalars formed once by the kernel that finishes their reductions
+  // (GB300 has little FP64 throughput: a division per thread of a vector
+  // kernel costs more than its memory traffic)
+  double inv_scale;                  // 1 / scale
+  double beta_next;                  // BiCGStab: beta of the next iteration
+  double gm_inv;                     // GMRES: 1 / h_{j+1,j}
   int iter, max_it, done, status;
   int restart_pos;
   unsigned int counter;              // arrival counter of the last-block reductions
