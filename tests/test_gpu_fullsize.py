@@ -1,7 +1,8 @@
 """CUDA path against the oracle at the benchmark sizes (GB300 only).
 
 The workloads and launch configuration are the ones bench.py times (graph
-mode, autotuned tail, sorted rows and 16-bit columns on the large levels):
+mode, autotuned tail, sorted rows and 16-bit columns on the large levels, the
+bench's smoothing steps):
 
 * adaptive transport-diffusion, 1,212,011 nodes: the oracle assembles the
   whole finest system; the library's right-hand side equals the oracle's
@@ -22,6 +23,7 @@ itself (||b - A x|| <= 1e-8 ||b_free||, 1 % slack for the summation order).
 import numpy as np
 import pytest
 
+import bench
 import workloads as W
 from oracle import fem
 from oracle import mesh as M
@@ -87,7 +89,7 @@ def test_td_adaptive_fullsize(ctx):
     prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
     pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
     xy = B.mg_mesh_nodes(lm)
-    _check_system(ctx, lm, pb, B.make_opts(krylov=B.MG_BICGSTAB), prob,
+    _check_system(ctx, lm, pb, B.make_opts(krylov=B.MG_BICGSTAB, nu1=bench.NU_TD, nu2=bench.NU_TD), prob,
                   W.f_transport(xy, 1e-3, (1.0, 0.5)), None)
 
 
