@@ -181,21 +181,20 @@ def cpu_baseline(steps=4, rounds=7, rtol=1e-8, threads=1):
 def _cpu_baseline_inproc(steps, rounds, rtol, threads=1):
     from oracle import krylov, mg
     from oracle import problems as PB
-    if True:
-        lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
-        prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    t0 = time.perf_counter()
+    Hh = mg.Hierarchy(lm, prob, nu1=NU_TD, nu2=NU_TD)
+    s = PB.build_system(Hh.fine.mesh, prob)
+    b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
+    t_setup = time.perf_counter() - t0
+    n_free = int((~s.fixed).sum())
+    times, iters = [], []
+    for _ in range(steps):
         t0 = time.perf_counter()
-        Hh = mg.Hierarchy(lm, prob, nu1=NU_TD, nu2=NU_TD)
-        s = PB.build_system(Hh.fine.mesh, prob)
-        b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
-        t_setup = time.perf_counter() - t0
-        n_free = int((~s.fixed).sum())
-        times, iters = [], []
-        for _ in range(steps):
-            t0 = time.perf_counter()
-            x, info = krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=rtol, maxit=500)
-            times.append(time.perf_counter() - t0)
-            iters.append(info["iters"])
+        x, info = krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=rtol, maxit=500)
+        times.append(time.perf_counter() - t0)
+        iters.append(info["iters"])
     t = statistics.mean(times)
     return {"value": n_free / t, "unit": "DoF/s", "cores": threads, "kind": "oracle",
             "sample": f"oracle BiCGStab+V({NU_TD},{NU_TD}) FP64 solve to {rtol:g} of the same TD workload with {rounds} "
@@ -213,19 +212,18 @@ def run_reference(args):
     from oracle import krylov, mg
     from oracle import problems as PB
     rounds = 6
-    if True:
-        lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
-        prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
-        Hh = mg.Hierarchy(lm, prob, nu1=NU_TD, nu2=NU_TD)
-        s = PB.build_system(Hh.fine.mesh, prob)
-        b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
-        n_free = int((~s.fixed).sum())
-        for _ in range(warm):
-            krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
-        dt = (time.perf_counter() - t0) / steps
+    lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    Hh = mg.Hierarchy(lm, prob, nu1=NU_TD, nu2=NU_TD)
+    s = PB.build_system(Hh.fine.mesh, prob)
+    b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
+    n_free = int((~s.fixed).sum())
+    for _ in range(warm):
+        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
+    dt = (time.perf_counter() - t0) / steps
     value = n_free / dt
     sample = (f"oracle BiCGStab+V({NU_TD},{NU_TD}) FP64 solve to 1e-8 of the TD workload with {rounds} refinement rounds "
               f"({n_free} free DoFs), 1 host thread")
@@ -433,11 +431,12 @@ def main():
     x = torch.zeros_like(b)
     flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MB > L2
 
-    def timed_solves(prec, k, warm):
+    def timed_solves(prec, k, warm, hh=None):
+        hh = hh or h
         stats = []
         for _ in range(warm):
             x.zero_()
-            h.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
+            hh.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
         ms = []
         for _ in range(k):
             x.zero_()
@@ -446,7 +445,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = h.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
+            st = hh.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -469,6 +468,19 @@ def main():
     # ablation: BF16-stored matrix values in the FP32 V-cycle
     ms16, st16 = timed_solves(B.MG_MIXED_BF16, max(2, args.steps // 2), 1)
     barrier()
+    # elasticity: FP64 defect correction around the mixed Krylov-MG solve
+    # (rounds that each reduce the recomputed FP64 defect by 1e-4)
+    dc = None
+    if args.workload.startswith("elasticity"):
+        okd = dict(ok)
+        okd["inner_rtol"] = 1e-4
+        hd = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**okd))
+        msd, std = timed_solves(B.MG_MIXED_FP32, max(2, args.steps // 2), 1, hd)
+        dc = {"value": world * n_free / (statistics.mean(msd) * 1e-3), "ms_per_step": statistics.mean(msd),
+              "inner_rtol": 1e-4, "iters": [s.iters for s in std], "rel_res": max(s.rel_res for s in std),
+              "converged": all(s.status == 0 for s in std)}
+        hd.free()
+        barrier()
     value, t_max = whole_job_rate(n_free, args.steps, sum(ms_mixed), world, "cuda")
     assert all(s.status == 0 for s in st_mixed + st64), [s.as_dict() for s in st_mixed + st64]
 
@@ -577,6 +589,7 @@ def main():
                                  "ms_per_step": statistics.mean(ms16), "iters": [s.iters for s in st16],
                                  "rel_res": max(s.rel_res for s in st16),
                                  "converged": all(s.status == 0 for s in st16)},
+        "defect_correction": dc,
         "setup_s": setup_s,
         "gpu_launches": int(sum(s.launches for s in st_mixed)),
         "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": int(2 * 8 * h.n_dofs),
