@@ -188,6 +188,34 @@ def test_vcycle_fp64(ctx, name):
     assert np.abs(z.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
+def test_vcycle_and_solve_with_five_sweeps(ctx):
+    """The V(5,5) cycle of the transport-diffusion bench: the FP64 V-cycle
+    equals the oracle's V(5,5) cycle, and the mixed-precision BiCGStab solve
+    matches the oracle's direct solve."""
+    mk, prob, pkw, okw = CASES["td_adaptive"]
+    lm = mk()
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(krylov=B.MG_BICGSTAB, nu1=5, nu2=5))
+    oh = mg.Hierarchy(lm, prob, nu1=5, nu2=5)
+    rng = np.random.default_rng(15)
+    n = oh.fine.A.shape[0]
+    r = rng.standard_normal(n)
+    r[oh.fine.sys.fixed] = 0.0
+    z = torch.empty(n, device="cuda", dtype=torch.float64)
+    h.vcycle(dev(r), z, B.MG_FP64)
+    ref = oh.precondition(r)
+    assert np.abs(z.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+    s = system_for(oh, prob)
+    bref = s.rhs(rhs_for("td_adaptive", oh.fine.mesh.coords, 1))
+    xstar = s.H @ spl.spsolve(oh.fine.A.tocsc(), bref)
+    x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(dev(bref), x, rtol=1e-10, max_it=200, prec=B.MG_MIXED_FP32)
+    assert st.status == 0 and st.rel_res <= 1e-10, st.as_dict()
+    w = lumped_weights(oh, prob)
+    xg = x.cpu().numpy()
+    assert math.sqrt(np.sum(w * (xg - xstar) ** 2) / np.sum(w * xstar ** 2)) <= 1e-8
+    h.free()
+
+
 def test_vcycle_fp32_close_to_fp64(ctx):
     lm, prob, oh, h = setup_case(ctx, "poisson64")
     rng = np.random.default_rng(6)
@@ -344,15 +372,16 @@ def test_not_converged_status(ctx):
     assert st.status == B.MG_ERR_NOT_CONVERGED and st.iters == 2
 
 
-@pytest.mark.parametrize("name", ["td_adaptive", "elasticity16"])
-def test_tail_kernel_bitwise_equals_level_kernels(ctx, name):
+@pytest.mark.parametrize("name,nu", [("td_adaptive", 2), ("elasticity16", 2), ("td_adaptive", 5)])
+def test_tail_kernel_bitwise_equals_level_kernels(ctx, name, nu):
     """The tail V-cycle runs the same row steps as the grid kernels: identical
     bits without it, with it on a cluster of 1, 2, 4 or 8 CTAs, and on one CTA
     working in shared memory (cluster 0: all vectors staged, matrices staged
-    coarsest first while they fit), in FP64, FP32 and with BF16 values."""
+    coarsest first while they fit), in FP64, FP32 and with BF16 values; with
+    V(2,2) and with the V(5,5) cycle of the transport-diffusion bench."""
     mk, prob, pkw, okw = CASES[name]
     lm = mk()
-    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(autotune=0, store_bf16=1, **okw))
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(autotune=0, store_bf16=1, nu1=nu, nu2=nu, **okw))
     n = h.n_dofs
     rng = np.random.default_rng(9)
     r = rng.standard_normal(n)
