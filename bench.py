@@ -367,6 +367,7 @@ def run_serving(args):
                    "operators_resident": len(hiers), "mean_dofs": float(np.mean(sizes)),
                    "setup_s": setup_s},
         "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "all_converged": base["all_converged"],
+        "lib_p50_ms": base["lib_p50_ms"], "lib_p99_ms": base["lib_p99_ms"],
         "sweep": sweep,
     }))
     for h in hiers.values():
