@@ -969,8 +969,8 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
     CU(cudaMemsetAsync(w.q, 0, h->n_dofs * sizeof(double), s));
   }
   if (prof) {
-    // per-kernel timing: one iteration captured as a plain graph (every kernel
-    // between two event-record nodes), run once per iteration, status polled
+    // per-kernel timing: one iteration captured as a plain graph (an
+    // event-record node after every kernel), run once per iteration, status polled
     cudaStream_t cs;
     CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     prof->begin_capture();
@@ -993,6 +993,10 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
     if (g1) cudaGraphDestroy(g1);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("profiled iteration graph: ") + cudaGetErrorString(e));
+    struct ExecGuard {           // the graph goes on every return path
+      cudaGraphExec_t x;
+      ~ExecGuard() { cudaGraphExecDestroy(x); }
+    } guard{ex};
     bool ran = false;
     for (int it = 0; it < w.max_it + 1; ++it) {
       CU(cudaMemcpyAsync(w.st_host, w.st, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
@@ -1008,7 +1012,6 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
       CU(cudaStreamSynchronize(s));
       prof->collect_graph();
     }
-    cudaGraphExecDestroy(ex);
   } else if (h->opts.launch_mode == 1) {
     // direct launches (profilers): one iteration at a time, status polled
     const int64_t before = h->launch_count;
