@@ -278,13 +278,14 @@ int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, voi
 
 /* Launch shape of the smallest levels: levels with at most tail_rows dofs
  * (and all coarser ones) run as one kernel on a cluster of `cluster` CTAs
- * (1..8), or, for cluster == 0, on one CTA that first copies their vectors
+ * (1..16; sizes above the portable 8 only where the GPU schedules such a
+ * cluster of 1024-thread CTAs), or, for cluster == 0, on one CTA that first copies their vectors
  * and, coarsest first, as many of their matrices as fit into 200 KB of
  * shared memory (the threshold is lowered until the vectors fit).
  * tail_rows < 0: time V-cycles of precision prec over a set of thresholds and
  * launch shapes and keep the fastest (what opts.autotune does at setup).
  * Results are bitwise identical for every choice.  Errors: MG_ERR_INVALID
- * (cluster outside 0..8, unknown precision), MG_ERR_OOM (the shared-memory
+ * (cluster outside 0..16 or not schedulable, unknown precision), MG_ERR_OOM (the shared-memory
  * image of the tail could not be allocated). */
 int mg_tune(mg_hier* h, int prec, int tail_rows, int cluster);
 

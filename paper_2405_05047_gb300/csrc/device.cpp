@@ -635,7 +635,8 @@ void ws_destroy(mg_hier* h, Workspace* w) {
 
 int set_tail(mg_hier* h, int rows, int cluster) {
   int top = tail_top_for(h, rows);
-  cluster = std::max(0, std::min(cluster, 8));
+  cluster = std::max(0, std::min(cluster, 16));
+  if (!tail_cluster_fits(cluster)) return fail(MG_ERR_INVALID, "tail cluster size not schedulable on this GPU");
   if (cluster == 0) {
     top = staged_top_cap(h, top);
     for (int pi = 0; pi < 3 && top > 0; ++pi) {
@@ -653,7 +654,7 @@ int set_tail(mg_hier* h, int rows, int cluster) {
 }
 
 int autotune(mg_hier* h, int prec) {
-  std::vector<int64_t> key = {h->dim, h->nc, prec};
+  std::vector<int64_t> key = {h->dim, h->nc, prec, h->opts.nu1, h->opts.nu2};
   for (const LevelMats& L : h->L) key.push_back(L.n);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -666,7 +667,7 @@ int autotune(mg_hier* h, int prec) {
   cudaStream_t s = h->ctx->stream;
   const int fine = h->nlev - 1;
   const int rows_c[] = {0, 256, 1024, 4096, 16384, 65536};
-  const int cl_c[] = {1, 0, 2, 4, 8};   // 0: one CTA in shared memory
+  const int cl_c[] = {1, 0, 2, 4, 8, 16};   // 0: one CTA in shared memory
   double best = 1e30;
   int best_rows = 0, best_cl = 1, last_top = -1;
   for (int rows : rows_c) {
@@ -675,6 +676,7 @@ int autotune(mg_hier* h, int prec) {
     last_top = top;
     for (int cl : cl_c) {
       if (top == 0 && cl != 1) break;
+      if (!tail_cluster_fits(cl)) continue;
       int rc = set_tail(h, rows, cl);
       if (rc) return rc;
       auto once = [&]() {

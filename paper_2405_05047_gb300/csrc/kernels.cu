@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 
 #include <algorithm>
@@ -1688,6 +1689,11 @@ void launch_tail_k(cudaLaunchConfig_t& cfg, const TailParams& P, const T* b, T* 
     std::call_once(once, [] {
       cudaFuncSetAttribute(k_tail<T, V, NC, TLM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
     });
+  } else {
+    static std::once_flag once;   // clusters of up to 16 CTAs (beyond the portable 8)
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(k_tail<T, V, NC, TLM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    });
   }
   launch_ex(cfg, k_tail<T, V, NC, TLM>, P, b, out, fd, done, o64, scale);
 }
@@ -1742,6 +1748,36 @@ void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_don
 }
 template void launch_tail<double>(const TailParams&, int, const double*, double*, bool, const int*, cudaStream_t,
                                   double*, const double*);
+
+// Whether this GPU schedules a cluster of `cl` tail CTAs (kTailThreads each):
+// sizes above 8 are not portable and need that many SMs free in one GPC.
+bool tail_cluster_fits(int cl) {
+  if (cl <= 8) return true;
+  static std::mutex mu;
+  static std::map<int, bool> known;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find(cl);
+  if (it != known.end()) return it->second;
+  const void* fn = (const void*)k_tail<float, float, 1, 1>;
+  bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl);
+    cfg.blockDim = dim3(kTailThreads);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    ok = cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0;
+  }
+  cudaGetLastError();   // a refused query leaves no sticky error
+  known[cl] = ok;
+  return ok;
+}
 template void launch_tail<float>(const TailParams&, int, const float*, float*, bool, const int*, cudaStream_t,
                                  double*, const double*);
 

@@ -163,6 +163,8 @@ struct TailParams {
   uint32_t staged_mask = 0;
 };
 constexpr uint32_t kTailSmemMax = 200 * 1024;   // dynamic shared memory of the staged tail
+// true when the GPU schedules a cluster of cl tail CTAs (always for cl <= 8)
+bool tail_cluster_fits(int cl);
 template <typename T>
 // o64 (optional): FP64 copy of the output times *scale, written by the last
 // post-smoothing sweep (nothing when nu2 == 0)

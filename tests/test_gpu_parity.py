@@ -375,7 +375,8 @@ def test_not_converged_status(ctx):
 @pytest.mark.parametrize("name,nu", [("td_adaptive", 2), ("elasticity16", 2), ("td_adaptive", 5)])
 def test_tail_kernel_bitwise_equals_level_kernels(ctx, name, nu):
     """The tail V-cycle runs the same row steps as the grid kernels: identical
-    bits without it, with it on a cluster of 1, 2, 4 or 8 CTAs, and on one CTA
+    bits without it, with it on a cluster of 1, 2, 4, 8 or 16 CTAs (16 where
+    the GPU schedules it), and on one CTA
     working in shared memory (cluster 0: all vectors staged, matrices staged
     coarsest first while they fit), in FP64, FP32 and with BF16 values; with
     V(2,2) and with the V(5,5) cycle of the transport-diffusion bench."""
@@ -388,12 +389,16 @@ def test_tail_kernel_bitwise_equals_level_kernels(ctx, name, nu):
     oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
     r[oh.fine.sys.fixed] = 0.0
     shapes = ((0, 1), (1 << 20, 1), (1 << 20, 2), (1 << 20, 4), (1 << 20, 8), (1024, 4),
-              (1 << 20, 0), (4096, 0), (256, 0))
+              (1 << 20, 0), (4096, 0), (256, 0), (1 << 20, 16), (4096, 16))
     for prec, dt in ((B.MG_FP64, torch.float64), (B.MG_MIXED_FP32, torch.float32),
                      (B.MG_MIXED_BF16, torch.float32)):
         outs, staged_levels = [], []
         for rows, cl in shapes:
-            h.tune(prec, rows, cl)
+            try:
+                h.tune(prec, rows, cl)
+            except G.MGError:
+                assert cl > 8            # only the non-portable cluster size may be refused
+                continue
             if cl == 0:
                 staged_levels.append(h.info.tail_levels)
             z = torch.empty(n, device="cuda", dtype=dt)
@@ -404,7 +409,7 @@ def test_tail_kernel_bitwise_equals_level_kernels(ctx, name, nu):
         assert max(staged_levels) >= 2      # the shared-memory tail really ran
     # the autotuner picks one of these shapes and the solve still matches
     h.tune(B.MG_MIXED_FP32, -1)
-    assert 0 <= h.info.tail_cluster <= 8
+    assert 0 <= h.info.tail_cluster <= 16
     h.free()
 
 
