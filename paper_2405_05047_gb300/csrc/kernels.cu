@@ -59,20 +59,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// Sum of the first n partials of one quantity, identical in every block;
-// result broadcast to all threads.
-__device__ __forceinline__ double sum_partials(const double* part, int n, double* sh) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
-  double t = block_sum(v, sh);
-  __syncthreads();
-  if (threadIdx.x == 0) sh[32] = t;
-  __syncthreads();
-  double r = sh[32];
-  __syncthreads();
-  return r;
-}
-
 // Vector loads: through the read-only path where the vector is constant for
 // the kernel's lifetime, plain (coherent) loads in the single-CTA tail kernel
 // that rewrites its vectors between __syncthreads().
