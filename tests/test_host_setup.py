@@ -74,6 +74,28 @@ def test_host_hierarchy_oseen_matches_oracle(rounds):
     assert close(hh.matrix(hh.levels - 1, HV.LIFT), Lo, 1e-12)
 
 
+@pytest.mark.parametrize("rounds", [2, 6])
+def test_oseen_level_blocks_have_velocity_pressure_pattern(rounds):
+    """Every 3x3 block of every Oseen level operator the setup builds is
+    [[a, 0, g1], [0, a, g2], [d1, d2, c]] exactly (the two velocity
+    components share one operator and do not couple): the condition under
+    which the library stores 6 values per block.  Elasticity blocks are not."""
+    lm = W.oseen_channel(1, rounds)
+    beta = W.oseen_beta(B.mg_mesh_nodes(lm))
+    hh = HV.HostHierarchy(lm, B.make_problem(kind=B.MG_OSEEN, conv=beta, dirichlet=(0xD, 0xD, 0x0), nu=1e-3,
+                                             dt=0.01))
+    for l in range(hh.levels):
+        A = hh.matrix(l, HV.A).tocsr()
+        C = A.tocoo()
+        ru, cu = C.row % 3, C.col % 3
+        assert not np.any(C.data[(ru == 0) & (cu == 1)]) and not np.any(C.data[(ru == 1) & (cu == 0)])
+        assert (A[0::3, 0::3] != A[1::3, 1::3]).nnz == 0
+    he = HV.HostHierarchy(W.uniform_leaves(3, (1, 1, 1), 2),
+                          B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)))
+    C = he.matrix(he.levels - 1, HV.A).tocoo()
+    assert np.any(C.data[(C.row % 3 == 0) & (C.col % 3 == 1)])
+
+
 def test_oseen_rejects_non_patch_mesh():
     lm = W.oseen_channel(1, 0)
     lm = W.refine(lm, np.arange(lm.n_leaves) == 5)       # one leaf refined alone: its family is incomplete
