@@ -357,13 +357,15 @@ def test_vcycle_contraction_mesh_independent():
     assert max(rates) < 0.2 and max(rates) / min(rates) < 2.0, rates
 
 
-def test_vcycle_symmetric():
+@pytest.mark.parametrize("nu", [2, 5])
+def test_vcycle_symmetric(nu):
     """With R = P^T, nu1 = nu2 and a symmetric smoother the V-cycle is a
-    symmetric operator: (M r1, r2) = (r1, M r2)."""
+    symmetric operator: (M r1, r2) = (r1, M r2); a wrong sweep count on one
+    side or a missing transpose breaks it."""
     for lm, prob, om in ((W.uniform_leaves(2, (1, 1), 5), PB.Problem(PB.POISSON), 0.8),
                          (W.uniform_leaves(3, (1, 1, 1), 3),
                           PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), 0.5)):
-        Hh = mg.Hierarchy(lm, prob, omega=om)
+        Hh = mg.Hierarchy(lm, prob, omega=om, nu1=nu, nu2=nu)
         rng = np.random.default_rng(3)
         r1, r2 = rng.standard_normal((2, Hh.fine.A.shape[0]))
         r1[Hh.fine.sys.fixed] = 0
