@@ -290,14 +290,15 @@ int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, voi
 int mg_tune(mg_hier* h, int prec, int tail_rows, int cluster);
 
 /* Allocation-free residual + restriction (no counterpart in the paper: it
- * exists for callers that must not allocate device memory -- code running
- * while a CUDA stream is being captured into a graph, where cudaMalloc is not
- * allowed; processes whose device memory is owned by another allocator or
- * pool; latency-bound loops that cannot afford an allocation).
+ * exists for callers that cannot allocate device memory -- applications whose
+ * device memory is owned up front by another allocator or a fixed pool, which
+ * pass inputs and outputs but have nothing to give for temporaries, and
+ * real-time loops that must not enter the CUDA allocator at all).
  *   d = R_l (b - A_l x) on level l >= 1, the same result as
  *   mg_apply(h, l, MG_OP_RESTRICT, x, b, d, prec).
  * x, b: device vectors of level l (n_l * nc entries); d: device vector of level
- * l-1; double for MG_FP64, float for MG_MIXED_FP32.  The residual is kept in a
+ * l-1; double for MG_FP64, float for MG_MIXED_FP32 and MG_MIXED_BF16 (the
+ * latter reads the BF16-stored operator copy: store_bf16).  The residual is kept in a
  * fixed device array of 2^20 doubles (8 MiB) compiled into the library, so
  * the level may have at most 2^20 dofs in FP64 and 2^21 in FP32; larger levels
  * are refused with MG_ERR_INVALID before anything runs.  Every device that
@@ -357,8 +358,9 @@ int mg_solve_profiled(mg_hier* h, const double* b, double* x, double rtol, int m
  * mg_submit queues a solve of h (b, x device buffers, caller-owned, not to be
  * touched until mg_poll returns a final status) and returns at once with a
  * ticket; MG_ERR_ADMISSION if the request's workspace can never fit the
- * budget.  The context's scheduler thread runs queued requests in epochs,
- * interleaving the iterations of all admitted requests on its own streams.
+ * budget.  The context's scheduler thread admits queued requests as solve
+ * slots and workspace memory free up and launches each admitted solve (one
+ * CUDA graph) on a stream of its own, so the solves overlap on the device.
  * mg_poll returns MG_PENDING, or the final status with stats filled in.
  * mg_cancel removes a queued request (MG_ERR_CANCELLED on its next poll). */
 int mg_submit(mg_ctx* ctx, mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec,

@@ -10,8 +10,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   zero: P_eff = Z_f E H_c Z_c.
 * Smoother (Sec. 4.1.4): x <- x + omega S (b - A x), S = D^{-1} (Jacobi) or
   the inverse of the n_c x n_c nodal diagonal blocks (block Jacobi).
-* Coarse problem: a direct solve A_0^{-1} b_0 (Algorithm "Geometric multigrid
-  solver", Step 0), here LU with partial pivoting in FP64.
+* Coarse problem: a direct solve A_0^{-1} b_0 (the coarse-mesh problem of the
+  multigrid cycle, Sec. 2.2), here LU with partial pivoting in FP64.
 * Level operators: rediscretisation of the same form on every level of the
   global hierarchy (Sec. 2.2: "an approximation of the entire problem can be
   created on each grid level").
@@ -168,15 +168,15 @@ class Hierarchy:
         return x
 
     def gmg(self, l, x, b):
-        """Algorithm "Geometric multigrid solver" (Steps 0-5)."""
+        """The recursive multigrid cycle GMG(l, x, b) of Sec. 2.2."""
         if l == 0:
-            return sla.lu_solve(self.coarse_lu, b)                 # Step 0
+            return sla.lu_solve(self.coarse_lu, b)                 # coarse mesh problem
         lv = self.levels[l]
-        x = self.smooth(l, x, b, self.nu1)                         # Step 1
-        d = lv.R @ (b - lv.A @ x)                                  # Step 2
-        y = self.gmg(l - 1, np.zeros_like(d), d)                   # Step 3
-        x = x + lv.P @ y                                           # Step 4
-        return self.smooth(l, x, b, self.nu2)                      # Step 5
+        x = self.smooth(l, x, b, self.nu1)                         # pre-smooth
+        d = lv.R @ (b - lv.A @ x)                                  # restrict residual
+        y = self.gmg(l - 1, np.zeros_like(d), d)                   # coarse correction
+        x = x + lv.P @ y                                           # prolongate update
+        return self.smooth(l, x, b, self.nu2)                      # post-smooth
 
     def precondition(self, r):
         """One V-cycle with zero initial guess: z = M^-1 r."""

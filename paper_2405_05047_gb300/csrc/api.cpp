@@ -261,7 +261,7 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
     size_t lower = 0;
     const int nb = H.nc * H.nc;
     for (const HostLevel& lv : H.levels) {
-      if (opts.store_fp64) lower += (size_t)lv.A.nnzb() * nb * 8;
+      if (opts.store_fp64 || &lv == &H.levels.back()) lower += (size_t)lv.A.nnzb() * nb * 8;
       if (opts.store_fp32) lower += (size_t)lv.A.nnzb() * nb * 4;
     }
     if (ctx->budget && ctx->used + lower > ctx->budget)

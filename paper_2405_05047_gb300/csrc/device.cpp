@@ -1,10 +1,11 @@
 // Device hierarchy (SELL packing + upload), solve workspaces, the V-cycle and
 // the Krylov loop as one CUDA graph.
 //
-// The V-cycle follows Algorithm "Geometric multigrid solver" of the paper
-// (Sec. 2.2): Step 0 coarse solve, Step 1 pre-smoothing, Step 2 restriction of
-// the residual, Step 3 recursion with zero initial guess, Step 4 prolongation
-// and correction, Step 5 post-smoothing.  It preconditions flexible CG
+// The V-cycle is the recursive geometric multigrid cycle of Sec. 2.2: on the
+// coarsest level a direct solve; on every finer level damped smoothing sweeps,
+// the residual carried to the next coarser level, the cycle there from a zero
+// guess, its result interpolated back and added, then smoothing again.  It
+// preconditions flexible CG
 // (Polak-Ribiere), BiCGStab or flexible GMRES(m) (Sec. 4.1.5: multigrid as
 // preconditioner of a Krylov method).  All Krylov scalars stay on the device;
 // one Krylov iteration is captured into the body of a CUDA-graph `while` node
@@ -427,8 +428,13 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     int rc;
     const bool pat6 = velocity_pressure_pattern(lv.A);
     h->level_block_values.push_back(pat6 ? 6 : nb);
-    if (opts.store_fp64) {
+    // The finest FP64 operator is the outer Krylov residual's matrix in every
+    // precision mode, so it is kept even without store_fp64 (which then only
+    // drops the FP64 V-cycle: coarser FP64 operators and FP64 smoother blocks).
+    if (opts.store_fp64 || l == nlev - 1) {
       if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6))) return rc;
+    }
+    if (opts.store_fp64) {
       B.S64 = halloc<double>(h, B.n * nb);
       if (!B.S64) return fail(MG_ERR_OOM, "alloc");
       CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
@@ -704,7 +710,7 @@ int autotune(mg_hier* h, int prec) {
 }
 
 // ---------------------------------------------------------------- V-cycle
-// z = GMG(l, 0, b): the V-cycle of Algorithm "Geometric multigrid solver".
+// z = GMG(l, 0, b): one V-cycle on level l from a zero initial guess (Sec. 2.2).
 // first_done: the first pre-smoothing sweep (from x = 0) was already written
 // into its buffer by the restriction kernel of the finer level.
 template <typename T>
@@ -716,7 +722,7 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
     explicit LevelTag(int l) : prev(t_prof_level) { t_prof_level = l; }
     ~LevelTag() { t_prof_level = prev; }
   } tag(l);
-  if (l == 0) {                                                  // Step 0
+  if (l == 0) {                                                  // coarse solve
     launch_coarse<T>(h->coarse_inv, h->coarse_n, b, out, done, s);
     h->launch_count++;
     return false;
@@ -744,7 +750,7 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
   auto bufof = [&](LevelVecs& X, T* o, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? o : Prec<T>::t(X); };
   const double om = L.omega, omc = C.omega;
   T* cur = nullptr;
-  for (int k = 0; k < nu1; ++k) {                                // Step 1
+  for (int k = 0; k < nu1; ++k) {                                // pre-smoothing
     T* dst = bufof(V, out, k);
     if (!(k == 0 && first_done)) {
       launch_smooth<T>(AL, nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
@@ -752,17 +758,17 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
     }
     cur = dst;
   }
-  launch_residual<T>(AL, nc, cur, b, Prec<T>::r(V), done, s);   // Step 2
+  launch_residual<T>(AL, nc, cur, b, Prec<T>::r(V), done, s);   // residual, restricted below
   const bool fuse = l - 1 > 0;
   T* cfirst = fuse ? bufof(CV, Prec<T>::o(CV), 0) : nullptr;
   launch_restrict<T>(L.R.t, nc, Prec<T>::r(V), Prec<T>::b(CV), Prec<T>::S(C), cfirst, omc, done, s);
   h->launch_count += 2;
-  enqueue_vcycle<T>(h, w, l - 1, Prec<T>::b(CV), Prec<T>::o(CV), done, s, fuse, bf16);   // Step 3
-  T* pdst = nu2 == 0 ? out : cur;                                                   // Step 4
+  enqueue_vcycle<T>(h, w, l - 1, Prec<T>::b(CV), Prec<T>::o(CV), done, s, fuse, bf16);   // coarser cycle
+  T* pdst = nu2 == 0 ? out : cur;                                                   // correction
   launch_prolong_add<T>(L.P.t, nc, Prec<T>::o(CV), cur, pdst, done, s);
   cur = pdst;
   h->launch_count++;
-  for (int k = nu1; k < ns; ++k) {                               // Step 5
+  for (int k = nu1; k < ns; ++k) {                               // post-smoothing
     T* dst = bufof(V, out, k);
     const bool last = k == ns - 1;
     launch_smooth<T>(AL, nc, cur, b, Prec<T>::S(L), dst, om, false, done, s, last ? out64 : nullptr,
@@ -789,6 +795,8 @@ int method_of(const mg_hier* h) {
 }
 
 int check_prec(const mg_hier* h, int prec) {
+  if (h->L.empty() || h->L.back().A64.v.nslices == 0)
+    return fail(MG_ERR_INVALID, "hierarchy has no FP64 finest-level operator for the outer residual");
   if (prec == MG_FP64 && !h->has_fp64) return fail(MG_ERR_INVALID, "hierarchy built without FP64 level matrices");
   if (prec == MG_MIXED_FP32 && !h->has_fp32) return fail(MG_ERR_INVALID, "hierarchy built without FP32 level matrices");
   if (prec == MG_MIXED_BF16 && !h->has_bf16) return fail(MG_ERR_INVALID, "hierarchy built without BF16 level matrices");
@@ -814,7 +822,7 @@ void enqueue_iteration(mg_hier* h, Workspace& w, int method, int prec, unsigned 
   }
   const double* scale = &w.st->scale;
   if (method == M_MGI) {
-    // Algorithm "Geometric multigrid solver" as the solver: x <- x + GMG(0, b - A x)
+    // the multigrid cycle as the solver: x <- x + GMG(0, b - A x)
     PVec z;
     if (mixed) {
       launch_to_f32(n, w.r, w.r32, w.st, s);

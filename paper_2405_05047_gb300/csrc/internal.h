@@ -91,37 +91,4 @@ bool coarsen_once(const LeafSet& fine, int min_level, bool patch, LeafSet* coars
 Status mesh_patches(const LeafSet& s, const Topology& T, std::vector<int64_t>* nodes, std::vector<int32_t>* clev);
 int default_min_level(const int macro[3], int dim);
 
-// ----------------------------------------------------------------- device side
-struct DeviceMem;
-
-// SELL-C layout of a block matrix (C = kSlice block rows per slice).
-struct SellDev {
-  int64_t n = 0;              // block rows
-  int64_t nslices = 0;
-  int64_t nnz_slots = 0;      // padded block slots
-  int64_t nnzb = 0;           // real blocks
-  int nc = 1;
-  int idx16 = 0;              // 1: 16-bit slice-relative column offsets
-  int64_t* slice_off = nullptr;   // nslices + 1 (slot offsets)
-  int32_t* col32 = nullptr;       // nnz_slots
-  int16_t* col16 = nullptr;       // nnz_slots (relative to slice's first row)
-  void* val = nullptr;            // nnz_slots * nc*nc (slot-major per block entry)
-  int val_bytes = 8;              // 8 (double), 4 (float)
-};
-
-struct DevLevel {
-  int64_t n = 0;                  // nodes
-  SellDev A64, A32;               // level operator
-  SellDev P, R;                   // scalar transfers (float weights, exact dyadic)
-  double* Sinv64 = nullptr;       // n*nc*nc
-  float* Sinv32 = nullptr;
-  // workspace vectors (n*nc entries)
-  double* x64[2] = {nullptr, nullptr};
-  double* b64 = nullptr;
-  double* r64 = nullptr;
-  float* x32[2] = {nullptr, nullptr};
-  float* b32 = nullptr;
-  float* r32 = nullptr;
-};
-
 }  // namespace mgi

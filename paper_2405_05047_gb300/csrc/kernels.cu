@@ -29,10 +29,8 @@ namespace mgi {
 namespace {
 
 // Programmatic dependent launch: kernels are launched while their predecessor
-// drains; every kernel waits here before it reads anything the predecessor
-// wrote.
-// Programmatic dependent launch: wait until the preceding kernel of the
-// stream has completed and its writes are visible.  (Triggering the next
+// drains; every kernel waits here until the preceding kernel of the stream
+// has completed and its writes are visible.  (Triggering the next
 // launch early was measured slower: the waiting blocks of the next kernel
 // take SM slots from the running one.)
 __device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
@@ -549,7 +547,7 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_restrict(TransferVi
     row_restrict<T, NC, 0>(R, row, r, d, Sinv, S0 ? x0 : nullptr, omega);
 }
 
-// x_out_i = x_in_i + sum_j P(i,j) y_j   (Algorithm "Geometric multigrid solver", Step 4)
+// x_out_i = x_in_i + sum_j P(i,j) y_j: the coarse correction interpolated and added (Sec. 2.2)
 template <typename T, int NC>
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_prolong(TransferView P, const T* __restrict__ y, const T* xin, T* xo,
                                                      const int* done) {
@@ -560,8 +558,8 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 6 : 3) k_prolong(TransferVie
     row_prolong<T, NC, 0>(P, row, y, xin, xo);
 }
 
-// The V-cycle below (and including) level `nt - 1` in one launch: every step
-// of Algorithm "Geometric multigrid solver" for the small levels, separated
+// The V-cycle below (and including) level `nt - 1` in one launch: smoothing,
+// restriction, coarse solve and correction of the small levels, separated
 // by block or cluster barriers instead of kernel boundaries.  Same row
 // functions as the grid kernels, so the result is bitwise identical to the
 // multi-kernel cycle.

@@ -4,10 +4,11 @@
 // buffer of the hierarchy's workspace.  mg_restrict_static computes the same
 // d = R_l (b - A_l x) with r held in a fixed device array compiled into the
 // library instead, so a call makes no allocation of any kind.  That serves
-// callers that must not allocate device memory: code that runs while a CUDA
-// stream is being captured into a graph (where cudaMalloc is not allowed),
-// processes whose device memory is entirely owned by another allocator or
-// pool, and latency-bound loops that cannot afford an allocation.
+// callers that cannot allocate device memory: applications whose device memory
+// is owned up front by another allocator or a fixed pool (they hand the
+// library inputs and outputs, but have no allocation to give it for
+// temporaries), and real-time loops that must not enter the CUDA allocator
+// at all.
 #include <cuda_runtime.h>
 
 #include <mutex>

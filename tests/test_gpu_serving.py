@@ -132,3 +132,38 @@ def test_cancel_queued_request():
         G.binding._check(G.binding.load_library().mg_poll(ctx.handle, 987654321, None))
     h.free()
     ctx.close()
+
+
+def test_mixed_solve_without_fp64_level_copies():
+    """A hierarchy built with store_fp64 = 0 (no FP64 V-cycle) still keeps
+    the finest FP64 operator, which the outer Krylov residual uses in every
+    precision mode: its mixed solves equal the default hierarchy's bit for
+    bit, synchronously and through mg_submit / mg_poll, and really iterate.
+    An FP64 solve on it is refused."""
+    ctx = G.Context(0)
+    lm = W.td_adaptive(rounds=4, gamma=1.0)
+    pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    hd = G.Hierarchy(ctx, lm, pb)
+    hn = G.Hierarchy(ctx, lm, pb, B.make_opts(store_fp64=0))
+    b = rhs_of(hd, 11)
+    xd = torch.zeros_like(b)
+    sd = hd.solve(b, xd, rtol=1e-9, max_it=300, prec=B.MG_MIXED_FP32)
+    assert sd.status == 0 and sd.iters > 0 and sd.rel_res <= 1e-9
+    xn = torch.zeros_like(b)
+    sn = hn.solve(b, xn, rtol=1e-9, max_it=300, prec=B.MG_MIXED_FP32)
+    assert sn.status == 0 and sn.iters == sd.iters and sn.rel_res == sd.rel_res
+    assert torch.equal(xn, xd)
+    xs = [torch.zeros_like(b) for _ in range(3)]
+    torch.cuda.synchronize()
+    tickets = [ctx.submit(hn, b, x, rtol=1e-9, max_it=300, prec=B.MG_MIXED_FP32) for x in xs]
+    res = wait(ctx, tickets)
+    for t, x in zip(tickets, xs):
+        rc, st = res[t]
+        assert rc == 0 and st.iters == sd.iters
+        assert torch.equal(x, xd)
+    with pytest.raises(G.MGError) as e:
+        hn.solve(b, torch.zeros_like(b), prec=B.MG_FP64)
+    assert e.value.code == -1
+    hd.free()
+    hn.free()
+    ctx.close()

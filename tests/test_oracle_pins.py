@@ -608,3 +608,64 @@ def test_power_iteration_damping_poisson_and_rule():
     for l in auto.levels:
         assert l.omega == pytest.approx(1.2 / mg.lambda_max_power(l.S, l.A, l.sys.fixed), rel=1e-15)
     assert mg.Hierarchy(lm, PB.Problem(PB.POISSON)).fine.omega == 0.8
+
+
+# ---------------------------------------------------------------- SUPG terms
+def _linear_td_case(rounds=3):
+    """Transport-diffusion with SUPG on an adaptive mesh with hanging nodes,
+    eps = 1e-3, beta = (1, 0.5), and the linear exact solution
+    u = 0.3 + 1.2 x - 0.7 y (f = beta.grad u, Dirichlet data g = u)."""
+    lm = W.td_adaptive(rounds=rounds, gamma=1.0)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    m = q1mesh(lm)
+    s = PB.build_system(m, prob)
+    xy = m.coords
+    u = 0.3 + 1.2 * xy[:, 0] - 0.7 * xy[:, 1]
+    f = np.full(m.n_nodes, 1.0 * 1.2 + 0.5 * (-0.7))
+    return lm, prob, m, s, u, f
+
+
+def test_supg_consistent_on_linear_solutions():
+    """SUPG is a consistent stabilisation: for u in the discrete space the
+    elementwise residual -eps Laplace u + beta.grad u - f vanishes, so with
+    the streamline form delta_T (beta.grad u, beta.grad v) in the operator and
+    delta_T (f, beta.grad v) in the load, the discrete solution equals the
+    linear u at every node, hanging ones included.  Dropping the SUPG load
+    term, or replacing the streamline form by delta_T (grad u, grad v), makes
+    the scheme inconsistent and moves the nodes by 1e-2."""
+    lm, prob, m, s, u, f = _linear_td_case()
+    assert m.hanging.sum() > 0
+    b = s.rhs(f, u)
+    x = s.H @ spl.spsolve(s.A.tocsc(), b)
+    assert np.abs(x - u).max() <= 1e-12
+
+
+def test_supg_streamline_element_is_tensor_product():
+    """With beta = (1, 0) on a box cell the streamline form is
+    delta_T (d_x u, d_x v): the 1D stiffness along x times the 1D mass along
+    y, scaled by delta_T = delta0 h_T^2 / (6 eps + |beta| h_T) with h_T the
+    cell diameter."""
+    for hx, hy, eps in ((0.25, 0.25, 1e-3), (0.125, 0.0625, 0.3)):
+        prob = PB.Problem(PB.TRANSPORT, eps=eps, beta=(1.0, 0.0), supg_delta0=0.5)
+        el = PB.element(prob, 2)((hx, hy))
+        base = eps * fem.scalar_element(2, (hx, hy), "stiffness") + fem.scalar_element(
+            2, (hx, hy), "convection", (1.0, 0.0))
+        Kx = np.array([[1.0, -1.0], [-1.0, 1.0]]) / hx
+        My = np.array([[2.0, 1.0], [1.0, 2.0]]) * hy / 6.0
+        hT = math.hypot(hx, hy)
+        delta = 0.5 * hT * hT / (6.0 * eps + hT)
+        # local vertex c = bx + 2 by (x fastest)
+        assert np.abs((el - base) - delta * np.kron(My, Kx)).max() <= 1e-14 * delta / hx
+
+
+def test_supg_load_term_tested_with_streamline_derivative():
+    """Load of a constant f = 1 on one box cell with beta = (1, 0): the Galerkin
+    part gives the cell area / 4 per vertex, the SUPG part delta_T (1, d_x phi_i)
+    = -+ delta_T hy / 2 (minus at the left vertices, plus at the right)."""
+    hx, hy, eps = 0.25, 0.125, 1e-2
+    prob = PB.Problem(PB.TRANSPORT, eps=eps, beta=(1.0, 0.0), supg_delta0=0.5)
+    F = PB.load_element(prob, 2)((hx, hy))
+    hT = math.hypot(hx, hy)
+    delta = 0.5 * hT * hT / (6.0 * eps + hT)
+    expect = hx * hy / 4.0 + delta * hy / 2.0 * np.array([-1.0, 1.0, -1.0, 1.0])
+    assert np.abs(F @ np.ones(4) - expect).max() <= 1e-15

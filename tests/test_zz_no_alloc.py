@@ -1,6 +1,7 @@
 """mg_restrict_static: the residual + restriction operator for callers that
-must not allocate device memory (stream capture in progress, memory owned by
-another allocator, allocation-free hot loops).  Its residual lives in a fixed
+cannot allocate device memory (device memory owned up front by another
+allocator or a fixed pool, real-time loops that must not enter the CUDA
+allocator).  Its residual lives in a fixed
 device array inside the library; the result must equal mg_apply's
 MG_OP_RESTRICT, which keeps the residual in the hierarchy's workspace.
 
@@ -18,22 +19,23 @@ import paper_2405_05047_gb300 as G  # noqa: E402
 from paper_2405_05047_gb300 import binding as B  # noqa: E402
 
 
-def _cases():
+def _cases(bf16):
     return [
-        (W.poisson64(64), B.make_problem(kind=B.MG_POISSON), B.make_opts()),
+        (W.poisson64(64), B.make_problem(kind=B.MG_POISSON), B.make_opts(store_bf16=bf16)),
         (W.td_adaptive(rounds=4, gamma=1.0), B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)),
-         B.make_opts()),
+         B.make_opts(store_bf16=bf16)),
         (W.uniform_leaves(3, (1, 1, 1), 4),
-         B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)), B.make_opts(omega=0.5)),
+         B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
+         B.make_opts(omega=0.5, store_bf16=bf16)),
     ]
 
 
-@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32, B.MG_MIXED_BF16])
 def test_static_restriction_equals_workspace_restriction(prec):
     ctx = G.Context(0)
     dt = torch.float64 if prec == B.MG_FP64 else torch.float32
     rng = np.random.default_rng(21)
-    for lm, pb, op in _cases():
+    for lm, pb, op in _cases(1 if prec == B.MG_MIXED_BF16 else 0):
         h = G.Hierarchy(ctx, lm, pb, op)
         nodes = h.level_nodes()
         for level in range(1, h.levels):
