@@ -20,6 +20,8 @@ GPU acceleration", arXiv:2405.05047):
                 x <- x + omega S (b - A x) (Sec. 4.1.4), the direct coarse solve
                 and the V-cycle of Algorithm "Geometric multigrid solver".
 * ``krylov``    CG, BiCGStab and restarted GMRES (Sec. 4.1.5, Saad 2003).
+* ``timestep``  backward-Euler steps of the time-dependent transport-diffusion
+                problem (Sec. 5.1; Algorithm "Nonstationary Linear Problem").
 
 Every function states the passage it follows.  Pins (tests that tie this
 code to facts other than itself) live in ``tests/test_oracle_*.py``.

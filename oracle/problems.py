@@ -41,6 +41,7 @@ class Problem:
     dt: float = 0.01                    # Oseen: time step of the mass term
     lps_alpha0: float = 0.5             # Oseen: LPS parameter
     conv: object = None                 # Oseen: nodal beta (n_nodes, 2) on the finest mesh
+    mass: float = 0.0                   # Poisson/transport: coefficient s of s (u, v)
 
     @property
     def nc(self):
@@ -52,17 +53,29 @@ class Problem:
 
 
 def element(prob: Problem, dim: int):
-    """Function h -> element matrix of the problem's bilinear form."""
+    """Function h -> element matrix of the problem's bilinear form.
+
+    A mass coefficient s = prob.mass > 0 adds s (u, v): with s = 1/dt this is
+    the matrix of one backward-Euler step of the time-dependent problem
+    (Sec. 5.1, Eq. "condif_a").  With SUPG the stabilisation tests the whole
+    residual, so the mass part also enters it: delta_T s (u, beta.grad v)_T."""
+    s = float(prob.mass)
     if prob.kind == POISSON:
-        return lambda h: fem.scalar_element(dim, h, "stiffness")
+        if s == 0.0:
+            return lambda h: fem.scalar_element(dim, h, "stiffness")
+        return lambda h: fem.scalar_element(dim, h, "stiffness") + s * fem.scalar_element(dim, h, "mass")
     if prob.kind == TRANSPORT:
         beta = np.asarray(prob.beta[:dim], dtype=np.float64)
 
         def el(h):
             d = fem.supg_delta(h, prob.eps, beta, prob.supg_delta0)
-            return (prob.eps * fem.scalar_element(dim, h, "stiffness")
-                    + fem.scalar_element(dim, h, "convection", beta)
-                    + d * fem.scalar_element(dim, h, "streamline", beta))
+            K = (prob.eps * fem.scalar_element(dim, h, "stiffness")
+                 + fem.scalar_element(dim, h, "convection", beta)
+                 + d * fem.scalar_element(dim, h, "streamline", beta))
+            if s != 0.0:
+                K = K + s * (fem.scalar_element(dim, h, "mass")
+                             + d * fem.scalar_element(dim, h, "convection", beta).T)
+            return K
         return el
     if prob.kind == ELASTICITY:
         assert dim == 3

@@ -1,0 +1,89 @@
+"""Pins of the backward-Euler transport-diffusion oracle (the paper's Sec. 5.1
+problem) against facts other than itself: exactness on solutions that are
+linear in space and time (hanging nodes, with and without SUPG), first-order
+convergence in dt to the paper's manufactured solution, the mass term, and
+the source term against finite differences of the exact solution."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mesh as M
+from oracle import problems as PB
+from oracle import timestep as TS
+
+
+def q1mesh(lm):
+    return M.Q1Mesh(lm.dim, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+
+
+@pytest.mark.parametrize("supg", [0.0, 0.5])
+def test_backward_euler_exact_for_linear_space_time_solutions(supg):
+    """theta = a + c.x + d t lies in the discrete space at every step and
+    backward Euler differentiates it exactly in time, so the discrete
+    solution equals it at every node after every step: f = d + beta.grad theta,
+    Dirichlet data theta(t_n).  With SUPG the stabilisation must test the
+    whole residual, the mass part included."""
+    lm = W.td_adaptive(rounds=3, gamma=1.0, base_level=4)
+    m = q1mesh(lm)
+    assert m.hanging.sum() > 0
+    beta = (1.0, 0.5)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=beta, supg_delta0=supg)
+    a, c, d = 0.3, (1.2, -0.7), 0.9
+    xy = m.coords
+    lin = lambda t: a + c[0] * xy[:, 0] + c[1] * xy[:, 1] + d * t   # noqa: E731
+    f = d + beta[0] * c[0] + beta[1] * c[1]
+    dt = 0.1
+    _, thetas = TS.run(m, prob, dt, lin(0.0), lambda t: np.full(m.n_nodes, f), lin, 5)
+    for n, th in enumerate(thetas, 1):
+        assert np.abs(th - lin(n * dt)).max() <= 1e-12
+
+
+def test_time_stepping_converges_first_order_in_dt():
+    """The paper's problem (lambda = 0.01, b = (0, -1)) against its exact
+    solution at T = 0.16 on a 32 x 32 mesh: backward Euler is first order,
+    so halving dt halves the error (the Q1 space error of this smooth
+    solution, about 2e-5, stays far below the time error)."""
+    m = q1mesh(W.td_uniform(32))
+    xy = m.coords
+    prob = PB.Problem(PB.TRANSPORT, eps=W.TD_LAMBDA, beta=W.TD_B, supg_delta0=0.0)
+    T = 0.16
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        _, th = TS.run(m, prob, dt, W.td_theta(0.0, xy), lambda t: W.td_source(t, xy),
+                       lambda t: W.td_theta(t, xy), int(round(T / dt)))
+        errs.append(np.abs(th[-1] - W.td_theta(T, xy)).max())
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.abs(ratios - 2.0) < 0.15), (errs, ratios)
+
+
+def test_source_term_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    xy = rng.uniform(0.1, 0.9, size=(20, 2))
+    e = 1e-4
+    for t in (0.0, 0.37, 1.5):
+        dth = (W.td_theta(t + e, xy) - W.td_theta(t - e, xy)) / (2 * e)
+        gx = (W.td_theta(t, xy + [e, 0]) - W.td_theta(t, xy - [e, 0])) / (2 * e)
+        gy = (W.td_theta(t, xy + [0, e]) - W.td_theta(t, xy - [0, e])) / (2 * e)
+        lap = sum((W.td_theta(t, xy + s) - 2 * W.td_theta(t, xy) + W.td_theta(t, xy - s)) / e ** 2
+                  for s in ([e, 0], [0, e]))
+        f = dth - W.TD_LAMBDA * lap + W.TD_B[0] * gx + W.TD_B[1] * gy
+        assert np.abs(f - W.td_source(t, xy)).max() <= 1e-6
+
+
+def test_mass_term_adds_scaled_mass_matrix():
+    """The step matrix minus the stationary one is s M (no SUPG), with M the
+    pinned Q1 mass matrix: an interior row of s M has (s h^2 / 36) {16, 4, 1}."""
+    m = q1mesh(W.td_uniform(8))
+    s = 50.0
+    p0 = PB.Problem(PB.TRANSPORT, eps=0.01, beta=(0.0, -1.0), supg_delta0=0.0)
+    A0 = PB.build_system(m, p0, with_load=False).A_raw
+    A1 = PB.build_system(m, TS.step_problem(p0, 1.0 / s), with_load=False).A_raw
+    D = (A1 - A0).tocsr()
+    h = 1.0 / 8
+    i = int(np.nonzero((m.X[:, 0] == 4) & (m.X[:, 1] == 4))[0][0])
+    row = D.getrow(i)
+    for j, v in zip(row.indices, row.data):
+        dist = int(np.abs(m.X[j] - m.X[i]).sum())
+        assert v == pytest.approx(s * {0: 16, 1: 4, 2: 1}[dist] * h * h / 36, rel=1e-13)

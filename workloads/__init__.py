@@ -287,3 +287,42 @@ def stream_coeffs(seed: int = MASTER_SEED, modes: int = 4) -> np.ndarray:
     """a_mn ~ N(0,1), m,n = 1..modes, for the seeded stream function."""
     rng = np.random.Generator(np.random.PCG64([seed, 7]))
     return rng.standard_normal((modes, modes))
+
+
+# ---------------------------------------------------------------------------
+# time-dependent transport-diffusion (the paper's Sec. 5.1 example)
+# ---------------------------------------------------------------------------
+TD_LAMBDA = 0.01            # diffusion
+TD_B = (0.0, -1.0)          # transport direction
+TD_DT = 0.02                # backward-Euler step
+TD_STEPS = 100              # T = 2
+
+
+def td_m(t: float, z: np.ndarray) -> np.ndarray:
+    return 0.5 + 0.25 * math.cos(0.5 * math.pi * t) - z
+
+
+def td_theta(t: float, xy: np.ndarray) -> np.ndarray:
+    """theta_ex(t, x, y) = exp(-(m(t,x)^2 + m(t,y)^2) / 4)."""
+    mx, my = td_m(t, xy[:, 0]), td_m(t, xy[:, 1])
+    return np.exp(-0.25 * (mx * mx + my * my))
+
+
+def td_source(t: float, xy: np.ndarray, lam: float = TD_LAMBDA, b=TD_B) -> np.ndarray:
+    """f = d_t theta - lam Laplace theta + b.grad theta for theta_ex: with
+    Q = m_x^2 + m_y^2, d_z m = -1 and d_t m = -(pi/8) sin(pi t / 2),
+    d_t theta = -theta (m_x + m_y) d_t m / 2, grad theta = theta (m_x, m_y) / 2,
+    Laplace theta = theta (Q / 4 - 1)."""
+    mx, my = td_m(t, xy[:, 0]), td_m(t, xy[:, 1])
+    th = np.exp(-0.25 * (mx * mx + my * my))
+    mdot = -0.125 * math.pi * math.sin(0.5 * math.pi * t)
+    q = mx * mx + my * my
+    return th * (-0.5 * (mx + my) * mdot - lam * (0.25 * q - 1.0) + 0.5 * (b[0] * mx + b[1] * my))
+
+
+def td_uniform(n: int) -> LeafMesh:
+    """Uniform n x n mesh of the unit square for the time-dependent problem
+    (n = 2^7 .. 2^10 in the paper's study: 16,641 .. 1,050,625 DoFs)."""
+    m = uniform_leaves(2, (1, 1), int(round(math.log2(n))))
+    m.meta.update(workload=f"td_timedep_{n}x{n}")
+    return m
