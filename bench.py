@@ -169,6 +169,91 @@ def measured_peaks():
 ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
+def start_oracle_child(outdir, steps=2, rtol=1e-8, procs=8):
+    """The oracle on the headline workload itself, in a child process started
+    before this process touches the GPU (it runs on the host cores while the
+    GPU is measured).  It writes oracle.json (CPU baseline: one thread, then
+    `procs` concurrent single-thread solves) and the FP64 reference solution
+    to rtol 1e-12 with the lumped-mass weights (xref.npy, w.npy) to outdir."""
+    env = dict(os.environ, **ONE_THREAD)
+    code = f"import bench; bench._oracle_child({outdir!r}, {steps}, {rtol}, {procs})"
+    log = open(os.path.join(outdir, "oracle.log"), "w")
+    return subprocess.Popen([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=log, stderr=subprocess.STDOUT)
+
+
+def _oracle_system(rounds=8):
+    """Oracle hierarchy, finest system and right-hand side of the adaptive TD
+    workload (setup, not timed)."""
+    from oracle import fem, mg
+    from oracle import problems as PB
+    lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    Hh = mg.Hierarchy(lm, prob, nu1=NU_TD, nu2=NU_TD)
+    S = Hh.fine.sys
+    S.F = fem.assemble(Hh.fine.mesh, PB.load_element(prob, 2), 1)
+    b = S.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
+    return Hh, S, b
+
+
+def _oracle_child(outdir, steps, rtol, procs):
+    import multiprocessing as mp
+    from oracle import krylov
+    t0 = time.perf_counter()
+    Hh, S, b = _oracle_system()
+    t_setup = time.perf_counter() - t0
+    n_free = int((~S.fixed).sum())
+    times, iters = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        _, info = krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=rtol, maxit=500)
+        times.append(time.perf_counter() - t0)
+        iters.append(info["iters"])
+    t1 = statistics.mean(times)
+    out = {"value": n_free / t1, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+           "sample": f"oracle (numpy/scipy FP64) BiCGStab+V({NU_TD},{NU_TD}) solve to {rtol:g} of the headline TD "
+                     f"workload itself ({n_free} free DoFs, {len(Hh.levels)} levels), mean of {steps} solves, one "
+                     f"host thread, setup {t_setup:.0f} s untimed",
+           "iters": iters, "sec_per_solve": t1}
+
+    # `procs` concurrent single-thread solves (forked after setup; no GPU in this process)
+    def one(q):
+        t = time.perf_counter()
+        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=rtol, maxit=500)
+        q.put(time.perf_counter() - t)
+    try:
+        ctx = mp.get_context("fork")
+        q = ctx.Queue()
+        t0 = time.perf_counter()
+        ps = [ctx.Process(target=one, args=(q,)) for _ in range(procs)]
+        for p in ps:
+            p.start()
+        walls = [q.get(timeout=900) for _ in ps]
+        for p in ps:
+            p.join()
+        span = time.perf_counter() - t0
+        out["concurrent"] = {"cores": procs, "value": procs * n_free / span, "unit": "DoF/s",
+                             "sample": f"{procs} single-thread oracle solves of the same system at once "
+                                       f"(forked processes, {os.cpu_count()} host cores); value = {procs} x free "
+                                       f"DoFs / wall time of all",
+                             "sec_per_solve_max": max(walls)}
+    except Exception as e:          # reported, never required
+        out["concurrent"] = {"error": str(e)}
+    t0 = time.perf_counter()
+    xref, info = krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-12, maxit=500)
+    xall = S.H @ xref
+    np.save(os.path.join(outdir, "xref.npy"), xall)
+    np.save(os.path.join(outdir, "w.npy"), np.asarray(S.F.sum(axis=1)).ravel())
+    out["reference_solve"] = {"rtol": 1e-12, "true_rel": info["true_rel"], "sec": time.perf_counter() - t0}
+    with open(os.path.join(outdir, "oracle.json"), "w") as f:
+        json.dump(out, f)
+
+
+def rel_err(x, xref, w):
+    """Relative lumped-mass-weighted L2 error ||x - xref||_M / ||xref||_M."""
+    e = np.asarray(x, dtype=np.float64) - xref
+    return float(np.sqrt(np.sum(w * e * e) / np.sum(w * xref * xref)))
+
+
 def cpu_baseline(steps=4, rounds=7, rtol=1e-8, threads=1):
     """The oracle (numpy/scipy FP64, as it stands) on a bounded sample of the
     same workload (the adaptive TD mesh with `rounds` refinement rounds), run
@@ -380,258 +465,243 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="td_adaptive")
-    ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--requests", type=int, default=1000, help="serving: requests per stream")
-    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
-    ap.add_argument("--slots", type=int, default=16, help="serving: solves in flight")
-    ap.add_argument("--sweep", type=float, nargs="*", default=[10.0, 100.0], help="serving: rate multipliers")
-    ap.add_argument("--launch", default="graph", choices=["graph", "direct"],
-                    help="direct: per-kernel launches (for profilers that cannot see inside graphs)")
-    ap.add_argument("--tail", default=None,
-                    help="ROWS,CLUSTER: fixed tail shape instead of the setup autotuner (profiling runs, "
-                         "where the autotuner's timings would be distorted)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "serving":
-        return run_serving(args)
+class Solver:
+    """One resident hierarchy of a workload with its right-hand side, timed
+    through mg_solve (CUDA events on the library's stream, L2 flushed before
+    every timed solve)."""
 
-    import torch
-    import torch.distributed as dist
-    import paper_2405_05047_gb300 as G
-    from paper_2405_05047_gb300 import binding as B
-    from paper_2405_05047_gb300 import build as BLD
+    def __init__(self, G, B, ctx, name, flush, launch="graph", tail=None):
+        import torch
+        self.B, self.ctx, self.flush, self.name = B, ctx, flush, name
+        lm, pk, ok, ffun, desc, gfun = workload(name)
+        self.lm, self.pk, self.ok, self.desc = lm, pk, dict(ok), desc
+        ok["launch_mode"] = 1 if launch == "direct" else 0
+        ok["store_bf16"] = 1
+        if tail:
+            ok["autotune"] = 0
+        t0 = time.perf_counter()
+        self.h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
+        if tail:
+            rows, cl = (int(v) for v in tail.split(","))
+            for p in (B.MG_MIXED_FP32, B.MG_FP64, B.MG_MIXED_BF16):
+                self.h.tune(p, rows, cl)
+        self.setup_s = time.perf_counter() - t0
+        self.info = self.h.info
+        self.coords = self.h.coords()
+        self.f_host = np.ascontiguousarray(ffun(self.coords), dtype=np.float64)
+        self.g_host = None if gfun is None else np.ascontiguousarray(gfun(self.coords), dtype=np.float64).ravel()
+        f = torch.from_numpy(self.f_host).cuda()
+        self.b = torch.empty(self.h.n_dofs, device="cuda", dtype=torch.float64)
+        g = None if self.g_host is None else torch.from_numpy(self.g_host).cuda()
+        self.h.assemble_rhs(f, self.b, g)
+        self.x = torch.zeros_like(self.b)
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    BLD.build()
-    torch.cuda.set_device(local)
-
-    lm, pk, ok, ffun, desc, gfun = workload(args.workload)
-    ctx = G.Context(local)
-    stream = ctx.stream
-    t0 = time.perf_counter()
-    ok["launch_mode"] = 1 if args.launch == "direct" else 0
-    ok["store_bf16"] = 1
-    if args.tail:
-        ok["autotune"] = 0
-    h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**ok))
-    if args.tail:
-        rows, cl = (int(v) for v in args.tail.split(","))
-        for p in (B.MG_MIXED_FP32, B.MG_FP64, B.MG_MIXED_BF16):
-            h.tune(p, rows, cl)
-    setup_s = time.perf_counter() - t0
-    info = h.info
-    # kernels launched by setup (autotuner V-cycles): a profiler skips these to reach the solves
-    print(f"launches after setup: {h.launch_count()}", file=sys.stderr, flush=True)
-    n_free = info.n_free
-    coords = h.coords()
-    f = torch.from_numpy(np.ascontiguousarray(ffun(coords), dtype=np.float64)).cuda()
-    b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
-    g = None
-    if gfun is not None:
-        g = torch.from_numpy(np.ascontiguousarray(gfun(coords), dtype=np.float64).ravel()).cuda()
-    h.assemble_rhs(f, b, g)
-    x = torch.zeros_like(b)
-    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MB > L2
-
-    def timed_solves(prec, k, warm, hh=None):
-        hh = hh or h
-        stats = []
+    def timed(self, prec, k, warm, rtol, hh=None):
+        import torch
+        hh = hh or self.h
+        stats, ms = [], []
         for _ in range(warm):
-            x.zero_()
-            hh.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
-        ms = []
+            self.x.zero_()
+            hh.solve(self.b, self.x, rtol=rtol, max_it=500, prec=prec)
         for _ in range(k):
-            x.zero_()
-            flush_l2(flush)
+            self.x.zero_()
+            flush_l2(self.flush)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = hh.solve(b, x, rtol=args.rtol, max_it=500, prec=prec)
-            e1.record(stream)
+            e0.record(self.ctx.stream)
+            st = hh.solve(self.b, self.x, rtol=rtol, max_it=500, prec=prec)
+            e1.record(self.ctx.stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
             stats.append(st)
-        return ms, stats
+        return ms, stats, self.x.cpu().numpy()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+    def profile(self, prec, k, rtol, iters_expected=None):
+        """Per-kernel device time inside k solves (mg_solve_profiled), summed
+        per (kernel, level); returns (table, floor_ms per interval)."""
+        import torch
+        prof = {}
+        for _ in range(k):
+            self.x.zero_()
+            flush_l2(self.flush)
+            torch.cuda.synchronize()
+            st_p, ents = self.h.solve_profiled(self.b, self.x, rtol=rtol, max_it=500, prec=prec)
+            assert st_p.status == 0, st_p.as_dict()
+            if iters_expected is not None:
+                assert st_p.iters == iters_expected, (st_p.iters, iters_expected)
+            for e in ents:
+                a = prof.setdefault((e["kernel"], e["level"]), [0, 0.0])
+                a[0] += e["launches"]
+                a[1] += e["ms"]
+        floor_n, floor_ms = prof.pop(("k_prof_empty", -2), [1, 0.0])
+        return prof, floor_ms / floor_n
 
-    barrier()
-    with ClockSampler(local) as clk:
-        barrier()
-        ms_mixed, st_mixed = timed_solves(B.MG_MIXED_FP32, args.steps, args.warmup)
-        barrier()
-    # FP64 path of the same fused kernels (reported beside the value)
-    ms64, st64 = timed_solves(B.MG_FP64, max(2, args.steps // 2), 1)
-    barrier()
-    # ablation: BF16-stored matrix values in the FP32 V-cycle
-    ms16, st16 = timed_solves(B.MG_MIXED_BF16, max(2, args.steps // 2), 1)
-    barrier()
-    # elasticity: FP64 defect correction around the mixed Krylov-MG solve
-    # (rounds that each reduce the recomputed FP64 defect by 1e-4)
-    dc = None
-    if args.workload.startswith("elasticity"):
-        okd = dict(ok)
-        okd["inner_rtol"] = 1e-4
-        hd = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(**okd))
-        msd, std = timed_solves(B.MG_MIXED_FP32, max(2, args.steps // 2), 1, hd)
-        dc = {"value": world * n_free / (statistics.mean(msd) * 1e-3), "ms_per_step": statistics.mean(msd),
-              "inner_rtol": 1e-4, "iters": [s.iters for s in std], "rel_res": max(s.rel_res for s in std),
-              "converged": all(s.status == 0 for s in std)}
+    def smoother_roofline(self, prof, floor_ms, peak):
+        """Roofline of the finest-level fused FP32 smoother sweep (a2 / a3):
+        algorithmic bytes per launch / its mean interval inside the solve."""
+        from paper_2405_05047_gb300 import opbench
+        fine = self.h.levels - 1
+        total = sum(v[1] for v in prof.values())
+        cand = [kv for kv in prof.items() if kv[0][0].startswith("k_smooth<float") and ", false," in kv[0][0]
+                and kv[0][1] == fine]
+        (name, _), (n, ms) = max(cand, key=lambda kv: kv[1][1])
+        alg = opbench.alg_bytes(self.info, fine, self.h.nc, "smooth", 4)
+        ach = alg / (ms / n * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": f"{name} on the finest level", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "alg_bytes_per_launch": int(alg), "ms_per_launch": ms / n,
+                "launches_timed": int(n), "share_of_solve": ms / total, "interval_floor_ms": floor_ms}
+
+    def free(self):
+        self.h.free()
+
+
+def top_table(prof, k=12):
+    total = sum(v[1] for v in prof.values())
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1][1])
+    return [{"kernel": kk, "level": l, "launches": n, "ms": round(t, 4), "share": round(t / total, 4)}
+            for (kk, l), (n, t) in ranked[:k]]
+
+
+def oracle_reference(name, coords_check=None):
+    """The oracle's FP64 solution of a (small) workload by sparse LU, with the
+    lumped-mass weights: (x_all, w)."""
+    import scipy.sparse.linalg as spl
+    from oracle import mesh as M
+    from oracle import problems as PB
+    lm, pk, _, ffun, _, gfun = workload(name)
+    from paper_2405_05047_gb300 import binding as B
+    kind = {B.MG_POISSON: PB.POISSON, B.MG_TRANSPORT: PB.TRANSPORT, B.MG_ELASTICITY: PB.ELASTICITY,
+            B.MG_OSEEN: PB.OSEEN}[pk["kind"]]
+    kw = {k: v for k, v in pk.items() if k in ("eps", "beta", "mu", "nu", "dt", "conv")}
+    if "lam" in pk:
+        kw["lam"] = pk["lam"]
+    if "dirichlet" in pk:
+        kw["dirichlet"] = pk["dirichlet"]
+    prob = PB.Problem(kind, **kw)
+    m = M.Q1Mesh(lm.dim, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+    if coords_check is not None:
+        assert np.array_equal(m.coords, coords_check)
+    S = PB.build_system(m, prob, beta=prob.conv)
+    g = None if gfun is None else gfun(m.coords).ravel()
+    x = S.H @ spl.spsolve(S.A.tocsc(), S.rhs(ffun(m.coords), g))
+    w = np.repeat(np.asarray(S.F.sum(axis=1)).ravel(), prob.nc)
+    return x, w
+
+
+def err_on_sample(G, B, ctx, name, flush, rtol=1e-10):
+    """Error of both GPU paths against the oracle's direct solve on a smaller
+    instance of the same workload (the full-size system does not fit the
+    oracle's direct solver): relative lumped-mass L2 at rtol 1e-10."""
+    sv = Solver(G, B, ctx, name, flush)
+    xref, w = oracle_reference(name, sv.coords)
+    out = {"workload": name, "n_free_dofs": int(sv.info.n_free), "rtol": rtol}
+    for key, prec in (("mixed", B.MG_MIXED_FP32), ("fp64", B.MG_FP64)):
+        _, st, x = sv.timed(prec, 1, 0, rtol)
+        out[key] = {"err": rel_err(x, xref, w), "rel_res": st[0].rel_res, "iters": st[0].iters}
+    sv.free()
+    return out
+
+
+def measure_config(G, B, ctx, name, flush, peak, steps=3, rtol=1e-8, err_sample=None):
+    """Compact record of one more configuration: both precisions, the BF16
+    ablation, the in-solve roofline of the finest smoother sweep and the error
+    against the oracle (on the full size where the oracle's direct solve fits,
+    else on `err_sample`, a smaller instance of the same workload)."""
+    sv = Solver(G, B, ctx, name, flush)
+    n_free = int(sv.info.n_free)
+    ms32, st32, x32 = sv.timed(B.MG_MIXED_FP32, steps, 1, rtol)
+    ms64, st64, x64 = sv.timed(B.MG_FP64, max(2, steps - 1), 1, rtol)
+    ms16, st16, _ = sv.timed(B.MG_MIXED_BF16, 2, 1, rtol)
+    prof, floor = sv.profile(B.MG_MIXED_FP32, 1, rtol, st32[0].iters)
+    rec = {"description": sv.desc, "n_nodes": int(sv.info.n_nodes), "n_free_dofs": n_free,
+           "levels": int(sv.info.levels), "setup_s": sv.setup_s,
+           "value": n_free / (statistics.mean(ms32) * 1e-3), "unit": "DoF/s", "ms_per_step": statistics.mean(ms32),
+           "iters": [s.iters for s in st32], "rel_res": max(s.rel_res for s in st32),
+           "converged": all(s.status == 0 for s in st32 + st64),
+           "fp64": {"value": n_free / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
+                    "iters": [s.iters for s in st64], "rel_res": max(s.rel_res for s in st64)},
+           "speedup_mixed_vs_fp64": statistics.mean(ms64) / statistics.mean(ms32),
+           "bf16_values_ablation": {"value": n_free / (statistics.mean(ms16) * 1e-3),
+                                    "ms_per_step": statistics.mean(ms16), "iters": [s.iters for s in st16],
+                                    "converged": all(s.status == 0 for s in st16)},
+           "roofline": sv.smoother_roofline(prof, floor, peak),
+           "top_kernels_in_solve": top_table(prof, 5)}
+    if err_sample is None:
+        xref, w = oracle_reference(name, sv.coords)
+        rec["err_vs_oracle"] = rel_err(x32, xref, w)
+        rec["fp64_err_vs_oracle"] = rel_err(x64, xref, w)
+        rec["err_note"] = f"relative lumped-mass L2 against the oracle's sparse LU solve, at rtol {rtol:g}"
+    if name.startswith("elasticity"):
+        okd = dict(sv.ok, store_bf16=0, inner_rtol=1e-4)
+        hd = G.Hierarchy(ctx, sv.lm, B.make_problem(**sv.pk), B.make_opts(**okd))
+        msd, std, _ = sv.timed(B.MG_MIXED_FP32, 2, 1, rtol, hd)
+        rec["defect_correction"] = {"value": n_free / (statistics.mean(msd) * 1e-3),
+                                    "ms_per_step": statistics.mean(msd), "inner_rtol": 1e-4,
+                                    "iters": [s.iters for s in std], "rel_res": max(s.rel_res for s in std),
+                                    "converged": all(s.status == 0 for s in std)}
         hd.free()
-        barrier()
-    value, t_max = whole_job_rate(n_free, args.steps, sum(ms_mixed), world, "cuda")
-    assert all(s.status == 0 for s in st_mixed + st64), [s.as_dict() for s in st_mixed + st64]
+    sv.free()
+    if err_sample is not None:
+        rec["err_vs_oracle_sample"] = err_on_sample(G, B, ctx, err_sample, flush)
+    return rec
 
-    # end to end through the public host-buffer entry point (pinned host memory)
-    bh = torch.empty(h.n_dofs, dtype=torch.float64, pin_memory=True)
-    bh.copy_(b.cpu())
-    xh = torch.zeros(h.n_dofs, dtype=torch.float64, pin_memory=True)
-    bhn, xhn = bh.numpy(), xh.numpy()
-    h.solve_host(bhn, xhn, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
-    e2e_ms = []
-    for _ in range(args.steps):
-        xhn[:] = 0.0
-        flush_l2(flush)
+
+TD_SIZES = (128, 256, 512, 1024)
+TD_PAPER_H100_S = {128: 2.05, 256: 2.85, 512: 4.47, 1024: 9.0}   # Table "tab:td", GPU solve column
+
+
+def measure_timedep(G, B, ctx, n, krylov, rtol=1e-8, steps=None, oracle_check=False):
+    """The paper's time-dependent transport-diffusion run (Sec. 5.1) on the
+    uniform n x n mesh: 100 backward-Euler steps (dt = 0.02) through
+    mg_time_steps, right-hand side and warm-started solve per step on the
+    device, hierarchy resident.  Source and boundary data of every step are
+    inputs, resident before the timed region."""
+    import torch
+    steps = steps or W.TD_STEPS
+    dt = W.TD_DT
+    lm = W.td_uniform(n)
+    pk = dict(kind=B.MG_TRANSPORT, eps=W.TD_LAMBDA, beta=W.TD_B, supg_delta0=0.0, mass=1.0 / dt)
+    t0 = time.perf_counter()
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pk), B.make_opts(krylov=krylov))
+    setup_s = time.perf_counter() - t0
+    xy = h.coords()
+    f = torch.from_numpy(np.stack([W.td_source((k + 1) * dt, xy) for k in range(steps)])).cuda()
+    g = torch.from_numpy(np.stack([W.td_theta((k + 1) * dt, xy) for k in range(steps)])).cuda()
+    th0 = torch.from_numpy(W.td_theta(0.0, xy)).cuda()
+    out = {"n": n, "dofs": int(h.n_dofs), "steps": steps, "setup_s": setup_s}
+    for key, prec in (("mixed", B.MG_MIXED_FP32), ("fp64", B.MG_FP64)):
+        th = th0.clone()
+        h.time_steps(th, f, g, 3, rtol=rtol, max_it=200, prec=prec)        # warm-up
+        th = th0.clone()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.solve_host(bhn, xhn, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
-        e1.record(stream)
+        e0.record(ctx.stream)
+        rc, sts = h.time_steps(th, f, g, steps, rtol=rtol, max_it=200, prec=prec)
+        e1.record(ctx.stream)
         e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = world * n_free * args.steps / (sum(e2e_ms) * 1e-3)
-
-    # roofline of the dominant kernel, timed inside the solve: the same K
-    # solves (L2 flushed before each) with every kernel between two CUDA
-    # events on the library's stream, summed per (kernel, level)
-    fine = h.levels - 1
-    from paper_2405_05047_gb300 import opbench
-    alg_bytes = opbench.alg_bytes(info, fine, h.nc, "smooth", 4)
-    prof = {}
-    for _ in range(args.steps):
-        x.zero_()
-        flush_l2(flush)
-        torch.cuda.synchronize()
-        st_p, ents = h.solve_profiled(b, x, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
-        assert st_p.status == 0 and st_p.iters == st_mixed[0].iters, st_p.as_dict()
-        for e in ents:
-            a = prof.setdefault((e["kernel"], e["level"]), [0, 0.0])
-            a[0] += e["launches"]
-            a[1] += e["ms"]
-    floor_n, floor_ms = prof.pop(("k_prof_empty", -2), [1, 0.0])
-    prof_total = sum(v[1] for v in prof.values())
-    ranked = sorted(prof.items(), key=lambda kv: -kv[1][1])
-    sweep = [kv for kv in ranked if kv[0][0].startswith("k_smooth<float") and ", false," in kv[0][0]
-             and kv[0][1] == fine]
-    (ker_name, _), (ker_launches, ker_ms_tot) = sweep[0]
-    ker_ms_avg = ker_ms_tot / ker_launches
-    top_kernels = [{"kernel": k, "level": l, "launches": n, "ms": round(t, 4),
-                    "share": round(t / prof_total, 4)} for (k, l), (n, t) in ranked[:12]]
-    for (k, l), (n, t) in ranked:       # the whole table, for the profile summaries
-        print(f"prof {k:48s} level {l:3d} launches {n:6d} ms {t:9.4f} us/launch {1e3 * t / n:8.2f} "
-              f"share {t / prof_total:.4f}", file=sys.stderr)
-    # the same sweep alone: cold (L2 flushed before each single launch) and warm
-    cold = []
-    for _ in range(10):
-        flush_l2(flush)
-        torch.cuda.synchronize()
-        cold.append(h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=1))
-    hot_ms = h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=50)
-    per_level = []
-    for lvl in range(h.levels):
-        row = {"level": lvl, "nodes": int(info.level_nodes[lvl])}
-        for opn, op in (("smooth", B.MG_OP_SMOOTH), ("restrict", B.MG_OP_RESTRICT),
-                        ("prolong", B.MG_OP_PROLONG_ADD)):
-            if lvl == 0 and op != B.MG_OP_SMOOTH:
-                continue
-            row[opn + "_us"] = 1e3 * h.time_op(lvl, op, B.MG_MIXED_FP32, reps=20)
-        per_level.append(row)
-    peaks = measured_peaks()
-    peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg_bytes / (ker_ms_avg * 1e-3) / 1e9
-    traffic = None       # DRAM bytes per launch from the ncu capture, while it matches the current kernel
-    tr_path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.txt")
-    if os.path.exists(tr_path):
-        for line in open(tr_path):
-            if line.startswith("bytes_per_launch:"):
-                v = line.split(":", 1)[1].strip()
-                traffic = None if v == "null" else int(v)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "td_adaptive":
-        try:
-            cpu = cpu_baseline()
-            allc = cpu_baseline(steps=2, threads=os.cpu_count() or 1)
-            if "value" in allc:
-                # the oracle's sparse kernels are single-threaded scipy; more BLAS threads barely matter
-                cpu["all_cores"] = {"cores": allc["cores"], "value": allc["value"]}
-        except Exception as e:       # the baseline is reported, never required
-            cpu = {"error": str(e)}
-
-    out = {
-        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.mean(ms_mixed), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32-mg+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n_nodes": int(info.n_nodes),
-                   "n_free_dofs": int(n_free), "levels": int(info.levels), "hanging_nodes": int(info.n_hanging),
-                   "rtol": args.rtol, "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}", "tail_levels": int(info.tail_levels),
-                   "tail_cluster": int(info.tail_cluster), "tuned_vcycle_ms": info.vcycle_ms,
-                   "col16_slices": int(info.col16_slices), "col32_slices": int(info.col32_slices)},
-        "iters": [s.iters for s in st_mixed], "rel_res": max(s.rel_res for s in st_mixed),
-        "fp64": {"value": world * n_free / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
-                 "iters": [s.iters for s in st64], "rel_res": max(s.rel_res for s in st64)},
-        "speedup_mixed_vs_fp64": statistics.mean(ms64) / statistics.mean(ms_mixed),
-        "bf16_values_ablation": {"value": world * n_free / (statistics.mean(ms16) * 1e-3),
-                                 "ms_per_step": statistics.mean(ms16), "iters": [s.iters for s in st16],
-                                 "rel_res": max(s.rel_res for s in st16),
-                                 "converged": all(s.status == 0 for s in st16)},
-        "defect_correction": dc,
-        "setup_s": setup_s,
-        "gpu_launches": int(sum(s.launches for s in st_mixed)),
-        "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": int(2 * 8 * h.n_dofs),
-                "d2h_bytes_per_step": int(8 * h.n_dofs), "ms_per_step": statistics.mean(e2e_ms)},
-        "roofline": {"bound": "hbm", "kernel": f"{ker_name} on the finest level (fused residual + (block-)Jacobi sweep)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "alg_bytes_per_launch": int(alg_bytes), "ms_per_launch": ker_ms_avg,
-                     "launches_timed": int(ker_launches), "share_of_solve": ker_ms_tot / prof_total,
-                     "timing": "CUDA events between consecutive kernels inside the solve (one graph per Krylov "
-                               "iteration, L2 flushed before each solve); an empty kernel timed the same way takes "
-                               f"{floor_ms / floor_n * 1e3:.2f} us",
-                     "interval_floor_ms": floor_ms / floor_n,
-                     "ms_per_launch_alone_cold": statistics.mean(cold), "ms_per_launch_alone_l2_warm": hot_ms,
-                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peaks else "fallback"},
-        "clocks": clk.summary(),
-        "per_level_fp32_us": per_level,
-        "top_kernels_in_solve": top_kernels,
-        "cpu_baseline": cpu,
-    }
-    if rank == 0:
-        print(json.dumps(out))
+        ms = e0.elapsed_time(e1)
+        thn = th.cpu().numpy()
+        r = {"s": ms * 1e-3, "dof_solves_per_s": h.n_dofs * steps / (ms * 1e-3), "status": rc,
+             "iters_total": int(sum(s.iters for s in sts)), "iters_max": int(max(s.iters for s in sts)),
+             "rel_res_max": float(max(s.rel_res for s in sts)),
+             "launches": int(sum(s.launches for s in sts)),
+             "err_vs_exact_max": float(np.abs(thn - W.td_theta(steps * dt, xy)).max())}
+        out[key] = (r, thn)
+    if oracle_check:
+        from oracle import mesh as M
+        from oracle import problems as PB
+        from oracle import timestep as TS
+        m = M.Q1Mesh(2, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+        prob = PB.Problem(PB.TRANSPORT, eps=W.TD_LAMBDA, beta=W.TD_B, supg_delta0=0.0)
+        S, ref = TS.run(m, prob, dt, W.td_theta(0.0, xy), lambda t: W.td_source(t, xy),
+                        lambda t: W.td_theta(t, xy), steps)
+        w = np.asarray(S.F.sum(axis=1)).ravel()
+        for key in ("mixed", "fp64"):
+            out[key][0]["err_vs_oracle"] = rel_err(out[key][1], ref[-1], w)
+    for key in ("mixed", "fp64"):
+        out[key] = out[key][0]
+    out["paper_h100_solve_s"] = TD_PAPER_H100_S.get(n)
     h.free()
-    ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
-
-
-if __name__ == "__main__":
-    main()
+    return out

@@ -124,6 +124,13 @@ typedef struct {
                                   convection field at the finest nodes in the
                                   external order (see mg_mesh_nodes); read
                                   during mg_setup only                          */
+  double mass;                 /* POISSON, TRANSPORT: coefficient s >= 0 of an
+                                  added mass term s (u, v); s = 1/dt gives the
+                                  matrix of one backward-Euler step of the
+                                  time-dependent problem (Sec. 5.1).  With
+                                  SUPG the stabilisation also tests it:
+                                  + sum_T delta_T s (u, beta.grad v)_T.
+                                  0: stationary                                 */
 } mg_problem;
 
 typedef struct {
@@ -248,6 +255,32 @@ int mg_free(mg_hier* h);
  * (homogeneous data), only its Dirichlet entries are read; b: device,
  * n_nodes * nc doubles. */
 int mg_assemble_rhs(mg_hier* h, const double* f_nodal, const double* g_nodal, double* b);
+
+/* Backward-Euler time stepping with the hierarchy resident (Sec. 5.1;
+ * Algorithm "Nonstationary Linear Problem": the matrices are assembled and
+ * uploaded once, every step assembles its right-hand side and solves on the
+ * device).  The hierarchy's problem must have mass = 1/dt > 0; its operator
+ * is then the step matrix M/dt + A.  For n = 1..n_steps:
+ *   b_n = H^T F (theta_{n-1} / dt + f_n)   (F: the load matrix of
+ *         mg_assemble_rhs, i.e. the consistent mass, plus the SUPG load when
+ *         stabilised), Dirichlet data g_n eliminated as in mg_assemble_rhs;
+ *   theta_n = solution of (M/dt + A) theta_n = b_n, the Krylov method
+ *         started from theta_{n-1} (warm start) and stopped at
+ *         ||b_n - A theta_n|| <= rtol ||b_n,free||.
+ * theta: device, n_nodes * nc doubles; in: theta_0, out: theta_{n_steps}
+ * (all nodes; hanging values filled by H, Dirichlet values g_n).
+ * f: device, n_steps blocks of n_nodes * nc doubles (nodal source values at
+ * t_1, ..., t_n_steps, block n-1 for step n) or NULL (no source).
+ * g: device, the same layout, nodal Dirichlet data (only its Dirichlet
+ * entries are read) or NULL (homogeneous data).
+ * steps: host array of n_steps mg_stats (per-step statistics) or NULL.
+ * Returns MG_OK when every step converged; otherwise stops at the first step
+ * that did not and returns its status (theta holds that step's iterate and
+ * steps[] is filled up to it).  MG_ERR_INVALID if the problem has no mass
+ * term.  Buffers for the step's source and right-hand side come from the
+ * hierarchy's solve workspace; nothing is allocated. */
+int mg_time_steps(mg_hier* h, double* theta, const double* f, const double* g, int n_steps, double rtol,
+                  int max_it, int prec, mg_stats* steps);
 
 /* Krylov solve (CG / BiCGStab / GMRES per opts.krylov) preconditioned by one
  * V-cycle per iteration (Sec. 4.1.5).  b, x: device, n_nodes * nc doubles,

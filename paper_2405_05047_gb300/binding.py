@@ -51,7 +51,8 @@ class MgMesh(C.Structure):
 class MgProblem(C.Structure):
     _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("beta", C.c_double * 3), ("mu", C.c_double),
                 ("lambda_", C.c_double), ("supg_delta0", C.c_double), ("dirichlet_mask", C.c_uint32 * 3),
-                ("nu", C.c_double), ("dt", C.c_double), ("lps_alpha0", C.c_double), ("conv", C.c_void_p)]
+                ("nu", C.c_double), ("dt", C.c_double), ("lps_alpha0", C.c_double), ("conv", C.c_void_p),
+                ("mass", C.c_double)]
 
 
 class MgOpts(C.Structure):
@@ -128,6 +129,8 @@ _SIGS = {
     "mg_serve_config": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "mg_restrict_static": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_time_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
+                                C.c_int, C.POINTER(MgStats)]),
 }
 
 
@@ -236,9 +239,12 @@ def make_mesh(leafmesh):
 
 
 def make_problem(kind=MG_POISSON, eps=1.0, beta=(0.0, 0.0, 0.0), mu=1.0, lam=1.0, supg_delta0=0.5,
-                 dirichlet=(0xFF,), nu=1e-3, dt=0.01, lps_alpha0=0.5, conv=None):
-    """conv (OSEEN): nodal convection field at the finest nodes, (n_nodes, dim)."""
+                 dirichlet=(0xFF,), nu=1e-3, dt=0.01, lps_alpha0=0.5, conv=None, mass=0.0):
+    """conv (OSEEN): nodal convection field at the finest nodes, (n_nodes, dim).
+    mass (POISSON, TRANSPORT): coefficient s of s (u, v); 1/dt for a
+    backward-Euler step."""
     p = MgProblem()
+    p.mass = mass
     p.kind = kind
     p.eps = eps
     for d in range(3):
@@ -334,6 +340,16 @@ def mg_solve_host(h, b: np.ndarray, x: np.ndarray, rtol, max_it, prec=MG_FP64):
     rc = load_library().mg_solve_host(h, _host_ptr(b), _host_ptr(x), rtol, max_it, prec, C.byref(st))
     _check(rc, allow=SOLVE_OUTCOMES)
     return st
+
+
+def mg_time_steps(h, theta, f, g, n_steps, rtol, max_it, prec=MG_FP64):
+    """Backward-Euler steps in place on theta; f, g: (n_steps, n_dofs) device
+    arrays or None.  Returns (status, [MgStats per step])."""
+    sts = (MgStats * max(n_steps, 1))()
+    rc = load_library().mg_time_steps(h, _ptr(theta), _ptr(f) if f is not None else None,
+                                      _ptr(g) if g is not None else None, n_steps, rtol, max_it, prec, sts)
+    _check(rc, allow=SOLVE_OUTCOMES)
+    return rc, list(sts)[:n_steps]
 
 
 def mg_vcycle(h, r, z, prec=MG_FP64):
@@ -435,6 +451,9 @@ class Hierarchy:
 
     def solve(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_solve(self.handle, b, x, rtol, max_it, prec)
+
+    def time_steps(self, theta, f, g, n_steps, rtol=1e-10, max_it=200, prec=MG_FP64):
+        return mg_time_steps(self.handle, theta, f, g, n_steps, rtol, max_it, prec)
 
     def solve_profiled(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_solve_profiled(self.handle, b, x, rtol, max_it, prec)

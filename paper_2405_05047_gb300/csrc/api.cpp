@@ -389,6 +389,41 @@ static int solve_sync(mg_hier* h, const double* b, bool bh, double* x, bool xh, 
   return rc;
 }
 
+int mg_time_steps(mg_hier* h, double* theta, const double* f, const double* g, int n_steps, double rtol, int max_it,
+                  int prec, mg_stats* steps) {
+  if (!h || !theta || n_steps < 0 || !(rtol > 0) || max_it < 1) return fail(MG_ERR_INVALID, "bad argument");
+  if (!(h->prob.mass > 0)) return fail(MG_ERR_INVALID, "time stepping needs a problem with mass = 1/dt > 0");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  CU(cudaSetDevice(h->ctx->device));
+  cudaStream_t s = h->ctx->stream;
+  Workspace& w = *h->ws0;
+  const int64_t n = h->n_dofs;
+  for (int k = 0; k < n_steps; ++k) {
+    // right-hand side of step k+1 straight into the solve's b buffer; the
+    // step's nodal load field goes through w.t, which the solve overwrites
+    const double* fk = f ? f + (int64_t)k * n : nullptr;
+    const double* gk = g ? g + (int64_t)k * n : nullptr;
+    launch_step_load(n, h->prob.mass, theta, fk, w.t, s);
+    launch_rhs(h->F.v, h->nc, w.t, h->fixmask, h->dirmask, gk, w.bi, s);
+    if (gk) launch_lift(h->Lift.v, h->nc, gk, w.bi, s);
+    h->launch_count += gk ? 3 : 2;
+    mg_stats st{};
+    rc = solve_start(h, w, w.bi, false, theta, false, theta, false, rtol, max_it, prec, s);
+    while (rc == MG_OK || rc == MG_PENDING) {
+      CU(cudaEventSynchronize(w.ev1));
+      rc = solve_check(h, w, s, &st);
+      if (rc != MG_PENDING) break;
+    }
+    st.launches += gk ? 3 : 2;
+    if (steps) steps[k] = st;
+    if (rc != MG_OK) break;
+  }
+  CU(cudaGetLastError());
+  return rc;
+}
+
 // "k_smooth<float, float, 1, false, 1>" from the kernel's symbol: demangled,
 // without the return type, namespace and parameter list.
 static void kernel_label(const void* fn, char* out, size_t cap) {

@@ -1138,7 +1138,8 @@ int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const do
   if (w.method == M_GMRES && !w.gm.V) return fail(MG_ERR_INVALID, "hierarchy set up without GMRES workspace");
   CU(cudaEventRecord(w.ev0, s));
   CU(cudaMemsetAsync(&w.st->counter, 0, sizeof(unsigned int), s));   // reduction arrival counter
-  CU(cudaMemcpyAsync(w.bi, b, n * 8, b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  if (b != w.bi)   // a time step assembles its right-hand side in place
+    CU(cudaMemcpyAsync(w.bi, b, n * 8, b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   CU(cudaMemcpyAsync(w.p, x0, n * 8, x0_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   launch_copy_fixed(h->n_nodes, h->nc, h->fixmask, w.bi, w.p, w.xi, s);
   // defect correction: the first round stops at inner_rtol (relative to b; x0

@@ -808,6 +808,16 @@ __global__ void k_copy_fixed(int64_t n, int nc, const uint8_t* __restrict__ fix,
     for (int c = 0; c < nc; ++c) x[nc * i + c] = ((fix[i] >> c) & 1) ? b[nc * i + c] : xin[nc * i + c];
 }
 
+// Nodal field of one backward-Euler step's load: out = s theta + f (f may be
+// NULL: no source).  Scalar loads: theta and f are caller pointers (f is a
+// block of a steps x n array) with no alignment beyond 8 bytes.
+__global__ void k_step_load(int64_t n, double s, const double* __restrict__ theta, const double* __restrict__ f,
+                            double* __restrict__ out) {
+  pdl_wait();
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads)
+    out[i] = f ? fma(s, theta[i], f[i]) : s * theta[i];
+}
 
 // ------------------------------------------------------------------ Krylov
 // All Krylov kernels run one thread per node (nc dofs) or per vector entry.
@@ -1780,6 +1790,9 @@ void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t
 void launch_copy_fixed(int64_t n, int nc, const uint8_t* fixmask, const double* b, const double* xin, double* x,
                        cudaStream_t s) {
   launch(k_copy_fixed, grid_for_rows(n), s, n, nc, fixmask, b, xin, x);
+}
+void launch_step_load(int64_t n, double sc, const double* theta, const double* f, double* out, cudaStream_t s) {
+  launch(k_step_load, grid_for_rows(n), s, n, sc, theta, f, out);
 }
 void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
                           KrylovState* st, int test, cudaStream_t s, unsigned long long cond) {

@@ -175,6 +175,8 @@ void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_don
 void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, const uint8_t* dirmask,
                 const double* g, double* b, cudaStream_t s);
 void launch_lift(const SellView& L, int nc, const double* g, double* b, cudaStream_t s);
+// out = sc * theta + f (f NULL: out = sc * theta), n entries
+void launch_step_load(int64_t n, double sc, const double* theta, const double* f, double* out, cudaStream_t s);
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s);
 void launch_copy_fixed(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, const double* xin,
                        double* x, cudaStream_t s);

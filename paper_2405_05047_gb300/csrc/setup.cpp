@@ -499,6 +499,13 @@ std::vector<double> element_matrix(const mg_problem& P, int dim, const double* h
         for (int i = 0; i < dim; ++i)
           for (int j = 0; j < dim; ++j) v += delta * P.beta[i] * P.beta[j] * I.G(i, j, A, B);
       }
+      if (P.mass != 0.0) {
+        // s (u, v), and its SUPG test delta_T s (u, beta.grad v)
+        double m = I.G(-1, -1, A, B);
+        if (P.kind == MG_TRANSPORT)
+          for (int i = 0; i < dim; ++i) m += delta * P.beta[i] * I.G(i, -1, A, B);
+        v += P.mass * m;
+      }
       K[A * nv + B] = v;
     }
   return K;
@@ -1040,6 +1047,9 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
   if (prob.kind < MG_POISSON || prob.kind > MG_OSEEN) return Status::err(MG_ERR_INVALID, "unknown problem kind");
   if (prob.kind == MG_ELASTICITY && mesh.dim != 3) return Status::err(MG_ERR_INVALID, "elasticity needs dim = 3");
   if (prob.kind == MG_TRANSPORT && !(prob.eps > 0)) return Status::err(MG_ERR_INVALID, "transport needs eps > 0");
+  if (!(prob.mass >= 0.0) || !std::isfinite(prob.mass)) return Status::err(MG_ERR_INVALID, "mass must be finite and >= 0");
+  if (prob.mass != 0.0 && prob.kind != MG_POISSON && prob.kind != MG_TRANSPORT)
+    return Status::err(MG_ERR_INVALID, "a mass term is supported for POISSON and TRANSPORT");
   const bool oseen = prob.kind == MG_OSEEN;
   if (oseen) {
     if (mesh.dim != 2) return Status::err(MG_ERR_INVALID, "oseen needs dim = 2");

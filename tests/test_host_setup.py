@@ -29,6 +29,15 @@ CASES = {
                                              W._cell_box(W.uniform_leaves(3, (1, 1, 1), 2))[1][:, 0] <= 0.5 + 1e-12),
                             PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
                             dict(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,))),
+    # backward-Euler step matrices of the time-dependent problem (mass 1/dt)
+    "td_step": (lambda: W.td_uniform(32),
+                PB.Problem(PB.TRANSPORT, eps=0.01, beta=(0.0, -1.0), supg_delta0=0.0, mass=50.0),
+                dict(kind=B.MG_TRANSPORT, eps=0.01, beta=(0.0, -1.0), supg_delta0=0.0, mass=50.0)),
+    "td_step_supg_adaptive": (lambda: W.td_adaptive(rounds=3, gamma=1.0),
+                              PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5), mass=10.0),
+                              dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5), mass=10.0)),
+    "poisson_mass": (lambda: W.uniform_leaves(2, (1, 1), 4), PB.Problem(PB.POISSON, mass=3.0),
+                     dict(kind=B.MG_POISSON, mass=3.0)),
     "channel": (lambda: W.oseen_channel(uniform=1, rounds=3),
                 PB.Problem(PB.TRANSPORT, eps=1e-2, beta=(1.0, 0.3), dirichlet=(0b1101,)),
                 dict(kind=B.MG_TRANSPORT, eps=1e-2, beta=(1.0, 0.3), dirichlet=(0b1101,))),
