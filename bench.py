@@ -60,13 +60,14 @@ def workload(name):
     """(leaf mesh, problem kwargs, opts kwargs, rhs function, description,
     Dirichlet data function or None)."""
     from paper_2405_05047_gb300 import binding as B
-    if name == "oseen":
-        lm = W.oseen_channel(1, OSEEN_ROUNDS)
+    if name in ("oseen", "oseen_small"):
+        rounds = OSEEN_ROUNDS if name == "oseen" else 7
+        lm = W.oseen_channel(1, rounds)
         xy = B.mg_mesh_nodes(lm)
         pk = dict(kind=B.MG_OSEEN, dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01, conv=W.oseen_beta(xy))
         return lm, pk, dict(krylov=B.MG_GMRES, restart=30), (lambda c: np.zeros(c.shape[0] * 3)), (
             "2D Oseen (one backward-Euler step, nu=1e-3, dt=0.01) equal-order Q1 (u,v,p) + LPS on the channel "
-            f"[0,2.2]x[0,0.41], 22x4 macro cells refined once, then {OSEEN_ROUNDS} rounds towards the circle "
+            f"[0,2.2]x[0,0.41], 22x4 macro cells refined once, then {rounds} rounds towards the circle "
             "|x-(0.2,0.2)|=0.05 by sibling families, 2:1; seeded divergence-free convection field, parabolic "
             "inflow (lifted), no-slip walls, do-nothing outflow; GMRES(30) + V(2,2) point-block (Vanka) "
             "Jacobi, w_l = 1.2/lambda_max(S_l A_l) per level"), W.oseen_inflow
@@ -294,33 +295,32 @@ def _cpu_baseline_inproc(steps, rounds, rtol, threads=1):
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle as it stands (numpy/scipy FP64, one host thread) on the
+    headline workload itself: setup untimed, then --warmup and --steps solves
+    of the same system to 1e-8."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
-    from oracle import krylov, mg
-    from oracle import problems as PB
-    rounds = 6
-    lm = W.td_adaptive(rounds=rounds, gamma=GAMMA_TD)
-    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
-    Hh = mg.Hierarchy(lm, prob, nu1=NU_TD, nu2=NU_TD)
-    s = PB.build_system(Hh.fine.mesh, prob)
-    b = s.rhs(W.f_transport(Hh.fine.mesh.coords, 1e-3, (1.0, 0.5)))
-    n_free = int((~s.fixed).sum())
+    from oracle import krylov
+    t0 = time.perf_counter()
+    Hh, S, b = _oracle_system()
+    t_setup = time.perf_counter() - t0
+    n_free = int((~S.fixed).sum())
     for _ in range(warm):
-        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
+        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=args.rtol)
     t0 = time.perf_counter()
     for _ in range(steps):
-        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=1e-8)
-    dt = (time.perf_counter() - t0) / steps
+        krylov.bicgstab(Hh.fine.A, b, Hh.precondition, rtol=args.rtol)
+    dt = (time.perf_counter() - t0) / max(steps, 1)
     value = n_free / dt
-    sample = (f"oracle BiCGStab+V({NU_TD},{NU_TD}) FP64 solve to 1e-8 of the TD workload with {rounds} refinement rounds "
-              f"({n_free} free DoFs), 1 host thread")
+    sample = (f"oracle BiCGStab+V({NU_TD},{NU_TD}) FP64 solve to {args.rtol:g} of the headline TD workload itself "
+              f"({n_free} free DoFs), one host thread, setup {t_setup:.0f} s untimed")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "td_adaptive", "sample_rounds": rounds, "n_free": n_free},
+        "config": {"workload": "td_adaptive", "n_free_dofs": n_free, "same_config": True},
         "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -564,8 +564,9 @@ def top_table(prof, k=12):
 
 
 def oracle_reference(name, coords_check=None):
-    """The oracle's FP64 solution of a (small) workload by sparse LU, with the
-    lumped-mass weights: (x_all, w)."""
+    """The oracle's FP64 solution of a (small) workload by sparse LU (3D
+    elasticity: the oracle's MG-CG to 1e-12), with the lumped-mass weights:
+    (x_all, w)."""
     import scipy.sparse.linalg as spl
     from oracle import mesh as M
     from oracle import problems as PB
@@ -584,15 +585,21 @@ def oracle_reference(name, coords_check=None):
         assert np.array_equal(m.coords, coords_check)
     S = PB.build_system(m, prob, beta=prob.conv)
     g = None if gfun is None else gfun(m.coords).ravel()
-    x = S.H @ spl.spsolve(S.A.tocsc(), S.rhs(ffun(m.coords), g))
+    b = S.rhs(ffun(m.coords), g)
+    if kind == PB.ELASTICITY:     # 3D: sparse LU fills in; the oracle's own MG-CG to 1e-12 instead
+        from oracle import krylov, mg
+        Hh = mg.Hierarchy(lm, prob)
+        x, _ = krylov.pcg(Hh.fine.A, b, Hh.precondition, rtol=1e-12, maxit=500)
+    else:
+        x = spl.spsolve(S.A.tocsc(), b)
     w = np.repeat(np.asarray(S.F.sum(axis=1)).ravel(), prob.nc)
-    return x, w
+    return S.H @ x, w
 
 
 def err_on_sample(G, B, ctx, name, flush, rtol=1e-10):
-    """Error of both GPU paths against the oracle's direct solve on a smaller
+    """Error of both GPU paths against the oracle's solve on a smaller
     instance of the same workload (the full-size system does not fit the
-    oracle's direct solver): relative lumped-mass L2 at rtol 1e-10."""
+    oracle): relative lumped-mass L2 at rtol 1e-10."""
     sv = Solver(G, B, ctx, name, flush)
     xref, w = oracle_reference(name, sv.coords)
     out = {"workload": name, "n_free_dofs": int(sv.info.n_free), "rtol": rtol}
@@ -705,3 +712,224 @@ def measure_timedep(G, B, ctx, n, krylov, rtol=1e-8, steps=None, oracle_check=Fa
     out["paper_h100_solve_s"] = TD_PAPER_H100_S.get(n)
     h.free()
     return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="td_adaptive")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="headline workload only (no records of the other configurations)")
+    ap.add_argument("--requests", type=int, default=1000, help="serving: requests per stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=16, help="serving: solves in flight")
+    ap.add_argument("--sweep", type=float, nargs="*", default=[10.0, 100.0], help="serving: rate multipliers")
+    ap.add_argument("--launch", default="graph", choices=["graph", "direct"],
+                    help="direct: per-kernel launches (for profilers that cannot see inside graphs)")
+    ap.add_argument("--tail", default=None,
+                    help="ROWS,CLUSTER: fixed tail shape instead of the setup autotuner (profiling runs, "
+                         "where the autotuner's timings would be distorted)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    headline = args.workload == "td_adaptive"
+    # the oracle on the host cores, started before this process touches the GPU
+    tmp = tempfile.mkdtemp(prefix="mg_bench_")
+    orc = None
+    if rank == 0 and world == 1 and headline and not args.no_cpu_baseline:
+        orc = start_oracle_child(tmp)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2405_05047_gb300 as G
+    from paper_2405_05047_gb300 import binding as B
+    from paper_2405_05047_gb300 import build as BLD
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    BLD.build()
+    torch.cuda.set_device(local)
+    ctx = G.Context(local)
+    stream = ctx.stream
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MB > L2
+    sv = Solver(G, B, ctx, args.workload, flush, args.launch, args.tail)
+    h, info = sv.h, sv.info
+    # kernels launched by setup (autotuner V-cycles): a profiler skips these to reach the solves
+    print(f"launches after setup: {h.launch_count()}", file=sys.stderr, flush=True)
+    n_free = info.n_free
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        barrier()
+        ms_mixed, st_mixed, x_mixed = sv.timed(B.MG_MIXED_FP32, args.steps, args.warmup, args.rtol)
+        barrier()
+    # FP64 path of the same fused kernels (reported beside the value)
+    ms64, st64, x_fp64 = sv.timed(B.MG_FP64, max(2, args.steps // 2), 1, args.rtol)
+    barrier()
+    # ablation: BF16-stored matrix values in the FP32 V-cycle
+    ms16, st16, _ = sv.timed(B.MG_MIXED_BF16, max(2, args.steps // 2), 1, args.rtol)
+    barrier()
+    value, t_max = whole_job_rate(n_free, args.steps, sum(ms_mixed), world, "cuda")
+    assert all(s.status == 0 for s in st_mixed + st64), [s.as_dict() for s in st_mixed + st64]
+
+    # end to end through the public host-buffer entry point (pinned host memory)
+    bh = torch.empty(h.n_dofs, dtype=torch.float64, pin_memory=True)
+    bh.copy_(sv.b.cpu())
+    xh = torch.zeros(h.n_dofs, dtype=torch.float64, pin_memory=True)
+    bhn, xhn = bh.numpy(), xh.numpy()
+    h.solve_host(bhn, xhn, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
+    e2e_ms = []
+    for _ in range(args.steps):
+        xhn[:] = 0.0
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.solve_host(bhn, xhn, rtol=args.rtol, max_it=500, prec=B.MG_MIXED_FP32)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = world * n_free * args.steps / (sum(e2e_ms) * 1e-3)
+
+    # roofline of the dominant kernel, timed inside the solve: the same K
+    # solves (L2 flushed before each) with every kernel between two CUDA
+    # events on the library's stream, summed per (kernel, level)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    prof, floor_ms = sv.profile(B.MG_MIXED_FP32, args.steps, args.rtol, st_mixed[0].iters)
+    prof_total = sum(v[1] for v in prof.values())
+    for (k, l), (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):   # whole table, for the profiles
+        print(f"prof {k:48s} level {l:3d} launches {n:6d} ms {t:9.4f} us/launch {1e3 * t / n:8.2f} "
+              f"share {t / prof_total:.4f}", file=sys.stderr)
+    roof = sv.smoother_roofline(prof, floor_ms, peak)
+    fine = h.levels - 1
+    # the same sweep alone: cold (L2 flushed before each single launch) and warm
+    cold = []
+    for _ in range(10):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        cold.append(h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=1))
+    hot_ms = h.time_op(fine, B.MG_OP_SMOOTH, B.MG_MIXED_FP32, reps=50)
+    per_level = []
+    for lvl in range(h.levels):
+        row = {"level": lvl, "nodes": int(info.level_nodes[lvl])}
+        for opn, op in (("smooth", B.MG_OP_SMOOTH), ("restrict", B.MG_OP_RESTRICT),
+                        ("prolong", B.MG_OP_PROLONG_ADD)):
+            if lvl == 0 and op != B.MG_OP_SMOOTH:
+                continue
+            row[opn + "_us"] = 1e3 * h.time_op(lvl, op, B.MG_MIXED_FP32, reps=20)
+        per_level.append(row)
+    traffic = None       # DRAM bytes per launch from the ncu capture, while it matches the current kernel
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.txt")
+    if os.path.exists(tr_path):
+        for line in open(tr_path):
+            if line.startswith("bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                traffic = None if v == "null" else int(v)
+    roof.update({"traffic": traffic,
+                 "timing": "CUDA events between consecutive kernels inside the solve (one graph per Krylov "
+                           "iteration, L2 flushed before each solve); an empty kernel timed the same way takes "
+                           f"{floor_ms * 1e3:.2f} us",
+                 "ms_per_launch_alone_cold": statistics.mean(cold), "ms_per_launch_alone_l2_warm": hot_ms,
+                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peaks else "fallback"})
+    sv.free()
+
+    # the other configurations (one GPU, rank 0 only)
+    configs = None
+    if rank == 0 and world == 1 and headline and not args.no_configs:
+        configs = {}
+        for name, sample in (("poisson64", None), ("elasticity128", "elasticity32"), ("oseen", "oseen_small")):
+            try:
+                configs[name] = measure_config(G, B, ctx, name, flush, peak, rtol=args.rtol, err_sample=sample)
+            except Exception as e:        # a failing record is reported, never hides the headline
+                configs[name] = {"error": repr(e)}
+        try:
+            runs = [measure_timedep(G, B, ctx, n, B.MG_BICGSTAB, args.rtol, oracle_check=(n == 128))
+                    for n in TD_SIZES]
+            big = runs[-1]
+            configs["td_timedep"] = {
+                "description": "the paper's time-dependent transport-diffusion problem (lambda=0.01, b=(0,-1), "
+                               "exact solution theta_ex, backward Euler dt=0.02, 100 steps, uniform meshes "
+                               "h=2^-7..2^-10): per step the right-hand side and a warm-started BiCGStab + "
+                               "V(2,2) solve to 1e-8 on the device, hierarchy resident",
+                "metric": "DoF*solves/s (FP32-MG + FP64 Krylov)", "value": big["mixed"]["dof_solves_per_s"],
+                "unit": "DoF*solves/s", "sizes": runs,
+                "paper_context": "Table tab:td, GPU solve column on an H100 PCIe (FP64, GMRES+MG; rhs on the CPU "
+                                 "and not included there): 2.05 / 2.85 / 4.47 / 9.0 s for 100 steps"}
+        except Exception as e:
+            configs["td_timedep"] = {"error": repr(e)}
+
+    # error against the oracle and the CPU baseline on the headline mesh
+    cpu, err = None, None
+    if orc is not None:
+        try:
+            orc.wait(timeout=1200)
+            oj = json.load(open(os.path.join(tmp, "oracle.json")))
+            xref, w = np.load(os.path.join(tmp, "xref.npy")), np.load(os.path.join(tmp, "w.npy"))
+            err = {"err_vs_oracle": rel_err(x_mixed, xref, w), "fp64_err_vs_oracle": rel_err(x_fp64, xref, w),
+                   "note": f"relative lumped-mass L2 of the bench's solutions (rtol {args.rtol:g}) against the "
+                           f"oracle's FP64 solve to {oj['reference_solve']['rtol']:g}"}
+            cpu = {k: oj[k] for k in ("value", "unit", "cores", "kind", "sample", "iters", "sec_per_solve")}
+            cpu["concurrent"] = oj.get("concurrent")
+        except Exception as e:       # the baseline is reported, never required
+            cpu = {"error": repr(e)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms_mixed), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-mg+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": sv.desc, "n_nodes": int(info.n_nodes),
+                   "n_free_dofs": int(n_free), "levels": int(info.levels), "hanging_nodes": int(info.n_hanging),
+                   "rtol": args.rtol, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}", "tail_levels": int(info.tail_levels),
+                   "tail_cluster": int(info.tail_cluster), "tuned_vcycle_ms": info.vcycle_ms,
+                   "col16_slices": int(info.col16_slices), "col32_slices": int(info.col32_slices)},
+        "iters": [s.iters for s in st_mixed], "rel_res": max(s.rel_res for s in st_mixed),
+        "fp64": {"value": world * n_free / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
+                 "iters": [s.iters for s in st64], "rel_res": max(s.rel_res for s in st64)},
+        "speedup_mixed_vs_fp64": statistics.mean(ms64) / statistics.mean(ms_mixed),
+        "bf16_values_ablation": {"value": world * n_free / (statistics.mean(ms16) * 1e-3),
+                                 "ms_per_step": statistics.mean(ms16), "iters": [s.iters for s in st16],
+                                 "rel_res": max(s.rel_res for s in st16),
+                                 "converged": all(s.status == 0 for s in st16)},
+        "err_vs_oracle": err["err_vs_oracle"] if err else None,
+        "fp64_err_vs_oracle": err["fp64_err_vs_oracle"] if err else None,
+        "err_note": err["note"] if err else None,
+        "setup_s": sv.setup_s,
+        "gpu_launches": int(sum(s.launches for s in st_mixed)),
+        "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": int(2 * 8 * h.n_dofs),
+                "d2h_bytes_per_step": int(8 * h.n_dofs), "ms_per_step": statistics.mean(e2e_ms)},
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "per_level_fp32_us": per_level,
+        "top_kernels_in_solve": top_table(prof),
+        "cpu_baseline": cpu,
+        "configs": configs,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
