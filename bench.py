@@ -327,23 +327,40 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- serving workload
-SERVE_2D = (16, 32, 64, 128, 256, 512, 1024)
-SERVE_3D = (8, 16, 32, 64, 96)
 SERVE_EPS = (1e-3, 1e-2, 1e-1, 1.0)
 
 
+def serve_sizes(lo, hi, mult, odd_max):
+    """Mesh sizes n = m 2^L (m odd <= odd_max) in [lo, hi] that are multiples
+    of `mult`: the macro grid is m^dim cells, so the coarsest level (and its
+    dense direct solve) stays small."""
+    out = set()
+    for m in range(1, odd_max + 1, 2):
+        n = m
+        while n <= hi:
+            if n >= lo and n % mult == 0:
+                out.add(n)
+            n *= 2
+    return tuple(sorted(out))
+
+
+SERVE_2D = serve_sizes(16, 1024, 8, 15)
+SERVE_3D = serve_sizes(8, 96, 4, 7)
+
+
 def _serve_mesh(dim, n):
-    if dim == 2:
-        return W.uniform_leaves(2, (1, 1), int(round(np.log2(n))))
-    if n == 96:
-        return W.uniform_leaves(3, (3, 3, 3), 5)
-    return W.uniform_leaves(3, (1, 1, 1), int(round(np.log2(n))))
+    m = n
+    while m % 2 == 0:
+        m //= 2
+    return W.uniform_leaves(dim, (m,) * dim, int(round(np.log2(n // m))))
 
 
 def serving_stream(n_req, rate, seed=W.MASTER_SEED):
     """Seeded request stream: arrival times (Poisson process), kind, size,
-    eps and RHS seed.  Sizes log-uniform 16..1024 (2D) / 8..96 (3D) and eps
-    log-uniform in [1e-3, 1], each rounded to the nearest catalogue value."""
+    eps and RHS seed.  Sizes log-uniform in 16..1024 (2D) / 8..96 (3D),
+    rounded to the nearest multiple of 8 (2D) / 4 (3D) whose odd factor is
+    small (SERVE_2D, SERVE_3D); eps log-uniform in [1e-3, 1], rounded to the
+    nearest power of ten so that operators are shared by requests."""
     rng = np.random.Generator(np.random.PCG64([seed, 4]))
     t = np.cumsum(rng.exponential(1.0 / rate, n_req))
     out = []
@@ -431,17 +448,31 @@ def run_serving(args):
         span = max(done_t.values()) - reqs[0][0] / rate_scale
         dofs = sum(reqs[k][1].info.n_free for k in range(len(reqs)))
         ok = all(stats[k][0] == 0 and stats[k][2] <= 1e-8 for k in stats)
+        iterated = all(stats[k][1] > 0 for k in stats)
         # the library's own submit-to-finish time (queue + device), without the client's polling
         lib = np.array([stats[k][3] for k in range(len(reqs))])
         return {"rate_req_s": args.rate * rate_scale, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                 "lib_p50_ms": float(np.percentile(lib, 50)), "lib_p99_ms": float(np.percentile(lib, 99)),
-                "dof_per_s": dofs / span, "span_s": span, "all_converged": ok}
+                "dof_per_s": dofs / span, "span_s": span, "all_converged": ok, "all_iterated": iterated}
 
     play(1.0)                                   # warm-up: graphs, pooled workspaces
     base = play(1.0)
+    mixed = [r[3].clone() for r in reqs]        # every result of the measured stream
     sweep = [play(s) for s in args.sweep]
     sizes = [r[1].info.n_free for r in reqs]
+    # verification: each result solved (iterations > 0, residual reached) and,
+    # on a seeded subset, bitwise equal to the same solve run alone
+    rng = np.random.Generator(np.random.PCG64([W.MASTER_SEED, 5]))
+    subset = sorted(rng.choice(len(reqs), size=min(64, len(reqs)), replace=False).tolist())
+    same = 0
+    for k in subset:
+        _, h, b, x = reqs[k]
+        x.zero_()
+        st = h.solve(b, x, rtol=1e-8, max_it=500, prec=B.MG_MIXED_FP32)
+        same += int(st.status == 0 and torch.equal(x, mixed[k]))
+    verified = {"all_converged": base["all_converged"], "all_iterated": base["all_iterated"],
+                "alone_equals_mix": f"{same}/{len(subset)}"}
     print(json.dumps({
         "metric": "serving p50/p99 latency and aggregate DoF/s (FP32-MG + FP64 Krylov, rtol 1e-8)",
         "value": base["dof_per_s"], "unit": "DoF/s", "n_gpus": 1, "steps": len(reqs), "warmup": len(reqs),
@@ -451,7 +482,7 @@ def run_serving(args):
                    "catalogue": {"2d": SERVE_2D, "3d": SERVE_3D, "eps": SERVE_EPS},
                    "operators_resident": len(hiers), "mean_dofs": float(np.mean(sizes)),
                    "setup_s": setup_s},
-        "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "all_converged": base["all_converged"],
+        "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "verified": verified,
         "lib_p50_ms": base["lib_p50_ms"], "lib_p99_ms": base["lib_p99_ms"],
         "sweep": sweep,
     }))

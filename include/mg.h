@@ -124,11 +124,13 @@ typedef struct {
                                   convection field at the finest nodes in the
                                   external order (see mg_mesh_nodes); read
                                   during mg_setup only                          */
-  double mass;                 /* POISSON, TRANSPORT: coefficient s >= 0 of an
-                                  added mass term s (u, v); s = 1/dt gives the
-                                  matrix of one backward-Euler step of the
-                                  time-dependent problem (Sec. 5.1).  With
-                                  SUPG the stabilisation also tests it:
+  double mass;                 /* POISSON, TRANSPORT, ELASTICITY: coefficient
+                                  s >= 0 of an added mass term s (u, v) (every
+                                  component); s = 1/dt gives the matrix of one
+                                  backward-Euler step of a first-order-in-time
+                                  problem (Sec. 5.1), s = 1/dt^2 that of
+                                  d_t^2 u + A u = f (Sec. 5.2).  With SUPG the
+                                  stabilisation also tests it:
                                   + sum_T delta_T s (u, beta.grad v)_T.
                                   0: stationary                                 */
 } mg_problem;
@@ -282,6 +284,26 @@ int mg_assemble_rhs(mg_hier* h, const double* f_nodal, const double* g_nodal, do
 int mg_time_steps(mg_hier* h, double* theta, const double* f, const double* g, int n_steps, double rtol,
                   int max_it, int prec, mg_stats* steps);
 
+/* Backward-Euler steps of the second-order-in-time problem d_t^2 u + A u = f
+ * (Sec. 5.2: elastodynamics d_t^2 u - div sigma(u) = f), written as the
+ * first-order system d_t u - v = 0, d_t v + A u = f in the unknowns (u, v).
+ * Eliminating v_n = (u_n - u_{n-1})/dt from the step's coupled equations
+ * leaves one system for u_n with the matrix M/dt^2 + A: the hierarchy's
+ * problem must have mass = 1/dt^2 (checked to 1e-12 relative).  For
+ * n = 1..n_steps:
+ *   b_n = H^T F ((u_{n-1}/dt + v_{n-1})/dt + f_n), Dirichlet data g_n of u
+ *         eliminated as in mg_assemble_rhs;
+ *   u_n = solution of (M/dt^2 + A) u_n = b_n from u_{n-1} (warm start);
+ *   v_n = (u_n - u_{n-1}) / dt on every dof (Dirichlet dofs included, so
+ *         v follows the data's difference quotient there).
+ * u, v: device, n_nodes * nc doubles each; in: u_0, v_0; out: u_n, v_n.
+ * f, g: as in mg_time_steps (NULL: no source / homogeneous data).
+ * Returns MG_OK when every step converged, else the first failing step's
+ * status (u and v then hold that step's iterate).  Buffers come from the
+ * hierarchy's solve workspace; nothing is allocated. */
+int mg_time_steps2(mg_hier* h, double* u, double* v, const double* f, const double* g, int n_steps, double dt,
+                   double rtol, int max_it, int prec, mg_stats* steps);
+
 /* Krylov solve (CG / BiCGStab / GMRES per opts.krylov) preconditioned by one
  * V-cycle per iteration (Sec. 4.1.5).  b, x: device, n_nodes * nc doubles,
  * caller-owned.  x in: initial guess; out: solution on all nodes, hanging
@@ -357,9 +379,12 @@ int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms);
 /* Per-kernel device time of one solve.  Runs the solve of mg_solve (same
  * kernels in the same order, so x and stats are bitwise the same) but issues
  * one Krylov iteration at a time as a plain CUDA graph with a CUDA
- * event-record node after every kernel (and one before the first): a
- * kernel's interval runs from the end of the previous kernel to its own end,
- * so the intervals of an iteration add up to its device time.  The graph
+ * event-record node before the first kernel and after every run of
+ * consecutive launches of the same kernel on the same level (e.g. the
+ * smoothing sweeps of one level, which follow each other as in mg_solve with
+ * no event node between them): an interval runs from the end of the previous
+ * run to the end of its own, so the intervals of an iteration add up to its
+ * device time and a run's launches share one interval.  The graph
  * starts with an empty kernel (`k_prof_empty`, level -2, not part of the
  * solve and not counted in stats->launches) whose interval is the floor of
  * any interval: launch latency plus event overhead, which the chained kernels

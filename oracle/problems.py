@@ -79,7 +79,11 @@ def element(prob: Problem, dim: int):
         return el
     if prob.kind == ELASTICITY:
         assert dim == 3
-        return lambda h: fem.elasticity_element(h, prob.mu, prob.lam)
+        if s == 0.0:
+            return lambda h: fem.elasticity_element(h, prob.mu, prob.lam)
+        # s (u, v) for vector fields: the scalar mass matrix on every component
+        return lambda h: (fem.elasticity_element(h, prob.mu, prob.lam)
+                          + s * np.kron(fem.scalar_element(3, h, "mass"), np.eye(3)))
     raise ValueError(prob.kind)
 
 

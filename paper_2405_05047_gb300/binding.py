@@ -131,6 +131,8 @@ _SIGS = {
     "mg_restrict_static": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_time_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                 C.c_int, C.POINTER(MgStats)]),
+    "mg_time_steps2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                 C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
 }
 
 
@@ -352,6 +354,16 @@ def mg_time_steps(h, theta, f, g, n_steps, rtol, max_it, prec=MG_FP64):
     return rc, list(sts)[:n_steps]
 
 
+def mg_time_steps2(h, u, v, f, g, n_steps, dt, rtol, max_it, prec=MG_FP64):
+    """Backward-Euler steps of d_t^2 u + A u = f in place on (u, v); f, g:
+    (n_steps, n_dofs) device arrays or None.  Returns (status, [MgStats])."""
+    sts = (MgStats * max(n_steps, 1))()
+    rc = load_library().mg_time_steps2(h, _ptr(u), _ptr(v), _ptr(f) if f is not None else None,
+                                       _ptr(g) if g is not None else None, n_steps, dt, rtol, max_it, prec, sts)
+    _check(rc, allow=SOLVE_OUTCOMES)
+    return rc, list(sts)[:n_steps]
+
+
 def mg_vcycle(h, r, z, prec=MG_FP64):
     return _check(load_library().mg_vcycle(h, _ptr(r), _ptr(z), prec))
 
@@ -454,6 +466,9 @@ class Hierarchy:
 
     def time_steps(self, theta, f, g, n_steps, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_time_steps(self.handle, theta, f, g, n_steps, rtol, max_it, prec)
+
+    def time_steps2(self, u, v, f, g, n_steps, dt, rtol=1e-10, max_it=200, prec=MG_FP64):
+        return mg_time_steps2(self.handle, u, v, f, g, n_steps, dt, rtol, max_it, prec)
 
     def solve_profiled(self, b, x, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_solve_profiled(self.handle, b, x, rtol, max_it, prec)

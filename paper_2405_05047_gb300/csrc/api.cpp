@@ -424,6 +424,44 @@ int mg_time_steps(mg_hier* h, double* theta, const double* f, const double* g, i
   return rc;
 }
 
+int mg_time_steps2(mg_hier* h, double* u, double* v, const double* f, const double* g, int n_steps, double dt,
+                   double rtol, int max_it, int prec, mg_stats* steps) {
+  if (!h || !u || !v || n_steps < 0 || !(dt > 0) || !(rtol > 0) || max_it < 1)
+    return fail(MG_ERR_INVALID, "bad argument");
+  if (!(std::fabs(h->prob.mass * dt * dt - 1.0) <= 1e-12))
+    return fail(MG_ERR_INVALID, "second-order steps need a problem with mass = 1/dt^2");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  CU(cudaSetDevice(h->ctx->device));
+  cudaStream_t s = h->ctx->stream;
+  Workspace& w = *h->ws0;
+  const int64_t n = h->n_dofs;
+  const double inv_dt = 1.0 / dt;
+  for (int k = 0; k < n_steps; ++k) {
+    const double* fk = f ? f + (int64_t)k * n : nullptr;
+    const double* gk = g ? g + (int64_t)k * n : nullptr;
+    launch_step_load2(n, inv_dt, u, v, fk, w.t, s);   // v now holds -u_{n-1}/dt
+    launch_rhs(h->F.v, h->nc, w.t, h->fixmask, h->dirmask, gk, w.bi, s);
+    if (gk) launch_lift(h->Lift.v, h->nc, gk, w.bi, s);
+    mg_stats st{};
+    rc = solve_start(h, w, w.bi, false, u, false, u, false, rtol, max_it, prec, s);
+    while (rc == MG_OK || rc == MG_PENDING) {
+      CU(cudaEventSynchronize(w.ev1));
+      rc = solve_check(h, w, s, &st);
+      if (rc != MG_PENDING) break;
+    }
+    launch_step_velocity(n, inv_dt, u, v, s);           // v = (u_n - u_{n-1}) / dt
+    h->launch_count += gk ? 4 : 3;
+    st.launches += gk ? 4 : 3;
+    if (steps) steps[k] = st;
+    if (rc != MG_OK) break;
+  }
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  return rc;
+}
+
 // "k_smooth<float, float, 1, false, 1>" from the kernel's symbol: demangled,
 // without the return type, namespace and parameter list.
 static void kernel_label(const void* fn, char* out, size_t cap) {

@@ -980,7 +980,8 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
   }
   if (prof) {
     // per-kernel timing: one iteration captured as a plain graph (an
-    // event-record node after every kernel), run once per iteration, status polled
+    // event-record node after every run of the same kernel), run once per
+    // iteration, status polled
     cudaStream_t cs;
     CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     prof->begin_capture();
@@ -994,6 +995,7 @@ int enqueue_round(mg_hier* h, Workspace& w, cudaStream_t s) {
       t_prof_level = lv;
       before = h->launch_count;
       enqueue_iteration(h, w, method, prec, 0ull, cs);
+      prof->end_capture();
       e = cudaStreamEndCapture(cs, &g1);
     }
     const int64_t per_iter = h->launch_count - before;
@@ -1062,6 +1064,11 @@ void EventProfiler::before(const void* fn, cudaStream_t s) {
   cudaStreamIsCapturing(s, &cap);
   pending = false;
   if (cap == cudaStreamCaptureStatusActive) {
+    if (run_open && graph_recs.back().fn == fn && graph_recs.back().level == t_prof_level) {
+      graph_recs.back().n += 1;          // the run goes on: no event between its launches
+      return;
+    }
+    close_run();
     const bool first = graph_recs.empty();
     if (graph_used + (first ? 2 : 1) > graph_pool.size()) {
       ++dropped;
@@ -1076,6 +1083,9 @@ void EventProfiler::before(const void* fn, cudaStream_t s) {
     }
     r.e1 = graph_pool[graph_used++];
     graph_recs.push_back(r);
+    run_open = true;                     // its end event follows the run's last launch
+    run_stream = s;
+    return;
   } else {
     Rec r{fn, t_prof_level, nullptr, nullptr};
     if (cudaEventCreate(&r.e0) != cudaSuccess) return;
@@ -1092,12 +1102,15 @@ void EventProfiler::before(const void* fn, cudaStream_t s) {
 }
 
 void EventProfiler::after(cudaStream_t s) {
-  if (!pending) return;
+  if (!pending) return;                  // captured launches: the run's end event comes later
   pending = false;
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cap);
-  if (cap == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(graph_recs.back().e1, s, cudaEventRecordExternal);
-  else cudaEventRecord(direct_recs.back().e1, s);
+  cudaEventRecord(direct_recs.back().e1, s);
+}
+
+void EventProfiler::close_run() {
+  if (!run_open) return;
+  run_open = false;
+  cudaEventRecordWithFlags(graph_recs.back().e1, run_stream, cudaEventRecordExternal);
 }
 
 static void add_recs(std::map<std::pair<const void*, int>, std::pair<int64_t, double>>& acc,
@@ -1106,7 +1119,7 @@ static void add_recs(std::map<std::pair<const void*, int>, std::pair<int64_t, do
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) continue;
     auto& a = acc[{r.fn, r.level}];
-    a.first += 1;
+    a.first += r.n;
     a.second += ms;
   }
 }

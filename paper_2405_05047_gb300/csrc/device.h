@@ -81,8 +81,10 @@ struct Workspace {
 
 // Per-kernel timing of a solve (mg_solve_profiled).  Launches made while a
 // stream is being captured use a fixed pool of events and are timed as a
-// chain: one event after every kernel (and one before the first), so a
-// kernel's interval runs from the end of the previous kernel to its own end
+// chain: one event before the first kernel and one after every run of
+// consecutive launches of the same kernel on the same level (the launches of
+// a run follow each other as in the solve, with no event node between them),
+// so an interval runs from the end of the previous run to the end of its own
 // and the intervals add up to the captured iteration.  The graph re-records
 // the same events on every run (collect_graph after each).  Other launches
 // are bracketed by events of their own, read once at the end.  Results are
@@ -92,11 +94,14 @@ struct EventProfiler : LaunchProfiler {
     const void* fn;
     int level;
     cudaEvent_t e0, e1;
+    int64_t n = 1;               // launches in the interval (a run of the same kernel and level)
   };
   std::vector<cudaEvent_t> graph_pool, direct_pool;
   size_t graph_used = 0;
   std::vector<Rec> graph_recs, direct_recs;
   bool pending = false;          // the last before() recorded a start event
+  bool run_open = false;         // the captured run's end event is not recorded yet
+  cudaStream_t run_stream = nullptr;
   int64_t dropped = 0;           // launches beyond the graph pool
   std::map<std::pair<const void*, int>, std::pair<int64_t, double>> acc;   // launches, ms
   int init(size_t graph_events);
@@ -105,7 +110,10 @@ struct EventProfiler : LaunchProfiler {
   void begin_capture() {
     graph_used = 0;
     graph_recs.clear();
+    run_open = false;
   }
+  void close_run();              // record the end event of the open captured run
+  void end_capture() { close_run(); }   // before the capture ends
   void collect_graph();          // after the graph's run completed
   void collect_direct();         // after every direct launch completed
   ~EventProfiler() override;

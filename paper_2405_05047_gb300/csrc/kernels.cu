@@ -819,6 +819,29 @@ __global__ void k_step_load(int64_t n, double s, const double* __restrict__ thet
     out[i] = f ? fma(s, theta[i], f[i]) : s * theta[i];
 }
 
+// Second-order-in-time steps (d_t^2 u + A u = f as the first-order system in
+// (u, v), backward Euler): the step's nodal load (u/dt + v)/dt + f, and v
+// replaced by -u/dt so that k_step_velocity can finish v_n = (u_n - u_{n-1})/dt
+// after the solve without another buffer.
+__global__ void k_step_load2(int64_t n, double inv_dt, const double* __restrict__ u, double* __restrict__ v,
+                             const double* __restrict__ f, double* __restrict__ out) {
+  pdl_wait();
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+    const double ui = u[i];
+    const double l = fma(ui, inv_dt, v[i]) * inv_dt;
+    out[i] = f ? l + f[i] : l;
+    v[i] = -ui * inv_dt;
+  }
+}
+
+__global__ void k_step_velocity(int64_t n, double inv_dt, const double* __restrict__ u, double* __restrict__ v) {
+  pdl_wait();
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads)
+    v[i] = fma(u[i], inv_dt, v[i]);
+}
+
 // ------------------------------------------------------------------ Krylov
 // All Krylov kernels run one thread per node (nc dofs) or per vector entry.
 // A kernel that produces dot products writes one partial per block; the block
@@ -1790,6 +1813,13 @@ void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t
 void launch_copy_fixed(int64_t n, int nc, const uint8_t* fixmask, const double* b, const double* xin, double* x,
                        cudaStream_t s) {
   launch(k_copy_fixed, grid_for_rows(n), s, n, nc, fixmask, b, xin, x);
+}
+void launch_step_load2(int64_t n, double inv_dt, const double* u, double* v, const double* f, double* out,
+                       cudaStream_t s) {
+  launch(k_step_load2, grid_for_rows(n), s, n, inv_dt, u, v, f, out);
+}
+void launch_step_velocity(int64_t n, double inv_dt, const double* u, double* v, cudaStream_t s) {
+  launch(k_step_velocity, grid_for_rows(n), s, n, inv_dt, u, v);
 }
 void launch_step_load(int64_t n, double sc, const double* theta, const double* f, double* out, cudaStream_t s) {
   launch(k_step_load, grid_for_rows(n), s, n, sc, theta, f, out);

@@ -177,6 +177,11 @@ void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixma
 void launch_lift(const SellView& L, int nc, const double* g, double* b, cudaStream_t s);
 // out = sc * theta + f (f NULL: out = sc * theta), n entries
 void launch_step_load(int64_t n, double sc, const double* theta, const double* f, double* out, cudaStream_t s);
+// out = (u / dt + v) / dt + f, then v = -u / dt (f NULL: no source)
+void launch_step_load2(int64_t n, double inv_dt, const double* u, double* v, const double* f, double* out,
+                       cudaStream_t s);
+// v += u / dt
+void launch_step_velocity(int64_t n, double inv_dt, const double* u, double* v, cudaStream_t s);
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s);
 void launch_copy_fixed(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, const double* xin,
                        double* x, cudaStream_t s);

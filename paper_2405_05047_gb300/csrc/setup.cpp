@@ -477,7 +477,8 @@ std::vector<double> element_matrix(const mg_problem& P, int dim, const double* h
         for (int i = 0; i < nc; ++i)
           for (int j = 0; j < nc; ++j)
             K[(A * nc + i) * w + B * nc + j] =
-                P.mu * ((i == j ? lap : 0.0) + I.G(j, i, A, B)) + P.lambda * I.G(i, j, A, B);
+                P.mu * ((i == j ? lap : 0.0) + I.G(j, i, A, B)) + P.lambda * I.G(i, j, A, B) +
+                (i == j ? P.mass * I.G(-1, -1, A, B) : 0.0);   // s (u, v) per component
       }
     return K;
   }
@@ -1048,8 +1049,8 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
   if (prob.kind == MG_ELASTICITY && mesh.dim != 3) return Status::err(MG_ERR_INVALID, "elasticity needs dim = 3");
   if (prob.kind == MG_TRANSPORT && !(prob.eps > 0)) return Status::err(MG_ERR_INVALID, "transport needs eps > 0");
   if (!(prob.mass >= 0.0) || !std::isfinite(prob.mass)) return Status::err(MG_ERR_INVALID, "mass must be finite and >= 0");
-  if (prob.mass != 0.0 && prob.kind != MG_POISSON && prob.kind != MG_TRANSPORT)
-    return Status::err(MG_ERR_INVALID, "a mass term is supported for POISSON and TRANSPORT");
+  if (prob.mass != 0.0 && prob.kind == MG_OSEEN)
+    return Status::err(MG_ERR_INVALID, "OSEEN takes its mass term from dt, not from mass");
   const bool oseen = prob.kind == MG_OSEEN;
   if (oseen) {
     if (mesh.dim != 2) return Status::err(MG_ERR_INVALID, "oseen needs dim = 2");

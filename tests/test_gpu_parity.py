@@ -546,7 +546,7 @@ def test_direct_launch_mode_equals_graph(ctx):
 @pytest.mark.parametrize("name", ["td_adaptive", "oseen"])
 def test_profiled_solve_equals_solve(ctx, name):
     """mg_solve_profiled runs the kernels of mg_solve in the same order (one
-    graph per iteration, event nodes between the kernels): the same bits and
+    graph per iteration, event nodes between runs of the same kernel): the same bits and
     iterations; every launch of the solve is in its table, and the finest
     level's sweeps appear with three launches per V-cycle (V(2,2), the first
     sweep from zero being a kernel of its own)."""

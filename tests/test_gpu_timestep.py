@@ -137,3 +137,80 @@ def test_time_steps_zero_steps_and_homogeneous_data(ctx):
         assert all(b < a * (1.0 - 1e-3) for a, b in zip(norms[:-1], norms[1:])), norms
     finally:
         h.free()
+
+
+# ---------------------------------------------------------------- elastodynamics (Sec. 5.2)
+def el_problem(dt, dirichlet=(0x3F,)):
+    prob = PB.Problem(PB.ELASTICITY, mu=W.EL_MU, lam=W.EL_LAMBDA, dirichlet=dirichlet)
+    pb = B.make_problem(kind=B.MG_ELASTICITY, mu=W.EL_MU, lam=W.EL_LAMBDA, dirichlet=dirichlet, mass=1.0 / dt ** 2)
+    return prob, pb
+
+
+@pytest.mark.parametrize("prec", [B.MG_FP64, B.MG_MIXED_FP32])
+def test_time_steps2_match_first_order_oracle(ctx, prec):
+    """Sec. 5.2 on the edge-refined mesh (level 3, 4129 nodes, hanging nodes):
+    the library solves the step for u with the matrix M/dt^2 + K and recovers
+    v; the oracle solves the coupled first-order system in (u, v).  Every
+    step agrees in u and v (relative lumped-mass L2)."""
+    dt, steps = W.EL_DT, 4
+    lm = W.elasticity_adaptive("edge", 3)
+    prob, pb = el_problem(dt)
+    m = q1mesh(lm)
+    nd = 3 * m.n_nodes
+    f = np.tile(W.EL_F, m.n_nodes)
+    S, ref = TS.run_first_order(m, prob, dt, np.zeros(nd), np.zeros(nd), lambda t: f, lambda t: None, steps)
+    w = np.repeat(np.asarray(S.F.sum(axis=1)).ravel(), 3)
+    h = G.Hierarchy(ctx, lm, pb, B.make_opts(krylov=B.MG_CG))
+    try:
+        assert np.array_equal(h.coords(), m.coords) and h.info.n_hanging > 0
+        u = torch.zeros(nd, device="cuda", dtype=torch.float64)
+        v = torch.zeros_like(u)
+        fd = dev(np.tile(f, (steps, 1)))
+        tol = 1e-8 if prec == B.MG_FP64 else 1e-7
+        for k in range(steps):
+            rc, sts = h.time_steps2(u, v, fd[k], None, 1, dt, rtol=1e-11, max_it=200, prec=prec)
+            assert rc == 0 and sts[0].iters > 0
+            for got, want in ((u, ref[k][0]), (v, ref[k][1])):
+                e = got.cpu().numpy() - want
+                rel = np.sqrt(np.sum(w * e * e) / np.sum(w * want * want))
+                assert rel <= tol, (k, rel)
+    finally:
+        h.free()
+
+
+def test_time_steps2_linear_motion_exact(ctx):
+    """u = a + C x + d t, v = d, f = 0, Dirichlet data u(t_n) on every face,
+    face-refined mesh with hanging nodes: reproduced at every node."""
+    dt, steps = W.EL_DT, 3
+    lm = W.elasticity_adaptive("face", 3)
+    _, pb = el_problem(dt)
+    h = G.Hierarchy(ctx, lm, pb, B.make_opts(krylov=B.MG_CG))
+    try:
+        xyz = h.coords()
+        a = np.array([0.1, -0.2, 0.05])
+        C = np.array([[0.3, 0.1, -0.2], [0.0, -0.4, 0.25], [0.15, 0.2, 0.1]])
+        d = np.array([0.7, -0.3, 0.4])
+        lin = lambda t: (a + xyz @ C.T + d * t).ravel()   # noqa: E731
+        u = dev(lin(0.0))
+        v = dev(np.tile(d, h.n_nodes))
+        g = dev(np.stack([lin((k + 1) * dt) for k in range(steps)]))
+        rc, sts = h.time_steps2(u, v, None, g, steps, dt, rtol=1e-12, max_it=300)
+        assert rc == 0
+        assert np.abs(u.cpu().numpy() - lin(steps * dt)).max() <= 1e-9
+        assert np.abs(v.cpu().numpy() - np.tile(d, h.n_nodes)).max() <= 1e-6
+    finally:
+        h.free()
+
+
+def test_time_steps2_need_the_matching_mass(ctx):
+    _, pb = el_problem(0.05)
+    h = G.Hierarchy(ctx, W.elasticity_adaptive("vertex", 2), pb)
+    try:
+        u = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+        with pytest.raises(G.MGError) as e:
+            h.time_steps2(u, torch.zeros_like(u), None, None, 1, 0.025)
+        assert e.value.code == -1
+        rc, _ = h.time_steps2(u, torch.zeros_like(u), None, None, 1, 0.05)
+        assert rc == 0
+    finally:
+        h.free()

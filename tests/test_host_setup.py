@@ -36,6 +36,11 @@ CASES = {
     "td_step_supg_adaptive": (lambda: W.td_adaptive(rounds=3, gamma=1.0),
                               PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5), mass=10.0),
                               dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5), mass=10.0)),
+    "elasticity_step_edge": (lambda: W.elasticity_adaptive("edge", 2),
+                             PB.Problem(PB.ELASTICITY, mu=W.EL_MU, lam=W.EL_LAMBDA, dirichlet=(0x3F,),
+                                        mass=1.0 / W.EL_DT ** 2),
+                             dict(kind=B.MG_ELASTICITY, mu=W.EL_MU, lam=W.EL_LAMBDA, dirichlet=(0x3F,),
+                                  mass=1.0 / W.EL_DT ** 2)),
     "poisson_mass": (lambda: W.uniform_leaves(2, (1, 1), 4), PB.Problem(PB.POISSON, mass=3.0),
                      dict(kind=B.MG_POISSON, mass=3.0)),
     "channel": (lambda: W.oseen_channel(uniform=1, rounds=3),

@@ -239,13 +239,7 @@ def test_uniform_dof_counts_match_paper():
 
 
 def _table2_mesh(kind, nlev):
-    m = W.uniform_leaves(3, (1, 1, 1), 3)
-    ax = {"face": [0], "edge": [0, 1], "vertex": [0, 1, 2]}[kind]
-    for r in range(1, nlev):
-        lo, hi, _ = W._cell_box(m)
-        mark = (m.level == m.level.max()) & np.all(hi[:, ax] <= 2.0 ** -r + 1e-12, axis=1)
-        m = W.refine(m, mark)
-    return q1mesh(m)
+    return q1mesh(W.elasticity_adaptive(kind, nlev))
 
 
 @pytest.mark.parametrize("kind", ["face", "edge", "vertex"])

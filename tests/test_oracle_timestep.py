@@ -87,3 +87,59 @@ def test_mass_term_adds_scaled_mass_matrix():
     for j, v in zip(row.indices, row.data):
         dist = int(np.abs(m.X[j] - m.X[i]).sum())
         assert v == pytest.approx(s * {0: 16, 1: 4, 2: 1}[dist] * h * h / 36, rel=1e-13)
+
+
+# ---------------------------------------------------------------- elastodynamics (Sec. 5.2)
+def _el_prob(dirichlet=(0x3F,)):
+    return PB.Problem(PB.ELASTICITY, mu=W.EL_MU, lam=W.EL_LAMBDA, dirichlet=dirichlet)
+
+
+def test_first_order_elasticity_exact_for_linear_space_time_motion():
+    """u = a + C x + d t (v = d) has a constant stress and no acceleration, so
+    with f = 0 and Dirichlet data u(t_n) on every face the backward-Euler
+    steps of the first-order system reproduce it at every node, hanging ones
+    included, on the edge-refined mesh of Sec. 5.2."""
+    m = q1mesh(W.elasticity_adaptive("edge", 2))
+    assert m.hanging.sum() > 0
+    xyz = m.coords
+    a = np.array([0.1, -0.2, 0.05])
+    C = np.array([[0.3, 0.1, -0.2], [0.0, -0.4, 0.25], [0.15, 0.2, 0.1]])
+    d = np.array([0.7, -0.3, 0.4])
+    lin = lambda t: (a + xyz @ C.T + d * t).ravel()   # noqa: E731
+    dt = 0.025
+    _, out = TS.run_first_order(m, _el_prob(), dt, lin(0.0), np.tile(d, m.n_nodes), lambda t: None, lin, 4)
+    for n, (u, v) in enumerate(out, 1):
+        assert np.abs(u - lin(n * dt)).max() <= 1e-11
+        # v carries the rounding of the stiff block system (K ~ 1e4 h against M / dt ~ 40 h^3)
+        assert np.abs(v - np.tile(d, m.n_nodes)).max() <= 1e-5
+
+
+def test_first_order_elasticity_energy_decays():
+    """f = 0, homogeneous data: backward Euler dissipates the energy
+    (v, v)_M / 2 + (K u, u) / 2 in every step."""
+    m = q1mesh(W.elasticity_adaptive("vertex", 2))
+    prob = _el_prob()
+    xyz = m.coords
+    bump = np.prod(np.sin(np.pi * xyz), axis=1)
+    u0 = np.stack([bump, 0.5 * bump, -bump], axis=1).ravel() * 1e-3
+    S, out = TS.run_first_order(m, prob, W.EL_DT, u0, np.zeros_like(u0), lambda t: None, lambda t: None, 5)
+    from oracle import fem
+    M3 = fem.expand(S.F, 3)
+    K = S.A_raw
+    energy = [0.5 * u0 @ (K @ u0)] + [0.5 * v @ (M3 @ v) + 0.5 * u @ (K @ u) for u, v in out]
+    assert all(b < a for a, b in zip(energy[:-1], energy[1:])), energy
+
+
+def test_first_order_elasticity_tends_to_the_static_solution():
+    """With a constant load the backward-Euler iteration is damped and its
+    fixed point is the static problem K u = F: after many long steps u equals
+    the static solution of the (pinned) elasticity operator."""
+    m = q1mesh(W.elasticity_adaptive("vertex", 2))
+    prob = _el_prob()
+    f = np.tile(W.EL_F, m.n_nodes)
+    S, out = TS.run_first_order(m, prob, 2.0, np.zeros(3 * m.n_nodes), np.zeros(3 * m.n_nodes),
+                                lambda t: f, lambda t: None, 60)
+    import scipy.sparse.linalg as spl
+    ustat = S.H @ spl.spsolve(S.A.tocsc(), S.rhs(f))
+    u = out[-1][0]
+    assert np.abs(u - ustat).max() <= 1e-8 * np.abs(ustat).max()

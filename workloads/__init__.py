@@ -326,3 +326,28 @@ def td_uniform(n: int) -> LeafMesh:
     m = uniform_leaves(2, (1, 1), int(round(math.log2(n))))
     m.meta.update(workload=f"td_timedep_{n}x{n}")
     return m
+
+
+# ---------------------------------------------------------------------------
+# time-dependent linear elasticity on adaptive hex meshes (the paper's Sec. 5.2)
+# ---------------------------------------------------------------------------
+EL_LAMBDA = 8.0e4           # Lame parameters
+EL_MU = 2.0e4
+EL_F = (0.0, -1.0, 0.0)     # body force
+EL_DT = 0.025               # backward-Euler step
+EL_STEPS = 100              # T = 2.5
+
+
+def elasticity_adaptive(kind: str, levels: int) -> LeafMesh:
+    """Sec. 5.2 meshes: the uniform 8^3 grid of the unit cube (mesh level 1),
+    then levels-1 rounds that refine every finest cell lying within 2^-r of
+    the face x = 0 ("face"), the edge x = y = 0 ("edge") or the vertex 0
+    ("vertex").  Node counts match Table "table:ndofs"."""
+    m = uniform_leaves(3, (1, 1, 1), 3)
+    ax = {"face": [0], "edge": [0, 1], "vertex": [0, 1, 2]}[kind]
+    for r in range(1, levels):
+        _, hi, _ = _cell_box(m)
+        mark = (m.level == m.level.max()) & np.all(hi[:, ax] <= 2.0 ** -r + 1e-12, axis=1)
+        m = refine(m, mark)
+    m.meta.update(workload=f"elasticity_{kind}_l{levels}")
+    return m
