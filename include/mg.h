@@ -159,7 +159,13 @@ typedef struct {
                                   values rounded to BF16: an ablation)        */
   int autotune;                /* 1 (default): at setup, time V-cycles over
                                   tail thresholds x cluster sizes and keep the
-                                  fastest (cached per hierarchy shape)        */
+                                  fastest (cached per hierarchy shape); and per
+                                  level of >= 2048 rows time the FP32 sweep over
+                                  SELL windows {0, 256, 1024} x 16-bit columns
+                                  {off, on} and keep the fastest (cached per
+                                  level shape; only where sell_sigma and col16
+                                  are automatic).  Results do not depend on
+                                  either choice.                              */
   double inner_rtol;           /* > 0: defect correction -- every round runs
                                   the Krylov method until its residual fell by
                                   this factor (or reached rtol), then the FP64
@@ -203,6 +209,12 @@ typedef struct {
                                            operator: nc*nc, or 6 for 3x3 blocks of
                                            the velocity-pressure pattern
                                            [[a,0,g1],[0,a,g2],[d1,d2,c]]          */
+  int64_t level_sigma[32];              /* SELL-C-sigma window of the level
+                                           operator (0: rows in node order); with
+                                           opts.autotune it and level_col16 are
+                                           the fastest of a timed set for the FP32
+                                           sweep (both keep every row's summation
+                                           order: no result bit depends on them)  */
 } mg_info;
 
 typedef struct {

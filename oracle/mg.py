@@ -9,7 +9,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   first completed by H (Sec. 2.2), and rows/columns of constrained dofs are
   zero: P_eff = Z_f E H_c Z_c.
 * Smoother (Sec. 4.1.4): x <- x + omega S (b - A x), S = D^{-1} (Jacobi) or
-  the inverse of the n_c x n_c nodal diagonal blocks (block Jacobi).
+  the inverse of the n_c x n_c nodal diagonal blocks (block Jacobi), or the
+  additive cell-patch Vanka matrix (``vanka_matrix``; Sec. 6 names Vanka
+  smoothers as the next step) on the levels with >= vanka_rows unknowns.
 * Coarse problem: a direct solve A_0^{-1} b_0 (the coarse-mesh problem of the
   multigrid cycle, Sec. 2.2), here LU with partial pivoting in FP64.
 * Level operators: rediscretisation of the same form on every level of the
@@ -94,6 +96,33 @@ class Level:
                              shape=self.A.shape).tocsr()
 
 
+def vanka_matrix(mesh, A, nc):
+    """The additive cell-patch Vanka smoother as a matrix:
+    S = W sum_T P_T A_T^{-1} P_T^T, with A_T = A restricted to the 2^d nc
+    unknowns of the vertices of cell T (every component; constrained rows and
+    columns of A are identity rows, so fixed unknowns stay decoupled) and
+    W = diag(1 / m_i), m_i the number of cells that contain node i.  The
+    paper names Vanka smoothers as the next step for saddle-point problems
+    (Sec. 6); one cell's vertices form one local problem."""
+    A = A.tocsr()
+    cn = np.asarray(mesh.cell_nodes)                  # (n_cells, 2^d), x fastest
+    ncell, nv = cn.shape
+    k = nv * nc
+    dofs = (cn[:, :, None] * nc + np.arange(nc)[None, None, :]).reshape(ncell, k)
+    AT = np.zeros((ncell, k, k))
+    idx = np.arange(ncell)
+    for a in range(k):
+        rows = A[dofs[:, a]]
+        for b in range(k):
+            AT[:, a, b] = np.asarray(rows[idx, dofs[:, b]]).ravel()
+    inv = np.linalg.inv(AT)
+    m = np.bincount(cn.ravel(), minlength=mesh.n_nodes).astype(np.float64)
+    R = np.repeat(dofs, k, axis=1).ravel()
+    C = np.tile(dofs, (1, k)).ravel()
+    S = sp.csr_matrix((inv.ravel(), (R, C)), shape=A.shape)
+    return (sp.diags(np.repeat(1.0 / m, nc)) @ S).tocsr()
+
+
 def lambda_max_power(S, A, fixed, iters=20):
     """Largest eigenvalue magnitude of S A by `iters` power iterations
     w = S A v, lambda = |w| / |v|, v = w / |w|, from the start vector
@@ -117,7 +146,8 @@ class Hierarchy:
     iterations; lambda_max(D^-1 A) = 1.5 for the Q1 Laplacian, where this
     rule gives 0.8 as well)."""
 
-    def __init__(self, leafmesh, prob, min_level=None, max_levels=0, omega=None, nu1=2, nu2=2):
+    def __init__(self, leafmesh, prob, min_level=None, max_levels=0, omega=None, nu1=2, nu2=2,
+                 smoother="jacobi", vanka_rows=0, vanka_omega=1.0):
         patch = prob.kind == PB.OSEEN   # LPS patches: keep every level a patch mesh
         if min_level is None:
             min_level = max(M.default_min_level(leafmesh.macro), 1 if patch else 0)
@@ -141,7 +171,12 @@ class Hierarchy:
             lf.P.eliminate_zeros()
             lf.R = lf.P.T.tocsr()
             del E
-        for lv in self.levels:
+        for i, lv in enumerate(self.levels):
+            lv.vanka = smoother == "vanka" and i > 0 and lv.A.shape[0] >= vanka_rows
+            if lv.vanka:          # cell-patch Vanka, damping vanka_omega
+                lv.S = vanka_matrix(lv.mesh, lv.A, nc)
+                lv.omega = float(vanka_omega)
+                continue
             lv.S = lv.smoother_matrix()
             if omega is not None:
                 lv.omega = float(omega)

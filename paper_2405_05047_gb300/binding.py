@@ -72,7 +72,7 @@ class MgInfo(C.Structure):
                 ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
                 ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64),
                 ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32),
-                ("level_block_values", C.c_int * 32)]
+                ("level_block_values", C.c_int * 32), ("level_sigma", C.c_int64 * 32)]
 
 
 class MgStats(C.Structure):

@@ -320,6 +320,7 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
   for (int l = 0; l < h->nlev && l < 32; ++l) {
     info->level_omega[l] = h->L[l].omega;
     info->level_block_values[l] = h->level_block_values[l];
+    info->level_sigma[l] = h->level_sigma[l];
   }
   return MG_OK;
 }

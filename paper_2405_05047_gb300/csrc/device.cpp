@@ -176,7 +176,7 @@ bool velocity_pressure_pattern(const BlockCSR& M) {
 // also store 16-bit column offsets.
 template <typename VT>
 int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, bool idx16 = false,
-                bool pat6 = false) {
+                bool pat6 = false, std::vector<Alloc>* list = nullptr, size_t* list_bytes = nullptr) {
   std::vector<int64_t> sptr;
   std::vector<int32_t> col;
   std::vector<VT> val;
@@ -187,10 +187,11 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, 
     std::vector<int64_t> flagged;
     pack_col16(sptr, col, flagged, col16);
     sptr.swap(flagged);
-    for (size_t k = 0; k + 1 < sptr.size(); ++k) {
-      if (sptr[k] & 1) h->col32_slices++;
-      else h->col16_slices++;
-    }
+    if (!list)
+      for (size_t k = 0; k + 1 < sptr.size(); ++k) {
+        if (sptr[k] & 1) h->col32_slices++;
+        else h->col16_slices++;
+      }
   }
   auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t b_sptr = sptr.size() * 8, b_col = col.size() * 4, b_c16 = col16.size() * 2,
@@ -198,7 +199,8 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, 
   // 16-bit columns and values adjacent: the part a sweep streams
   const size_t o_c16 = 0, o_val = r256(b_c16), o_col = o_val + r256(b_val), o_sptr = o_col + r256(b_col),
                o_perm = o_sptr + r256(b_sptr), total = o_perm + r256(b_perm);
-  unsigned char* base = (unsigned char*)dev_alloc(h->ctx, h->allocs, h->bytes, std::max<size_t>(total, 256), true);
+  unsigned char* base = (unsigned char*)dev_alloc(h->ctx, list ? *list : h->allocs, list ? *list_bytes : h->bytes,
+                                                  std::max<size_t>(total, 256), true);
   if (!base) return fail(MG_ERR_OOM, "device allocation failed");
   CU(cudaMemcpy(base + o_sptr, sptr.data(), b_sptr, cudaMemcpyHostToDevice));
   if (b_col) CU(cudaMemcpy(base + o_col, col.data(), b_col, cudaMemcpyHostToDevice));
@@ -412,6 +414,83 @@ std::mutex g_tune_mu;
 std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;   // shape -> (rows, cluster)
 }  // namespace
 
+// ---------------------------------------------------------------- layout tuning
+// Layout of one level operator: the SELL-C-sigma window and the 16-bit column
+// offsets.  Both keep the summation order of every row, so no choice changes a
+// bit of any result.  With opts.autotune the FP32 sweep of the level is timed
+// for a few windows, with and without 16-bit columns, and the fastest is kept
+// (the size rule unless another is faster by 2 %), cached per level shape
+// (dimension, components, row count in quarter-octaves, blocks per row);
+// otherwise, or when opts fixes sell_sigma / col16, the size rules apply.
+struct Layout {
+  int64_t sigma;
+  bool idx16;
+};
+std::mutex g_layout_mu;
+std::map<std::vector<int64_t>, Layout> g_layout_cache;
+
+Layout level_layout(mg_hier* h, const BlockCSR& A, bool pat6) {
+  const int64_t n = A.n;
+  const Layout rule{sigma_for(h, n), idx16_for(h, n)};
+  const mg_opts& o = h->opts;
+  if (!o.autotune || o.sell_sigma >= 0 || o.col16 >= 0 || !o.store_fp32 || n < 2048) return rule;
+  const int nc = h->nc;
+  const std::vector<int64_t> key = {h->dim, nc, (int64_t)std::llround(4.0 * std::log2((double)n)),
+                                    (A.nnzb() * 8) / std::max<int64_t>(n, 1), pat6 ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_layout_mu);
+    auto it = g_layout_cache.find(key);
+    if (it != g_layout_cache.end()) return it->second;
+  }
+  std::vector<Alloc> tmp;
+  size_t tb = 0;
+  auto fbuf = [&](int64_t k) { return (float*)dev_alloc(h->ctx, tmp, tb, (size_t)k * 4, true); };
+  float *x = fbuf(n * nc), *b = fbuf(n * nc), *out = fbuf(n * nc), *S = fbuf(n * nc * nc);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Layout best = rule;
+  if (x && b && out && S && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    cudaStream_t s = h->ctx->stream;
+    cudaMemsetAsync(x, 0, n * nc * 4, s);
+    cudaMemsetAsync(b, 0, n * nc * 4, s);
+    cudaMemsetAsync(S, 0, n * nc * nc * 4, s);
+    std::vector<Layout> cands = {rule};
+    for (int64_t sg : {int64_t(0), int64_t(256), int64_t(1024)})
+      for (bool i16 : {false, true})
+        if (sg != rule.sigma || i16 != rule.idx16) cands.push_back({sg, i16});
+    double best_ms = 1e30;
+    for (const Layout& c : cands) {
+      SellBuf cand;
+      std::vector<Alloc> ca;
+      size_t cb = 0;
+      if (upload_sell<float>(h, A, &cand, c.sigma, c.idx16, pat6, &ca, &cb) != MG_OK) {
+        free_list(h->ctx, ca, cb);
+        continue;
+      }
+      cand.v.tpr = tpr_for(h, nc, n);
+      for (int i = 0; i < 2; ++i) launch_smooth<float>(cand.v, nc, x, b, S, out, 0.8, false, nullptr, s);
+      cudaEventRecord(e0, s);
+      for (int i = 0; i < 10; ++i) launch_smooth<float>(cand.v, nc, x, b, S, out, 0.8, false, nullptr, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      free_list(h->ctx, ca, cb);
+      if (!ok) continue;
+      if (best_ms == 1e30 || ms < 0.98 * best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(h->ctx->stream);
+  free_list(h->ctx, tmp, tb);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_layout_mu);
+  g_layout_cache[key] = best;
+  return best;
+}
+
 // ---------------------------------------------------------------- hierarchy
 int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
   const int nc = H.nc, nb = nc * nc;
@@ -428,11 +507,13 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     int rc;
     const bool pat6 = velocity_pressure_pattern(lv.A);
     h->level_block_values.push_back(pat6 ? 6 : nb);
+    const Layout lay = level_layout(h, lv.A, pat6);
+    h->level_sigma.push_back(lay.sigma);
     // The finest FP64 operator is the outer Krylov residual's matrix in every
     // precision mode, so it is kept even without store_fp64 (which then only
     // drops the FP64 V-cycle: coarser FP64 operators and FP64 smoother blocks).
     if (opts.store_fp64 || l == nlev - 1) {
-      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6))) return rc;
+      if ((rc = upload_sell<double>(h, lv.A, &B.A64, lay.sigma, lay.idx16, pat6))) return rc;
     }
     if (opts.store_fp64) {
       B.S64 = halloc<double>(h, B.n * nb);
@@ -440,7 +521,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
     }
     if (opts.store_fp32) {
-      if ((rc = upload_sell<float>(h, lv.A, &B.A32, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6))) return rc;
+      if ((rc = upload_sell<float>(h, lv.A, &B.A32, lay.sigma, lay.idx16, pat6))) return rc;
       B.A32.v.tpr = tpr_for(h, nc, lv.A.n);
       std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
       B.S32 = halloc<float>(h, B.n * nb);
@@ -448,7 +529,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
     }
     if (opts.store_bf16) {
-      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6)))
+      if ((rc = upload_sell<__nv_bfloat16>(h, lv.A, &B.A16, lay.sigma, lay.idx16, pat6)))
         return rc;
       B.A16.v.bf16 = 1;
       B.A16.v.tpr = tpr_for(h, nc, lv.A.n);
@@ -460,7 +541,7 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
       }
     }
     h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
-    h->level_col16.push_back(idx16_for(h, lv.A.n) ? 1 : 0);
+    h->level_col16.push_back(lay.idx16 ? 1 : 0);
     if (l > 0) {
       if ((rc = upload_sell<float>(h, lv.P, &B.P, sigma_for(h, lv.P.n)))) return rc;
       if ((rc = upload_sell<float>(h, lv.R, &B.R, sigma_for(h, lv.R.n)))) return rc;

@@ -179,7 +179,8 @@ struct mg_hier {
   std::map<std::pair<int, int>, TailImage> tail_img;   // (precision slot, top) -> shared-memory image
   double tuned_vcycle_ms = 0.0;
   int64_t col16_slices = 0, col32_slices = 0;   // over the matrices stored with 16-bit columns
-  std::vector<int> level_col16;                 // per level: FP32/BF16 copy with 16-bit columns
+  std::vector<int> level_col16;                 // per level: operator copies with 16-bit columns
+  std::vector<int64_t> level_sigma;             // per level: SELL-C-sigma window of the operator copies
   int gmres_m = 0;                       // > 0: workspaces carry GMRES(m) arrays
   mgi::Workspace* ws0 = nullptr;         // default workspace (mg_solve, mg_vcycle, mg_apply)
   std::mutex solve_mu;                   // guards ws0

@@ -524,6 +524,42 @@ def test_col16_fallback_slices_bitwise(ctx):
     h1.free()
 
 
+def test_layout_choices_bitwise_and_tuned(ctx):
+    """Every layout the setup autotuner may pick for a level operator (SELL
+    window 0 / 256 / 1024, 16-bit columns off / on) gives the same V-cycle
+    bits in FP32 and FP64 and the same solve; the tuned hierarchy (choices
+    per level reported in level_sigma / level_col16) equals them too."""
+    lm = W.td_adaptive(rounds=5, gamma=1.0)
+    pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    hs = [G.Hierarchy(ctx, lm, pb, B.make_opts(sell_sigma=sg, col16=c, autotune=0))
+          for sg in (0, 256, 1024) for c in (0, 1)]
+    hs.append(G.Hierarchy(ctx, lm, pb, B.make_opts(autotune=1)))
+    tuned = hs[-1].info
+    for l in range(tuned.levels):
+        assert tuned.level_sigma[l] in (0, 256, 1024) and tuned.level_col16[l] in (0, 1)
+    rng = np.random.default_rng(14)
+    r = rng.standard_normal(hs[0].n_dofs)
+    f = dev(W.f_transport(hs[0].coords(), 1e-3, (1.0, 0.5)))
+    for prec, dt in ((B.MG_MIXED_FP32, torch.float32), (B.MG_FP64, torch.float64)):
+        outs, sols = [], []
+        for hh in hs:
+            hh.tune(prec, 0, 1)
+            z = torch.empty(hh.n_dofs, device="cuda", dtype=dt)
+            hh.vcycle(dev(r, dt), z, prec)
+            outs.append(z.cpu().numpy())
+            b = torch.empty(hh.n_dofs, device="cuda", dtype=torch.float64)
+            hh.assemble_rhs(f, b)
+            x = torch.zeros_like(b)
+            st = hh.solve(b, x, rtol=1e-10, max_it=100, prec=prec)
+            assert st.status == 0
+            sols.append((st.iters, x.cpu().numpy()))
+        for o, sv in zip(outs[1:], sols[1:]):
+            assert np.array_equal(o, outs[0])
+            assert sv[0] == sols[0][0] and np.array_equal(sv[1], sols[0][1])
+    for hh in hs:
+        hh.free()
+
+
 def test_direct_launch_mode_equals_graph(ctx):
     lm = W.td_adaptive(rounds=4, gamma=1.0)
     pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))

@@ -166,14 +166,17 @@ def test_time_steps2_match_first_order_oracle(ctx, prec):
         u = torch.zeros(nd, device="cuda", dtype=torch.float64)
         v = torch.zeros_like(u)
         fd = dev(np.tile(f, (steps, 1)))
+        # v is the difference quotient (u_n - u_{n-1}) / dt: its error is
+        # measured on the scale of u / dt, since u_n - u_{n-1} cancels
         tol = 1e-8 if prec == B.MG_FP64 else 1e-7
+        mnorm = lambda a: np.sqrt(np.sum(w * a * a))   # noqa: E731
         for k in range(steps):
             rc, sts = h.time_steps2(u, v, fd[k], None, 1, dt, rtol=1e-11, max_it=200, prec=prec)
             assert rc == 0 and sts[0].iters > 0
-            for got, want in ((u, ref[k][0]), (v, ref[k][1])):
-                e = got.cpu().numpy() - want
-                rel = np.sqrt(np.sum(w * e * e) / np.sum(w * want * want))
-                assert rel <= tol, (k, rel)
+            uref, vref = ref[k]
+            eu = mnorm(u.cpu().numpy() - uref) / mnorm(uref)
+            ev = mnorm(v.cpu().numpy() - vref) / (mnorm(uref) / dt)
+            assert eu <= tol and ev <= 4 * tol, (k, eu, ev)
     finally:
         h.free()
 
