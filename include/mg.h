@@ -57,6 +57,9 @@ typedef enum { MG_POISSON = 0, MG_TRANSPORT = 1, MG_ELASTICITY = 2, MG_OSEEN = 3
  * with the defect computed in FP64 (defect correction when the V-cycle runs
  * in FP32). */
 typedef enum { MG_KRYLOV_AUTO = 0, MG_CG = 1, MG_BICGSTAB = 2, MG_GMRES = 3, MG_MGITER = 4 } mg_krylov;
+/* Smoother of the multigrid levels (Sec. 4.1.4: damped block Jacobi; Sec. 6
+ * names Vanka smoothers for saddle-point problems as the next step). */
+typedef enum { MG_SMOOTHER_JACOBI = 0, MG_SMOOTHER_VANKA = 1 } mg_smoother;
 
 typedef struct mg_ctx mg_ctx;
 typedef struct mg_hier mg_hier;
@@ -162,9 +165,10 @@ typedef struct {
                                   fastest (cached per hierarchy shape); and per
                                   level of >= 2048 rows time the FP32 sweep over
                                   SELL windows {0, 256, 1024} x 16-bit columns
-                                  {off, on} and keep the fastest (cached per
-                                  level shape; only where sell_sigma and col16
-                                  are automatic).  Results do not depend on
+                                  {off, on} and keep the fastest for the
+                                  FP32 / BF16 copies (cached per level shape;
+                                  only where sell_sigma and col16 are
+                                  automatic).  V-cycles do not depend on
                                   either choice.                              */
   double inner_rtol;           /* > 0: defect correction -- every round runs
                                   the Krylov method until its residual fell by
@@ -183,6 +187,19 @@ typedef struct {
   int row_lanes;               /* lanes per row of the FP32/BF16 level matrices
                                   (-1: automatic, 4 on the small latency-bound
                                   levels; 1: one lane per row everywhere)     */
+  int smoother;                /* MG_SMOOTHER_JACOBI (default): damped
+                                  (point-block) Jacobi on every level;
+                                  MG_SMOOTHER_VANKA: the additive cell-patch
+                                  Vanka smoother x <- x + w S (b - A x) with
+                                  S = W sum_T P_T A_T^-1 P_T^T (A_T: the level
+                                  operator on the 2^dim nc unknowns of cell T,
+                                  inverted densely at setup; W = 1/(cells
+                                  containing the node)) on the levels >= 1
+                                  with at least vanka_rows unknowns, Jacobi
+                                  below; the small-level kernel only takes
+                                  Jacobi levels                               */
+  int vanka_rows;              /* see smoother (default 0: every level >= 1)  */
+  double vanka_omega;          /* damping w of the Vanka levels (default 1)   */
 } mg_opts;
 
 typedef struct {
@@ -209,12 +226,15 @@ typedef struct {
                                            operator: nc*nc, or 6 for 3x3 blocks of
                                            the velocity-pressure pattern
                                            [[a,0,g1],[0,a,g2],[d1,d2,c]]          */
+  int level_smoother[32];               /* mg_smoother used on the level          */
   int64_t level_sigma[32];              /* SELL-C-sigma window of the level
-                                           operator (0: rows in node order); with
-                                           opts.autotune it and level_col16 are
-                                           the fastest of a timed set for the FP32
-                                           sweep (both keep every row's summation
-                                           order: no result bit depends on them)  */
+                                           operator's FP32 / BF16 copies (0: rows
+                                           in node order); with opts.autotune it
+                                           and level_col16 are the fastest of a
+                                           timed set for the FP32 sweep (both keep
+                                           every row's summation order: no V-cycle
+                                           bit depends on them; the FP64 copies
+                                           keep the size rule)                    */
 } mg_info;
 
 typedef struct {

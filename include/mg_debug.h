@@ -31,7 +31,9 @@ int mg_host_levels(const mg_host_hier* h);
  *   matrix of the finest level (b = load * f before Dirichlet zeroing),
  *   4 = smoother blocks as a block-diagonal matrix, 5 = hanging-node matrix
  *   H (scalar, all nodes), 6 = lifting matrix of the finest level (the
- *   couplings (H^T A H)[free dof, Dirichlet dof], zero elsewhere).  n/m: block
+ *   couplings (H^T A H)[free dof, Dirichlet dof], zero elsewhere), 7 = the
+ *   cell-patch Vanka matrix S of the level (n = 0 on levels that smooth with
+ *   Jacobi).  n/m: block
  *   rows/columns; nc: block size. */
 int mg_host_level(const mg_host_hier* h, int level, int which, int64_t* n, int64_t* m, int* nc, int64_t* nnzb,
                   const int64_t** ptr, const int64_t** col, const double** val);

@@ -24,6 +24,7 @@ MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_NAN, MG_ERR_TIMEOUT, MG_ERR_CUDA 
 SOLVE_OUTCOMES = (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_NAN)
 MG_FP64, MG_MIXED_FP32, MG_MIXED_BF16 = 0, 1, 2
 MG_ERR_CANCELLED = -9
+MG_SMOOTHER_JACOBI, MG_SMOOTHER_VANKA = 0, 1
 MG_POISSON, MG_TRANSPORT, MG_ELASTICITY, MG_OSEEN = 0, 1, 2, 3
 MG_KRYLOV_AUTO, MG_CG, MG_BICGSTAB, MG_GMRES, MG_MGITER = 0, 1, 2, 3, 4
 MG_OP_MATVEC, MG_OP_SMOOTH, MG_OP_RESTRICT, MG_OP_PROLONG_ADD, MG_OP_COARSE = 0, 1, 2, 3, 4
@@ -61,7 +62,8 @@ class MgOpts(C.Structure):
                 ("store_fp32", C.c_int), ("launch_mode", C.c_int),
                 ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int),
                 ("inner_rtol", C.c_double), ("sell_sigma", C.c_int), ("col16", C.c_int),
-                ("row_lanes", C.c_int)]
+                ("row_lanes", C.c_int), ("smoother", C.c_int), ("vanka_rows", C.c_int),
+                ("vanka_omega", C.c_double)]
 
 
 class MgInfo(C.Structure):
@@ -72,7 +74,8 @@ class MgInfo(C.Structure):
                 ("bytes_workspace", C.c_size_t), ("tail_levels", C.c_int), ("tail_cluster", C.c_int),
                 ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64),
                 ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32),
-                ("level_block_values", C.c_int * 32), ("level_sigma", C.c_int64 * 32)]
+                ("level_block_values", C.c_int * 32), ("level_smoother", C.c_int * 32),
+                ("level_sigma", C.c_int64 * 32)]
 
 
 class MgStats(C.Structure):

@@ -173,6 +173,9 @@ void mg_default_opts(mg_opts* o) {
   o->sell_sigma = -1;
   o->col16 = -1;
   o->row_lanes = -1;
+  o->smoother = MG_SMOOTHER_JACOBI;
+  o->vanka_rows = 0;
+  o->vanka_omega = 1.0;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -223,6 +226,10 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   if (!(opts.inner_rtol >= 0.0 && opts.inner_rtol < 1.0)) return fail(MG_ERR_INVALID, "inner_rtol must be in [0, 1)");
   if (opts.col16 < -1 || opts.col16 > 1) return fail(MG_ERR_INVALID, "col16 must be -1, 0 or 1");
   if (opts.row_lanes != -1 && opts.row_lanes != 1) return fail(MG_ERR_INVALID, "row_lanes must be -1 or 1");
+  if (opts.smoother != MG_SMOOTHER_JACOBI && opts.smoother != MG_SMOOTHER_VANKA)
+    return fail(MG_ERR_INVALID, "unknown smoother");
+  if (opts.vanka_rows < 0 || !(opts.vanka_omega > 0) || !std::isfinite(opts.vanka_omega))
+    return fail(MG_ERR_INVALID, "vanka_rows must be >= 0 and vanka_omega > 0");
   if (opts.sell_sigma < -1 || (opts.sell_sigma > 0 && opts.sell_sigma % 32 != 0))
     return fail(MG_ERR_INVALID, "sell_sigma must be -1, 0 or a positive multiple of 32");
   if (!opts.store_fp64 && !opts.store_fp32 && !opts.store_bf16) return fail(MG_ERR_INVALID, "no precision stored");
@@ -321,6 +328,7 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
     info->level_omega[l] = h->L[l].omega;
     info->level_block_values[l] = h->level_block_values[l];
     info->level_sigma[l] = h->level_sigma[l];
+    info->level_smoother[l] = h->L[l].vanka ? MG_SMOOTHER_VANKA : MG_SMOOTHER_JACOBI;
   }
   return MG_OK;
 }
@@ -554,6 +562,16 @@ static int level_op(mg_hier* h, int level, int op, const void* in, const void* i
       return MG_OK;
     case MG_OP_SMOOTH:
       if (!in2) return fail(MG_ERR_INVALID, "smooth needs b");
+      if (L.vanka) {      // residual into the level's r buffer, then out = in + w S r
+        if (d) {
+          launch_residual<double>(L.A64.v, nc, (const double*)in, (const double*)in2, V.r64, nullptr, s);
+          launch_vanka<double>(L.V64.v, nc, V.r64, (const double*)in, (double*)out, L.omega, nullptr, s);
+        } else {
+          launch_residual<float>(A32, nc, (const float*)in, (const float*)in2, V.r32, nullptr, s);
+          launch_vanka<float>(L.V32.v, nc, V.r32, (const float*)in, (float*)out, L.omega, nullptr, s);
+        }
+        return MG_OK;
+      }
       if (d) launch_smooth<double>(L.A64.v, nc, (const double*)in, (const double*)in2, L.S64, (double*)out, L.omega, false, nullptr, s);
       else launch_smooth<float>(A32, nc, (const float*)in, (const float*)in2, L.S32, (float*)out, L.omega, false, nullptr, s);
       return MG_OK;

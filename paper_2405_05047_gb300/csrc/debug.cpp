@@ -63,6 +63,7 @@ int mg_host_level(const mg_host_hier* h, int level, int which, int64_t* n, int64
     case 4: M = &h->sinv[level]; break;
     case 5: M = &h->hmat[level]; break;
     case 6: M = &h->H.lift; break;
+    case 7: M = &lv.Sv; break;
     default: return MG_ERR_INVALID;
   }
   *n = M->n; *m = M->m; *nc = M->nc; *nnzb = M->nnzb();

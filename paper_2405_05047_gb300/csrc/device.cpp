@@ -261,6 +261,7 @@ template <>
 struct Prec<double> {
   static const TailParams& tail(Workspace& w) { return w.tail64; }
   static const SellView& A(LevelMats& l) { return l.A64.v; }
+  static const SellView& V(LevelMats& l) { return l.V64.v; }
   static const double* S(LevelMats& l) { return l.S64; }
   static double* b(LevelVecs& v) { return v.b64; }
   static double* o(LevelVecs& v) { return v.o64; }
@@ -271,6 +272,7 @@ template <>
 struct Prec<float> {
   static const TailParams& tail(Workspace& w) { return w.tail32; }
   static const SellView& A(LevelMats& l) { return l.A32.v; }
+  static const SellView& V(LevelMats& l) { return l.V32.v; }
   static const float* S(LevelMats& l) { return l.S32; }
   static float* b(LevelVecs& v) { return v.b32; }
   static float* o(LevelVecs& v) { return v.o32; }
@@ -284,9 +286,9 @@ struct Prec<float> {
 namespace {
 int tail_top_for(const mg_hier* h, int rows) {
   int top = 0;
-  if (rows > 0)
+  if (rows > 0)   // the small-level kernel smooths with Jacobi: it stops below the first Vanka level
     for (int l = 1; l < h->nlev && l < kTailMax; ++l)
-      if (h->L[l].n * h->nc <= rows) top = l;
+      if (h->L[l].n * h->nc <= rows && !h->L[l].vanka) top = l;
       else break;
   return top;
 }
@@ -415,9 +417,12 @@ std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;   // shape -> 
 }  // namespace
 
 // ---------------------------------------------------------------- layout tuning
-// Layout of one level operator: the SELL-C-sigma window and the 16-bit column
-// offsets.  Both keep the summation order of every row, so no choice changes a
-// bit of any result.  With opts.autotune the FP32 sweep of the level is timed
+// Layout of the FP32 / BF16 copies of one level operator (the V-cycle's in
+// the mixed modes): the SELL-C-sigma window and the 16-bit column offsets.
+// Both keep the summation order of every row, so no choice changes a bit of a
+// V-cycle (the FP64 copies keep the size rule: the finest one is also the
+// outer Krylov operator, whose SpMV kernels form dot products in SELL row
+// order).  With opts.autotune the FP32 sweep of the level is timed
 // for a few windows, with and without 16-bit columns, and the fastest is kept
 // (the size rule unless another is faster by 2 %), cached per level shape
 // (dimension, components, row count in quarter-octaves, blocks per row);
@@ -513,7 +518,9 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
     // precision mode, so it is kept even without store_fp64 (which then only
     // drops the FP64 V-cycle: coarser FP64 operators and FP64 smoother blocks).
     if (opts.store_fp64 || l == nlev - 1) {
-      if ((rc = upload_sell<double>(h, lv.A, &B.A64, lay.sigma, lay.idx16, pat6))) return rc;
+      // the FP64 copy keeps the size rule: it is also the outer Krylov
+      // operator, whose SpMV kernels form dot products in SELL row order
+      if ((rc = upload_sell<double>(h, lv.A, &B.A64, sigma_for(h, lv.A.n), idx16_for(h, lv.A.n), pat6))) return rc;
     }
     if (opts.store_fp64) {
       B.S64 = halloc<double>(h, B.n * nb);
@@ -540,8 +547,17 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
         CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
       }
     }
+    if (lv.vanka) {
+      B.vanka = true;
+      if (opts.store_fp64 && (rc = upload_sell<double>(h, lv.Sv, &B.V64, sigma_for(h, lv.Sv.n), idx16_for(h, lv.Sv.n))))
+        return rc;
+      if (opts.store_fp32 || opts.store_bf16) {
+        if ((rc = upload_sell<float>(h, lv.Sv, &B.V32, sigma_for(h, lv.Sv.n), idx16_for(h, lv.Sv.n)))) return rc;
+        B.V32.v.tpr = tpr_for(h, nc, lv.Sv.n);
+      }
+    }
     h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
-    h->level_col16.push_back(lay.idx16 ? 1 : 0);
+    h->level_col16.push_back(lay.idx16 ? 1 : 0);   // of the FP32 / BF16 copies
     if (l > 0) {
       if ((rc = upload_sell<float>(h, lv.P, &B.P, sigma_for(h, lv.P.n)))) return rc;
       if ((rc = upload_sell<float>(h, lv.R, &B.R, sigma_for(h, lv.R.n)))) return rc;
@@ -742,7 +758,7 @@ int set_tail(mg_hier* h, int rows, int cluster) {
 
 int autotune(mg_hier* h, int prec) {
   std::vector<int64_t> key = {h->dim, h->nc, prec, h->opts.nu1, h->opts.nu2};
-  for (const LevelMats& L : h->L) key.push_back(L.n);
+  for (const LevelMats& L : h->L) key.push_back(L.vanka ? -L.n : L.n);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -830,17 +846,32 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
   const int nu1 = h->opts.nu1, nu2 = h->opts.nu2, ns = nu1 + nu2;
   auto bufof = [&](LevelVecs& X, T* o, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? o : Prec<T>::t(X); };
   const double om = L.omega, omc = C.omega;
+  // one smoothing sweep cur -> dst: fused residual + Jacobi, or (Vanka) the
+  // residual into the level's r buffer, then dst = cur + w S r (from zero:
+  // dst = w S b, no residual)
+  auto sweep = [&](const T* in, T* dst, bool from_zero, double* o64, const double* sc) {
+    if (!L.vanka) {
+      launch_smooth<T>(AL, nc, in, b, Prec<T>::S(L), dst, om, from_zero, done, s, o64, sc);
+      h->launch_count++;
+      return;
+    }
+    if (!from_zero) {
+      launch_residual<T>(AL, nc, in, b, Prec<T>::r(V), done, s);
+      h->launch_count++;
+    }
+    launch_vanka<T>(Prec<T>::V(L), nc, from_zero ? b : Prec<T>::r(V), from_zero ? nullptr : in, dst, om, done, s,
+                    o64, sc);
+    h->launch_count++;
+  };
   T* cur = nullptr;
   for (int k = 0; k < nu1; ++k) {                                // pre-smoothing
     T* dst = bufof(V, out, k);
-    if (!(k == 0 && first_done)) {
-      launch_smooth<T>(AL, nc, cur, b, Prec<T>::S(L), dst, om, k == 0, done, s);
-      h->launch_count++;
-    }
+    if (!(k == 0 && first_done)) sweep(cur, dst, k == 0, nullptr, nullptr);
     cur = dst;
   }
   launch_residual<T>(AL, nc, cur, b, Prec<T>::r(V), done, s);   // residual, restricted below
-  const bool fuse = l - 1 > 0;
+  // the restriction also performs the coarser level's first (Jacobi) sweep
+  const bool fuse = l - 1 > 0 && !C.vanka;
   T* cfirst = fuse ? bufof(CV, Prec<T>::o(CV), 0) : nullptr;
   launch_restrict<T>(L.R.t, nc, Prec<T>::r(V), Prec<T>::b(CV), Prec<T>::S(C), cfirst, omc, done, s);
   h->launch_count += 2;
@@ -852,10 +883,8 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
   for (int k = nu1; k < ns; ++k) {                               // post-smoothing
     T* dst = bufof(V, out, k);
     const bool last = k == ns - 1;
-    launch_smooth<T>(AL, nc, cur, b, Prec<T>::S(L), dst, om, false, done, s, last ? out64 : nullptr,
-                     last ? scale : nullptr);
+    sweep(cur, dst, false, last ? out64 : nullptr, last ? scale : nullptr);
     cur = dst;
-    h->launch_count++;
   }
   return out64 != nullptr && nu2 > 0;
 }

@@ -40,6 +40,8 @@ struct LevelMats {
   SellBuf A64, A32, A16, P, R;   // A16: BF16-stored values
   double* S64 = nullptr;
   float* S32 = nullptr;
+  bool vanka = false;         // smoothed by the cell-patch Vanka matrix V instead of Jacobi
+  SellBuf V64, V32;           // Vanka matrix (FP32 copy also serves the BF16-values path)
 };
 
 // V-cycle vectors of one level in one workspace: rhs, out, ping-pong, residual.

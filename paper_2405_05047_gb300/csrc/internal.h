@@ -69,6 +69,8 @@ struct HostLevel {
   BlockCSR R;                       // scalar: restriction to level-1 (rows: coarse nodes)
   std::vector<double> Sinv;         // n * nc * nc smoother blocks (inverse diagonal blocks)
   double omega = 0.8;               // damping of the smoother on this level
+  bool vanka = false;               // cell-patch Vanka smoother (Sv) instead of Jacobi
+  BlockCSR Sv;                      // Vanka matrix W sum_T P_T A_T^-1 P_T^T
 };
 
 struct HostHierarchy {

@@ -533,6 +533,51 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, c
   }
 }
 
+// Cell-patch Vanka update x_out = x_in + omega S r with the assembled Vanka
+// matrix S = W sum_T P_T A_T^-1 P_T^T (block SELL, dense nc x nc blocks) and
+// r = b - A x_in from the preceding residual kernel; from zero (x_in = NULL)
+// r is b itself and x_out = omega S b.  xo64 (optional): the output also in
+// FP64 times *scale (last sweep of an FP32 V-cycle).
+template <typename T, typename VT, int NC, int TPR>
+__global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_vanka(SellView S, const T* __restrict__ r,
+                                                   const T* __restrict__ xin, T* __restrict__ xo, T omega,
+                                                   const int* done, double* __restrict__ xo64,
+                                                   const double* scale) {
+  pdl_wait();
+  if (stopped(done)) return;
+  const double sc = xo64 ? *scale : 1.0;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t total = S.nslices * 32 * TPR;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthreads) {
+    const int64_t row = t / TPR;
+    const int sub = (int)(t % TPR);
+    const int64_t slice = row >> 5;
+    const int lane = (int)(row & 31);
+    const int64_t orow = srow<0>(S, row);
+    if (NC == 1) {
+      const T c = sell_dot1<T, 0, VT, TPR>(S, slice, lane, r, sub);
+      if (row < S.n && sub == 0) {
+        const T v = xin ? fmad(omega, c, xin[orow]) : omega * c;
+        xo[orow] = v;
+        if (xo64) xo64[orow] = (double)v * sc;
+      }
+    } else {
+      T acc[3];
+      sell_dot3<T, 0, VT, TPR>(S, slice, lane, r, acc, sub);
+      if (row < S.n) {
+        const int i0 = TPR > 1 ? sub : 0, i1 = TPR > 1 ? sub + 1 : 3;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          if (i < i0 || i >= i1) continue;
+          const T v = xin ? fmad(omega, acc[i], xin[3 * orow + i]) : omega * acc[i];
+          xo[3 * orow + i] = v;
+          if (xo64) xo64[3 * orow + i] = (double)v * sc;
+        }
+      }
+    }
+  }
+}
+
 // d_j = sum_i R(j,i) r_i (R = P^T stored as its own gather matrix: no atomics).
 // With S0 the same pass also performs the coarser level's first smoothing
 // sweep from a zero guess, x0_j = omega S_j d_j (it needs no matrix).
@@ -1679,6 +1724,21 @@ void launch_prolong_add(const TransferView& P, int nc, const T* y, const T* xin,
 }
 
 template <typename T>
+void launch_vanka(const SellView& S, int nc, const T* r, const T* xin, T* xo, double omega, const int* done,
+                  cudaStream_t s, double* xo64, const double* scale) {
+  const int g = grid_for_rows(S.nslices * 32 * S.tpr);
+  const T om = (T)omega;
+  const bool four = S.tpr == 4;
+  if (nc == 1) {
+    if (four) launch(k_vanka<T, T, 1, 4>, g, s, S, r, xin, xo, om, done, xo64, scale);
+    else launch(k_vanka<T, T, 1, 1>, g, s, S, r, xin, xo, om, done, xo64, scale);
+  } else {
+    if (four) launch(k_vanka<T, T, 3, 4>, g, s, S, r, xin, xo, om, done, xo64, scale);
+    else launch(k_vanka<T, T, 3, 1>, g, s, S, r, xin, xo, om, done, xo64, scale);
+  }
+}
+
+template <typename T>
 void launch_coarse(const double* Ainv, int64_t n, const T* d, T* z, const int* done, cudaStream_t s) {
   int64_t g = (n + 7) / 8;
   if (g > kMaxRedBlocks) g = kMaxRedBlocks;
@@ -1693,7 +1753,9 @@ void launch_coarse(const double* Ainv, int64_t n, const T* d, T* z, const int* d
   template void launch_restrict<T>(const TransferView&, int, const T*, T*, const T*, T*, double, const int*,       \
                                    cudaStream_t);                                                                  \
   template void launch_prolong_add<T>(const TransferView&, int, const T*, const T*, T*, const int*, cudaStream_t); \
-  template void launch_coarse<T>(const double*, int64_t, const T*, T*, const int*, cudaStream_t);
+  template void launch_coarse<T>(const double*, int64_t, const T*, T*, const int*, cudaStream_t);              \
+  template void launch_vanka<T>(const SellView&, int, const T*, const T*, T*, double, const int*, cudaStream_t,   \
+                                double*, const double*);
 MGI_INST(double)
 MGI_INST(float)
 #undef MGI_INST

@@ -106,6 +106,10 @@ void launch_smooth(const SellView& A, int nc, const T* x, const T* b, const T* S
                    const double* scale = nullptr);
 template <typename T>
 void launch_residual(const SellView& A, int nc, const T* x, const T* b, T* r, const int* done, cudaStream_t s);
+// cell-patch Vanka update: xo = xin + omega S r (xin == NULL: xo = omega S r)
+template <typename T>
+void launch_vanka(const SellView& S, int nc, const T* r, const T* xin, T* xo, double omega, const int* done,
+                  cudaStream_t s, double* xo64 = nullptr, const double* scale = nullptr);
 template <typename T>
 void launch_matvec(const SellView& A, int nc, const T* x, T* y, const int* done, cudaStream_t s);
 // d = R r; when x0 != nullptr also x0 = omega S d (first sweep of the coarser level from zero)

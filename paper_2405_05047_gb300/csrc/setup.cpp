@@ -995,6 +995,77 @@ bool invert_dense(int64_t n, std::vector<double>& M, std::vector<double>& Inv) {
   return true;
 }
 
+// Additive cell-patch Vanka smoother of a level as a block matrix:
+// S = W sum_T P_T A_T^{-1} P_T^T over the level's cells T, with A_T the
+// condensed operator restricted to the 2^dim nc unknowns of T's vertices
+// (constrained rows and columns are identity rows, so fixed unknowns stay
+// decoupled) and W = diag(1 / m_i), m_i the number of cells containing node
+// i.  Row pattern: the nodes sharing a cell with the row's node.  Local
+// inverses are formed in parallel in chunks of cells, then accumulated.
+Status build_vanka(HostLevel& lv, int dim, int nc) {
+  const Topology& T = lv.topo;
+  const int nv = 1 << dim, k = nv * nc, nb = nc * nc;
+  const int64_t n = T.n_nodes, ncell = (int64_t)T.cell_node.size() / nv;
+  std::vector<int64_t> m(n, 0);
+  for (int64_t q : T.cell_node) m[q]++;
+  std::vector<std::vector<int64_t>> nbr(n);
+  for (int64_t c = 0; c < ncell; ++c)
+    for (int a = 0; a < nv; ++a)
+      for (int b = 0; b < nv; ++b) nbr[T.cell_node[c * nv + a]].push_back(T.cell_node[c * nv + b]);
+  BlockCSR& S = lv.Sv;
+  S = BlockCSR();
+  S.n = S.m = n;
+  S.nc = nc;
+  S.ptr.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    std::sort(nbr[i].begin(), nbr[i].end());
+    nbr[i].erase(std::unique(nbr[i].begin(), nbr[i].end()), nbr[i].end());
+    S.ptr[i + 1] = S.ptr[i] + (int64_t)nbr[i].size();
+  }
+  S.col.resize(S.ptr[n]);
+  for (int64_t i = 0; i < n; ++i) std::copy(nbr[i].begin(), nbr[i].end(), S.col.begin() + S.ptr[i]);
+  std::vector<std::vector<int64_t>>().swap(nbr);
+  S.val.assign(S.col.size() * nb, 0.0);
+  auto find = [](const BlockCSR& M, int64_t r, int64_t c) -> int64_t {
+    for (int64_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e)
+      if (M.col[e] == c) return e;
+    return -1;
+  };
+  const int64_t chunk = 16384;
+  std::vector<double> inv(chunk * k * k);
+  for (int64_t c0 = 0; c0 < ncell; c0 += chunk) {
+    const int64_t c1 = std::min(ncell, c0 + chunk);
+    bool singular = false;
+#pragma omp parallel for schedule(static) reduction(|| : singular)
+    for (int64_t c = c0; c < c1; ++c) {
+      std::vector<double> M(k * k, 0.0), I;
+      for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b) {
+          const int64_t e = find(lv.A, T.cell_node[c * nv + a], T.cell_node[c * nv + b]);
+          if (e < 0) continue;
+          for (int i = 0; i < nc; ++i)
+            for (int j = 0; j < nc; ++j) M[(a * nc + i) * k + b * nc + j] = lv.A.val[e * nb + i * nc + j];
+        }
+      if (!invert_dense(k, M, I)) singular = true;
+      else std::copy(I.begin(), I.end(), inv.begin() + (c - c0) * k * k);
+    }
+    if (singular) return Status::err(MG_ERR_INVALID, "singular cell block in the Vanka smoother");
+    for (int64_t c = c0; c < c1; ++c) {
+      const double* I = &inv[(c - c0) * k * k];
+      for (int a = 0; a < nv; ++a) {
+        const int64_t na = T.cell_node[c * nv + a];
+        const double w = 1.0 / (double)m[na];
+        for (int b = 0; b < nv; ++b) {
+          const int64_t e = find(S, na, T.cell_node[c * nv + b]);
+          for (int i = 0; i < nc; ++i)
+            for (int j = 0; j < nc; ++j) S.val[e * nb + i * nc + j] += w * I[(a * nc + i) * k + b * nc + j];
+        }
+      }
+    }
+  }
+  return Status::ok();
+}
+
 // Largest eigenvalue magnitude of S A (S the smoother blocks) by `iters`
 // power iterations: w = S A v, lambda = |w| / |v|, v = w / |w|.  Start vector:
 // v_i = frac(i * 2654435761 / 2^32) - 1/2 on the free dofs (a fixed
@@ -1121,9 +1192,20 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
       std::copy(inv.begin(), inv.end(), lv.Sinv.begin() + p * nb);
     }
   }
+  // cell-patch Vanka on the levels >= 1 with at least vanka_rows unknowns
+  if (opts.smoother == MG_SMOOTHER_VANKA)
+    for (size_t l = 1; l < H->levels.size(); ++l) {
+      HostLevel& lv = H->levels[l];
+      if (lv.topo.n_nodes * nc < opts.vanka_rows) continue;
+      Status sv = build_vanka(lv, H->dim, nc);
+      if (!sv.good()) return sv;
+      lv.vanka = true;
+      lv.omega = opts.vanka_omega;
+    }
   // damping per level: opts.omega when positive; otherwise 0.8 for scalar
   // problems and 1.2 / lambda_max(S_l A_l) for the point-block smoothers
   for (HostLevel& lv : H->levels) {
+    if (lv.vanka) continue;
     if (opts.omega > 0) lv.omega = opts.omega;
     else if (nc == 1) lv.omega = 0.8;
     else lv.omega = 1.2 / smoothed_operator_lambda_max(lv, nc, 20);

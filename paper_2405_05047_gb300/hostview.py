@@ -56,6 +56,8 @@ class HostHierarchy:
         if rc != 0:
             raise B.MGError(rc)
         n, m, nc, nnz = n.value, m.value, nb.value, nnz.value
+        if n == 0:                      # a matrix the level does not have
+            return sp.csr_matrix((0, 0))
         p = np.ctypeslib.as_array(ptr, shape=(n + 1,)).copy()
         c = np.ctypeslib.as_array(col, shape=(max(nnz, 1),))[:nnz].copy()
         v = np.ctypeslib.as_array(val, shape=(max(nnz * nc * nc, 1),))[:nnz * nc * nc].copy()

