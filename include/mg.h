@@ -227,6 +227,8 @@ typedef struct {
                                            the velocity-pressure pattern
                                            [[a,0,g1],[0,a,g2],[d1,d2,c]]          */
   int level_smoother[32];               /* mg_smoother used on the level          */
+  int64_t level_vanka_nnzb[32];         /* blocks of the level's Vanka matrix
+                                           (0 on Jacobi levels)                   */
   int64_t level_sigma[32];              /* SELL-C-sigma window of the level
                                            operator's FP32 / BF16 copies (0: rows
                                            in node order); with opts.autotune it

@@ -75,6 +75,7 @@ class MgInfo(C.Structure):
                 ("vcycle_ms", C.c_double), ("col16_slices", C.c_int64), ("col32_slices", C.c_int64),
                 ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32),
                 ("level_block_values", C.c_int * 32), ("level_smoother", C.c_int * 32),
+                ("level_vanka_nnzb", C.c_int64 * 32),
                 ("level_sigma", C.c_int64 * 32)]
 
 

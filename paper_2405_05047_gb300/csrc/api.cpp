@@ -329,6 +329,7 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
     info->level_block_values[l] = h->level_block_values[l];
     info->level_sigma[l] = h->level_sigma[l];
     info->level_smoother[l] = h->L[l].vanka ? MG_SMOOTHER_VANKA : MG_SMOOTHER_JACOBI;
+    info->level_vanka_nnzb[l] = h->L[l].vanka ? std::max(h->L[l].V32.nnz_real, h->L[l].V64.nnz_real) : 0;
   }
   return MG_OK;
 }

@@ -50,7 +50,7 @@ def make(workload):
 
 def alg_bytes(info, level, nc, op, vbytes):
     """Bytes the operator must move once: stored values + column indices of
-    the level matrix (2 bytes where the level stores 16-bit column offsets,
+    the level matrix (for "vanka": of the level's Vanka matrix) (2 bytes where the level stores 16-bit column offsets,
     else 4; 6 values per 3x3 block where the level stores the
     velocity-pressure pattern, else nc*nc), plus its vectors (x, b, S^-1 and
     the output for a sweep)."""
@@ -61,6 +61,8 @@ def alg_bytes(info, level, nc, op, vbytes):
         return nnz * vbytes + info.level_rows_nnzb[level] * ib + rows * vbytes * 3 + info.level_nodes[level] * nc * nc * vbytes
     if op == "matvec":
         return nnz * vbytes + info.level_rows_nnzb[level] * ib + rows * vbytes * 2
+    if op == "vanka":       # x_out = x_in + w S r: S (dense nc x nc blocks), r, x_in, x_out
+        return info.level_vanka_nnzb[level] * (nc * nc * vbytes + ib) + rows * vbytes * 3
     return None
 
 
