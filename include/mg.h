@@ -462,6 +462,15 @@ int mg_cancel(mg_ctx* ctx, uint64_t ticket);
 /* Maximum number of solves the scheduler keeps in flight at once (default 16;
  * each runs on its own stream with its own workspace). */
 int mg_serve_config(mg_ctx* ctx, int max_slots);
+/* Reserve `slots` solve slots of hierarchy h for serving: up to that many
+ * workspaces are allocated now (through the context's allocator, on the
+ * calling thread) and their solve graphs for precision prec are built, and
+ * the scheduler never holds more than `slots` workspaces of h at once (a
+ * request waits for a free one instead of allocating on the serving path).
+ * Without a reservation the scheduler creates a workspace (cudaMalloc) and
+ * builds its graph when a request finds none free.  MG_ERR_ADMISSION when the
+ * slots do not fit the budget (the ones created stay reserved). */
+int mg_serve_reserve(mg_ctx* ctx, mg_hier* h, int slots, int prec);
 /* Kernels the library has enqueued on behalf of this hierarchy so far. */
 int64_t mg_launch_count(const mg_hier* h);
 

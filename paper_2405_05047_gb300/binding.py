@@ -131,6 +131,7 @@ _SIGS = {
     "mg_launch_count": (C.c_int64, [C.c_void_p]),
     "mg_time_op": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mg_serve_config": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_serve_reserve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "mg_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "mg_restrict_static": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_time_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
@@ -423,6 +424,9 @@ class Context:
 
     def serve_config(self, max_slots):
         return mg_serve_config(self.handle, max_slots)
+
+    def serve_reserve(self, hier, slots, prec=MG_MIXED_FP32):
+        return _check(load_library().mg_serve_reserve(self.handle, hier.handle, slots, prec))
 
     def close(self):
         """Free every hierarchy of this context, then the context."""

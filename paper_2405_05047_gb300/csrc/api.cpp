@@ -56,6 +56,10 @@ Workspace* acquire_ws(mg_hier* h, cudaStream_t s) {
   }
   mg_ctx* c = h->ctx;
   if (c->budget && c->used + h->ws_bytes > c->budget) return nullptr;
+  {
+    std::lock_guard<std::mutex> lk(h->pool_mu);
+    if (h->serve_cap > 0 && (int)h->all_ws.size() >= h->serve_cap) return nullptr;   // wait for a reserved one
+  }
   Workspace* w = nullptr;
   if (ws_create(h, false, s, &w) != MG_OK) return nullptr;
   std::lock_guard<std::mutex> lk(h->pool_mu);
@@ -754,6 +758,41 @@ int mg_cancel(mg_ctx* c, uint64_t ticket) {
     if ((*q)->ticket == ticket) { c->queue.erase(q); break; }
   r->state = 2;
   r->status = MG_ERR_CANCELLED;
+  return MG_OK;
+}
+
+int mg_serve_reserve(mg_ctx* c, mg_hier* h, int slots, int prec) {
+  if (!c || !h || h->ctx != c || slots < 1 || slots > 256) return fail(MG_ERR_INVALID, "bad argument");
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  CU(cudaSetDevice(c->device));
+  std::lock_guard<std::mutex> lk(c->mu);      // the scheduler does not touch the pool meanwhile
+  const int method = method_of(h);
+  int have;
+  {
+    std::lock_guard<std::mutex> pk(h->pool_mu);
+    have = (int)h->all_ws.size();
+  }
+  for (; have < slots; ++have) {
+    if (c->budget && c->used + h->ws_bytes > c->budget)
+      return fail(MG_ERR_ADMISSION, "reserved solve slots exceed the HBM budget");
+    Workspace* w = nullptr;
+    if ((rc = ws_create(h, true, c->stream, &w))) return rc;
+    std::lock_guard<std::mutex> pk(h->pool_mu);
+    h->all_ws.push_back(w);
+    h->pool.push_back(w);
+  }
+  std::vector<Workspace*> ws;
+  {
+    std::lock_guard<std::mutex> pk(h->pool_mu);
+    ws = h->pool;
+    h->serve_cap = std::max(h->serve_cap, slots);
+  }
+  for (Workspace* w : ws) {       // idle workspaces: build their solve graphs now, not on the first request
+    SolveGraph* g = nullptr;
+    if (h->opts.launch_mode != 1 && (rc = get_graph(h, *w, method, prec, &g))) return rc;
+  }
+  CU(cudaStreamSynchronize(c->stream));
   return MG_OK;
 }
 

@@ -1046,6 +1046,8 @@ int build_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph* out)
   return MG_OK;
 }
 
+}  // namespace
+
 int get_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph** g) {
   for (auto& x : w.graphs)
     if (x.method == method && x.prec == prec) { *g = &x; return MG_OK; }
@@ -1056,6 +1058,8 @@ int get_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph** g) {
   *g = &w.graphs.back();
   return MG_OK;
 }
+
+namespace {
 
 // One round: residual of the current iterate, the device loop (graph or
 // direct launches), the true residual, outputs and the state mirror.

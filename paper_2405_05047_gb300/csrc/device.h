@@ -190,6 +190,7 @@ struct mg_hier {
   std::vector<mgi::Workspace*> pool;     // idle serving workspaces
   std::vector<mgi::Workspace*> all_ws;   // every serving workspace
   size_t ws_bytes = 0;                   // device bytes of one workspace
+  int serve_cap = 0;                     // > 0: serving never holds more workspaces (mg_serve_reserve)
   std::atomic<int64_t> launch_count{0};  // kernels enqueued (host-side count)
 };
 
@@ -229,5 +230,7 @@ bool enqueue_vcycle(mg_hier* h, Workspace& w, int l, const T* b, T* out, const i
 int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const double* x0, bool x0_host,
                 double* x_out, bool x_out_host, double rtol, int max_it, int prec, cudaStream_t s);
 int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats);
+// The cached solve graph of (method, prec) of a workspace, built on first use.
+int get_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph** g);
 
 }  // namespace mgi

@@ -167,3 +167,28 @@ def test_mixed_solve_without_fp64_level_copies():
     hd.free()
     hn.free()
     ctx.close()
+
+
+def test_reserved_slots_bound_the_workspaces():
+    """mg_serve_reserve allocates the slots and builds their graphs up front;
+    with 2 reserved slots 8 requests on one hierarchy still all finish (they
+    wait for a free slot instead of allocating), bitwise equal to the solve
+    alone."""
+    ctx = G.Context(0)
+    h = G.Hierarchy(ctx, W.td_adaptive(rounds=4, gamma=1.0),
+                    B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)))
+    ctx.serve_reserve(h, 2, B.MG_MIXED_FP32)
+    b = rhs_of(h, 21)
+    xa = torch.zeros_like(b)
+    st = h.solve(b, xa, rtol=1e-9, max_it=300, prec=B.MG_MIXED_FP32)
+    assert st.status == 0
+    xs = [torch.zeros_like(b) for _ in range(8)]
+    torch.cuda.synchronize()
+    tickets = [ctx.submit(h, b, x, rtol=1e-9, max_it=300, prec=B.MG_MIXED_FP32) for x in xs]
+    res = wait(ctx, tickets)
+    for t, x in zip(tickets, xs):
+        assert res[t][0] == 0 and torch.equal(x, xa)
+    with pytest.raises(G.MGError):
+        ctx.serve_reserve(h, 0)
+    h.free()
+    ctx.close()
