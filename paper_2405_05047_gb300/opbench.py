@@ -40,11 +40,14 @@ def make(workload):
         return (W.elasticity3d(n), B.make_problem(kind=B.MG_ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x1,)),
                 {"omega": 0.5})
     if workload.startswith("oseen"):
-        rounds = int(workload[len("oseen"):] or 12)
+        vanka = workload.startswith("oseen_vanka")      # oseen_vanka[rounds]: cell-patch Vanka levels
+        rounds = int(workload[len("oseen_vanka" if vanka else "oseen"):] or 12)
         lm = W.oseen_channel(1, rounds)
         beta = W.oseen_beta(B.mg_mesh_nodes(lm))
-        return (lm, B.make_problem(kind=B.MG_OSEEN, dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01, conv=beta),
-                {"krylov": B.MG_GMRES})
+        okw = {"krylov": B.MG_GMRES}
+        if vanka:
+            okw["smoother"] = B.MG_SMOOTHER_VANKA
+        return (lm, B.make_problem(kind=B.MG_OSEEN, dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01, conv=beta), okw)
     raise SystemExit(f"unknown workload {workload}")
 
 
@@ -85,7 +88,8 @@ def main():
     h = G.Hierarchy(ctx, lm, pb, B.make_opts(**okw))
     level = args.level if args.level >= 0 else h.levels - 1
     ms = h.time_op(level, OPS[args.op], prec, reps=args.reps)
-    nb = alg_bytes(h.info, level, h.nc, args.op, 4 if prec != B.MG_FP64 else 8)
+    op = "vanka" if args.op == "smooth" and h.info.level_smoother[level] == B.MG_SMOOTHER_VANKA else args.op
+    nb = alg_bytes(h.info, level, h.nc, op, 4 if prec != B.MG_FP64 else 8)   # Vanka: the k_vanka update
     print(json.dumps({"workload": args.workload, "op": args.op, "prec": args.prec, "level": level,
                       "rows": int(h.info.level_nodes[level] * h.nc), "ms_per_launch": ms, "alg_bytes": nb,
                       "achieved_gbs": (nb / (ms * 1e-3) / 1e9) if nb else None}))

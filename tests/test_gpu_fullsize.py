@@ -11,6 +11,10 @@ bench's smoothing steps):
   <= 1e-8 in the oracle's own matrix.
 * Oseen/LPS channel, 657,975 nodes: the same three checks (with the lifted
   inflow data), GMRES(30).
+* the solutions themselves: adaptive transport at the full size against the
+  oracle's FP64 Krylov-MG solve to 1e-12, and the Oseen channel with the
+  bench's Vanka configuration on 9 refinement rounds against sparse LU
+  (FP64 path within 1e-9, mixed within 1e-8, relative lumped-mass L2).
 * elasticity 128^3 (2,146,689 nodes): the oracle's matrix does not fit a
   Python process, so rows are sampled: on 300 seeded free nodes the oracle
   forms (A x)_i and b_i from the element matrices of the surrounding cells;
@@ -164,4 +168,60 @@ def test_elasticity128_fullsize_sampled_rows(ctx):
     bnorm = np.linalg.norm(bl[~fixed])
     assert np.abs(bref - axs).max() <= 1.01 * RTOL * bnorm
     assert np.all(xg[fixed] == 0.0)
+    h.free()
+
+
+def _mass_rel(x, xref, w):
+    e = x - xref
+    return float(np.sqrt(np.sum(w * e * e) / np.sum(w * xref * xref)))
+
+
+def test_td_adaptive_fullsize_solution_matches_oracle(ctx):
+    """The solution itself at the benchmark size (1,212,011 nodes, the bench's
+    V(5,5) BiCGStab configuration): against the oracle's FP64 BiCGStab + MG
+    solve to 1e-12, the FP64 path at rtol 1e-10 is within 1e-9 and the mixed
+    path within 1e-8 (relative lumped-mass L2)."""
+    from oracle import krylov
+    Hh, S, bref = bench._oracle_system()
+    xo, info = krylov.bicgstab(Hh.fine.A, bref, Hh.precondition, rtol=1e-12, maxit=500)
+    assert info["true_rel"] <= 1e-11
+    xref = S.H @ xo
+    w = np.asarray(S.F.sum(axis=1)).ravel()
+    lm = W.td_adaptive(rounds=8, gamma=bench.GAMMA_TD)
+    h = G.Hierarchy(ctx, lm, B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5)),
+                    B.make_opts(krylov=B.MG_BICGSTAB, nu1=bench.NU_TD, nu2=bench.NU_TD))
+    b = dev(bref)
+    for prec, tol in ((B.MG_FP64, 1e-9), (B.MG_MIXED_FP32, 1e-8)):
+        x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+        st = h.solve(b, x, rtol=1e-10, max_it=200, prec=prec)
+        assert st.status == 0 and st.rel_res <= 1e-10, st.as_dict()
+        assert _mass_rel(x.cpu().numpy(), xref, w) <= tol
+    h.free()
+
+
+def test_oseen_vanka_solution_matches_direct_solve(ctx):
+    """The bench's Oseen configuration (GMRES(30) + V(2,2) cell-patch Vanka)
+    on the channel refined 9 rounds (82,955 nodes, 248,865 DoFs; the
+    benchmark's 12 rounds do not fit the oracle's sparse LU): FP64 within
+    1e-9, mixed within 1e-8 of the direct solve (relative lumped-mass L2)."""
+    import scipy.sparse.linalg as spl
+    lm = W.oseen_channel(1, 9)
+    xy = B.mg_mesh_nodes(lm)
+    beta = W.oseen_beta(xy)
+    kw = dict(dirichlet=(0xD, 0xD, 0x0), nu=1e-3, dt=0.01)
+    prob = PB.Problem(PB.OSEEN, conv=beta, **kw)
+    fm = M.Q1Mesh(2, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor)
+    S = PB.build_system(fm, prob, beta=beta)
+    bref = S.rhs(np.zeros(fm.n_nodes * 3), W.oseen_inflow(fm.coords).ravel())
+    xref = S.H @ spl.spsolve(S.A.tocsc(), bref)
+    w = np.repeat(np.asarray(S.F.sum(axis=1)).ravel(), 3)
+    h = G.Hierarchy(ctx, lm, B.make_problem(kind=B.MG_OSEEN, conv=beta, **kw),
+                    B.make_opts(krylov=B.MG_GMRES, restart=30, smoother=B.MG_SMOOTHER_VANKA))
+    assert all(h.info.level_smoother[l] == B.MG_SMOOTHER_VANKA for l in range(1, h.levels))
+    b = dev(bref)
+    for prec, tol in ((B.MG_FP64, 1e-9), (B.MG_MIXED_FP32, 1e-8)):
+        x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+        st = h.solve(b, x, rtol=1e-10, max_it=500, prec=prec)
+        assert st.status == 0 and st.rel_res <= 1e-10, st.as_dict()
+        assert _mass_rel(x.cpu().numpy(), xref, w) <= tol
     h.free()
