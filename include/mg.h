@@ -163,7 +163,7 @@ typedef struct {
   int autotune;                /* 1 (default): at setup, time V-cycles over
                                   tail thresholds x cluster sizes and keep the
                                   fastest (cached per hierarchy shape); and per
-                                  level of >= 2048 rows time the FP32 sweep over
+                                  level of >= 32768 rows time the FP32 sweep over
                                   SELL windows {0, 256, 1024} x 16-bit columns
                                   {off, on} and keep the fastest for the
                                   FP32 / BF16 copies (cached per level shape;
@@ -214,7 +214,9 @@ typedef struct {
   size_t bytes_workspace;               /* one extra solve workspace (serving)   */
   int tail_levels;                      /* levels run by the cluster tail kernel  */
   int tail_cluster;                     /* CTAs in that kernel's cluster (0: one
-                                           CTA working in shared memory)         */
+                                           CTA working in shared memory; < 0: a
+                                           cluster-resident tail of -tail_cluster
+                                           CTAs, see mg_tune)                    */
   double vcycle_ms;                     /* tuned V-cycle time (0 if not tuned)    */
   int64_t col16_slices;                 /* slices read with 16-bit columns        */
   int64_t col32_slices;                 /* slices of those matrices that keep
@@ -370,11 +372,17 @@ int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, voi
  * (1..16; sizes above the portable 8 only where the GPU schedules such a
  * cluster of 1024-thread CTAs), or, for cluster == 0, on one CTA that first copies their vectors
  * and, coarsest first, as many of their matrices as fit into 200 KB of
- * shared memory (the threshold is lowered until the vectors fit).
+ * shared memory (the threshold is lowered until the vectors fit), or, for
+ * cluster = -2, -4, -8, -16 (scalar problems), cluster-resident on that many
+ * CTAs: every level is cut into equal power-of-two row chunks, one per CTA;
+ * each CTA keeps its chunks of the vectors and its rows of the level and
+ * transfer matrices in shared memory and reads the other CTAs' vector entries
+ * through distributed shared memory (MG_ERR_INVALID when the levels do not
+ * fit 200 KB per CTA or the cluster is not schedulable).
  * tail_rows < 0: time V-cycles of precision prec over a set of thresholds and
  * launch shapes and keep the fastest (what opts.autotune does at setup).
  * Results are bitwise identical for every choice.  Errors: MG_ERR_INVALID
- * (cluster outside 0..16 or not schedulable, unknown precision), MG_ERR_OOM (the shared-memory
+ * (cluster outside -16..16 or not schedulable, unknown precision), MG_ERR_OOM (the shared-memory
  * image of the tail could not be allocated). */
 int mg_tune(mg_hier* h, int prec, int tail_rows, int cluster);
 

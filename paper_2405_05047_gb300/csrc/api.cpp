@@ -694,7 +694,7 @@ int mg_time_op(mg_hier* h, int level, int op, int prec, int reps, double* ms) {
 int64_t mg_launch_count(const mg_hier* h) { return h ? (int64_t)h->launch_count : 0; }
 
 int mg_tune(mg_hier* h, int prec, int tail_rows, int cluster) {
-  if (!h || (tail_rows >= 0 && (cluster < 0 || cluster > 16))) return fail(MG_ERR_INVALID, "bad argument");
+  if (!h || (tail_rows >= 0 && (cluster < -16 || cluster > 16))) return fail(MG_ERR_INVALID, "bad argument");
   int rc = check_prec(h, prec);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(h->solve_mu);

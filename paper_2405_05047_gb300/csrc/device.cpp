@@ -392,20 +392,221 @@ int tail_image(mg_hier* h, int pi, int top, mg_hier::TailImage* out) {
   return MG_OK;
 }
 
+// Cluster-resident image of levels 0..top for a cluster of C CTAs (scalar
+// problems, levels without row permutation).  Level l is cut into chunks of
+// 2^csh_l rows, chunk k belonging to CTA k; each CTA's section holds the
+// header and the rows of its chunks of A, S, P (rows: level l) and R (rows:
+// level l-1), copied from the device arrays; its vectors (b, o, t, r of every
+// level, one chunk each) follow the largest section in shared memory, at the
+// same offsets in every CTA.  Header offsets are shifted by the first index
+// of the CTA's part of each array, so level-wide row, slot and column indices
+// address the staged arrays directly.
+constexpr int64_t kDsmWhole = 1024;
+
+int tail_image_dsm(mg_hier* h, int pi, int top, int C, mg_hier::TailImage* out) {
+  const int key = top | (C << 8);
+  if (h->L[top].n <= kDsmWhole) return fail(MG_ERR_INVALID, "cluster-resident tail: no level to distribute");
+  auto it = h->tail_img.find({pi, key});
+  if (it != h->tail_img.end()) { *out = it->second; return MG_OK; }
+  if (h->nc != 1) return fail(MG_ERR_INVALID, "cluster-resident tail: scalar problems only");
+  const int nt = top + 1;
+  const uint32_t ts = slot_tsize(pi), vs = slot_vsize(pi);
+  struct Arr {
+    std::vector<unsigned char> bytes;
+  };
+  auto down = [&](const void* src, size_t bytes, std::vector<unsigned char>& dst) -> int {
+    dst.resize(bytes);
+    if (bytes) CU(cudaMemcpy(dst.data(), src, bytes, cudaMemcpyDeviceToHost));
+    return MG_OK;
+  };
+  std::vector<int> csh(nt);
+  std::vector<TailLevel> base(nt);
+  // host copies of the tail levels' arrays
+  struct LevelHost {
+    std::vector<unsigned char> sptr, col, col16, val, S, Psptr, Pcol, Pw, Rsptr, Rcol, Rw;
+  };
+  std::vector<LevelHost> LH(nt);
+  int rc;
+  for (int l = 0; l < nt; ++l) {
+    const LevelMats& B = h->L[l];
+    const SellBuf& A = slot_A(B, pi);
+    if (A.v.perm || (l > 0 && (B.P.t.perm || B.R.t.perm || B.P.t.fix || B.R.t.fix)) || B.vanka)
+      return fail(MG_ERR_INVALID, "cluster-resident tail: permuted, masked or Vanka level");
+    // levels of at most kDsmWhole rows stay whole in CTA 0 (their steps need
+    // no cluster barrier); larger ones are cut into C chunks
+    int c = 5;
+    if (B.n <= kDsmWhole)
+      while (((int64_t)1 << c) < B.n) ++c;
+    else
+      while (((int64_t)C << c) < B.n) ++c;
+    csh[l] = c;
+    TailLevel& T = base[l];
+    T.A = A.v;
+    T.omega = B.omega;
+    T.P = B.P.t;
+    T.R = B.R.t;
+    T.S = pi == 0 ? (const void*)B.S64 : (const void*)B.S32;   // device arrays unless the level is staged
+    T.csh = c;
+    LevelHost& H = LH[l];
+    const int64_t slots = A.slots;
+    if ((rc = down(A.v.sptr, (A.v.nslices + 1) * 8, H.sptr))) return rc;
+    if ((rc = down(A.v.col, slots * 4, H.col))) return rc;
+    if (A.v.col16 && (rc = down(A.v.col16, slots * 2, H.col16))) return rc;
+    if ((rc = down(A.v.val, slots * vs, H.val))) return rc;
+    if ((rc = down(pi == 0 ? (const void*)B.S64 : (const void*)B.S32, B.n * ts, H.S))) return rc;
+    if (l > 0) {
+      if ((rc = down(B.P.t.sptr, (B.P.t.nslices + 1) * 8, H.Psptr))) return rc;
+      if ((rc = down(B.P.t.col, B.P.slots * 4, H.Pcol))) return rc;
+      if ((rc = down(B.P.t.w, B.P.slots * 4, H.Pw))) return rc;
+      if ((rc = down(B.R.t.sptr, (B.R.t.nslices + 1) * 8, H.Rsptr))) return rc;
+      if ((rc = down(B.R.t.col, B.R.slots * 4, H.Rcol))) return rc;
+      if ((rc = down(B.R.t.w, B.R.slots * 4, H.Rw))) return rc;
+    }
+  }
+  // every column index a gather can meet must be a row of the gathered level
+  for (int l = 0; l < nt; ++l) {
+    const LevelHost& H = LH[l];
+    const int32_t* col = (const int32_t*)H.col.data();
+    for (size_t k = 0; k < H.col.size() / 4; ++k)
+      if (col[k] < 0 || col[k] >= h->L[l].n) return fail(MG_ERR_INVALID, "cluster-resident tail: column out of range");
+    if (l > 0) {
+      const int32_t* pc = (const int32_t*)H.Pcol.data();
+      for (size_t k = 0; k < H.Pcol.size() / 4; ++k)
+        if (pc[k] < 0 || pc[k] >= h->L[l - 1].n) return fail(MG_ERR_INVALID, "cluster-resident tail: P column");
+      const int32_t* rcl = (const int32_t*)H.Rcol.data();
+      for (size_t k = 0; k < H.Rcol.size() / 4; ++k)
+        if (rcl[k] < 0 || rcl[k] >= h->L[l].n) return fail(MG_ERR_INVALID, "cluster-resident tail: R column");
+    }
+  }
+  const uint64_t hdr_bytes = rnd16((uint64_t)nt * sizeof(TailLevel));
+  // vectors: one chunk per level and vector, at the same offsets in every CTA
+  // (after the largest section, known once the sections are built)
+  uint64_t vec_bytes = 0;
+  for (int l = 0; l < nt; ++l) vec_bytes += 4 * (uint64_t)rnd16(((uint64_t)1 << csh[l]) * ts);
+  if (hdr_bytes + vec_bytes > kTailSmemMax)
+    return fail(MG_ERR_INVALID, "cluster-resident tail does not fit in shared memory");
+  // per CTA: header + its rows of the matrices of the staged levels (coarsest
+  // first while every CTA's section fits next to the vectors; the other
+  // levels read the device arrays, whose level-wide indices work for any row)
+  std::vector<std::vector<unsigned char>> sec(C, std::vector<unsigned char>(hdr_bytes, 0));
+  std::vector<std::vector<TailLevel>> hdrs(C, base);
+  uint32_t mask = 0;
+  for (int l = 0; l < nt; ++l) {
+    std::vector<std::vector<unsigned char>> trial = sec;
+    std::vector<std::vector<TailLevel>> th = hdrs;
+    uint64_t worst = 0;
+    for (int c = 0; c < C; ++c) {
+      std::vector<unsigned char>& out_c = trial[c];
+      auto put = [&](const unsigned char* src, uint64_t bytes, int64_t first, uint32_t esize) -> const void* {
+        const uint64_t q = out_c.size();
+        out_c.resize(q + rnd16(bytes), 0);
+        if (bytes) std::memcpy(out_c.data() + q, src, bytes);
+        return (const void*)(intptr_t)((int64_t)q - first * (int64_t)esize);
+      };
+      // slices [s0, s1) of a SELL array whose chunk is rows [c 2^sh, (c+1) 2^sh)
+      auto slices = [&](int64_t nslices, int sh, int64_t& s0, int64_t& s1) {
+        s0 = std::min<int64_t>(nslices, ((int64_t)c << sh) >> 5);
+        s1 = std::min<int64_t>(nslices, ((int64_t)(c + 1) << sh) >> 5);
+      };
+      const LevelHost& H = LH[l];
+      TailLevel& T = th[c][l];
+      int64_t s0, s1;
+      slices(T.A.nslices, csh[l], s0, s1);
+      const int64_t* sp = (const int64_t*)H.sptr.data();
+      const int64_t o0 = sp[s0] & kSptrMask, o1 = sp[s1] & kSptrMask;
+      T.A.sptr = (const int64_t*)put((const unsigned char*)(sp + s0), (s1 - s0 + 1) * 8, s0, 8);
+      T.A.col = (const int32_t*)put(H.col.data() + o0 * 4, (o1 - o0) * 4, o0, 4);
+      if (!H.col16.empty()) {
+        T.A.col16 = (const int16_t*)put(H.col16.data() + o0 * 2, (o1 - o0) * 2, o0, 2);
+        T.c16 = 1;
+      }
+      T.A.val = put(H.val.data() + o0 * vs, (o1 - o0) * vs, o0, vs);
+      const int64_t r0 = std::min<int64_t>(h->L[l].n, (int64_t)c << csh[l]);
+      const int64_t r1 = std::min<int64_t>(h->L[l].n, (int64_t)(c + 1) << csh[l]);
+      T.S = put(H.S.data() + r0 * ts, (r1 - r0) * ts, r0, ts);
+      if (l > 0) {
+        for (int which = 0; which < 2; ++which) {     // P: rows of level l; R: rows of level l - 1
+          TransferView& V = which == 0 ? T.P : T.R;
+          const std::vector<unsigned char>& vsp = which == 0 ? H.Psptr : H.Rsptr;
+          const std::vector<unsigned char>& vcol = which == 0 ? H.Pcol : H.Rcol;
+          const std::vector<unsigned char>& vw = which == 0 ? H.Pw : H.Rw;
+          int64_t t0, t1;
+          slices(V.nslices, which == 0 ? csh[l] : csh[l - 1], t0, t1);
+          const int64_t* tsp = (const int64_t*)vsp.data();
+          const int64_t q0 = tsp[t0], q1 = tsp[t1];
+          V.sptr = (const int64_t*)put((const unsigned char*)(tsp + t0), (t1 - t0 + 1) * 8, t0, 8);
+          V.col = (const int32_t*)put(vcol.data() + q0 * 4, (q1 - q0) * 4, q0, 4);
+          V.w = (const float*)put(vw.data() + q0 * 4, (q1 - q0) * 4, q0, 4);
+        }
+      }
+      worst = std::max<uint64_t>(worst, out_c.size());
+    }
+    if (rnd16(worst) + vec_bytes > kTailSmemMax) break;   // levels only grow: stage a prefix
+    sec.swap(trial);
+    hdrs.swap(th);
+    mask |= 1u << l;
+  }
+  // the levels left in device memory must have every array there
+  for (int l = 0; l < nt; ++l) {
+    if ((mask >> l) & 1u) continue;
+    const TailLevel& T = base[l];
+    if (!T.A.sptr || !T.A.col || !T.A.val || !T.S || (l > 0 && (!T.P.sptr || !T.P.col || !T.P.w || !T.R.sptr ||
+                                                               !T.R.col || !T.R.w)))
+      return fail(MG_ERR_INVALID, "cluster-resident tail: a level's arrays are missing");
+  }
+  uint64_t section = 0;
+  for (auto& x : sec) section = std::max<uint64_t>(section, x.size());
+  section = rnd16(section);
+  uint64_t v = section;
+  std::vector<uint64_t> vb(nt);
+  for (int l = 0; l < nt; ++l) {
+    vb[l] = v;
+    v += 4 * (uint64_t)rnd16(((uint64_t)1 << csh[l]) * ts);
+  }
+  if (v > kTailSmemMax) return fail(MG_ERR_INVALID, "cluster-resident tail does not fit in shared memory");
+  for (int c = 0; c < C; ++c) {
+    std::vector<TailLevel>& hdr = hdrs[c];
+    for (int l = 0; l < nt; ++l) {
+      const int64_t chunk = rnd16(((uint64_t)1 << csh[l]) * ts), shift = ((int64_t)c << csh[l]) * (int64_t)ts;
+      hdr[l].b = (void*)(intptr_t)((int64_t)vb[l] - shift);
+      hdr[l].o = (void*)(intptr_t)((int64_t)vb[l] + chunk - shift);
+      hdr[l].t = (void*)(intptr_t)((int64_t)vb[l] + 2 * chunk - shift);
+      hdr[l].r = (void*)(intptr_t)((int64_t)vb[l] + 3 * chunk - shift);
+    }
+    std::memcpy(sec[c].data(), hdr.data(), nt * sizeof(TailLevel));
+    sec[c].resize(section, 0);
+  }
+  unsigned char* img = (unsigned char*)dev_alloc(h->ctx, h->allocs, h->bytes, section * C, true);
+  if (!img) return fail(MG_ERR_OOM, "alloc");
+  for (int c = 0; c < C; ++c) CU(cudaMemcpy(img + c * section, sec[c].data(), section, cudaMemcpyHostToDevice));
+  mg_hier::TailImage ti;
+  ti.p = img;
+  ti.image_bytes = (uint32_t)section;
+  ti.section = (uint32_t)section;
+  ti.smem = (uint32_t)v;
+  ti.staged_mask = mask;
+  h->tail_img[{pi, key}] = ti;
+  *out = ti;
+  return MG_OK;
+}
+
 void apply_tail(mg_hier* h, Workspace* w) {
   for (int pi = 0; pi < 3; ++pi) {
     TailParams* P = pi == 0 ? &w->tail64 : (pi == 1 ? &w->tail32 : &w->tail16);
     P->nt = h->tail_top + 1;
-    P->cluster = h->tail_cluster;
+    P->cluster = h->tail_cluster < 0 ? -h->tail_cluster : h->tail_cluster;
+    P->dsm = h->tail_cluster < 0 ? 1 : 0;
     P->image = nullptr;
-    P->image_bytes = P->smem = P->staged_mask = 0;
-    if (h->tail_cluster == 0 && h->tail_top > 0 && has_slot(h, pi)) {
-      auto it = h->tail_img.find({pi, h->tail_top});
+    P->image_bytes = P->smem = P->staged_mask = P->section = 0;
+    if (h->tail_cluster <= 0 && h->tail_top > 0 && has_slot(h, pi)) {
+      const int key = h->tail_top | (h->tail_cluster < 0 ? (-h->tail_cluster) << 8 : 0);
+      auto it = h->tail_img.find({pi, key});
       if (it != h->tail_img.end()) {
         P->image = it->second.p;
         P->image_bytes = it->second.image_bytes;
         P->smem = it->second.smem;
         P->staged_mask = it->second.staged_mask;
+        P->section = it->second.section;
       }
     }
   }
@@ -422,7 +623,7 @@ std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;   // shape -> 
 // Both keep the summation order of every row, so no choice changes a bit of a
 // V-cycle (the FP64 copies keep the size rule: the finest one is also the
 // outer Krylov operator, whose SpMV kernels form dot products in SELL row
-// order).  With opts.autotune the FP32 sweep of the level is timed
+// order).  With opts.autotune the FP32 sweep of a level of >= 32768 rows is timed
 // for a few windows, with and without 16-bit columns, and the fastest is kept
 // (the size rule unless another is faster by 2 %), cached per level shape
 // (dimension, components, row count in quarter-octaves, blocks per row);
@@ -438,7 +639,9 @@ Layout level_layout(mg_hier* h, const BlockCSR& A, bool pat6) {
   const int64_t n = A.n;
   const Layout rule{sigma_for(h, n), idx16_for(h, n)};
   const mg_opts& o = h->opts;
-  if (!o.autotune || o.sell_sigma >= 0 || o.col16 >= 0 || !o.store_fp32 || n < 2048) return rule;
+  // the small levels keep rows in node order (the cluster-resident tail
+  // needs that; there the window barely changes the padding)
+  if (!o.autotune || o.sell_sigma >= 0 || o.col16 >= 0 || !o.store_fp32 || n < kSigmaMinRows) return rule;
   const int nc = h->nc;
   const std::vector<int64_t> key = {h->dim, nc, (int64_t)std::llround(4.0 * std::log2((double)n)),
                                     (A.nnzb() * 8) / std::max<int64_t>(n, 1), pat6 ? 1 : 0};
@@ -738,8 +941,21 @@ void ws_destroy(mg_hier* h, Workspace* w) {
 
 int set_tail(mg_hier* h, int rows, int cluster) {
   int top = tail_top_for(h, rows);
-  cluster = std::max(0, std::min(cluster, 16));
-  if (!tail_cluster_fits(cluster)) return fail(MG_ERR_INVALID, "tail cluster size not schedulable on this GPU");
+  cluster = std::max(-16, std::min(cluster, 16));
+  if (cluster < 0) {   // cluster-resident tail of -cluster CTAs
+    if (cluster != -2 && cluster != -4 && cluster != -8 && cluster != -16)
+      return fail(MG_ERR_INVALID, "cluster-resident tail: 2, 4, 8 or 16 CTAs");
+    if (top == 0) cluster = 1;
+    for (int pi = 0; pi < 3 && top > 0; ++pi) {
+      mg_hier::TailImage ti;
+      int rc;
+      if (!has_slot(h, pi)) continue;
+      if ((rc = tail_image_dsm(h, pi, top, -cluster, &ti))) return rc;
+      if (!tail_dsm_fits(-cluster, ti.smem)) return fail(MG_ERR_INVALID, "cluster-resident tail not schedulable");
+    }
+  } else if (!tail_cluster_fits(cluster)) {
+    return fail(MG_ERR_INVALID, "tail cluster size not schedulable on this GPU");
+  }
   if (cluster == 0) {
     top = staged_top_cap(h, top);
     for (int pi = 0; pi < 3 && top > 0; ++pi) {
@@ -770,7 +986,12 @@ int autotune(mg_hier* h, int prec) {
   cudaStream_t s = h->ctx->stream;
   const int fine = h->nlev - 1;
   const int rows_c[] = {0, 256, 1024, 4096, 16384, 65536};
-  const int cl_c[] = {1, 0, 2, 4, 8, 16};   // 0: one CTA in shared memory
+  // 0: one CTA in shared memory.  The cluster-resident shapes (mg_tune with a
+  // negative cluster) are not among the candidates: on the adaptive
+  // transport hierarchy every one of them was slower than the shared-memory
+  // CTA (V(5,5) cycle 487-575 us against 460 us; the gathers that cross CTA
+  // chunks wait on distributed-shared-memory latency in every batch)
+  const int cl_c[] = {1, 0, 2, 4, 8, 16};
   double best = 1e30;
   int best_rows = 0, best_cl = 1, last_top = -1;
   for (int rows : rows_c) {

@@ -173,12 +173,15 @@ struct mg_hier {
   mgi::SellBuf Lift;                     // finest: free-row x Dirichlet-column couplings (n = 0: none)
   bool has_fp64 = true, has_fp32 = true, has_bf16 = false;
   int tail_top = 0;                      // levels 0..tail_top run in the tail kernel
-  int tail_cluster = 1;                  // 0: one CTA in shared memory, else cluster CTAs
+  int tail_cluster = 1;                  // 0: one CTA in shared memory, > 0: cluster CTAs over device
+                                         // memory, < 0: -CTAs of a cluster-resident tail
   struct TailImage {
     void* p = nullptr;
     uint32_t image_bytes = 0, smem = 0, staged_mask = 0;
+    uint32_t section = 0;                  // cluster-resident image: bytes per CTA section
   };
-  std::map<std::pair<int, int>, TailImage> tail_img;   // (precision slot, top) -> shared-memory image
+  // (precision slot, top | CTAs << 8) -> shared-memory image (CTAs = 0: one CTA)
+  std::map<std::pair<int, int>, TailImage> tail_img;
   double tuned_vcycle_ms = 0.0;
   int64_t col16_slices = 0, col32_slices = 0;   // over the matrices stored with 16-bit columns
   std::vector<int> level_col16;                 // per level: operator copies with 16-bit columns

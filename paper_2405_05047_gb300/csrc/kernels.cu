@@ -84,6 +84,26 @@ __device__ __forceinline__ AT ldv(const VT* p) {
   else return (AT)mld<LM>(p);
 }
 
+// Entry c of a gathered vector.  LM 3 (the cluster-resident small levels):
+// the CTAs of the cluster hold the vector in chunks of 2^gsh entries, chunk k
+// in CTA k, each at the same shared-memory offset, and v is this CTA's chunk
+// minus its first index.  Entry c is in CTA c >> gsh: its address is v + c
+// moved by whole chunks into this CTA's window, then mapped into the owner's
+// window (mapa) when the owner is another CTA.
+template <int LM, typename T>
+__device__ __forceinline__ T xg(const T* v, int64_t c, int gsh) {
+  if constexpr (LM == 3) {
+    namespace cg = cooperative_groups;
+    const int64_t me = (int64_t)cg::this_cluster().block_rank();
+    const int64_t owner = c >> gsh;
+    const T* p = v + (c - (owner - me) * ((int64_t)1 << gsh));
+    if (owner == me) return *p;
+    return *cg::this_cluster().map_shared_rank(const_cast<T*>(p), (unsigned)owner);
+  } else {
+    return vld<LM>(v + c);
+  }
+}
+
 // Output row of SELL row `row` (< A.n): rows may be sorted by length within
 // windows (SELL-C-sigma); perm maps them back to node order.
 template <int LM = 0, typename V>
@@ -99,13 +119,13 @@ __device__ __forceinline__ int64_t srow(const V& A, int64_t row) {
 // warp-uniform.  The summation order is the plain sequential one.
 template <typename AT, int LM, typename VT, typename XT, typename CF>
 __device__ __forceinline__ AT sell_dot1x_loop(int64_t o, int64_t s1, const VT* __restrict__ val, const XT* __restrict__ x,
-                                              CF colat, int64_t S = 32) {
+                                              CF colat, int64_t S = 32, int gsh = 0) {
   AT acc = AT(0);
   for (; o + 3 * S < s1; o += 4 * S) {
     const int c0 = colat(o), c1 = colat(o + S), c2 = colat(o + 2 * S), c3 = colat(o + 3 * S);
     const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + S), v2 = ldv<AT, LM>(val + o + 2 * S),
              v3 = ldv<AT, LM>(val + o + 3 * S);
-    const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2), x3 = vld<LM>(x + c3);
+    const XT x0 = xg<LM>(x, c0, gsh), x1 = xg<LM>(x, c1, gsh), x2 = xg<LM>(x, c2, gsh), x3 = xg<LM>(x, c3, gsh);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
     acc = fmad(v2, (AT)x2, acc);
@@ -115,18 +135,18 @@ __device__ __forceinline__ AT sell_dot1x_loop(int64_t o, int64_t s1, const VT* _
   if (rem == 3) {
     const int c0 = colat(o), c1 = colat(o + S), c2 = colat(o + 2 * S);
     const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + S), v2 = ldv<AT, LM>(val + o + 2 * S);
-    const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1), x2 = vld<LM>(x + c2);
+    const XT x0 = xg<LM>(x, c0, gsh), x1 = xg<LM>(x, c1, gsh), x2 = xg<LM>(x, c2, gsh);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
     acc = fmad(v2, (AT)x2, acc);
   } else if (rem == 2) {
     const int c0 = colat(o), c1 = colat(o + S);
     const AT v0 = ldv<AT, LM>(val + o), v1 = ldv<AT, LM>(val + o + S);
-    const XT x0 = vld<LM>(x + c0), x1 = vld<LM>(x + c1);
+    const XT x0 = xg<LM>(x, c0, gsh), x1 = xg<LM>(x, c1, gsh);
     acc = fmad(v0, (AT)x0, acc);
     acc = fmad(v1, (AT)x1, acc);
   } else if (rem == 1) {
-    acc = fmad(ldv<AT, LM>(val + o), (AT)vld<LM>(x + colat(o)), acc);
+    acc = fmad(ldv<AT, LM>(val + o), (AT)xg<LM>(x, colat(o), gsh), acc);
   }
   return acc;
 }
@@ -141,15 +161,16 @@ template <typename AT, int LM = 0, typename VT, typename XT>
 __device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                          const VT* __restrict__ val, int64_t slice, int lane,
                                          const XT* __restrict__ x, const int16_t* __restrict__ col16 = nullptr,
-                                         int sub = 0, int tpr = 1) {
+                                         int sub = 0, int tpr = 1, int gsh = 0) {
   const int64_t r0 = mld<LM>(sptr + slice), r1 = mld<LM>(sptr + slice + 1);
   const int64_t s0 = (r0 & kSptrMask) + lane + 32 * sub, s1 = r1 & kSptrMask;
   const int64_t S = 32 * (int64_t)tpr;
   if (col16 && !(r0 & 1)) {
     const int base = (int)((slice >> 3) * kCol16Window);
-    return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return base + (int)mld<LM>(col16 + o); }, S);
+    return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return base + (int)mld<LM>(col16 + o); }, S,
+                                   gsh);
   }
-  return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return (int)mld<LM>(col + o); }, S);
+  return sell_dot1x_loop<AT, LM>(s0, s1, val, x, [&](int64_t o) { return (int)mld<LM>(col + o); }, S, gsh);
 }
 
 // Scalar row sum; with tpr > 1 lane sub of the row's group takes slot groups
@@ -157,8 +178,8 @@ __device__ __forceinline__ AT sell_dot1x(const int64_t* __restrict__ sptr, const
 // every lane of the group).
 template <typename T, int LM = 0, typename VT = T, int TPR = 1>
 __device__ __forceinline__ T sell_dot1(const SellView& A, int64_t slice, int lane, const T* __restrict__ x,
-                                       int sub = 0) {
-  T acc = sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x, A.col16, sub, TPR);
+                                       int sub = 0, int gsh = 0) {
+  T acc = sell_dot1x<T, LM>(A.sptr, A.col, (const VT*)A.val, slice, lane, x, A.col16, sub, TPR, gsh);
 #pragma unroll
   for (int o = 1; o < TPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
@@ -330,7 +351,7 @@ __device__ __forceinline__ void sell_dot3(const SellView& A, int64_t slice, int 
 // of 4 slots (loads first), warp-uniform remainder, sequential summation.
 template <typename T, int NC, int LM>
 __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t slice, int lane, const T* v,
-                                                T acc[NC]) {
+                                                T acc[NC], int gsh = 0) {
   const int64_t s0 = mld<LM>(W.sptr + slice) + lane, s1 = mld<LM>(W.sptr + slice + 1);
   int64_t o = s0;
   for (; o < s1; o += 4 * 32) {
@@ -345,7 +366,7 @@ __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t s
     for (int k = 0; k < 4; ++k)
       if (k < m)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) xv[k][c] = vld<LM>(v + (int64_t)NC * j[k] + c);
+        for (int c = 0; c < NC; ++c) xv[k][c] = xg<LM>(v, (int64_t)NC * j[k] + c, gsh);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (k < m)
@@ -363,12 +384,12 @@ __device__ __forceinline__ void transfer_gather(const TransferView& W, int64_t s
 template <typename T, int NC, int LM, typename VT = T, int TPR = 1>
 __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const T* x, const T* b, const T* Sinv,
                                            T* xo, T omega, bool from_zero, int sub = 0, double* xo64 = nullptr,
-                                           double sc = 1.0) {
+                                           double sc = 1.0, int gsh = 0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(A, row);
   if (NC == 1) {
-    T r = from_zero ? T(0) : sell_dot1<T, LM, VT, TPR>(A, slice, lane, x, sub);
+    T r = from_zero ? T(0) : sell_dot1<T, LM, VT, TPR>(A, slice, lane, x, sub, gsh);
     if (row < A.n && sub == 0) {
       const T bi = vld<LM>(b + orow);
       const T v = from_zero ? omega * Sinv[orow] * bi : fmad(omega * Sinv[orow], bi - r, vld<LM>(x + orow));
@@ -402,12 +423,12 @@ __device__ __forceinline__ void row_smooth(const SellView& A, int64_t row, const
 
 template <typename T, int NC, int LM, typename VT = T, int TPR = 1>
 __device__ __forceinline__ void row_residual(const SellView& A, int64_t row, const T* x, const T* b, T* y,
-                                             int sub = 0) {
+                                             int sub = 0, int gsh = 0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(A, row);
   if (NC == 1) {
-    T r = sell_dot1<T, LM, VT, TPR>(A, slice, lane, x, sub);
+    T r = sell_dot1<T, LM, VT, TPR>(A, slice, lane, x, sub, gsh);
     if (row < A.n && sub == 0) y[orow] = vld<LM>(b + orow) - r;
   } else {
     constexpr int tpr = TPR;
@@ -424,14 +445,14 @@ __device__ __forceinline__ void row_residual(const SellView& A, int64_t row, con
 
 template <typename T, int NC, int LM>
 __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row, const T* r, T* d, const T* Sinv,
-                                             T* x0, T omega) {
+                                             T* x0, T omega, int gsh = 0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(R, row);
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
-  transfer_gather<T, NC, LM>(R, slice, lane, r, acc);
+  transfer_gather<T, NC, LM>(R, slice, lane, r, acc, gsh);
   if (row < R.n) {
     if constexpr (NC > 1)
       if (R.fix) {
@@ -460,14 +481,15 @@ __device__ __forceinline__ void row_restrict(const TransferView& R, int64_t row,
 }
 
 template <typename T, int NC, int LM>
-__device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, const T* y, const T* xin, T* xo) {
+__device__ __forceinline__ void row_prolong(const TransferView& P, int64_t row, const T* y, const T* xin, T* xo,
+                                            int gsh = 0) {
   const int64_t slice = row >> 5;
   const int lane = (int)(row & 31);
   const int64_t orow = srow<LM>(P, row);
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
-  transfer_gather<T, NC, LM>(P, slice, lane, y, acc);
+  transfer_gather<T, NC, LM>(P, slice, lane, y, acc, gsh);
   if (row < P.n) {
     if constexpr (NC > 1)
       if (P.fix) {
@@ -618,6 +640,20 @@ __device__ __forceinline__ void tail_sync() {
   if (gridDim.x > 1) cooperative_groups::this_cluster().sync();
   else __syncthreads();
 }
+// Barrier between two steps of the tail.  TLM 3: cluster-wide only when the
+// data written by the step is read by another CTA in the next one (a level
+// cut into several chunks on either side); levels held by one CTA whole
+// need only its own barrier.  Every CTA evaluates the same condition, so all
+// take the same sequence of cluster barriers.
+template <int TLM>
+__device__ __forceinline__ void tail_bar(bool wide) {
+  if constexpr (TLM == 3) {
+    if (wide) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+  } else {
+    tail_sync();
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ void block_copy(T* dst, const T* src, int64_t n) {
@@ -628,12 +664,15 @@ template <typename T, typename VT, int NC, int TLM>
 __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* btop, T* otop, int first_done,
                                                         const int* done, double* o64, const double* scale) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
+  constexpr bool SM = TLM == 2 || TLM == 3;      // vectors (and staged matrices) in shared memory
   const int top = P.nt - 1, ns = P.nu1 + P.nu2;
   const TailLevel* LV = P.lv;
-  if constexpr (TLM == 2) {
+  int64_t me = 0;                                // CTA rank in the cluster (TLM 3)
+  if constexpr (TLM == 3) me = (int64_t)cooperative_groups::this_cluster().block_rank();
+  if constexpr (SM) {
     // the image holds only matrices and offsets: copy it before waiting on
     // the preceding kernel, four 16-byte loads in flight per thread
-    const uint4* src = (const uint4*)P.image;
+    const uint4* src = (const uint4*)((const unsigned char*)P.image + (TLM == 3 ? (size_t)me * P.section : 0));
     uint4* dst = (uint4*)tail_smem;
     const uint32_t n16 = P.image_bytes / 16, step = blockDim.x;
     uint32_t i = threadIdx.x;
@@ -647,12 +686,15 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
     TailLevel* hdr = (TailLevel*)tail_smem;
     for (int l = threadIdx.x; l < P.nt; l += blockDim.x) {
       TailLevel& L = hdr[l];
-      auto at = [&](const void* off) -> unsigned char* { return tail_smem + (uintptr_t)off; };
+      // offsets relative to this CTA's shared memory (TLM 3: shifted by the
+      // chunk's first row, so they may be negative)
+      auto at = [&](const void* off) -> unsigned char* { return tail_smem + (intptr_t)off; };
       L.b = at(L.b); L.o = at(L.o); L.t = at(L.t); L.r = at(L.r);
       if ((P.staged_mask >> l) & 1u) {
         L.A.sptr = (const int64_t*)at(L.A.sptr);
         L.A.col = (const int32_t*)at(L.A.col);
         L.A.val = at(L.A.val);
+        if (TLM == 3 && L.c16) L.A.col16 = (const int16_t*)at(L.A.col16);
         L.S = at(L.S);
         if (l > 0) {
           L.P.sptr = (const int64_t*)at(L.P.sptr); L.P.col = (const int32_t*)at(L.P.col); L.P.w = (const float*)at(L.P.w);
@@ -664,91 +706,128 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailParams P, const T* bt
   }
   pdl_wait();
   if (stopped(done)) return;
-  if constexpr (TLM == 2) {
+  // rows of a level this thread block works on: every row (TLM 1, 2) or the
+  // CTA's chunk (TLM 3)
+  auto own = [&](int64_t rows, int csh, int64_t& lo, int64_t& hi) {
+    if constexpr (TLM == 3) {
+      lo = min(rows, me << csh);
+      hi = min(rows, (me + 1) << csh);
+    } else {
+      lo = 0;
+      hi = rows;
+    }
+  };
+  if constexpr (SM) {
     __syncthreads();
-    const int64_t m = LV[top].A.n * NC;
-    block_copy((T*)LV[top].b, btop, m);
+    int64_t lo, hi;
+    own(LV[top].A.n * NC, TLM == 3 ? LV[top].csh : 0, lo, hi);
+    T* bt = (T*)LV[top].b;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) bt[i] = btop[i];
     if (first_done && P.nu1 > 0) {   // first pre-smoothing sweep, written by the finer level's restriction
       const bool in_o = (ns - 1) % 2 == 0;
-      block_copy((T*)(in_o ? LV[top].o : LV[top].t), in_o ? (const T*)otop : (const T*)P.lv[top].t, m);
+      T* d = (T*)(in_o ? LV[top].o : LV[top].t);
+      const T* sv = in_o ? (const T*)otop : (const T*)P.lv[top].t;
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) d[i] = sv[i];
     }
-    __syncthreads();
+    tail_bar<TLM>(true);             // TLM 3: every chunk is in place before any gather
   }
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  const int tid = SM ? threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = SM ? blockDim.x : gridDim.x * blockDim.x;
   auto bvec = [&](int l) -> T* { return (TLM == 1 && l == top) ? const_cast<T*>(btop) : (T*)LV[l].b; };
   auto ovec = [&](int l) -> T* { return (TLM == 1 && l == top) ? otop : (T*)LV[l].o; };
   auto bufof = [&](int l, int k) -> T* { return ((ns - 1 - k) % 2 == 0) ? ovec(l) : (T*)LV[l].t; };
+  auto csh = [&](int l) -> int { return TLM == 3 ? LV[l].csh : 0; };
+  // TLM 3: level l is cut into several chunks (else CTA 0 holds it whole)
+  auto dist = [&](int l) -> bool { return TLM == 3 && ((int64_t)1 << LV[l].csh) < LV[l].A.n * NC; };
   int fdone = first_done;
   for (int l = top; l >= 1; --l) {
     const TailLevel& L = LV[l];
     const T* S = (const T*)L.S;
     const T om = (T)L.omega;
     const int tpr = L.A.tpr;
+    int64_t lo, hi, clo, chi;
+    own(L.A.nslices * 32, csh(l), lo, hi);
+    own(L.R.nslices * 32, csh(l - 1), clo, chi);
     T* cur = nullptr;
     for (int k = 0; k < P.nu1; ++k) {
       T* dst = bufof(l, k);
       if (!(k == 0 && fdone)) {
         if (tpr == 4)
-          for (int64_t t = tid; t < L.A.nslices * 32 * 4; t += nth)
-            row_smooth<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), S, dst, om, k == 0, (int)(t % 4));
+          for (int64_t t = lo * 4 + tid; t < hi * 4; t += nth)
+            row_smooth<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), S, dst, om, k == 0, (int)(t % 4), nullptr, 1.0,
+                                          csh(l));
         else
-          for (int64_t t = tid; t < L.A.nslices * 32; t += nth)
-            row_smooth<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), S, dst, om, k == 0);
-        tail_sync();
+          for (int64_t t = lo + tid; t < hi; t += nth)
+            row_smooth<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), S, dst, om, k == 0, 0, nullptr, 1.0, csh(l));
+        tail_bar<TLM>(dist(l));
       }
       cur = dst;
     }
     if (tpr == 4)
-      for (int64_t t = tid; t < L.A.nslices * 32 * 4; t += nth)
-        row_residual<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), (T*)L.r, (int)(t % 4));
+      for (int64_t t = lo * 4 + tid; t < hi * 4; t += nth)
+        row_residual<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), (T*)L.r, (int)(t % 4), csh(l));
     else
-      for (int64_t t = tid; t < L.A.nslices * 32; t += nth) row_residual<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), (T*)L.r);
-    tail_sync();
+      for (int64_t t = lo + tid; t < hi; t += nth)
+        row_residual<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), (T*)L.r, 0, csh(l));
+    tail_bar<TLM>(dist(l) || dist(l - 1));
     T* x0 = l - 1 > 0 ? bufof(l - 1, 0) : nullptr;
-    for (int64_t row = tid; row < L.R.nslices * 32; row += nth)
-      row_restrict<T, NC, TLM>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)LV[l - 1].S, x0, (T)LV[l - 1].omega);
-    tail_sync();
+    for (int64_t row = clo + tid; row < chi; row += nth)
+      row_restrict<T, NC, TLM>(L.R, row, (const T*)L.r, bvec(l - 1), (const T*)LV[l - 1].S, x0, (T)LV[l - 1].omega,
+                               csh(l));
+    tail_bar<TLM>(dist(l - 1));
     fdone = l - 1 > 0;
   }
   {   // coarse direct solve, one warp per row
     const int lane = threadIdx.x & 31;
     const T* d = bvec(0);
     T* z = ovec(0);
-    for (int64_t row = tid >> 5; row < P.cn; row += nth >> 5) {
+    int64_t lo, hi;
+    own(P.cn, csh(0), lo, hi);
+    for (int64_t row = lo + (tid >> 5); row < hi; row += nth >> 5) {
       double acc = 0.0;
-      for (int64_t j = lane; j < P.cn; j += 32) acc = fma(P.cinv[row * P.cn + j], (double)vld<TLM>(d + j), acc);
+      for (int64_t j = lane; j < P.cn; j += 32)
+        acc = fma(P.cinv[row * P.cn + j], (double)xg<TLM == 3 ? 3 : TLM>(d, j, csh(0)), acc);
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) z[row] = (T)acc;
     }
-    tail_sync();
+    tail_bar<TLM>(dist(0) || (top >= 1 && dist(1)));
   }
   for (int l = 1; l <= top; ++l) {
     const TailLevel& L = LV[l];
     const T om = (T)L.omega;
     const int tpr = L.A.tpr;
+    int64_t lo, hi, plo, phi;
+    own(L.A.nslices * 32, csh(l), lo, hi);
+    own(L.P.nslices * 32, csh(l), plo, phi);
     T* cur = bufof(l, P.nu1 - 1);       // output of the last pre-smoothing sweep (nu1 >= 1)
     T* pdst = P.nu2 == 0 ? ovec(l) : cur;
-    for (int64_t row = tid; row < L.P.nslices * 32; row += nth)
-      row_prolong<T, NC, TLM>(L.P, row, ovec(l - 1), cur, pdst);
-    tail_sync();
+    for (int64_t row = plo + tid; row < phi; row += nth)
+      row_prolong<T, NC, TLM>(L.P, row, ovec(l - 1), cur, pdst, csh(l - 1));
+    tail_bar<TLM>(dist(l) || (P.nu2 == 0 && l < top && dist(l + 1)));
     cur = pdst;
     for (int k = P.nu1; k < ns; ++k) {
       T* dst = bufof(l, k);
       const bool out64 = o64 && l == top && k == ns - 1;   // last sweep: also the FP64 copy times *scale
       const double sc = out64 ? *scale : 1.0;
       if (tpr == 4)
-        for (int64_t t = tid; t < L.A.nslices * 32 * 4; t += nth)
+        for (int64_t t = lo * 4 + tid; t < hi * 4; t += nth)
           row_smooth<T, NC, TLM, VT, 4>(L.A, t / 4, cur, bvec(l), (const T*)L.S, dst, om, false, (int)(t % 4),
-                                        out64 ? o64 : nullptr, sc);
+                                        out64 ? o64 : nullptr, sc, csh(l));
       else
-        for (int64_t t = tid; t < L.A.nslices * 32; t += nth)
+        for (int64_t t = lo + tid; t < hi; t += nth)
           row_smooth<T, NC, TLM, VT, 1>(L.A, t, cur, bvec(l), (const T*)L.S, dst, om, false, 0,
-                                        out64 ? o64 : nullptr, sc);
-      tail_sync();
+                                        out64 ? o64 : nullptr, sc, csh(l));
+      // the last sweep of a level feeds the prolongation of the next finer one
+      tail_bar<TLM>(dist(l) || (k == ns - 1 && l < top && dist(l + 1)));
       cur = dst;
     }
   }
-  if constexpr (TLM == 2) block_copy(otop, (const T*)LV[top].o, LV[top].A.n * NC);
+  if constexpr (SM) {
+    int64_t lo, hi;
+    own(LV[top].A.n * NC, csh(top), lo, hi);
+    const T* o = (const T*)LV[top].o;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) otop[i] = o[i];
+  }
 }
 
 // z = A_0^{-1} d with the FP64 inverse of the coarse matrix; one warp per row.
@@ -1763,10 +1842,11 @@ MGI_INST(float)
 template <typename T, typename V, int NC, int TLM>
 void launch_tail_k(cudaLaunchConfig_t& cfg, const TailParams& P, const T* b, T* out, int fd, const int* done,
                    double* o64, const double* scale) {
-  if constexpr (TLM == 2) {
+  if constexpr (TLM == 2 || TLM == 3) {
     static std::once_flag once;   // opt in to the large dynamic shared memory, once per instantiation
     std::call_once(once, [] {
       cudaFuncSetAttribute(k_tail<T, V, NC, TLM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+      if (TLM == 3) cudaFuncSetAttribute(k_tail<T, V, NC, TLM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     });
   } else {
     static std::once_flag once;   // clusters of up to 16 CTAs (beyond the portable 8)
@@ -1782,7 +1862,8 @@ void launch_tail_v(cudaLaunchConfig_t& cfg, const TailParams& P, int nc, const T
                    double* o64, const double* scale) {
   const bool staged = P.cluster == 0;
   if (nc == 1) {
-    if (staged) launch_tail_k<T, V, 1, 2>(cfg, P, b, out, fd, done, o64, scale);
+    if (P.dsm) launch_tail_k<T, V, 1, 3>(cfg, P, b, out, fd, done, o64, scale);
+    else if (staged) launch_tail_k<T, V, 1, 2>(cfg, P, b, out, fd, done, o64, scale);
     else launch_tail_k<T, V, 1, 1>(cfg, P, b, out, fd, done, o64, scale);
   } else {
     if (staged) launch_tail_k<T, V, 3, 2>(cfg, P, b, out, fd, done, o64, scale);
@@ -1798,7 +1879,7 @@ void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_don
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cl);
   cfg.blockDim = dim3(kTailThreads);
-  cfg.dynamicSmemBytes = staged ? P.smem : 0;
+  cfg.dynamicSmemBytes = (staged || P.dsm) ? P.smem : 0;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
   int na = 0;
@@ -1859,6 +1940,35 @@ bool tail_cluster_fits(int cl) {
 }
 template void launch_tail<float>(const TailParams&, int, const float*, float*, bool, const int*, cudaStream_t,
                                  double*, const double*);
+
+bool tail_dsm_fits(int cl, uint32_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, uint32_t>, bool> known;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find({cl, smem});
+  if (it != known.end()) return it->second;
+  const void* fn = (const void*)k_tail<float, float, 1, 3>;
+  bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    ok = cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0;
+  }
+  cudaGetLastError();   // a refused query leaves no sticky error
+  known[{cl, smem}] = ok;
+  return ok;
+}
 
 void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, const uint8_t* dirmask,
                 const double* g, double* b, cudaStream_t s) {

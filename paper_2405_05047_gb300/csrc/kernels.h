@@ -146,6 +146,8 @@ struct TailLevel {
   void* t = nullptr;          // ping-pong buffer
   void* r = nullptr;          // residual
   double omega = 0.8;         // smoother damping of this level
+  int csh = 0;                // cluster-resident mode: rows per CTA chunk = 2^csh
+  int c16 = 0;                // cluster-resident mode: A.col16 is a staged offset
 };
 struct TailParams {
   TailLevel lv[kTailMax];     // [0] = coarsest level of the hierarchy
@@ -165,10 +167,24 @@ struct TailParams {
   uint32_t image_bytes = 0;
   uint32_t smem = 0;
   uint32_t staged_mask = 0;
+  // Cluster-resident mode (dsm = 1, scalar problems): a cluster of `cluster`
+  // CTAs, CTA k holding chunk k (rows [k 2^csh, (k+1) 2^csh) of every level)
+  // of every vector at the same shared-memory offset in each CTA, and the rows
+  // of its chunks of the level and transfer matrices; gathers of other CTAs'
+  // entries go through distributed shared memory.  The image has one section
+  // of `section` bytes per CTA (header, then the matrices; vectors follow in
+  // shared memory at offsets equal in every CTA); its header pointers are
+  // byte offsets relative to the CTA's shared memory, shifted by the chunk's
+  // first row so that rows keep their level-wide indices.
+  int dsm = 0;
+  uint32_t section = 0;
 };
 constexpr uint32_t kTailSmemMax = 200 * 1024;   // dynamic shared memory of the staged tail
 // true when the GPU schedules a cluster of cl tail CTAs (always for cl <= 8)
 bool tail_cluster_fits(int cl);
+// true when the GPU schedules a cluster-resident tail of cl CTAs with smem
+// bytes of dynamic shared memory each
+bool tail_dsm_fits(int cl, uint32_t smem);
 template <typename T>
 // o64 (optional): FP64 copy of the output times *scale, written by the last
 // post-smoothing sweep (nothing when nu2 == 0)

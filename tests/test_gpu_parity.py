@@ -454,7 +454,59 @@ def test_tail_kernel_bitwise_equals_level_kernels(ctx, name, nu):
         assert max(staged_levels) >= 2      # the shared-memory tail really ran
     # the autotuner picks one of these shapes and the solve still matches
     h.tune(B.MG_MIXED_FP32, -1)
-    assert 0 <= h.info.tail_cluster <= 16
+    assert -16 <= h.info.tail_cluster <= 16
+    h.free()
+
+
+@pytest.mark.parametrize("name", ["td_adaptive", "poisson64"])
+def test_cluster_resident_tail_bitwise(ctx, name):
+    """The cluster-resident tail (every level cut into power-of-two row chunks,
+    one per CTA, vectors gathered across the cluster through distributed
+    shared memory) runs the same row steps: V-cycles in FP64, FP32 and with
+    BF16 values equal the grid kernels' bit for bit for every cluster size and
+    threshold that fits, and so does a whole solve."""
+    mk, prob, pkw, okw = CASES[name]
+    lm = mk()
+    h = G.Hierarchy(ctx, lm, B.make_problem(**pkw), B.make_opts(autotune=0, store_bf16=1, **okw))
+    n = h.n_dofs
+    rng = np.random.default_rng(19)
+    r = rng.standard_normal(n)
+    oh = mg.Hierarchy(lm, prob, omega=okw.get("omega"))
+    r[oh.fine.sys.fixed] = 0.0
+    shapes = ((0, 1), (512, -2), (1024, -4), (4096, -8), (1 << 20, -8), (4096, -16), (1 << 20, -16))
+    ran = []
+    for prec, dt in ((B.MG_FP64, torch.float64), (B.MG_MIXED_FP32, torch.float32),
+                     (B.MG_MIXED_BF16, torch.float32)):
+        outs = []
+        for rows, cl in shapes:
+            try:
+                h.tune(prec, rows, cl)
+            except G.MGError:
+                assert cl < 0            # a cluster-resident tail may not fit or not be schedulable
+                continue
+            if cl < 0:
+                assert h.info.tail_cluster == cl or h.info.tail_levels == 0
+                ran.append(h.info.tail_levels)
+            z = torch.empty(n, device="cuda", dtype=dt)
+            h.vcycle(dev(r, dt), z, prec)
+            outs.append(z.cpu().numpy())
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o)
+    assert max(ran) >= 3                 # the cluster-resident tail really ran
+    b = torch.empty(n, device="cuda", dtype=torch.float64)
+    h.assemble_rhs(dev(rhs_for(name, h.coords(), 1)), b)
+    sols = []
+    for rows, cl in ((0, 1), (4096, -8)):
+        try:
+            h.tune(B.MG_MIXED_FP32, rows, cl)
+        except G.MGError:
+            continue
+        x = torch.zeros_like(b)
+        st = h.solve(b, x, rtol=1e-10, max_it=200, prec=B.MG_MIXED_FP32)
+        assert st.status == 0
+        sols.append((st.iters, x.cpu().numpy()))
+    for sv in sols[1:]:
+        assert sv[0] == sols[0][0] and np.array_equal(sv[1], sols[0][1])
     h.free()
 
 
