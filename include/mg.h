@@ -239,6 +239,9 @@ typedef struct {
                                            every row's summation order: no V-cycle
                                            bit depends on them; the FP64 copies
                                            keep the size rule)                    */
+  int level_lanes[32];                  /* lanes per row of the level operator's
+                                           FP32 / BF16 copies (1 or 4, the size
+                                           rule of opts.row_lanes)                */
 } mg_info;
 
 typedef struct {
@@ -453,6 +456,33 @@ typedef struct {
 } mg_prof_entry;
 int mg_solve_profiled(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats,
                       mg_prof_entry* entries, int cap, int* n_entries);
+
+/* Batched solve of many small problems in one kernel launch (the per-kernel
+ * launch overhead that dominates small solves, Sec. 6.1, paid once for the
+ * batch).  Problem k: hierarchy h[k], right-hand side b[k] (device, n_dofs
+ * doubles, e.g. from mg_assemble_rhs) and x[k] (device, n_dofs doubles; in:
+ * initial guess, out: solution on all nodes with hanging values filled, as
+ * mg_solve).  A thread block takes the next problem of a work list (largest
+ * first) and runs its whole solve: the Krylov method of mg_solve (CG or
+ * BiCGStab; the same iteration formulas, FP64 vectors, restarts from the
+ * true residual) with the V-cycle of every level in shared memory at
+ * precision prec.  Dot products are summed in a different order than in
+ * mg_solve, so iterates agree with it to rounding, not bit for bit.  The same
+ * hierarchy may appear several times.  Every problem must pass
+ * mg_batch_fits.  Scalar and 3-component problems may be mixed (one launch
+ * each).  stats (optional): count entries, per problem; solve_ms is the whole
+ * batch's device time.  Returns MG_OK when every problem converged, else the
+ * status of the first one that did not (all stats are filled either way);
+ * MG_ERR_INVALID (nothing run) when a problem does not fit.  count = 0: no-op.
+ * Work vectors come from a context arena that grows to the largest batch. */
+int mg_solve_batch(mg_ctx* ctx, int count, mg_hier* const* h, const double* const* b, double* const* x,
+                   double rtol, int max_it, int prec, mg_stats* stats);
+/* 1 when mg_solve_batch can solve h at precision prec (a CG or BiCGStab
+ * problem without defect correction or Vanka levels, at most 16 levels, the
+ * V-cycle vectors of all levels within 200 KiB of shared memory: about 90^2
+ * nodes in 2D or 21^3 in 3D with an FP32 V-cycle), 0 otherwise (the reason in
+ * mg_last_error), MG_ERR_INVALID for a NULL hierarchy. */
+int mg_batch_fits(mg_hier* h, int prec);
 
 /* Serving: continuous batching of solves on resident hierarchies.
  * mg_submit queues a solve of h (b, x device buffers, caller-owned, not to be

@@ -76,7 +76,8 @@ class MgInfo(C.Structure):
                 ("level_col16", C.c_int * 32), ("level_omega", C.c_double * 32),
                 ("level_block_values", C.c_int * 32), ("level_smoother", C.c_int * 32),
                 ("level_vanka_nnzb", C.c_int64 * 32),
-                ("level_sigma", C.c_int64 * 32)]
+                ("level_sigma", C.c_int64 * 32),
+                ("level_lanes", C.c_int * 32)]
 
 
 class MgStats(C.Structure):
@@ -136,6 +137,9 @@ _SIGS = {
     "mg_restrict_static": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_time_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                 C.c_int, C.POINTER(MgStats)]),
+    "mg_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                 C.POINTER(C.c_void_p), C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
+    "mg_batch_fits": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_time_steps2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                  C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
 }
@@ -328,6 +332,28 @@ def mg_solve(h, b, x, rtol, max_it, prec=MG_FP64):
     return st
 
 
+def mg_solve_batch(ctx, hs, bs, xs, rtol, max_it, prec=MG_MIXED_FP32):
+    """Batched solve of len(hs) problems in one launch; bs / xs: device
+    tensors (n_dofs doubles each).  Returns (status, [MgStats per problem])."""
+    k = len(hs)
+    if not (len(bs) == k and len(xs) == k):
+        raise ValueError("hs, bs and xs must have the same length")
+    H = (C.c_void_p * max(k, 1))(*[h for h in hs])
+    Bp = (C.c_void_p * max(k, 1))(*[_ptr(b) for b in bs])
+    Xp = (C.c_void_p * max(k, 1))(*[_ptr(x) for x in xs])
+    st = (MgStats * max(k, 1))()
+    rc = load_library().mg_solve_batch(ctx, k, H, Bp, Xp, rtol, max_it, prec, st)
+    _check(rc, allow=SOLVE_OUTCOMES)
+    return rc, [st[i] for i in range(k)]
+
+
+def mg_batch_fits(h, prec=MG_MIXED_FP32) -> bool:
+    rc = load_library().mg_batch_fits(h, prec)
+    if rc < 0:
+        _check(rc)
+    return rc == 1
+
+
 def mg_solve_profiled(h, b, x, rtol, max_it, prec=MG_FP64, cap=256):
     """mg_solve with per-kernel event timing: (stats, [{kernel, level,
     launches, ms}, ...] sorted by ms, largest first)."""
@@ -428,6 +454,10 @@ class Context:
     def serve_reserve(self, hier, slots, prec=MG_MIXED_FP32):
         return _check(load_library().mg_serve_reserve(self.handle, hier.handle, slots, prec))
 
+    def solve_batch(self, hiers, bs, xs, rtol=1e-8, max_it=200, prec=MG_MIXED_FP32):
+        """mg_solve_batch over Hierarchy objects: (status, [MgStats])."""
+        return mg_solve_batch(self.handle, [h.handle for h in hiers], bs, xs, rtol, max_it, prec)
+
     def close(self):
         """Free every hierarchy of this context, then the context."""
         if self.handle:
@@ -474,6 +504,9 @@ class Hierarchy:
 
     def time_steps(self, theta, f, g, n_steps, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_time_steps(self.handle, theta, f, g, n_steps, rtol, max_it, prec)
+
+    def batch_fits(self, prec=MG_MIXED_FP32):
+        return mg_batch_fits(self.handle, prec)
 
     def time_steps2(self, u, v, f, g, n_steps, dt, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_time_steps2(self.handle, u, v, f, g, n_steps, dt, rtol, max_it, prec)

@@ -214,6 +214,8 @@ int mg_destroy(mg_ctx* c) {
   for (cudaStream_t s : c->free_streams) cudaStreamDestroy(s);
   for (auto& r : c->running)
     if (r->stream) cudaStreamDestroy(r->stream);
+  cudaStreamSynchronize(c->stream);
+  free_batch(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return MG_OK;
@@ -332,6 +334,7 @@ int mg_hier_info(const mg_hier* h, mg_info* info) {
     info->level_omega[l] = h->L[l].omega;
     info->level_block_values[l] = h->level_block_values[l];
     info->level_sigma[l] = h->level_sigma[l];
+    info->level_lanes[l] = h->L[l].A32.slots ? h->L[l].A32.v.tpr : 1;
     info->level_smoother[l] = h->L[l].vanka ? MG_SMOOTHER_VANKA : MG_SMOOTHER_JACOBI;
     info->level_vanka_nnzb[l] = h->L[l].vanka ? std::max(h->L[l].V32.nnz_real, h->L[l].V64.nnz_real) : 0;
   }
@@ -794,6 +797,16 @@ int mg_serve_reserve(mg_ctx* c, mg_hier* h, int slots, int prec) {
   }
   CU(cudaStreamSynchronize(c->stream));
   return MG_OK;
+}
+
+int mg_solve_batch(mg_ctx* c, int count, mg_hier* const* h, const double* const* b, double* const* x, double rtol,
+                   int max_it, int prec, mg_stats* stats) {
+  return solve_batch(c, count, h, b, x, rtol, max_it, prec, stats);
+}
+
+int mg_batch_fits(mg_hier* h, int prec) {
+  if (!h) return fail(MG_ERR_INVALID, "NULL hierarchy");
+  return batch_check(h, prec) == MG_OK ? 1 : 0;
 }
 
 int mg_serve_config(mg_ctx* c, int max_slots) {

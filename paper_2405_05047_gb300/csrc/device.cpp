@@ -1551,4 +1551,208 @@ int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats) {
   return status;
 }
 
+
+// ---------------------------------------------------------------- batched solves
+// Many small problems in one launch (k_batch): every level of each hierarchy
+// runs in the staged tail of the thread block that takes the problem, so a
+// problem qualifies when the vectors of all its levels fit in shared memory
+// at the V-cycle precision.
+int batch_check(const mg_hier* h, int prec) {
+  int rc = check_prec(h, prec);
+  if (rc) return rc;
+  const int method = method_of(h);
+  if (method != M_CG && method != M_BICG)
+    return fail(MG_ERR_INVALID, "batched solves run CG or BiCGStab (not GMRES or the plain multigrid iteration)");
+  if (h->opts.inner_rtol > 0) return fail(MG_ERR_INVALID, "batched solves do not run defect correction");
+  if (h->nlev > kTailMax) return fail(MG_ERR_INVALID, "hierarchy has more levels than the staged tail holds");
+  for (const LevelMats& L : h->L)
+    if (L.vanka) return fail(MG_ERR_INVALID, "batched solves smooth with Jacobi only (no Vanka levels)");
+  const int pi = prec == MG_FP64 ? 0 : (prec == MG_MIXED_FP32 ? 1 : 2);
+  if (tail_vec_bytes(h, pi, h->nlev - 1) > kTailSmemMax)
+    return fail(MG_ERR_INVALID, "the V-cycle vectors of every level do not fit in shared memory");
+  return MG_OK;
+}
+
+namespace {
+
+// Device copy of the staged tail over every level of h for slot pi.
+int batch_tail(mg_hier* h, int pi) {
+  if (h->batch_tp[pi]) return MG_OK;
+  const int top = h->nlev - 1;
+  TailParams P;
+  P.nt = top + 1;
+  P.nu1 = h->opts.nu1;
+  P.nu2 = h->opts.nu2;
+  P.cinv = h->coarse_inv;
+  P.cn = h->coarse_n;
+  P.cluster = 0;
+  mg_hier::TailImage ti;
+  int rc = tail_image(h, pi, top, &ti);
+  if (rc) return rc;
+  P.image = ti.p;
+  P.image_bytes = ti.image_bytes;
+  P.smem = ti.smem;
+  P.staged_mask = ti.staged_mask;
+  void* d = dev_alloc(h->ctx, h->allocs, h->bytes, sizeof(TailParams), true);
+  if (!d) return fail(MG_ERR_OOM, "alloc");
+  CU(cudaMemcpy(d, &P, sizeof(TailParams), cudaMemcpyHostToDevice));
+  h->batch_tp[pi] = (const TailParams*)d;
+  h->batch_smem[pi] = P.smem;
+  return MG_OK;
+}
+
+constexpr size_t kBatchAlign = 256;
+size_t balign(size_t b) { return (b + kBatchAlign - 1) & ~(kBatchAlign - 1); }
+
+}  // namespace
+
+void free_batch(mg_ctx* c) {
+  free_list(c, c->batch_allocs, c->batch_bytes);
+  c->batch_arena = nullptr;
+  c->batch_cap = 0;
+  if (c->batch_host) cudaFreeHost(c->batch_host);
+  c->batch_host = nullptr;
+  c->batch_host_cap = 0;
+  if (c->batch_ev0) cudaEventDestroy(c->batch_ev0);
+  if (c->batch_ev1) cudaEventDestroy(c->batch_ev1);
+  c->batch_ev0 = c->batch_ev1 = nullptr;
+}
+
+int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b, double* const* x, double rtol,
+                int max_it, int prec, mg_stats* stats) {
+  if (!c || count < 0 || (count > 0 && (!hs || !b || !x)) || !(rtol > 0) || max_it < 1)
+    return fail(MG_ERR_INVALID, "bad argument");
+  if (count == 0) return MG_OK;
+  const int pi = prec == MG_FP64 ? 0 : (prec == MG_MIXED_FP32 ? 1 : 2);
+  for (int k = 0; k < count; ++k) {
+    mg_hier* h = hs[k];
+    if (!h || h->ctx != c || !b[k] || !x[k]) return fail(MG_ERR_INVALID, "bad problem " + std::to_string(k));
+    int rc = batch_check(h, prec);
+    if (rc) return rc;
+  }
+  CU(cudaSetDevice(c->device));
+  for (int k = 0; k < count; ++k) {
+    mg_hier* h = hs[k];
+    std::lock_guard<std::mutex> lk(h->solve_mu);   // the tail image map
+    int rc = batch_tail(h, pi);
+    if (rc) return rc;
+  }
+  std::lock_guard<std::mutex> lk(c->batch_mu);
+  cudaStream_t s = c->stream;
+  // arena: work list, order, two counters, then the FP64 work vectors
+  auto nvec = [&](const mg_hier* h) { return method_of(h) == M_CG ? 4 : 9; };
+  const size_t items_b = balign((size_t)count * sizeof(BatchItem));
+  const size_t order_b = balign((size_t)count * sizeof(int));
+  size_t total = items_b + order_b + kBatchAlign;
+  for (int k = 0; k < count; ++k) total += (size_t)nvec(hs[k]) * balign((size_t)hs[k]->n_dofs * 8);
+  if (total > c->batch_cap) {
+    free_list(c, c->batch_allocs, c->batch_bytes);
+    c->batch_arena = nullptr;
+    c->batch_cap = 0;
+    if (c->budget && c->used + total > c->budget) return fail(MG_ERR_ADMISSION, "batch work vectors exceed the HBM budget");
+    c->batch_arena = dev_alloc(c, c->batch_allocs, c->batch_bytes, total, true);
+    if (!c->batch_arena) return fail(MG_ERR_OOM, "batch arena");
+    c->batch_cap = total;
+  }
+  const size_t host_b = items_b + order_b;
+  if (host_b > c->batch_host_cap) {
+    if (c->batch_host) cudaFreeHost(c->batch_host);
+    c->batch_host = nullptr;
+    c->batch_host_cap = 0;
+    CU(cudaMallocHost(&c->batch_host, host_b));
+    c->batch_host_cap = host_b;
+  }
+  if (!c->batch_ev0) CU(cudaEventCreate(&c->batch_ev0));
+  if (!c->batch_ev1) CU(cudaEventCreate(&c->batch_ev1));
+  unsigned char* dev = (unsigned char*)c->batch_arena;
+  BatchItem* d_items = (BatchItem*)dev;
+  int* d_order = (int*)(dev + items_b);
+  unsigned int* d_next = (unsigned int*)(dev + items_b + order_b);
+  BatchItem* items = (BatchItem*)c->batch_host;
+  int* order = (int*)((unsigned char*)c->batch_host + items_b);
+  unsigned char* vp = dev + items_b + order_b + kBatchAlign;
+  for (int k = 0; k < count; ++k) {
+    const mg_hier* h = hs[k];
+    const size_t vb = balign((size_t)h->n_dofs * 8);
+    auto vec = [&]() {
+      double* p = (double*)vp;
+      vp += vb;
+      return p;
+    };
+    BatchItem it;
+    it.tail = h->batch_tp[pi];
+    it.A = h->L.back().A64.v;
+    it.Hc = h->Hc.t;
+    it.fix = h->fixmask;
+    it.b = b[k];
+    it.x = x[k];
+    it.xi = vec(); it.r = vec(); it.p = vec(); it.q = vec();
+    if (method_of(h) == M_BICG) { it.rhat = vec(); it.v = vec(); it.s = vec(); it.ph = vec(); it.sh = vec(); }
+    it.n_nodes = h->n_nodes;
+    it.n = h->n_dofs;
+    it.method = method_of(h) == M_CG ? 1 : 2;
+    it.max_it = max_it;
+    it.rtol = rtol;
+    items[k] = it;
+  }
+  // work list: scalar problems first, then block problems (one launch each),
+  // largest first within each so that the long solves start early
+  std::vector<int> idx(count);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int q) {
+    if (hs[a]->nc != hs[q]->nc) return hs[a]->nc < hs[q]->nc;
+    return hs[a]->n_dofs > hs[q]->n_dofs;
+  });
+  std::copy(idx.begin(), idx.end(), order);
+  int n1 = 0;
+  while (n1 < count && hs[idx[n1]]->nc == 1) ++n1;
+  CU(cudaMemcpyAsync(d_items, items, (size_t)count * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d_order, order, (size_t)count * sizeof(int), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(d_next, 0, 2 * sizeof(unsigned int), s));
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  CU(cudaEventRecord(c->batch_ev0, s));
+  int launches = 0;
+  for (int g = 0; g < 2; ++g) {
+    const int lo = g == 0 ? 0 : n1, hi = g == 0 ? n1 : count;
+    if (hi <= lo) continue;
+    const int nc = g == 0 ? 1 : 3;
+    uint32_t smem = 0;
+    for (int k = lo; k < hi; ++k) smem = std::max(smem, hs[idx[k]]->batch_smem[pi]);
+    const int per_sm = batch_blocks_per_sm(nc, pi, smem);
+    const int grid = std::min(hi - lo, sms * per_sm);
+    launch_batch(d_items, d_order + lo, hi - lo, d_next + g, nc, pi, smem, grid, s);
+    ++launches;
+  }
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(c->batch_ev1, s));
+  CU(cudaMemcpyAsync(items, d_items, (size_t)count * sizeof(BatchItem), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->batch_ev0, c->batch_ev1);
+  int first_bad = MG_OK;
+  for (int k = 0; k < count; ++k) {
+    const BatchItem& it = items[k];
+    int st;
+    if (it.status == -6) st = MG_ERR_NAN;
+    else if (it.status == -5) st = MG_ERR_BREAKDOWN;
+    else if (it.status == 0 && it.rel_res <= rtol) st = MG_OK;
+    else st = MG_ERR_NOT_CONVERGED;
+    if (st != MG_OK && first_bad == MG_OK) first_bad = st;
+    if (stats) {
+      mg_stats& o = stats[k];
+      o = mg_stats{};
+      o.status = st;
+      o.iters = it.iters;
+      o.vcycles = it.iters * (it.method == 2 ? 2 : 1);
+      o.precision = prec;
+      o.rel_res = it.rel_res;
+      o.solve_ms = ms;
+      o.launches = launches;
+    }
+  }
+  for (int k = 0; k < count; ++k) hs[k]->launch_count++;
+  return first_bad;
+}
+
 }  // namespace mgi

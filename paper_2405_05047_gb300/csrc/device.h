@@ -150,6 +150,16 @@ struct mg_ctx {
   std::vector<std::shared_ptr<ServeRequest>> running;
   std::map<uint64_t, std::shared_ptr<ServeRequest>> tickets;
   std::vector<cudaStream_t> free_streams;
+  // batched solves (mg_solve_batch): one batch at a time; device arena for
+  // the work list and the FP64 work vectors, pinned mirror of the work list
+  std::mutex batch_mu;
+  std::vector<mgi::Alloc> batch_allocs;
+  size_t batch_bytes = 0;
+  void* batch_arena = nullptr;
+  size_t batch_cap = 0;
+  void* batch_host = nullptr;
+  size_t batch_host_cap = 0;
+  cudaEvent_t batch_ev0 = nullptr, batch_ev1 = nullptr;
 };
 
 struct mg_hier {
@@ -194,6 +204,10 @@ struct mg_hier {
   std::vector<mgi::Workspace*> all_ws;   // every serving workspace
   size_t ws_bytes = 0;                   // device bytes of one workspace
   int serve_cap = 0;                     // > 0: serving never holds more workspaces (mg_serve_reserve)
+  // batched solves: device copy of the staged tail over every level, per
+  // precision slot (built on first use), and its shared-memory bytes
+  const mgi::TailParams* batch_tp[3] = {nullptr, nullptr, nullptr};
+  uint32_t batch_smem[3] = {0, 0, 0};
   std::atomic<int64_t> launch_count{0};  // kernels enqueued (host-side count)
 };
 
@@ -235,5 +249,13 @@ int solve_start(mg_hier* h, Workspace& w, const double* b, bool b_host, const do
 int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats);
 // The cached solve graph of (method, prec) of a workspace, built on first use.
 int get_graph(mg_hier* h, Workspace& w, int method, int prec, SolveGraph** g);
+// MG_OK when h can be solved by the batched kernel at prec (else the reason,
+// through fail()).
+int batch_check(const mg_hier* h, int prec);
+// Batched solve of count problems (mg_solve_batch).
+int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b, double* const* x, double rtol,
+                int max_it, int prec, mg_stats* stats);
+// Releases the context's batch arena and events.
+void free_batch(mg_ctx* c);
 
 }  // namespace mgi

@@ -191,6 +191,38 @@ template <typename T>
 void launch_tail(const TailParams& P, int nc, const T* b, T* out, bool first_done, const int* done, cudaStream_t s,
                  double* o64 = nullptr, const double* scale = nullptr);
 
+// ---- batched solves of small problems ---------------------------------------
+// One problem of a batched launch.  The thread block that takes it runs the
+// whole Krylov solve: FP64 outer vectors in device memory, the V-cycle as the
+// staged tail over every level of the hierarchy (vectors and matrices in
+// shared memory).  Scalars and the status stay in the block.
+struct BatchItem {
+  const TailParams* tail = nullptr;   // device copy of the hierarchy's staged tail (nt = all levels)
+  SellView A;                         // finest FP64 operator
+  TransferView Hc;                    // hanging rows of H (finest)
+  const uint8_t* fix = nullptr;       // per node: fixed-dof bits (hanging or Dirichlet)
+  const double* b = nullptr;          // assembled right-hand side, n entries
+  double* x = nullptr;                // in: initial guess; out: solution, hanging values filled
+  double *xi = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;   // work vectors, n each
+  double *rhat = nullptr, *v = nullptr, *s = nullptr, *ph = nullptr, *sh = nullptr;   // BiCGStab
+  int64_t n_nodes = 0, n = 0;         // nodes, dofs (n = n_nodes * nc)
+  int method = 1;                     // 1: flexible CG, 2: BiCGStab
+  int max_it = 1;
+  double rtol = 1e-8;
+  // results, written by the block
+  int status = 0;                     // 0, -4 (max_it), -5 (breakdown), -6 (not finite)
+  int iters = 0, rounds = 0;
+  double rel_res = 0.0;               // true ||b - A x|| / ||b_free||
+};
+// Solves count items, taken in the order order[0..count) by grid blocks of
+// kTailThreads threads (a block takes the next item when it finishes one);
+// *next must be 0 at launch.  prec 0: FP64 V-cycle, 1: FP32, 2: FP32 with
+// BF16-stored values.  smem: the largest staged tail of the items.
+void launch_batch(BatchItem* items, const int* order, int count, unsigned int* next, int nc, int prec, uint32_t smem,
+                  int grid, cudaStream_t s);
+// Blocks of the batched kernel resident on one SM with smem bytes of shared memory
+int batch_blocks_per_sm(int nc, int prec, uint32_t smem);
+
 // ---- vector kernels --------------------------------------------------------
 void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, const uint8_t* dirmask,
                 const double* g, double* b, cudaStream_t s);

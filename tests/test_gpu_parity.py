@@ -629,6 +629,44 @@ def test_layout_choices_bitwise_and_tuned(ctx):
         hh.free()
 
 
+@pytest.mark.parametrize("case", ["transport2d", "poisson3d"])
+def test_row_lanes_reported_and_equivalent(ctx, case):
+    """level_lanes reports the lane-count rule (one lane per row everywhere
+    with row_lanes = 1; four on the scalar levels of 1024..32767 rows
+    otherwise).  The lane count changes the row sums' order, so one- and
+    four-lane solves agree to the solver tolerance, not bit for bit."""
+    if case == "transport2d":
+        lm = W.td_adaptive(rounds=5, gamma=1.0)
+        pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    else:
+        lm = W.uniform_leaves(3, (1, 1, 1), 5)
+        pb = B.make_problem(kind=B.MG_POISSON)
+    hs = [G.Hierarchy(ctx, lm, pb, B.make_opts(row_lanes=1, store_bf16=1)),
+          G.Hierarchy(ctx, lm, pb, B.make_opts(store_bf16=1))]
+    info = hs[1].info
+    lanes = [list(hh.info.level_lanes[:hh.info.levels]) for hh in hs]
+    assert set(lanes[0]) == {1}
+    assert lanes[1] == [4 if 1024 <= info.level_nodes[l] < 32768 else 1 for l in range(info.levels)]
+    assert 4 in lanes[1]
+    if case == "transport2d":
+        f = dev(W.f_transport(hs[0].coords(), 1e-3, (1.0, 0.5)))
+    else:
+        f = dev(np.ones(hs[0].n_dofs))
+    for prec in (B.MG_MIXED_FP32, B.MG_MIXED_BF16):
+        sols = []
+        for hh in hs:
+            b = torch.empty(hh.n_dofs, device="cuda", dtype=torch.float64)
+            hh.assemble_rhs(f, b)
+            x = torch.zeros_like(b)
+            st = hh.solve(b, x, rtol=1e-10, max_it=100, prec=prec)
+            assert st.status == 0
+            sols.append((st.iters, x.cpu().numpy()))
+        assert abs(sols[0][0] - sols[1][0]) <= 1
+        assert np.linalg.norm(sols[0][1] - sols[1][1]) <= 1e-8 * np.linalg.norm(sols[0][1])
+    for hh in hs:
+        hh.free()
+
+
 def test_direct_launch_mode_equals_graph(ctx):
     lm = W.td_adaptive(rounds=4, gamma=1.0)
     pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
