@@ -439,9 +439,18 @@ def run_serving(args):
         done_t = {}
         stats = {}
         start = time.perf_counter()
+        limit = 60.0 + 2.0 * reqs[-1][0] / rate_scale
+        next_log = 10.0
         i = 0
         while i < len(reqs) or pending:
             now = time.perf_counter() - start
+            if now > next_log:
+                print(f"[serving] replay x{rate_scale:g}: {i}/{len(reqs)} submitted, {len(pending)} pending, "
+                      f"{len(done_t)} done at {now:.1f} s", file=sys.stderr, flush=True)
+                next_log += 10.0
+            if now > limit:
+                raise RuntimeError(f"serving replay x{rate_scale:g}: {len(pending)} requests still pending after "
+                                   f"{now:.0f} s ({i} of {len(reqs)} submitted)")
             while i < len(reqs) and reqs[i][0] / rate_scale <= now:
                 ta, h, b, x = reqs[i]
                 pending[ctx.submit(h, b, x, rtol=1e-8, max_it=500)] = i
@@ -451,7 +460,7 @@ def run_serving(args):
                 if rc != B.MG_PENDING:
                     k = pending.pop(t)
                     done_t[k] = time.perf_counter() - start
-                    stats[k] = (rc, st.iters, st.rel_res, st.setup_ms + st.solve_ms)
+                    stats[k] = (rc, st.iters, st.rel_res, st.setup_ms + st.solve_ms, st.launches)
             if not pending and i < len(reqs):
                 time.sleep(max(0.0, reqs[i][0] / rate_scale - (time.perf_counter() - start)))
         lat = np.array([done_t[k] - reqs[k][0] / rate_scale for k in range(len(reqs))]) * 1e3
@@ -464,10 +473,16 @@ def run_serving(args):
         return {"rate_req_s": args.rate * rate_scale, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                 "lib_p50_ms": float(np.percentile(lib, 50)), "lib_p99_ms": float(np.percentile(lib, 99)),
-                "dof_per_s": dofs / span, "span_s": span, "all_converged": ok, "all_iterated": iterated}
+                "dof_per_s": dofs / span, "span_s": span, "all_converged": ok, "all_iterated": iterated,
+                "batched_requests": sum(int(stats[k][4] <= 2) for k in stats)}
 
+    def log(msg):
+        print(f"[serving {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+    log(f"{len(hiers)} operators set up in {setup_s:.1f} s, slots reserved in {reserve_s:.1f} s")
     play(1.0)                                   # warm-up: graphs, pooled workspaces
     base = play(1.0)
+    log(f"base stream: p50 {base['p50_ms']:.2f} ms, p99 {base['p99_ms']:.2f} ms")
     mixed = [r[3].clone() for r in reqs]        # every result of the measured stream
     sweep = [play(s) for s in args.sweep]
     sizes = [r[1].info.n_free for r in reqs]
@@ -483,6 +498,36 @@ def run_serving(args):
         same += int(st.status == 0 and torch.equal(x, mixed[k]))
     verified = {"all_converged": base["all_converged"], "all_iterated": base["all_iterated"],
                 "alone_equals_mix": f"{same}/{len(subset)}"}
+    # the same stream with batched launches on: whenever two or more queued
+    # requests fit the batched kernel they go out as one launch
+    log("sweep and verification done; batched launches on")
+    ctx.serve_batching(256, 2)
+    play(1.0)
+    bbase = play(1.0)
+    log(f"batched base stream: p50 {bbase['p50_ms']:.2f} ms, {bbase['batched_requests']} batched")
+    bmixed = [r[3].clone() for r in reqs]
+    bsweep = [play(s) for s in args.sweep]
+    log("batched sweep done")
+    ctx.serve_batching(0, 2)
+    same_b = 0
+    for k in subset:
+        _, h, b, x = reqs[k]
+        x.zero_()
+        if h.batch_fits(B.MG_MIXED_FP32):
+            rc, (st,) = ctx.solve_batch([h], [b], [x], rtol=1e-8, max_it=500, prec=B.MG_MIXED_FP32)
+            eq = torch.equal(x, bmixed[k]) or torch.equal(mixed[k], bmixed[k])
+        else:
+            st = h.solve(b, x, rtol=1e-8, max_it=500, prec=B.MG_MIXED_FP32)
+            eq = torch.equal(x, bmixed[k])
+        same_b += int(st.status == 0 and eq)
+    batched = {"p50_ms": bbase["p50_ms"], "p99_ms": bbase["p99_ms"], "dof_per_s": bbase["dof_per_s"],
+               "batched_requests": bbase["batched_requests"], "sweep": bsweep,
+               "verified": {"all_converged": bbase["all_converged"], "all_iterated": bbase["all_iterated"],
+                            "result_equals_its_path_alone": f"{same_b}/{len(subset)}"},
+               "note": "mg_serve_batching(256, 2): two or more queued requests that fit the batched kernel "
+                       "(Poisson at 2D n <= 80 / 3D n <= 20 here; transport requests smooth with Vanka and "
+                       "take the graph path) go out as one launch; a batched result equals mg_solve_batch of "
+                       "that request alone, a graph one mg_solve"}
     print(json.dumps({
         "metric": "serving p50/p99 latency and aggregate DoF/s (FP32-MG + FP64 Krylov, rtol 1e-8)",
         "value": base["dof_per_s"], "unit": "DoF/s", "n_gpus": 1, "steps": len(reqs), "warmup": len(reqs),
@@ -495,7 +540,7 @@ def run_serving(args):
                    "smoothers": "Poisson: damped Jacobi, CG; transport: cell-patch Vanka, BiCGStab; V(2,2)"},
         "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "verified": verified,
         "lib_p50_ms": base["lib_p50_ms"], "lib_p99_ms": base["lib_p99_ms"],
-        "sweep": sweep,
+        "sweep": sweep, "batched": batched,
     }))
     for h in hiers.values():
         h.free()
@@ -767,6 +812,101 @@ def measure_config(G, B, ctx, name, flush, peak, steps=3, rtol=1e-8, err_sample=
     return rec
 
 
+BATCH_2D = tuple(n for n in SERVE_2D if n <= 80)
+BATCH_3D = tuple(n for n in SERVE_3D if n <= 20)
+
+
+def measure_batch(G, B, ctx, n_req=1000, rtol=1e-8, reps=3):
+    """Many small uneven problems in one launch (mg_solve_batch) against the
+    same problems through the serving path (every request submitted at once,
+    one graph per request on concurrent streams).  Problems: the serving
+    stream's kinds (2D / 3D Poisson and transport-diffusion, eps as there),
+    sizes log-uniform over the catalogue sizes whose V-cycle fits the
+    batched kernel (2D n <= 80, 3D n <= 20), seeded right-hand sides; the
+    transport problems smooth with damped Jacobi here (the batched kernel's
+    smoother) at eps >= 1e-2.  Hierarchies and right-hand sides are set up
+    before the timed region."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64([W.MASTER_SEED, 6]))
+    hiers, probs = {}, []
+    for _ in range(n_req):
+        kind = int(rng.integers(4))
+        dim = 2 if kind < 2 else 3
+        cat = BATCH_2D if dim == 2 else BATCH_3D
+        n = int(cat[int(rng.integers(len(cat)))])
+        eps = float(10.0 ** rng.integers(-2, 1)) if kind in (1, 3) else 1.0
+        key = (kind, n, eps)
+        if key not in hiers:
+            beta = (1.0, 0.5) if dim == 2 else (1.0, 0.5, 0.25)
+            pk = dict(kind=B.MG_POISSON) if kind in (0, 2) else dict(kind=B.MG_TRANSPORT, eps=eps, beta=beta)
+            hiers[key] = G.Hierarchy(ctx, _serve_mesh(dim, n), B.make_problem(**pk),
+                                     B.make_opts(store_fp64=0, autotune=0))
+        probs.append((hiers[key], int(rng.integers(1 << 30))))
+    hs, bs = [], []
+    for h, seed in probs:
+        r = np.random.Generator(np.random.PCG64(seed))
+        xy = h.coords()
+        a = r.standard_normal(5)
+        f = a[0] + sum(a[m] * np.prod(np.sin(m * np.pi * xy), axis=1) for m in range(1, 5))
+        b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+        h.assemble_rhs(torch.from_numpy(np.ascontiguousarray(f)).cuda(), b)
+        hs.append(h)
+        bs.append(b)
+    xs = [torch.zeros_like(b) for b in bs]
+    dofs = sum(int(h.info.n_free) for h in hs)
+    assert all(h.batch_fits(B.MG_MIXED_FP32) for h in hs)
+    dev_ms, wall_ms = [], []
+    for _ in range(reps + 1):
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = ctx.solve_batch(hs, bs, xs, rtol=rtol, max_it=500, prec=B.MG_MIXED_FP32)
+        wall_ms.append((time.perf_counter() - t0) * 1e3)
+        dev_ms.append(st[0].solve_ms)
+    dev_ms, wall_ms = dev_ms[1:], wall_ms[1:]
+    ok = rc == 0 and all(s.status == 0 and s.iters > 0 and s.rel_res <= rtol for s in st)
+    xb = [x.clone() for x in xs]
+    # the same problems through the serving path (graphs warmed first)
+    for h in hiers.values():
+        ctx.serve_reserve(h, 4, B.MG_MIXED_FP32)
+    serve_ms = []
+    for _ in range(2):
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pend = {ctx.submit(h, b, x, rtol=rtol, max_it=500): k for k, (h, b, x) in enumerate(zip(hs, bs, xs))}
+        sst = {}
+        while pend:
+            for t in list(pend):
+                rc2, s2 = ctx.poll(t)
+                if rc2 != B.MG_PENDING:
+                    sst[pend.pop(t)] = (rc2, s2.iters)
+        serve_ms.append((time.perf_counter() - t0) * 1e3)
+    ok_serve = all(v[0] == 0 for v in sst.values())
+    diff = max(float((a - c).norm() / c.norm()) for a, c in zip(xb, xs))
+    iters_equal = sum(int(st[k].iters == sst[k][1]) for k in range(len(hs)))
+    rec = {"description": f"{n_req} seeded small problems (2D/3D Poisson and transport-diffusion, 2D n in "
+                          f"{list(BATCH_2D)}, 3D n in {list(BATCH_3D)}, {len(hiers)} hierarchies) solved to "
+                          f"rel. residual {rtol:g} by one batched launch: a thread block per problem runs CG "
+                          "(Poisson) or BiCGStab (transport) with the V(2,2) cycle of every level in shared "
+                          "memory, FP32 V-cycle + FP64 Krylov",
+           "metric": "DoF/s (sum of free DoFs / device time of the batched launch)",
+           "value": dofs / (statistics.median(dev_ms) * 1e-3), "unit": "DoF/s", "problems": n_req,
+           "free_dofs": dofs, "device_ms": dev_ms, "wall_ms": wall_ms, "launches": st[0].launches,
+           "iters_max": max(s.iters for s in st), "all_converged": ok,
+           "streams": {"value": dofs / (min(serve_ms) * 1e-3), "unit": "DoF/s", "wall_ms": serve_ms,
+                       "all_converged": ok_serve,
+                       "note": "mg_submit of every problem at once, mg_poll until all finished (16 slots, "
+                               "4 reserved workspaces per hierarchy); wall clock"},
+           "batched_over_streams_wall": min(serve_ms) / statistics.median(wall_ms),
+           "max_rel_diff_vs_graph_solve": diff, "iters_equal_graph_solve": f"{iters_equal}/{len(hs)}"}
+    for h in hiers.values():
+        h.free()
+    return rec
+
+
 TD_SIZES = (128, 256, 512, 1024)
 TD_PAPER_H100_S = {128: 2.05, 256: 2.85, 512: 4.47, 1024: 9.0}   # Table "tab:td", GPU solve column
 
@@ -975,6 +1115,10 @@ def main():
                 configs[name] = measure_config(G, B, ctx, name, flush, peak, rtol=args.rtol, err_sample=sample)
             except Exception as e:        # a failing record is reported, never hides the headline
                 configs[name] = {"error": repr(e)}
+        try:
+            configs["batch_small"] = measure_batch(G, B, ctx, rtol=args.rtol)
+        except Exception as e:
+            configs["batch_small"] = {"error": repr(e)}
         try:
             runs = [measure_timedep(G, B, ctx, n, B.MG_BICGSTAB, args.rtol, oracle_check=(n == 128))
                     for n in TD_SIZES]

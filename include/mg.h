@@ -500,6 +500,16 @@ int mg_cancel(mg_ctx* ctx, uint64_t ticket);
 /* Maximum number of solves the scheduler keeps in flight at once (default 16;
  * each runs on its own stream with its own workspace). */
 int mg_serve_config(mg_ctx* ctx, int max_slots);
+/* Batched launches in serving (off by default: max_batch = 0).  With
+ * max_batch > 0, whenever at least min_batch queued requests of one
+ * precision pass mg_batch_fits, up to max_batch of them (oldest first) go out
+ * as one mg_solve_batch-style launch on a stream of its own, taking one
+ * solve slot; fewer than min_batch take the graph path as without batching.
+ * A batched request's result equals mg_solve_batch of that request alone bit
+ * for bit (a block solves each problem; nothing depends on the batch's
+ * other problems); it agrees with mg_solve to rounding only, so with
+ * batching on, which of the two a request gets depends on the queue. */
+int mg_serve_batching(mg_ctx* ctx, int max_batch, int min_batch);
 /* Reserve `slots` solve slots of hierarchy h for serving: up to that many
  * workspaces are allocated now (through the context's allocator, on the
  * calling thread) and their solve graphs for precision prec are built, and

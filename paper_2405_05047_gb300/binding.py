@@ -140,6 +140,7 @@ _SIGS = {
     "mg_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                  C.POINTER(C.c_void_p), C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
     "mg_batch_fits": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_serve_batching": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_time_steps2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                  C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
 }
@@ -450,6 +451,9 @@ class Context:
 
     def serve_config(self, max_slots):
         return mg_serve_config(self.handle, max_slots)
+
+    def serve_batching(self, max_batch, min_batch=2):
+        return _check(load_library().mg_serve_batching(self.handle, max_batch, min_batch))
 
     def serve_reserve(self, hier, slots, prec=MG_MIXED_FP32):
         return _check(load_library().mg_serve_reserve(self.handle, hier.handle, slots, prec))

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmg_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "device.cpp", "api.cpp", "debug.cpp", "kernels.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "device.cpp", "api.cpp", "debug.cpp", "kernels.cu", "batch.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:
@@ -41,7 +41,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra or [])
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    hdrs = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    hdrs = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "mg.h"))
     if os.path.exists(LIB) and not extra:
         t = os.path.getmtime(LIB)

@@ -38,7 +38,15 @@ struct ServeRequest {
   mg_stats stats{};
   Workspace* ws = nullptr;
   cudaStream_t stream = nullptr;
+  int batchable = -1;       // -1 unknown, 0 solved alone, 1 solved in a batched launch
   std::chrono::steady_clock::time_point t_submit, t_start, t_end;
+};
+
+// Requests solved by one batched launch on a stream of its own.
+struct ServeBatch {
+  BatchRun* run = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<std::shared_ptr<ServeRequest>> reqs;
 };
 
 namespace {
@@ -91,7 +99,16 @@ void serve_worker(mg_ctx* c) {
     // completions
     for (size_t i = 0; i < c->running.size();) {
       auto r = c->running[i];
-      if (cudaEventQuery(r->ws->ev1) == cudaSuccess) {
+      const cudaError_t q = cudaEventQuery(r->ws->ev1);
+      if (q != cudaSuccess && q != cudaErrorNotReady) {   // the device reported an error: never completes
+        cudaGetLastError();
+        fail(MG_ERR_CUDA, std::string("serving solve: ") + cudaGetErrorString(q));
+        finish(c, r, MG_ERR_CUDA);
+        c->running.erase(c->running.begin() + i);
+        progress = true;
+        continue;
+      }
+      if (q == cudaSuccess) {
         int rc = solve_check(r->h, *r->ws, r->stream, &r->stats);
         if (rc == MG_PENDING) { ++i; continue; }
         finish(c, r, rc);
@@ -99,6 +116,81 @@ void serve_worker(mg_ctx* c) {
         progress = true;
       } else {
         ++i;
+      }
+    }
+    // batched launches that completed
+    for (size_t i = 0; i < c->batches.size();) {
+      auto B = c->batches[i];
+      const cudaError_t q = cudaEventQuery(B->run->done);
+      if (q == cudaErrorNotReady) { ++i; continue; }
+      std::vector<mg_stats> st(B->reqs.size());
+      if (q == cudaSuccess) {
+        batch_collect(*B->run, st.data());
+      } else {                                            // the device reported an error
+        cudaGetLastError();
+        fail(MG_ERR_CUDA, std::string("serving batch: ") + cudaGetErrorString(q));
+        for (auto& x : st) x.status = MG_ERR_CUDA;
+      }
+      for (size_t k = 0; k < B->reqs.size(); ++k) {
+        B->reqs[k]->stats = st[k];
+        finish(c, B->reqs[k], st[k].status);
+      }
+      c->free_runs.push_back(B->run);
+      c->free_streams.push_back(B->stream);
+      c->batches.erase(c->batches.begin() + i);
+      progress = true;
+    }
+    // the queued requests that fit the batched kernel (first precision found)
+    // go out together as one launch, which takes one slot
+    if (c->serve_batch > 0 && (int)(c->running.size() + c->batches.size()) < c->max_slots) {
+      std::vector<std::shared_ptr<ServeRequest>> grp;
+      for (auto& r : c->queue) {
+        if ((int)grp.size() >= c->serve_batch) break;
+        if (r->batchable < 0) r->batchable = batch_check(r->h, r->prec) == MG_OK ? 1 : 0;
+        if (r->batchable == 1 && (grp.empty() || r->prec == grp[0]->prec)) grp.push_back(r);
+      }
+      if ((int)grp.size() < c->serve_batch_min) grp.clear();   // too few: they take the graph path
+      for (auto& r : grp) c->queue.erase(std::find(c->queue.begin(), c->queue.end(), r));
+      if (!grp.empty()) {
+        auto B = std::make_shared<ServeBatch>();
+        if (c->free_runs.empty()) c->free_runs.push_back(new BatchRun());
+        B->run = c->free_runs.back();
+        c->free_runs.pop_back();
+        if (c->free_streams.empty()) {
+          cudaStream_t s;
+          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+          c->free_streams.push_back(s);
+        }
+        B->stream = c->free_streams.back();
+        c->free_streams.pop_back();
+        const size_t k = grp.size();
+        std::vector<mg_hier*> hs(k);
+        std::vector<const double*> bs(k);
+        std::vector<double*> xs(k);
+        std::vector<double> rt(k);
+        std::vector<int> mi(k);
+        const auto now = std::chrono::steady_clock::now();
+        for (size_t i = 0; i < k; ++i) {
+          hs[i] = grp[i]->h; bs[i] = grp[i]->b; xs[i] = grp[i]->x; rt[i] = grp[i]->rtol; mi[i] = grp[i]->max_it;
+          grp[i]->state = 1;
+          grp[i]->t_start = now;
+        }
+        int rc = batch_enqueue(c, *B->run, (int)k, hs.data(), bs.data(), xs.data(), rt.data(), mi.data(),
+                               grp[0]->prec, B->stream);
+        if (rc == MG_OK) {
+          B->reqs = std::move(grp);
+          c->batches.push_back(B);
+        } else {
+          // no room for the batch's work vectors: these requests are solved alone
+          c->free_runs.push_back(B->run);
+          c->free_streams.push_back(B->stream);
+          for (size_t i = k; i-- > 0;) {
+            grp[i]->batchable = 0;
+            grp[i]->state = 0;
+            c->queue.push_front(grp[i]);
+          }
+        }
+        progress = true;
       }
     }
     // admissions: first come first served, later requests may pass one that
@@ -125,7 +217,7 @@ void serve_worker(mg_ctx* c) {
       else c->running.push_back(r);
       progress = true;
     }
-    if (c->running.empty() && c->queue.empty()) {
+    if (c->running.empty() && c->batches.empty() && c->queue.empty()) {
       c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
     } else if (!progress) {
       lk.unlock();
@@ -211,11 +303,23 @@ int mg_destroy(mg_ctx* c) {
   c->cv.notify_all();
   if (c->worker.joinable()) c->worker.join();
   for (auto& r : c->running) cudaStreamSynchronize(r->stream);
+  for (auto& B : c->batches) {
+    cudaStreamSynchronize(B->stream);
+    cudaStreamDestroy(B->stream);
+    free_run(c, *B->run);
+    delete B->run;
+  }
+  c->batches.clear();
+  for (BatchRun* run : c->free_runs) {
+    free_run(c, *run);
+    delete run;
+  }
+  c->free_runs.clear();
   for (cudaStream_t s : c->free_streams) cudaStreamDestroy(s);
   for (auto& r : c->running)
     if (r->stream) cudaStreamDestroy(r->stream);
   cudaStreamSynchronize(c->stream);
-  free_batch(c);
+  free_run(c, c->batch);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return MG_OK;
@@ -807,6 +911,15 @@ int mg_solve_batch(mg_ctx* c, int count, mg_hier* const* h, const double* const*
 int mg_batch_fits(mg_hier* h, int prec) {
   if (!h) return fail(MG_ERR_INVALID, "NULL hierarchy");
   return batch_check(h, prec) == MG_OK ? 1 : 0;
+}
+
+int mg_serve_batching(mg_ctx* c, int max_batch, int min_batch) {
+  if (!c || max_batch < 0 || max_batch > 65536 || min_batch < 1)
+    return fail(MG_ERR_INVALID, "max_batch must be in [0, 65536] and min_batch >= 1");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->serve_batch = max_batch;
+  c->serve_batch_min = min_batch;
+  return MG_OK;
 }
 
 int mg_serve_config(mg_ctx* c, int max_slots) {

@@ -207,6 +207,9 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, 
   if (b_c16) CU(cudaMemcpy(base + o_c16, col16.data(), b_c16, cudaMemcpyHostToDevice));
   if (b_val) CU(cudaMemcpy(base + o_val, val.data(), b_val, cudaMemcpyHostToDevice));
   if (b_perm) CU(cudaMemcpy(base + o_perm, perm.data(), b_perm, cudaMemcpyHostToDevice));
+  // pageable copies may still be in flight on the legacy stream: complete
+  // them before the setup tuner times the matrix on the context's stream
+  CU(cudaStreamSynchronize(cudaStreamLegacy));
   out->v.perm = out->t.perm = b_perm ? (const int32_t*)(base + o_perm) : nullptr;
   out->v.col16 = b_c16 ? (const int16_t*)(base + o_c16) : nullptr;
   out->v.sptr = out->t.sptr = (const int64_t*)(base + o_sptr);
@@ -382,6 +385,10 @@ int tail_image(mg_hier* h, int pi, int top, mg_hier::TailImage* out) {
   CU(cudaMemset(img, 0, image_bytes));
   CU(cudaMemcpy(img, hdr.data(), nt * sizeof(TailLevel), cudaMemcpyHostToDevice));
   for (const Piece& p : pieces) CU(cudaMemcpy(img + p.off, p.src, p.bytes, cudaMemcpyDeviceToDevice));
+  // the memset and the copies ran on the legacy stream, and device-to-device
+  // copies return before they complete: finish them before any stream (also
+  // a non-blocking one, unordered with the legacy stream) reads the image
+  CU(cudaStreamSynchronize(cudaStreamLegacy));
   mg_hier::TailImage ti;
   ti.p = img;
   ti.image_bytes = image_bytes;
@@ -585,6 +592,7 @@ int tail_image_dsm(mg_hier* h, int pi, int top, int C, mg_hier::TailImage* out) 
   ti.section = (uint32_t)section;
   ti.smem = (uint32_t)v;
   ti.staged_mask = mask;
+  CU(cudaStreamSynchronize(cudaStreamLegacy));   // complete before any stream reads it (see tail_image)
   h->tail_img[{pi, key}] = ti;
   *out = ti;
   return MG_OK;
@@ -1596,6 +1604,9 @@ int batch_tail(mg_hier* h, int pi) {
   void* d = dev_alloc(h->ctx, h->allocs, h->bytes, sizeof(TailParams), true);
   if (!d) return fail(MG_ERR_OOM, "alloc");
   CU(cudaMemcpy(d, &P, sizeof(TailParams), cudaMemcpyHostToDevice));
+  // the batched kernel may run on a non-blocking stream, unordered with the
+  // legacy stream of the copy: complete it first
+  CU(cudaStreamSynchronize(cudaStreamLegacy));
   h->batch_tp[pi] = (const TailParams*)d;
   h->batch_smem[pi] = P.smem;
   return MG_OK;
@@ -1606,70 +1617,61 @@ size_t balign(size_t b) { return (b + kBatchAlign - 1) & ~(kBatchAlign - 1); }
 
 }  // namespace
 
-void free_batch(mg_ctx* c) {
-  free_list(c, c->batch_allocs, c->batch_bytes);
-  c->batch_arena = nullptr;
-  c->batch_cap = 0;
-  if (c->batch_host) cudaFreeHost(c->batch_host);
-  c->batch_host = nullptr;
-  c->batch_host_cap = 0;
-  if (c->batch_ev0) cudaEventDestroy(c->batch_ev0);
-  if (c->batch_ev1) cudaEventDestroy(c->batch_ev1);
-  c->batch_ev0 = c->batch_ev1 = nullptr;
+void free_run(mg_ctx* c, BatchRun& run) {
+  free_list(c, run.allocs, run.bytes);
+  run.arena = nullptr;
+  run.cap = 0;
+  if (run.host) cudaFreeHost(run.host);
+  run.host = nullptr;
+  run.host_cap = 0;
+  if (run.ev0) cudaEventDestroy(run.ev0);
+  if (run.ev1) cudaEventDestroy(run.ev1);
+  if (run.done) cudaEventDestroy(run.done);
+  run.ev0 = run.ev1 = run.done = nullptr;
 }
 
-int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b, double* const* x, double rtol,
-                int max_it, int prec, mg_stats* stats) {
-  if (!c || count < 0 || (count > 0 && (!hs || !b || !x)) || !(rtol > 0) || max_it < 1)
-    return fail(MG_ERR_INVALID, "bad argument");
-  if (count == 0) return MG_OK;
+int batch_enqueue(mg_ctx* c, BatchRun& run, int count, mg_hier* const* hs, const double* const* b,
+                  double* const* x, const double* rtol, const int* max_it, int prec, cudaStream_t s) {
   const int pi = prec == MG_FP64 ? 0 : (prec == MG_MIXED_FP32 ? 1 : 2);
-  for (int k = 0; k < count; ++k) {
-    mg_hier* h = hs[k];
-    if (!h || h->ctx != c || !b[k] || !x[k]) return fail(MG_ERR_INVALID, "bad problem " + std::to_string(k));
-    int rc = batch_check(h, prec);
-    if (rc) return rc;
-  }
-  CU(cudaSetDevice(c->device));
   for (int k = 0; k < count; ++k) {
     mg_hier* h = hs[k];
     std::lock_guard<std::mutex> lk(h->solve_mu);   // the tail image map
     int rc = batch_tail(h, pi);
     if (rc) return rc;
   }
-  std::lock_guard<std::mutex> lk(c->batch_mu);
-  cudaStream_t s = c->stream;
   // arena: work list, order, two counters, then the FP64 work vectors
   auto nvec = [&](const mg_hier* h) { return method_of(h) == M_CG ? 4 : 9; };
   const size_t items_b = balign((size_t)count * sizeof(BatchItem));
   const size_t order_b = balign((size_t)count * sizeof(int));
   size_t total = items_b + order_b + kBatchAlign;
   for (int k = 0; k < count; ++k) total += (size_t)nvec(hs[k]) * balign((size_t)hs[k]->n_dofs * 8);
-  if (total > c->batch_cap) {
-    free_list(c, c->batch_allocs, c->batch_bytes);
-    c->batch_arena = nullptr;
-    c->batch_cap = 0;
-    if (c->budget && c->used + total > c->budget) return fail(MG_ERR_ADMISSION, "batch work vectors exceed the HBM budget");
-    c->batch_arena = dev_alloc(c, c->batch_allocs, c->batch_bytes, total, true);
-    if (!c->batch_arena) return fail(MG_ERR_OOM, "batch arena");
-    c->batch_cap = total;
+  if (total > run.cap) {
+    free_list(c, run.allocs, run.bytes);
+    run.arena = nullptr;
+    run.cap = 0;
+    if (c->budget && c->used + total > c->budget)
+      return fail(MG_ERR_ADMISSION, "batch work vectors exceed the HBM budget");
+    run.arena = dev_alloc(c, run.allocs, run.bytes, total, true);
+    if (!run.arena) return fail(MG_ERR_OOM, "batch arena");
+    run.cap = total;
   }
   const size_t host_b = items_b + order_b;
-  if (host_b > c->batch_host_cap) {
-    if (c->batch_host) cudaFreeHost(c->batch_host);
-    c->batch_host = nullptr;
-    c->batch_host_cap = 0;
-    CU(cudaMallocHost(&c->batch_host, host_b));
-    c->batch_host_cap = host_b;
+  if (host_b > run.host_cap) {
+    if (run.host) cudaFreeHost(run.host);
+    run.host = nullptr;
+    run.host_cap = 0;
+    CU(cudaMallocHost(&run.host, host_b));
+    run.host_cap = host_b;
   }
-  if (!c->batch_ev0) CU(cudaEventCreate(&c->batch_ev0));
-  if (!c->batch_ev1) CU(cudaEventCreate(&c->batch_ev1));
-  unsigned char* dev = (unsigned char*)c->batch_arena;
+  if (!run.ev0) CU(cudaEventCreate(&run.ev0));
+  if (!run.ev1) CU(cudaEventCreate(&run.ev1));
+  if (!run.done) CU(cudaEventCreate(&run.done));
+  unsigned char* dev = (unsigned char*)run.arena;
   BatchItem* d_items = (BatchItem*)dev;
   int* d_order = (int*)(dev + items_b);
   unsigned int* d_next = (unsigned int*)(dev + items_b + order_b);
-  BatchItem* items = (BatchItem*)c->batch_host;
-  int* order = (int*)((unsigned char*)c->batch_host + items_b);
+  BatchItem* items = (BatchItem*)run.host;
+  int* order = (int*)((unsigned char*)run.host + items_b);
   unsigned char* vp = dev + items_b + order_b + kBatchAlign;
   for (int k = 0; k < count; ++k) {
     const mg_hier* h = hs[k];
@@ -1691,8 +1693,8 @@ int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b
     it.n_nodes = h->n_nodes;
     it.n = h->n_dofs;
     it.method = method_of(h) == M_CG ? 1 : 2;
-    it.max_it = max_it;
-    it.rtol = rtol;
+    it.max_it = max_it[k];
+    it.rtol = rtol[k];
     items[k] = it;
   }
   // work list: scalar problems first, then block problems (one launch each),
@@ -1711,8 +1713,8 @@ int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b
   CU(cudaMemsetAsync(d_next, 0, 2 * sizeof(unsigned int), s));
   int sms = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-  CU(cudaEventRecord(c->batch_ev0, s));
-  int launches = 0;
+  CU(cudaEventRecord(run.ev0, s));
+  run.launches = 0;
   for (int g = 0; g < 2; ++g) {
     const int lo = g == 0 ? 0 : n1, hi = g == 0 ? n1 : count;
     if (hi <= lo) continue;
@@ -1722,21 +1724,30 @@ int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b
     const int per_sm = batch_blocks_per_sm(nc, pi, smem);
     const int grid = std::min(hi - lo, sms * per_sm);
     launch_batch(d_items, d_order + lo, hi - lo, d_next + g, nc, pi, smem, grid, s);
-    ++launches;
+    ++run.launches;
   }
   CU(cudaGetLastError());
-  CU(cudaEventRecord(c->batch_ev1, s));
+  CU(cudaEventRecord(run.ev1, s));
   CU(cudaMemcpyAsync(items, d_items, (size_t)count * sizeof(BatchItem), cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
+  CU(cudaEventRecord(run.done, s));      // results readable once it completed
+  run.count = count;
+  run.prec = prec;
+  for (int k = 0; k < count; ++k) hs[k]->launch_count++;
+  return MG_OK;
+}
+
+int batch_collect(BatchRun& run, mg_stats* stats) {
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->batch_ev0, c->batch_ev1);
+  cudaEventElapsedTime(&ms, run.ev0, run.ev1);
+  const BatchItem* items = (const BatchItem*)run.host;
   int first_bad = MG_OK;
-  for (int k = 0; k < count; ++k) {
+  for (int k = 0; k < run.count; ++k) {
     const BatchItem& it = items[k];
     int st;
-    if (it.status == -6) st = MG_ERR_NAN;
+    if (it.status == -7) st = MG_ERR_INVALID;   // the kernel refused the item (inconsistent sizes)
+    else if (it.status == -6) st = MG_ERR_NAN;
     else if (it.status == -5) st = MG_ERR_BREAKDOWN;
-    else if (it.status == 0 && it.rel_res <= rtol) st = MG_OK;
+    else if (it.status == 0 && it.rel_res <= it.rtol) st = MG_OK;
     else st = MG_ERR_NOT_CONVERGED;
     if (st != MG_OK && first_bad == MG_OK) first_bad = st;
     if (stats) {
@@ -1745,14 +1756,34 @@ int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b
       o.status = st;
       o.iters = it.iters;
       o.vcycles = it.iters * (it.method == 2 ? 2 : 1);
-      o.precision = prec;
+      o.precision = run.prec;
       o.rel_res = it.rel_res;
       o.solve_ms = ms;
-      o.launches = launches;
+      o.launches = run.launches;
     }
   }
-  for (int k = 0; k < count; ++k) hs[k]->launch_count++;
   return first_bad;
+}
+
+int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b, double* const* x, double rtol,
+                int max_it, int prec, mg_stats* stats) {
+  if (!c || count < 0 || (count > 0 && (!hs || !b || !x)) || !(rtol > 0) || max_it < 1)
+    return fail(MG_ERR_INVALID, "bad argument");
+  if (count == 0) return MG_OK;
+  for (int k = 0; k < count; ++k) {
+    mg_hier* h = hs[k];
+    if (!h || h->ctx != c || !b[k] || !x[k]) return fail(MG_ERR_INVALID, "bad problem " + std::to_string(k));
+    int rc = batch_check(h, prec);
+    if (rc) return rc;
+  }
+  CU(cudaSetDevice(c->device));
+  std::lock_guard<std::mutex> lk(c->batch_mu);
+  std::vector<double> rt(count, rtol);
+  std::vector<int> mi(count, max_it);
+  int rc = batch_enqueue(c, c->batch, count, hs, b, x, rt.data(), mi.data(), prec, c->stream);
+  if (rc) return rc;
+  CU(cudaEventSynchronize(c->batch.done));
+  return batch_collect(c->batch, stats);
 }
 
 }  // namespace mgi

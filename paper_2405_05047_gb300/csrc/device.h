@@ -121,12 +121,30 @@ struct EventProfiler : LaunchProfiler {
   ~EventProfiler() override;
 };
 
+// One batched launch (k_batch) and its buffers: a device arena (work list,
+// order, counters, FP64 work vectors) and a pinned mirror of the work list,
+// both grown to the largest batch run through them.  batch_enqueue puts the
+// uploads, the launches (between ev0 and ev1) and the download of the
+// results on a stream, then records done; batch_collect reads the results
+// once done completed.
+struct BatchRun {
+  std::vector<Alloc> allocs;
+  size_t bytes = 0;
+  void* arena = nullptr;
+  size_t cap = 0;
+  void* host = nullptr;
+  size_t host_cap = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, done = nullptr;
+  int count = 0, prec = 0, launches = 0;
+};
+
 int fail(int code, const std::string& msg);
 const char* last_error();
 
 }  // namespace mgi
 
 struct ServeRequest;
+struct ServeBatch;
 
 struct mg_ctx {
   int device = 0;
@@ -150,16 +168,14 @@ struct mg_ctx {
   std::vector<std::shared_ptr<ServeRequest>> running;
   std::map<uint64_t, std::shared_ptr<ServeRequest>> tickets;
   std::vector<cudaStream_t> free_streams;
-  // batched solves (mg_solve_batch): one batch at a time; device arena for
-  // the work list and the FP64 work vectors, pinned mirror of the work list
+  // batched solves: the run of mg_solve_batch (one call at a time), and the
+  // serving scheduler's runs (idle ones pooled)
   std::mutex batch_mu;
-  std::vector<mgi::Alloc> batch_allocs;
-  size_t batch_bytes = 0;
-  void* batch_arena = nullptr;
-  size_t batch_cap = 0;
-  void* batch_host = nullptr;
-  size_t batch_host_cap = 0;
-  cudaEvent_t batch_ev0 = nullptr, batch_ev1 = nullptr;
+  mgi::BatchRun batch;
+  int serve_batch = 0;                  // most requests per batched launch (0: no batching)
+  int serve_batch_min = 2;              // fewest queued fitting requests that go out as one
+  std::vector<std::shared_ptr<ServeBatch>> batches;   // batched launches in flight
+  std::vector<mgi::BatchRun*> free_runs;
 };
 
 struct mg_hier {
@@ -255,7 +271,15 @@ int batch_check(const mg_hier* h, int prec);
 // Batched solve of count problems (mg_solve_batch).
 int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b, double* const* x, double rtol,
                 int max_it, int prec, mg_stats* stats);
-// Releases the context's batch arena and events.
-void free_batch(mg_ctx* c);
+// Enqueues a batched solve on s (problems checked by batch_check; rtol and
+// max_it per problem) into run; MG_OK or an allocation / admission error
+// (nothing enqueued).
+int batch_enqueue(mg_ctx* c, BatchRun& run, int count, mg_hier* const* hs, const double* const* b,
+                  double* const* x, const double* rtol, const int* max_it, int prec, cudaStream_t s);
+// After run.done completed: per-problem stats; returns MG_OK when all converged,
+// else the status of the first problem that did not.
+int batch_collect(BatchRun& run, mg_stats* stats);
+// Releases a run's buffers and events.
+void free_run(mg_ctx* c, BatchRun& run);
 
 }  // namespace mgi

@@ -210,7 +210,8 @@ struct BatchItem {
   int max_it = 1;
   double rtol = 1e-8;
   // results, written by the block
-  int status = 0;                     // 0, -4 (max_it), -5 (breakdown), -6 (not finite)
+  int status = 0;                     // 0, -4 (max_it), -5 (breakdown), -6 (not finite),
+                                      // -7 (refused: inconsistent item, nothing computed)
   int iters = 0, rounds = 0;
   double rel_res = 0.0;               // true ||b - A x|| / ||b_free||
 };

@@ -192,3 +192,79 @@ def test_reserved_slots_bound_the_workspaces():
         ctx.serve_reserve(h, 0)
     h.free()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [B.MG_MIXED_FP32, B.MG_FP64])
+def test_batched_serving_equals_batch_alone(prec):
+    """With batching on (every fitting request batched), a served request's
+    result equals mg_solve_batch of that request alone bit for bit, whatever
+    else was in its launch; requests that do not fit (GMRES) take the graph
+    path and equal mg_solve."""
+    ctx = G.Context(0)
+    hs = make_hiers(ctx)
+    fits = [h.batch_fits(prec) for h in hs]
+    assert fits == [True, True, False, True]
+    reqs = []
+    for k in range(16):
+        h = hs[k % len(hs)]
+        reqs.append((h, rhs_of(h, 200 + k)))
+    alone = []
+    for h, b in reqs:
+        x = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+        if h.batch_fits(prec):
+            rc, (st,) = ctx.solve_batch([h], [b], [x], rtol=1e-9, max_it=300, prec=prec)
+        else:
+            st = h.solve(b, x, rtol=1e-9, max_it=300, prec=prec)
+        assert st.status == 0
+        alone.append((x.cpu().numpy(), st.iters))
+    ctx.serve_batching(256, 1)
+    xs = [torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64) for h, _ in reqs]
+    torch.cuda.synchronize()
+    tickets = [ctx.submit(h, b, x, rtol=1e-9, max_it=300, prec=prec) for (h, b), x in zip(reqs, xs)]
+    res = wait(ctx, tickets)
+    for t, x, (xa, ita) in zip(tickets, xs, alone):
+        rc, st = res[t]
+        assert rc == 0 and st.iters == ita
+        assert np.array_equal(x.cpu().numpy(), xa)
+    # a lone fitting request below min_batch takes the graph path
+    ctx.serve_batching(256, 4)
+    h, b = reqs[0]
+    xg = torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64)
+    st = h.solve(b, xg, rtol=1e-9, max_it=300, prec=prec)
+    x = torch.zeros_like(xg)
+    t = ctx.submit(h, b, x, rtol=1e-9, max_it=300, prec=prec)
+    rc, st2 = wait(ctx, [t])[t]
+    assert rc == 0 and torch.equal(x, xg) and st2.iters == st.iters
+    with pytest.raises(G.MGError):
+        ctx.serve_batching(-1, 1)
+    for h in hs:
+        h.free()
+    ctx.close()
+
+
+def test_first_batched_use_inside_the_scheduler():
+    """Fresh hierarchies whose batched-kernel data (the staged image of every
+    level) is first built by the scheduler and read by a launch on one of its
+    non-blocking streams: the image is complete before the launch, so every
+    request converges and equals the same request solved alone afterwards."""
+    ctx = G.Context(0)
+    hs = [G.Hierarchy(ctx, W.uniform_leaves(2, (m, m), 3), B.make_problem(kind=B.MG_POISSON))
+          for m in (1, 3, 5, 7, 9)]
+    hs += [G.Hierarchy(ctx, W.uniform_leaves(3, (m, m, m), 2), B.make_problem(kind=B.MG_POISSON))
+           for m in (1, 3, 5)]
+    ctx.serve_batching(256, 1)
+    reqs = [(h, rhs_of(h, 300 + k)) for k, h in enumerate(hs * 4)]
+    xs = [torch.zeros(h.n_dofs, device="cuda", dtype=torch.float64) for h, _ in reqs]
+    torch.cuda.synchronize()
+    tickets = [ctx.submit(h, b, x, rtol=1e-9, max_it=300) for (h, b), x in zip(reqs, xs)]
+    res = wait(ctx, tickets)
+    ctx.serve_batching(0, 1)
+    for t, (h, b), x in zip(tickets, reqs, xs):
+        rc, st = res[t]
+        assert rc == 0 and st.iters > 0 and st.launches <= 2, st.as_dict()
+        xa = torch.zeros_like(x)
+        rc2, (st2,) = ctx.solve_batch([h], [b], [xa], rtol=1e-9, max_it=300)
+        assert st2.iters == st.iters and torch.equal(xa, x)
+    for h in hs:
+        h.free()
+    ctx.close()
