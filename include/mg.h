@@ -87,6 +87,19 @@ typedef struct {
   int64_t n_leaves;
   const int32_t* leaf_level;   /* host, n_leaves */
   const int32_t* leaf_anchor;  /* host, n_leaves * dim */
+  const double* axis[3];       /* optional tensor-product (graded) geometry:
+                                  NULL, or for every d < dim a host array of
+                                  (macro[d] << L) + 1 strictly increasing node
+                                  coordinates along axis d, L the finest leaf
+                                  level; node (i, j, k) of the finest lattice
+                                  sits at (axis[0][i], axis[1][j], axis[2][k])
+                                  and a coarser lattice's nodes at the same
+                                  points (every 2^(L-l)-th entry).  Cells stay
+                                  axis-aligned boxes, each with its own sizes;
+                                  origin and extent are then taken from the
+                                  arrays.  Every leaf must have the same level
+                                  (a hanging node would not sit at its edge's
+                                  middle).  Not for OSEEN.                     */
 } mg_mesh;
 
 /* Problem: bilinear form and Dirichlet faces.  Face bit 2d = face x_d = min,
@@ -136,6 +149,12 @@ typedef struct {
                                   stabilisation also tests it:
                                   + sum_T delta_T s (u, beta.grad v)_T.
                                   0: stationary                                 */
+  int pin_origin;              /* 1: the node at the origin corner is also
+                                  prescribed (every component, every level;
+                                  value from g, else 0): with no Dirichlet face
+                                  this picks one solution of the pure Neumann
+                                  problem (constants are its null space), e.g.
+                                  the pressure increment of Sec. 5.3           */
 } mg_problem;
 
 typedef struct {

@@ -207,11 +207,14 @@ def assemble(mesh, element_of_size, nc=1):
     element_of_size(h) returns the (2^d nc)^2 element matrix for a cell with
     edge lengths h (all our forms depend on the cell only through h)."""
     hs = mesh.cell_size()
-    lv = mesh.level
+    # cells with the same edge lengths share one element matrix (one group
+    # per level on a uniform mesh, one per distinct box on a graded one)
+    _, group = np.unique(hs, axis=0, return_inverse=True)
+    group = np.asarray(group).ravel()
     rows, cols, vals = [], [], []
     nv = 1 << mesh.dim
-    for l in np.unique(lv):
-        sel = np.nonzero(lv == l)[0]
+    for g in np.unique(group):
+        sel = np.nonzero(group == g)[0]
         Ke = element_of_size(hs[sel[0]])
         dofs = (mesh.cell_nodes[sel][:, :, None] * nc + np.arange(nc)[None, None, :]).reshape(sel.size, nv * nc)
         rows.append(np.repeat(dofs, nv * nc, axis=1).ravel())

@@ -24,16 +24,33 @@ import scipy.sparse as sp
 class Q1Mesh:
     """Nodes, cell->node map, hanging constraints of a 1-irregular leaf set."""
 
-    def __init__(self, dim, origin, extent, macro, level, anchor, lattice_level=None):
+    def __init__(self, dim, origin, extent, macro, level, anchor, lattice_level=None, axis=None, axis_level=None):
+        """axis (optional, graded tensor-product geometry): per dimension the
+        node coordinates of the lattice of level axis_level (default: this
+        mesh's own lattice); a node at lattice index i of this mesh sits at
+        axis[d][i * 2^(axis_level - L)] and every cell is an axis-aligned box
+        with its own edge lengths."""
         self.dim = dim
         self.origin = np.asarray(origin, dtype=np.float64)
         self.extent = np.asarray(extent, dtype=np.float64)
+        self.axis = None if axis is None else [np.asarray(a, dtype=np.float64) for a in axis[:dim]]
         self.macro = np.asarray(macro, dtype=np.int64)
         self.level = np.asarray(level, dtype=np.int64)
         self.anchor = np.asarray(anchor, dtype=np.int64)
         # lattice: the finest level present, unless a finer one is requested
         self.L = int(self.level.max()) if lattice_level is None else int(lattice_level)
         self.n_lat = self.macro << self.L          # cells per axis on the lattice
+        if self.axis is not None:
+            # hanging-node weights of 1/2 put a hanging node at its edge's
+            # middle, which graded coordinates do not: uniform leaf sets only
+            assert np.all(self.level == self.level[0]), "graded meshes must be uniform"
+            self.axis_level = self.L if axis_level is None else int(axis_level)
+            assert self.axis_level >= self.L
+            for d in range(dim):
+                assert self.axis[d].size == (int(self.macro[d]) << self.axis_level) + 1
+                assert np.all(np.diff(self.axis[d]) > 0)
+            self.origin = np.array([a[0] for a in self.axis])
+            self.extent = np.array([a[-1] - a[0] for a in self.axis])
         self.stride = np.ones(dim, dtype=np.int64)
         for d in range(1, dim):
             self.stride[d] = self.stride[d - 1] * (self.n_lat[d - 1] + 1)
@@ -62,8 +79,12 @@ class Q1Mesh:
             Xn[:, d] = rem // self.stride[d]
             rem = rem - Xn[:, d] * self.stride[d]
         self.X = Xn                                            # integer lattice coordinates
-        self.h_lat = self.extent / self.n_lat                  # lattice spacing per axis
-        self.coords = self.origin + Xn * self.h_lat
+        self.h_lat = self.extent / self.n_lat                  # lattice spacing per axis (uniform)
+        if self.axis is None:
+            self.coords = self.origin + Xn * self.h_lat
+        else:
+            sh = self.axis_level - self.L
+            self.coords = np.stack([self.axis[d][Xn[:, d] << sh] for d in range(self.dim)], axis=1)
 
     def lookup(self, keys):
         """Node index of each lattice key, -1 where the key is not a node."""
@@ -160,7 +181,13 @@ class Q1Mesh:
         return on
 
     def cell_size(self):
-        return self.extent[None, :] / (self.macro[None, :] * (2.0 ** self.level[:, None]))
+        """Edge lengths of every cell, (n_cells, dim)."""
+        if self.axis is None:
+            return self.extent[None, :] / (self.macro[None, :] * (2.0 ** self.level[:, None]))
+        s = (1 << (self.axis_level - self.level))[:, None]     # cell size on the axis lattice
+        lo = self.anchor * s
+        return np.stack([self.axis[d][lo[:, d] + s[:, 0]] - self.axis[d][lo[:, d]] for d in range(self.dim)],
+                        axis=1)
 
 
 # ---------------------------------------------------------------------------

@@ -70,8 +70,10 @@ def embedding(fine: M.Q1Mesh, coarse: M.Q1Mesh):
 
 class Level:
     def __init__(self, leaf_level, leaf_anchor, leafmesh, prob, lattice_level=None, fine_mesh=None):
+        axis = getattr(leafmesh, "axis", None)
         self.mesh = M.Q1Mesh(leafmesh.dim, leafmesh.origin, leafmesh.extent, leafmesh.macro,
-                             leaf_level, leaf_anchor, lattice_level)
+                             leaf_level, leaf_anchor, lattice_level, axis=axis,
+                             axis_level=None if axis is None else int(np.max(leafmesh.level)))
         beta = None
         if prob.kind == PB.OSEEN:      # nodal convection field, injected from the finest mesh
             beta = PB.inject(fine_mesh, prob.conv, self.mesh) if fine_mesh is not None else prob.conv

@@ -42,6 +42,7 @@ class Problem:
     lps_alpha0: float = 0.5             # Oseen: LPS parameter
     conv: object = None                 # Oseen: nodal beta (n_nodes, 2) on the finest mesh
     mass: float = 0.0                   # Poisson/transport: coefficient s of s (u, v)
+    pin_origin: bool = False            # also prescribe the node at the origin corner
 
     @property
     def nc(self):
@@ -140,6 +141,7 @@ def oseen_matrix(mesh, prob: Problem, beta):
     A = None
     for l in np.unique(lev):
         sel = np.nonzero(lev == l)[0]
+        assert mesh.axis is None, "graded meshes are not available for Oseen"
         h = mesh.extent / (mesh.macro * 2.0 ** int(l))
         Kp = fem.oseen_patch_matrices(h, beta[nodes[sel]], prob.nu, prob.dt, prob.lps_alpha0)
         Al = fem.assemble_patches(mesh, nodes[sel], Kp, 3)
@@ -156,6 +158,10 @@ def build_system(mesh, prob: Problem, with_load=True, beta=None) -> System:
         A_raw = fem.assemble(mesh, element(prob, mesh.dim), nc)
     H = fem.expand(mesh.H(), nc)
     hang, dirichlet = fem.constrained_dofs(mesh, prob.masks(), nc)
+    if prob.pin_origin:               # one solution of a pure Neumann problem: fix the origin node
+        origin = np.nonzero(np.all(mesh.X == 0, axis=1))[0]
+        for c in range(nc):
+            dirichlet[origin * nc + c] = True
     A = fem.condense(A_raw, H, hang, dirichlet)
     F = fem.assemble(mesh, load_element(prob, mesh.dim), 1) if with_load else None
     return System(mesh, prob, A_raw, H, hang, dirichlet, A, F)

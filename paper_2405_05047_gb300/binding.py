@@ -46,14 +46,15 @@ class MGError(RuntimeError):
 class MgMesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("origin", C.c_double * 3), ("extent", C.c_double * 3),
                 ("macro", C.c_int * 3), ("n_leaves", C.c_int64),
-                ("leaf_level", C.POINTER(C.c_int32)), ("leaf_anchor", C.POINTER(C.c_int32))]
+                ("leaf_level", C.POINTER(C.c_int32)), ("leaf_anchor", C.POINTER(C.c_int32)),
+                ("axis", C.c_void_p * 3)]
 
 
 class MgProblem(C.Structure):
     _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("beta", C.c_double * 3), ("mu", C.c_double),
                 ("lambda_", C.c_double), ("supg_delta0", C.c_double), ("dirichlet_mask", C.c_uint32 * 3),
                 ("nu", C.c_double), ("dt", C.c_double), ("lps_alpha0", C.c_double), ("conv", C.c_void_p),
-                ("mass", C.c_double)]
+                ("mass", C.c_double), ("pin_origin", C.c_int)]
 
 
 class MgOpts(C.Structure):
@@ -247,16 +248,24 @@ def make_mesh(leafmesh):
     m.n_leaves = lev.shape[0]
     m.leaf_level = lev.ctypes.data_as(C.POINTER(C.c_int32))
     m.leaf_anchor = anc.ctypes.data_as(C.POINTER(C.c_int32))
-    return m, (lev, anc)
+    keep = [lev, anc]
+    axis = getattr(leafmesh, "axis", None)
+    if axis is not None:
+        for d in range(leafmesh.dim):
+            a = np.ascontiguousarray(axis[d], dtype=np.float64)
+            keep.append(a)
+            m.axis[d] = a.ctypes.data
+    return m, tuple(keep)
 
 
 def make_problem(kind=MG_POISSON, eps=1.0, beta=(0.0, 0.0, 0.0), mu=1.0, lam=1.0, supg_delta0=0.5,
-                 dirichlet=(0xFF,), nu=1e-3, dt=0.01, lps_alpha0=0.5, conv=None, mass=0.0):
+                 dirichlet=(0xFF,), nu=1e-3, dt=0.01, lps_alpha0=0.5, conv=None, mass=0.0, pin_origin=0):
     """conv (OSEEN): nodal convection field at the finest nodes, (n_nodes, dim).
     mass (POISSON, TRANSPORT): coefficient s of s (u, v); 1/dt for a
     backward-Euler step."""
     p = MgProblem()
     p.mass = mass
+    p.pin_origin = int(pin_origin)
     p.kind = kind
     p.eps = eps
     for d in range(3):

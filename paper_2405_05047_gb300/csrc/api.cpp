@@ -370,7 +370,8 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
     int64_t X[3];
     F.topo.lattice_coords(i, X);
     for (int d = 0; d < H.dim; ++d)
-      h->coords[i * H.dim + d] = H.origin[d] + (double)X[d] * (H.extent[d] / (double)F.topo.ncell[d]);
+      h->coords[i * H.dim + d] = H.axis_L >= 0 ? H.axis[d][X[d] << (H.axis_L - F.topo.L)]
+                                               : H.origin[d] + (double)X[d] * (H.extent[d] / (double)F.topo.ncell[d]);
   }
   // admission, first a lower bound without allocating anything (stored
   // values of the level operators); the exact check follows the upload
@@ -450,6 +451,10 @@ int mg_mesh_nodes(const mg_mesh* mesh, int64_t* n_nodes, double* xyz) {
   LeafSet s;
   Status st = validate_mesh(*mesh, &s);
   if (!st.good()) return fail(st.code, st.msg);
+  std::vector<double> axis[3];
+  int L = -1;
+  st = read_axes(*mesh, s, axis, &L);
+  if (!st.good()) return fail(st.code, st.msg);
   Topology T;
   build_topology(s, &T);
   *n_nodes = T.n_nodes;
@@ -458,7 +463,8 @@ int mg_mesh_nodes(const mg_mesh* mesh, int64_t* n_nodes, double* xyz) {
       int64_t X[3];
       T.lattice_coords(i, X);
       for (int d = 0; d < mesh->dim; ++d)
-        xyz[i * mesh->dim + d] = mesh->origin[d] + (double)X[d] * (mesh->extent[d] / (double)T.ncell[d]);
+        xyz[i * mesh->dim + d] = L >= 0 ? axis[d][X[d] << (L - T.L)]
+                                        : mesh->origin[d] + (double)X[d] * (mesh->extent[d] / (double)T.ncell[d]);
     }
   return MG_OK;
 }

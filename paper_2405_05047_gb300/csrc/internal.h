@@ -77,6 +77,10 @@ struct HostHierarchy {
   int dim = 2, nc = 1;
   double origin[3] = {0, 0, 0}, extent[3] = {1, 1, 1};
   int macro[3] = {1, 1, 1};
+  // graded geometry (mg_mesh.axis): node coordinates along each axis at the
+  // finest lattice level axis_L; empty: uniform boxes
+  std::vector<double> axis[3];
+  int axis_L = -1;
   mg_problem prob{};
   mg_opts opts{};
   std::vector<HostLevel> levels;    // [0] = coarsest
@@ -87,6 +91,9 @@ struct HostHierarchy {
 };
 
 Status validate_mesh(const mg_mesh& mesh, LeafSet* out);
+// Graded geometry of a mesh (mg_mesh.axis) at the finest leaf level *L
+// (-1 and empty arrays for a uniform mesh).
+Status read_axes(const mg_mesh& mesh, const LeafSet& s, std::vector<double> axis[3], int* L);
 Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opts& opts, HostHierarchy* H);
 void build_topology(const LeafSet& leaves, Topology* T);
 bool coarsen_once(const LeafSet& fine, int min_level, bool patch, LeafSet* coarse);

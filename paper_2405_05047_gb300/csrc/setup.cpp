@@ -637,6 +637,17 @@ std::vector<double> load_element(const mg_problem& P, int dim, const double* h) 
 void cell_size(const HostHierarchy& H, int lev, double* h) {
   for (int d = 0; d < H.dim; ++d) h[d] = H.extent[d] / ((double)H.macro[d] * std::ldexp(1.0, lev));
 }
+// Sizes of cell k of topology T on a graded mesh: its lowest and highest
+// corners (corner 0 and corner 2^dim - 1, x fastest) looked up in the axis
+// coordinates of the finest lattice.
+void cell_size_graded(const HostHierarchy& H, const Topology& T, int64_t k, double* h) {
+  const int nv = 1 << H.dim;
+  int64_t X0[3], X1[3];
+  T.lattice_coords(T.cell_node[k * nv], X0);
+  T.lattice_coords(T.cell_node[k * nv + nv - 1], X1);
+  const int sh = H.axis_L - T.L;
+  for (int d = 0; d < H.dim; ++d) h[d] = H.axis[d][X1[d] << sh] - H.axis[d][X0[d] << sh];
+}
 
 // node -> list of (element, local node) incidences through the constraints:
 // entry for every regular node p that receives a share of local node A of
@@ -688,6 +699,11 @@ uint8_t dirichlet_bits(const HostHierarchy& H, const Topology& T, int64_t node) 
       if (((m >> (2 * d)) & 1) && X[d] == 0) bits |= (uint8_t)(1 << c);
       if (((m >> (2 * d + 1)) & 1) && X[d] == T.ncell[d]) bits |= (uint8_t)(1 << c);
     }
+  }
+  if (H.prob.pin_origin) {
+    bool origin = true;
+    for (int d = 0; d < H.dim; ++d) origin = origin && X[d] == 0;
+    if (origin) bits |= (uint8_t)((1u << H.nc) - 1u);
   }
   return bits;
 }
@@ -831,6 +847,21 @@ Status assemble_level(const HostHierarchy& H, HostLevel& lv, const std::vector<d
     assemble_condensed(H, lv, np, 9, pn, [&](int64_t k) { return &Kp[(size_t)k * 729]; }, lift);
     return Status::ok();
   }
+  if (!H.axis[0].empty()) {
+    // graded mesh: one element matrix per cell
+    const size_t m = (size_t)nv * H.nc * nv * H.nc;
+    std::vector<double> Kc(s.size() * m);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < (int64_t)s.size(); ++k) {
+      double h[3];
+      cell_size_graded(H, T, k, h);
+      std::vector<double> e = element_matrix(H.prob, dim, h);
+      std::copy(e.begin(), e.end(), Kc.begin() + (size_t)k * m);
+    }
+    assemble_condensed(H, lv, (int64_t)s.size(), nv, T.cell_node, [&](int64_t k) { return &Kc[(size_t)k * m]; },
+                       lift);
+    return Status::ok();
+  }
   std::vector<std::vector<double>> Ke(32);
   for (size_t k = 0; k < s.size(); ++k) {
     int l = s.lev[k];
@@ -847,11 +878,21 @@ void assemble_load(const HostHierarchy& H, const HostLevel& lv, BlockCSR* F) {
   const LeafSet& s = lv.leaves;
   const Topology& T = lv.topo;
   const int dim = s.dim, nv = 1 << dim;
-  std::vector<std::vector<double>> Fe(32);
-  for (size_t k = 0; k < s.size(); ++k) {
-    int l = s.lev[k];
-    if (Fe[l].empty()) { double h[3]; cell_size(H, l, h); Fe[l] = load_element(H.prob, dim, h); }
+  std::vector<std::vector<double>> Fe(H.axis[0].empty() ? 32 : s.size());
+  if (!H.axis[0].empty()) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < (int64_t)s.size(); ++k) {
+      double h[3];
+      cell_size_graded(H, T, k, h);
+      Fe[k] = load_element(H.prob, dim, h);
+    }
+  } else {
+    for (size_t k = 0; k < s.size(); ++k) {
+      int l = s.lev[k];
+      if (Fe[l].empty()) { double h[3]; cell_size(H, l, h); Fe[l] = load_element(H.prob, dim, h); }
+    }
   }
+  const bool graded = !H.axis[0].empty();
   Incidence inc = expanded_incidence(s, T);
   F->n = F->m = T.n_nodes;
   F->nc = 1;
@@ -875,7 +916,7 @@ void assemble_load(const HostHierarchy& H, const HostLevel& lv, BlockCSR* F) {
     std::copy(cols.begin(), cols.end(), F->col.begin() + F->ptr[p]);
     for (int64_t o = inc.ptr[p]; o < inc.ptr[p + 1]; ++o) {
       int64_t k = inc.cell[o];
-      const std::vector<double>& Fk = Fe[s.lev[k]];
+      const std::vector<double>& Fk = Fe[graded ? (size_t)k : (size_t)s.lev[k]];
       for (int B = 0; B < nv; ++B) {
         int64_t c = T.cell_node[k * nv + B];
         int64_t pos = std::lower_bound(cols.begin(), cols.end(), c) - cols.begin();
@@ -1112,10 +1153,40 @@ double smoothed_operator_lambda_max(const HostLevel& lv, int nc, int iters) {
 
 }  // namespace
 
+Status read_axes(const mg_mesh& mesh, const LeafSet& s, std::vector<double> axis[3], int* L) {
+  for (int d = 0; d < 3; ++d) axis[d].clear();
+  *L = -1;
+  bool any = false, all = true;
+  for (int d = 0; d < mesh.dim; ++d) {
+    any = any || mesh.axis[d] != nullptr;
+    all = all && mesh.axis[d] != nullptr;
+  }
+  if (!any) return Status::ok();
+  if (!all) return Status::err(MG_ERR_INVALID, "graded mesh: give the axis coordinates of every dimension");
+  const int lmax = s.max_level();
+  // a hanging node's weights (1/2 per parent) place it at the middle of its
+  // edge, which graded lattice coordinates do not: graded meshes are uniform
+  for (int32_t l : s.lev)
+    if (l != lmax) return Status::err(MG_ERR_INVALID, "graded mesh: every leaf must have the same level");
+  for (int d = 0; d < mesh.dim; ++d) {
+    const int64_t n = ((int64_t)mesh.macro[d] << lmax) + 1;
+    axis[d].assign(mesh.axis[d], mesh.axis[d] + n);
+    for (int64_t i = 0; i < n; ++i)
+      if (!std::isfinite(axis[d][i]) || (i > 0 && !(axis[d][i] > axis[d][i - 1])))
+        return Status::err(MG_ERR_INVALID, "graded mesh: axis coordinates must be finite and strictly increasing");
+  }
+  *L = lmax;
+  return Status::ok();
+}
+
 Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opts& opts, HostHierarchy* H) {
   LeafSet fine;
   Status st = validate_mesh(mesh, &fine);
   if (!st.good()) return st;
+  st = read_axes(mesh, fine, H->axis, &H->axis_L);
+  if (!st.good()) return st;
+  if (H->axis_L >= 0 && prob.kind == MG_OSEEN)
+    return Status::err(MG_ERR_INVALID, "graded meshes are not available for OSEEN");
   if (prob.kind < MG_POISSON || prob.kind > MG_OSEEN) return Status::err(MG_ERR_INVALID, "unknown problem kind");
   if (prob.kind == MG_ELASTICITY && mesh.dim != 3) return Status::err(MG_ERR_INVALID, "elasticity needs dim = 3");
   if (prob.kind == MG_TRANSPORT && !(prob.eps > 0)) return Status::err(MG_ERR_INVALID, "transport needs eps > 0");
@@ -1135,6 +1206,10 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
     H->origin[d] = d < mesh.dim ? mesh.origin[d] : 0.0;
     H->extent[d] = d < mesh.dim ? mesh.extent[d] : 1.0;
     H->macro[d] = d < mesh.dim ? mesh.macro[d] : 1;
+    if (d < mesh.dim && H->axis_L >= 0) {
+      H->origin[d] = H->axis[d].front();
+      H->extent[d] = H->axis[d].back() - H->axis[d].front();
+    }
   }
   H->prob = prob;
   H->opts = opts;

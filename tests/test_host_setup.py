@@ -43,10 +43,26 @@ CASES = {
                                   mass=1.0 / W.EL_DT ** 2)),
     "poisson_mass": (lambda: W.uniform_leaves(2, (1, 1), 4), PB.Problem(PB.POISSON, mass=3.0),
                      dict(kind=B.MG_POISSON, mass=3.0)),
+    # graded box of the driven cavity: per-cell element matrices, pure
+    # Neumann problem with the origin node pinned
+    "ns_pressure_graded": (lambda: W.ns_cavity_mesh(8, 8, 16),
+                           PB.Problem(PB.POISSON, dirichlet=(0,), pin_origin=True),
+                           dict(kind=B.MG_POISSON, dirichlet=(0,), pin_origin=1)),
+    "graded_transport2d": (lambda: _graded2d(),
+                           PB.Problem(PB.TRANSPORT, eps=1e-2, beta=(1.0, 0.5)),
+                           dict(kind=B.MG_TRANSPORT, eps=1e-2, beta=(1.0, 0.5))),
     "channel": (lambda: W.oseen_channel(uniform=1, rounds=3),
                 PB.Problem(PB.TRANSPORT, eps=1e-2, beta=(1.0, 0.3), dirichlet=(0b1101,)),
                 dict(kind=B.MG_TRANSPORT, eps=1e-2, beta=(1.0, 0.3), dirichlet=(0b1101,))),
 }
+
+
+def _graded2d():
+    m = W.uniform_leaves(2, (3, 1), 3)
+    n = [3 * 8 + 1, 8 + 1]
+    m.axis = tuple(np.sort(np.concatenate([[0.0, 1.0], np.random.default_rng(7 + d).random(k - 2)]))
+                   for d, k in enumerate(n))
+    return m
 
 
 def close(a, b, tol=1e-13):
@@ -190,3 +206,36 @@ def test_host_vanka_matrices_match_oracle(case):
             continue
         assert close(S, lv.S, 1e-11)
         assert hh.omega(l) == 1.0
+
+
+def test_graded_coordinates_and_pin():
+    """Node coordinates of a graded mesh come from the axis arrays (library
+    and oracle); the pinned node is the origin corner on every level, and a
+    graded mesh with mixed leaf levels is refused."""
+    lm = W.ns_cavity_mesh(4, 4, 8)
+    xyz = B.mg_mesh_nodes(lm)
+    from oracle import mesh as M, ns
+    fm = M.Q1Mesh(3, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor, axis=lm.axis)
+    assert np.array_equal(xyz, fm.coords)
+    ax = ns.graded_axes(4, 4, 8)
+    assert all(np.allclose(a, b, atol=1e-15) for a, b in zip(ax, lm.axis))
+    hh = HV.HostHierarchy(lm, B.make_problem(kind=B.MG_POISSON, dirichlet=(0,), pin_origin=1))
+    for l in range(hh.levels):
+        fm_l = hh.fixmask(l)
+        assert fm_l[0] == 1 and fm_l[1:].sum() == 0
+    bad = W.refine(W.uniform_leaves(2, (1, 1), 2), np.arange(16) == 0)
+    bad.axis = (np.linspace(0, 1, 9) ** 2, np.linspace(0, 1, 9))
+    with pytest.raises(B.MGError):
+        B.mg_mesh_nodes(bad)
+
+
+def test_oracle_graded_stiffness_equals_tensor_assembly():
+    """Two oracle paths on the graded cavity mesh agree: the generic Q1
+    assembly over Q1Mesh cells (per-cell edge lengths) and the tensor-grid
+    assembly of the Navier-Stokes module."""
+    from oracle import mesh as M, ns
+    lm = W.ns_cavity_mesh(4, 4, 8)
+    fm = M.Q1Mesh(3, lm.origin, lm.extent, lm.macro, lm.level, lm.anchor, axis=lm.axis)
+    A = PB.build_system(fm, PB.Problem(PB.POISSON, dirichlet=(0,))).A_raw
+    _, K, _ = ns.assemble(ns.Grid(lm.axis))
+    assert close(A, K, 1e-13)

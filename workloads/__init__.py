@@ -42,6 +42,9 @@ class LeafMesh:
     level: np.ndarray          # (n,) int32
     anchor: np.ndarray         # (n, dim) int32
     meta: dict = field(default_factory=dict)
+    # graded tensor-product geometry: per axis the node coordinates of the
+    # finest lattice ((macro[d] << max level) + 1 increasing values), or None
+    axis: tuple | None = None
 
     @property
     def n_leaves(self) -> int:
@@ -350,4 +353,25 @@ def elasticity_adaptive(kind: str, levels: int) -> LeafMesh:
         mark = (m.level == m.level.max()) & np.all(hi[:, ax] <= 2.0 ** -r + 1e-12, axis=1)
         m = refine(m, mark)
     m.meta.update(workload=f"elasticity_{kind}_l{levels}")
+    return m
+
+
+def ns_cavity_mesh(nx: int = 32, ny: int = 32, nz: int = 64, graded: bool = True) -> LeafMesh:
+    """Pressure mesh of the 3D driven cavity (Sec. 5.3): nx x ny x nz cells of
+    the box (0, 1) x (0, 1) x (0, 2), as a uniform leaf set of level L (the
+    largest with nx, ny, nz divisible by 2^L) on the macro grid (n >> L), with
+    the cosine-graded node coordinates x_i = (1 - cos(i pi / nx)) / 2 (y
+    alike) and z_k = 1 - cos(k pi / nz) when graded, equidistant otherwise."""
+    L = 0
+    while all(n % (2 << L) == 0 for n in (nx, ny, nz)):
+        L += 1
+    m = uniform_leaves(3, (nx >> L, ny >> L, nz >> L), L, origin=(0.0, 0.0, 0.0), extent=(1.0, 1.0, 2.0))
+    if graded:
+        ax = (0.5 * (1.0 - np.cos(np.arange(nx + 1) * np.pi / nx)),
+              0.5 * (1.0 - np.cos(np.arange(ny + 1) * np.pi / ny)),
+              1.0 - np.cos(np.arange(nz + 1) * np.pi / nz))
+    else:
+        ax = (np.linspace(0.0, 1.0, nx + 1), np.linspace(0.0, 1.0, ny + 1), np.linspace(0.0, 2.0, nz + 1))
+    m.axis = ax
+    m.meta.update(workload=f"ns_cavity_{nx}x{ny}x{nz}" + ("_graded" if graded else ""))
     return m
