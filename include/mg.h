@@ -105,6 +105,11 @@ typedef struct {
 /* Problem: bilinear form and Dirichlet faces.  Face bit 2d = face x_d = min,
  * bit 2d+1 = face x_d = max; dirichlet_mask[c] selects the faces on which
  * component c is prescribed (values from mg_assemble_rhs's g, else 0).
+ * A POISSON problem with no prescribed dof at all (no Dirichlet face, no
+ * pin, no mass) is the pure Neumann problem: its null space are the
+ * constants, right-hand sides must be compatible (sum of b = 0), and the
+ * solve returns one solution (determined up to a constant; the coarse solve
+ * applies the pseudo-inverse of A_0).
  *   POISSON      (grad u, grad v)                                  nc = 1
  *   TRANSPORT    eps (grad u, grad v) + (beta.grad u, v)
  *                + sum_T delta_T (beta.grad u, beta.grad v)_T,
@@ -161,8 +166,9 @@ typedef struct {
   int nu1, nu2;                /* pre/post smoothing sweeps (default 2, 2)    */
   double omega;                /* damping of the (block-)Jacobi smoother: > 0
                                   on every level; <= 0 (default -1): 0.8 for
-                                  scalar problems, 1.2 / lambda_max(S_l A_l)
-                                  per level for the point-block smoothers
+                                  scalar problems on uniform boxes, 1.2 /
+                                  lambda_max(S_l A_l) per level for the
+                                  point-block smoothers and on graded meshes
                                   (20 power iterations at setup)             */
   int min_level;               /* coarsest level allowed (-1: automatic)      */
   int max_levels;              /* cap on the number of levels (0: no cap)     */
@@ -540,6 +546,71 @@ int mg_serve_batching(mg_ctx* ctx, int max_batch, int min_batch);
 int mg_serve_reserve(mg_ctx* ctx, mg_hier* h, int slots, int prec);
 /* Kernels the library has enqueued on behalf of this hierarchy so far. */
 int64_t mg_launch_count(const mg_hier* h);
+
+/* ------------------------------------------------------------------------
+ * Explicit Navier-Stokes pressure correction: the 3D driven cavity of
+ * Sec. 5.3 (Algorithm "The fully discrete solution procedure for the
+ * Navier-Stokes equations"), Re = 1/nu, on the box (0,1) x (0,1) x (0,2).
+ * Pressure Q1 on the nx x ny x nz mesh Omega_h (cosine-graded node
+ * coordinates x_i = (1 - cos(i pi/nx))/2, y alike, z_k = 1 - cos(k pi/nz)),
+ * velocity Q1 on its equidistant refinement Omega_{h/2} (the
+ * Q1-iso-Q2/Q1 pair); lumped masses; the convective term through the nodal
+ * interpolant of u (x) u and C_d = (phi_j, d_d phi_i) (Eqs. "tp", "multC").
+ * One step:
+ *   1. u^m = u^{m-1} + k M^-1 (-nu K u^{m-1} + N(u^{m-1}) + C P (p + q))
+ *      on interior velocity nodes; u = (0, lid, 0) on x = 1, 0 on the
+ *      other walls;
+ *   2. K_p q^m = -(1/k) d, d = ((div u^m, psi_j))_j: the pure Neumann
+ *      pressure-increment problem, solved by the library's Krylov + geometric
+ *      multigrid on the graded pressure mesh (warm start from q^{m-1}), then
+ *      shifted to mean zero (sum_j m^p_j q_j = 0: the space Q of Sec. 5.3);
+ *   3. p^m = p^{m-1} + q^m - nu d / m^p.
+ * Node numbering: lexicographic, x fastest; velocity vectors node-major
+ * (n_v x 3 doubles), pressure vectors n_p doubles; all on the device. */
+typedef struct mg_ns mg_ns;
+typedef struct {
+  int nx, ny, nz;              /* pressure cells per axis (each >= 2)          */
+  int graded;                  /* 1 (default): cosine-graded coordinates,
+                                  0: equidistant                               */
+  double re;                   /* Reynolds number (default 1000)               */
+  double dt;                   /* time step k (default 1e-4)                   */
+  double lid;                  /* lid speed (default 1)                        */
+  int prec;                    /* precision of the pressure solve (default
+                                  MG_MIXED_FP32: FP32 multigrid, FP64 Krylov)  */
+  int krylov;                  /* Krylov method of the pressure solve (default
+                                  MG_GMRES, as in Sec. 5.3)                    */
+  double rtol;                 /* pressure solve tolerance (default 1e-8)      */
+  int max_it;                  /* pressure solve iteration cap (default 200)   */
+} mg_ns_params;
+typedef struct {
+  int steps;                   /* steps run                                    */
+  int status;                  /* MG_OK or the first failing solve's status    */
+  int64_t iters;               /* Krylov iterations of all pressure solves     */
+  int iters_max;               /* most iterations of one pressure solve        */
+  double rel_res_max;          /* largest true relative residual               */
+  double ms_momentum;          /* device time of Step 1 (interpolation of p+q
+                                  and the fused momentum update)               */
+  double ms_pres_rhs;          /* divergence and its restriction (Step 2 rhs)  */
+  double ms_pres_solve;        /* the pressure-increment solves                */
+  double ms_pres_up;           /* Step 3                                       */
+  double ms_total;             /* wall time of mg_ns_steps                     */
+} mg_ns_stats;
+void mg_ns_default_params(mg_ns_params* p);
+/* Builds the meshes, the velocity operators (per-axis 1D coefficients) and
+ * the pressure hierarchy; velocity and pressure start at 0. */
+int mg_ns_setup(mg_ctx* ctx, const mg_ns_params* params, mg_ns** out);
+/* Velocity and pressure nodes per axis (n_v[d] = 2 n_p[d] - 1). */
+int mg_ns_sizes(const mg_ns* ns, int n_vel[3], int n_pres[3]);
+/* Copies the state in (dir = 0: u, p, q device buffers -> the solver) or
+ * out (dir = 1); any pointer may be NULL (that field is skipped). */
+int mg_ns_state(mg_ns* ns, double* u, double* p, double* q, int dir);
+/* Runs n_steps steps on the context's stream; stats may be NULL.  Returns
+ * MG_OK, or the status of the first pressure solve that failed (the state
+ * after that step is kept). */
+int mg_ns_steps(mg_ns* ns, int n_steps, mg_ns_stats* stats);
+/* The pressure hierarchy (for inspection: mg_hier_info and so on). */
+mg_hier* mg_ns_pressure_hierarchy(mg_ns* ns);
+int mg_ns_free(mg_ns* ns);
 
 #ifdef __cplusplus
 }

@@ -54,6 +54,13 @@ def embedding(fine: M.Q1Mesh, coarse: M.Q1Mesh):
             continue
         found[idx] = True
         t = (X[idx] - a[idx] * s) / float(s)           # local coordinates in [0,1]
+        if fine.axis is not None:
+            # graded boxes: the physical position inside the coarse cell (the
+            # coarse Q1 function is linear along each axis of its box)
+            sh = fine.axis_level - Lf
+            t = np.stack([(fine.axis[d][X[idx, d] << sh] - fine.axis[d][(a[idx, d] * s) << sh])
+                          / (fine.axis[d][((a[idx, d] + 1) * s) << sh] - fine.axis[d][(a[idx, d] * s) << sh])
+                          for d in range(dim)], axis=1)
         for c in range(1 << dim):
             w = np.ones(idx.size)
             for d in range(dim):
@@ -182,8 +189,11 @@ class Hierarchy:
             lv.S = lv.smoother_matrix()
             if omega is not None:
                 lv.omega = float(omega)
-            elif nc == 1:
+            elif nc == 1 and lv.mesh.axis is None:
                 lv.omega = 0.8
+            # graded boxes: anisotropic cells push lambda_max(D^-1 A) of the
+            # scalar Q1 operator well above its value on cubes, where 0.8
+            # diverges; the damping then comes from the estimate too
             else:
                 lv.omega = 1.2 / lambda_max_power(lv.S, lv.A, lv.sys.fixed)
         A0 = self.levels[0].A.toarray()

@@ -20,9 +20,9 @@ Navier-Stokes equations") directly:
   Omega_h to Omega_{h/2}, Dirichlet data on the boundary (lid: u = (0, 1, 0)
   on x = 1);
 * Step 2 (pressure increment): K_p q^m = -(1/k) d^m, d^m = P^T sum_c C_c^T u^m_c
-  = ((div u^m, psi_j))_j, K_p the Q1 stiffness on Omega_h (pure Neumann; the
-  origin node is pinned to 0, which picks one solution of the compatible
-  singular system);
+  = ((div u^m, psi_j))_j, K_p the Q1 stiffness on Omega_h (pure Neumann, a
+  compatible singular system); the solution of mean zero, sum_j m^p_j q_j = 0
+  (the space Q of Sec. 5.3, with the lumped mass as the inner product);
 * Step 3 (pressure update): p^m = p^{m-1} + q^m - nu d^m / m^p.
 
 Readings of the paper (where it is garbled or silent; the same list is in the
@@ -172,7 +172,7 @@ class Cavity:
     g: np.ndarray             # (n_v, 3) Dirichlet values
     nu: float
     dt: float
-    pin: int = 0              # pressure node fixed to 0 in Step 2
+    pin: int = 0              # node held at 0 in the direct solve of Step 2 (before the mean shift)
 
 
 def cavity(nx, ny, nz, re=1e3, dt=1e-4, lid=1.0, graded=True):
@@ -220,15 +220,16 @@ def momentum(S, u, p, q):
 
 
 def pressure_increment(S, d):
-    """Step 2: K_p q = -d / k with q[pin] = 0 (one solution of the compatible
-    pure Neumann system), by a sparse direct solve."""
+    """Step 2: K_p q = -d / k, the solution of mean zero.  One solution of the
+    compatible pure Neumann system by a sparse direct solve with the node
+    S.pin held at 0, then the constant that makes sum_j m^p_j q_j = 0."""
     n = S.pm.n_nodes
     keep = np.ones(n, dtype=bool)
     keep[S.pin] = False
     A = S.Kp[keep][:, keep].tocsc()
     q = np.zeros(n)
     q[keep] = spl.spsolve(A, -d[keep] / S.dt)
-    return q
+    return q - (S.mp @ q) / S.mp.sum()
 
 
 def step(S, u, p, q):

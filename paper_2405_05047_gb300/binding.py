@@ -98,6 +98,21 @@ _MALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
+class MgNsParams(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("graded", C.c_int), ("re", C.c_double),
+                ("dt", C.c_double), ("lid", C.c_double), ("prec", C.c_int), ("krylov", C.c_int),
+                ("rtol", C.c_double), ("max_it", C.c_int)]
+
+
+class MgNsStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("status", C.c_int), ("iters", C.c_int64), ("iters_max", C.c_int),
+                ("rel_res_max", C.c_double), ("ms_momentum", C.c_double), ("ms_pres_rhs", C.c_double),
+                ("ms_pres_solve", C.c_double), ("ms_pres_up", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MgAllocator(C.Structure):
     _fields_ = [("malloc_fn", _MALLOC), ("free_fn", _FREE), ("user", C.c_void_p)]
 
@@ -142,6 +157,13 @@ _SIGS = {
                                  C.POINTER(C.c_void_p), C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
     "mg_batch_fits": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_serve_batching": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_ns_default_params": (None, [C.POINTER(MgNsParams)]),
+    "mg_ns_setup": (C.c_int, [C.c_void_p, C.POINTER(MgNsParams), C.POINTER(C.c_void_p)]),
+    "mg_ns_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "mg_ns_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_ns_steps": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(MgNsStats)]),
+    "mg_ns_pressure_hierarchy": (C.c_void_p, [C.c_void_p]),
+    "mg_ns_free": (C.c_int, [C.c_void_p]),
     "mg_time_steps2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                  C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
 }
@@ -560,3 +582,52 @@ class Hierarchy:
             self.free()
         except Exception:
             pass
+
+
+class NavierStokes:
+    """The driven cavity's explicit pressure correction (mg_ns_*): velocity
+    (n_v x 3) and pressure (n_p) state on the device."""
+
+    def __init__(self, ctx, **params):
+        import torch
+        lib = load_library()
+        p = MgNsParams()
+        lib.mg_ns_default_params(C.byref(p))
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.params = p
+        h = C.c_void_p()
+        _check(lib.mg_ns_setup(ctx.handle, C.byref(p), C.byref(h)))
+        self.handle = h
+        nv, npr = (C.c_int * 3)(), (C.c_int * 3)()
+        _check(lib.mg_ns_sizes(h, nv, npr))
+        self.n_vel = tuple(nv)
+        self.n_pres = tuple(npr)
+        self.nv = int(np.prod(self.n_vel))
+        self.np = int(np.prod(self.n_pres))
+        self._torch = torch
+
+    def pressure_info(self):
+        return mg_hier_info(load_library().mg_ns_pressure_hierarchy(self.handle))
+
+    def set_state(self, u=None, p=None, q=None):
+        _check(load_library().mg_ns_state(self.handle, _ptr(u), _ptr(p), _ptr(q), 0))
+
+    def get_state(self):
+        t = self._torch
+        u = t.empty((self.nv, 3), device="cuda", dtype=t.float64)
+        p = t.empty(self.np, device="cuda", dtype=t.float64)
+        q = t.empty(self.np, device="cuda", dtype=t.float64)
+        _check(load_library().mg_ns_state(self.handle, _ptr(u), _ptr(p), _ptr(q), 1))
+        return u, p, q
+
+    def steps(self, n):
+        st = MgNsStats()
+        rc = load_library().mg_ns_steps(self.handle, n, C.byref(st))
+        _check(rc, allow=SOLVE_OUTCOMES)
+        return st
+
+    def free(self):
+        if self.handle:
+            load_library().mg_ns_free(self.handle)
+            self.handle = None

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmg_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "device.cpp", "api.cpp", "debug.cpp", "kernels.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "device.cpp", "api.cpp", "debug.cpp", "kernels.cu", "batch.cu", "ns.cpp", "ns_kernels.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

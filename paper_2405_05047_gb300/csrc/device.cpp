@@ -1560,6 +1560,11 @@ int solve_check(mg_hier* h, Workspace& w, cudaStream_t s, mg_stats* stats) {
 }
 
 
+void* ctx_alloc(mg_ctx* c, std::vector<Alloc>& list, size_t& total, size_t bytes, bool use_ctx) {
+  return dev_alloc(c, list, total, bytes, use_ctx);
+}
+void ctx_free(mg_ctx* c, std::vector<Alloc>& list, size_t& total) { free_list(c, list, total); }
+
 // ---------------------------------------------------------------- batched solves
 // Many small problems in one launch (k_batch): every level of each hierarchy
 // runs in the staged tail of the thread block that takes the problem, so a

@@ -143,6 +143,15 @@ const char* last_error();
 
 }  // namespace mgi
 
+struct mg_ctx;
+namespace mgi {
+// Device allocation through the context's allocator (ctx_alloc) or
+// cudaMalloc, recorded in list and counted against the context; free_list
+// releases a list.
+void* ctx_alloc(mg_ctx* c, std::vector<Alloc>& list, size_t& total, size_t bytes, bool ctx_alloc);
+void ctx_free(mg_ctx* c, std::vector<Alloc>& list, size_t& total);
+}  // namespace mgi
+
 struct ServeRequest;
 struct ServeBatch;
 

@@ -962,7 +962,15 @@ void build_transfer(const HostHierarchy& H, const HostLevel& coarse, HostLevel& 
       double w = 1.0;
       int64_t Y[3];
       for (int d = 0; d < dim; ++d) {
+        // position in the coarse cell: lattice fraction, or on a graded mesh
+        // the physical one (the coarse Q1 function is linear along each axis
+        // of its box, so this is its exact value at the fine node)
         double t = (double)(X[d] - a[d] * s) / (double)s;
+        if (H.axis_L >= 0) {
+          const int sh = H.axis_L - Lf;
+          const double x0 = H.axis[d][(a[d] * s) << sh], x1 = H.axis[d][((a[d] + 1) * s) << sh];
+          t = (H.axis[d][X[d] << sh] - x0) / (x1 - x0);
+        }
         int b = (c >> d) & 1;
         w *= b ? t : 1.0 - t;
         Y[d] = (a[d] + b) << (Lc - lev);
@@ -1282,7 +1290,10 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
   for (HostLevel& lv : H->levels) {
     if (lv.vanka) continue;
     if (opts.omega > 0) lv.omega = opts.omega;
-    else if (nc == 1) lv.omega = 0.8;
+    else if (nc == 1 && H->axis_L < 0) lv.omega = 0.8;
+    // point-block smoothers, and scalar levels of graded meshes (anisotropic
+    // boxes push lambda_max(D^-1 A) far above its value on cubes, where the
+    // fixed 0.8 diverges): from the estimate
     else lv.omega = 1.2 / smoothed_operator_lambda_max(lv, nc, 20);
     if (!(lv.omega > 0) || !std::isfinite(lv.omega)) return Status::err(MG_ERR_INVALID, "smoother damping estimate failed");
   }
@@ -1296,6 +1307,20 @@ Status build_hierarchy(const mg_mesh& mesh, const mg_problem& prob, const mg_opt
       for (int64_t e = c.A.ptr[p]; e < c.A.ptr[p + 1]; ++e)
         for (int i = 0; i < nc; ++i)
           for (int j = 0; j < nc; ++j) M[(p * nc + i) * n + c.A.col[e] * nc + j] = c.A.val[e * nb + i * nc + j];
+    // pure Neumann Poisson problem (no prescribed dof, no mass term): A_0 is
+    // singular with the constants as its null space.  For a compatible
+    // right-hand side (orthogonal to the constants, as every restricted
+    // residual of a compatible problem is: P reproduces constants) the
+    // inverse of A_0 + a 1 1^T (any a > 0) returns the solution orthogonal to
+    // the constants, the pseudo-inverse solution.
+    bool neumann = H->prob.kind == MG_POISSON && H->prob.mass == 0.0;
+    for (uint8_t f : c.fixmask) neumann = neumann && f == 0;
+    if (neumann) {
+      double tr = 0.0;
+      for (int64_t i = 0; i < n; ++i) tr += M[i * n + i];
+      const double a = tr / ((double)n * (double)n);
+      for (auto& v : M) v += a;
+    }
     if (!invert_dense(n, M, H->coarse_inv)) return Status::err(MG_ERR_INVALID, "singular coarse matrix");
   }
   assemble_load(*H, H->levels.back(), &H->load);

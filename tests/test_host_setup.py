@@ -239,3 +239,19 @@ def test_oracle_graded_stiffness_equals_tensor_assembly():
     A = PB.build_system(fm, PB.Problem(PB.POISSON, dirichlet=(0,))).A_raw
     _, K, _ = ns.assemble(ns.Grid(lm.axis))
     assert close(A, K, 1e-13)
+
+
+def test_pure_neumann_coarse_pseudo_inverse():
+    """A Poisson problem with no prescribed dof: the coarse solve applies the
+    pseudo-inverse, so for a compatible right-hand side (sum b = 0) it returns
+    the solution of A_0 x = b orthogonal to the constants."""
+    lm = W.ns_cavity_mesh(4, 4, 8)
+    hh = HV.HostHierarchy(lm, B.make_problem(kind=B.MG_POISSON, dirichlet=(0,)))
+    A0 = hh.matrix(0, HV.A).toarray()
+    assert np.abs(A0 @ np.ones(A0.shape[0])).max() < 1e-13 * np.abs(A0).max()
+    inv = hh.coarse_inverse()
+    b = np.random.default_rng(9).standard_normal(A0.shape[0])
+    b -= b.mean()
+    x = inv @ b
+    assert np.abs(A0 @ x - b).max() < 1e-10 * np.abs(b).max()
+    assert abs(x.sum()) < 1e-10 * np.abs(x).sum()
