@@ -581,6 +581,9 @@ typedef struct {
                                   MG_GMRES, as in Sec. 5.3)                    */
   double rtol;                 /* pressure solve tolerance (default 1e-8)      */
   int max_it;                  /* pressure solve iteration cap (default 200)   */
+  int nu;                      /* smoothing sweeps before and after the coarse
+                                  correction on every level (default 4: on the
+                                  graded cavity the fastest of 2, 3, 4, 6, 8)  */
 } mg_ns_params;
 typedef struct {
   int steps;                   /* steps run                                    */

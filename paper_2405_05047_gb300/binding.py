@@ -101,7 +101,7 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class MgNsParams(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("graded", C.c_int), ("re", C.c_double),
                 ("dt", C.c_double), ("lid", C.c_double), ("prec", C.c_int), ("krylov", C.c_int),
-                ("rtol", C.c_double), ("max_it", C.c_int)]
+                ("rtol", C.c_double), ("max_it", C.c_int), ("nu", C.c_int)]
 
 
 class MgNsStats(C.Structure):

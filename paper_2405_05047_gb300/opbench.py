@@ -1,6 +1,8 @@
 """Time one level operator of a hierarchy (a profiling target).
 
   python -m paper_2405_05047_gb300.opbench --workload td_adaptive --op smooth --prec fp32 --reps 3
+  python -m paper_2405_05047_gb300.opbench --workload ns_cavity --steps 3     (driven-cavity steps)
+  python -m paper_2405_05047_gb300.opbench --workload batch_small            (one batched launch)
 
 Sets up the hierarchy of the named workload, runs the operator `reps` times
 back to back on the finest level (or --level) through mg_time_op and prints
@@ -69,15 +71,56 @@ def alg_bytes(info, level, nc, op, vbytes):
     return None
 
 
+def run_ns(steps):
+    """Three-phase steps of the driven cavity (32x32x64, FP32 multigrid + CG)."""
+    import paper_2405_05047_gb300 as G
+    ctx = G.Context(0)
+    sim = B.NavierStokes(ctx, nx=32, ny=32, nz=64, prec=B.MG_MIXED_FP32, krylov=B.MG_CG, rtol=1e-8, max_it=400)
+    st = sim.steps(steps)
+    print(json.dumps({"workload": "ns_cavity", "steps": st.steps, "status": st.status, "iters": st.iters,
+                      "ms_momentum_per_step": st.ms_momentum / max(st.steps, 1)}))
+    sim.free()
+    ctx.close()
+
+
+def run_batch():
+    """One batched launch of 304 small Poisson problems (2D 24..72, 3D 12, 20)."""
+    import torch
+    import paper_2405_05047_gb300 as G
+    ctx = G.Context(0)
+    hs = [G.Hierarchy(ctx, W.uniform_leaves(2, (m, m), 3), B.make_problem(kind=B.MG_POISSON),
+                      B.make_opts(autotune=0)) for m in (3, 5, 7, 9)]
+    hs += [G.Hierarchy(ctx, W.uniform_leaves(3, (m, m, m), 2), B.make_problem(kind=B.MG_POISSON),
+                       B.make_opts(autotune=0)) for m in (3, 5)]
+    probs = [hs[k % len(hs)] for k in range(304)]
+    bs, xs = [], []
+    for h in probs:
+        b = torch.empty(h.n_dofs, device="cuda", dtype=torch.float64)
+        h.assemble_rhs(torch.ones(h.n_dofs, device="cuda", dtype=torch.float64), b)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    rc, st = ctx.solve_batch(probs, bs, xs, rtol=1e-8, max_it=200)
+    print(json.dumps({"workload": "batch_small", "problems": len(probs), "status": rc, "device_ms": st[0].solve_ms}))
+    for h in hs:
+        h.free()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="td_adaptive")
+    ap.add_argument("--workload", default="td_adaptive",
+                    help="a hierarchy workload (level operator timing), or ns_cavity / batch_small")
+    ap.add_argument("--steps", type=int, default=3, help="ns_cavity: time steps")
     ap.add_argument("--op", default="smooth", choices=sorted(OPS))
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--level", type=int, default=-1)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     BLD.build()
+    if args.workload == "ns_cavity":
+        return run_ns(args.steps)
+    if args.workload == "batch_small":
+        return run_batch()
     import paper_2405_05047_gb300 as G
     lm, pb, okw = make(args.workload)
     prec = B.MG_MIXED_FP32 if args.prec == "fp32" else B.MG_FP64
