@@ -78,28 +78,28 @@ __global__ void __launch_bounds__(kNsBlock) k_ns_momentum(NsView V, const double
       un[3 * t + 2] = 0.0;
       continue;
     }
+    // per-axis factors; -nu folded into the stiffness ones
     double Mx[3], Kx[3], Gx[3], My[3], Ky[3], Gy[3], Mz[3], Kz[3], Gz[3];
     for (int a = 0; a < 3; ++a) {
-      Mx[a] = V.ax[0].M[3 * i + a]; Kx[a] = V.ax[0].K[3 * i + a]; Gx[a] = V.ax[0].G[3 * i + a];
-      My[a] = V.ax[1].M[3 * j + a]; Ky[a] = V.ax[1].K[3 * j + a]; Gy[a] = V.ax[1].G[3 * j + a];
-      Mz[a] = V.ax[2].M[3 * k + a]; Kz[a] = V.ax[2].K[3 * k + a]; Gz[a] = V.ax[2].G[3 * k + a];
+      Mx[a] = V.ax[0].M[3 * i + a]; Kx[a] = -V.nu * V.ax[0].K[3 * i + a]; Gx[a] = V.ax[0].G[3 * i + a];
+      My[a] = V.ax[1].M[3 * j + a]; Ky[a] = -V.nu * V.ax[1].K[3 * j + a]; Gy[a] = V.ax[1].G[3 * j + a];
+      Mz[a] = V.ax[2].M[3 * k + a]; Kz[a] = -V.nu * V.ax[2].K[3 * k + a]; Gz[a] = V.ax[2].G[3 * k + a];
     }
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     for (int c = 0; c < 3; ++c) {
       for (int b = 0; b < 3; ++b) {
-        const double myz = My[b] * Mz[c], kyz = Ky[b] * Mz[c], mykz = My[b] * Kz[c];
+        const double myz = My[b] * Mz[c], kyz = fma(Ky[b], Mz[c], My[b] * Kz[c]);
         const double gyz = Gy[b] * Mz[c], mygz = My[b] * Gz[c];
         const int64_t row = t + (b - 1) * sy + (c - 1) * sz;
         for (int a = 0; a < 3; ++a) {
           const int64_t s = row + (a - 1);
           const double ux = u[3 * s], uy = u[3 * s + 1], uz = u[3 * s + 2], ps = pt[s];
-          const double kc = fma(Kx[a], myz, Mx[a] * (kyz + mykz));     // K(a, b, c)
           const double cx = Gx[a] * myz, cy = Mx[a] * gyz, cz = Mx[a] * mygz;
-          const double flux = fma(cx, ux, fma(cy, uy, cz * uz));       // sum_b C_b u_b
-          const double vk = -V.nu * kc;
-          acc0 = fma(flux, ux, fma(vk, ux, fma(cx, ps, acc0)));
-          acc1 = fma(flux, uy, fma(vk, uy, fma(cy, ps, acc1)));
-          acc2 = fma(flux, uz, fma(vk, uz, fma(cz, ps, acc2)));
+          // w = sum_b C_b u_b - nu K(a, b, c): acc_c += w u_c + C_c ps
+          const double w = fma(cx, ux, fma(cy, uy, fma(cz, uz, fma(Kx[a], myz, Mx[a] * kyz))));
+          acc0 = fma(w, ux, fma(cx, ps, acc0));
+          acc1 = fma(w, uy, fma(cy, ps, acc1));
+          acc2 = fma(w, uz, fma(cz, ps, acc2));
         }
       }
     }
@@ -126,14 +126,15 @@ __global__ void __launch_bounds__(kNsBlock) k_ns_div(NsView V, const double* __r
         const int jj = j + b - 1;
         if (jj < 0 || jj >= V.nv[1]) continue;
         const double my = V.ax[1].M[3 * j + b], gy = V.ax[1].GT[3 * j + b];
+        const double myz = my * mz, gyz = gy * mz, mygz = my * gz;
         for (int a = 0; a < 3; ++a) {
           const int ii = i + a - 1;
           if (ii < 0 || ii >= V.nv[0]) continue;
           const double mx = V.ax[0].M[3 * i + a], gx = V.ax[0].GT[3 * i + a];
           const int64_t s = t + (a - 1) + (b - 1) * sy + (c - 1) * sz;
-          acc = fma(gx * my * mz, u[3 * s], acc);
-          acc = fma(mx * gy * mz, u[3 * s + 1], acc);
-          acc = fma(mx * my * gz, u[3 * s + 2], acc);
+          acc = fma(gx * myz, u[3 * s], acc);
+          acc = fma(mx * gyz, u[3 * s + 1], acc);
+          acc = fma(mx * mygz, u[3 * s + 2], acc);
         }
       }
     }
