@@ -482,6 +482,21 @@ typedef struct {
 int mg_solve_profiled(mg_hier* h, const double* b, double* x, double rtol, int max_it, int prec, mg_stats* stats,
                       mg_prof_entry* entries, int cap, int* n_entries);
 
+/* New coefficients for a resident hierarchy (Algorithm "Nonstationary Linear
+ * Problem": the matrices stay on the device; only their values change): the
+ * host assembly runs again on the mesh the hierarchy was set up on, and the
+ * level operators, smoother blocks and damping, Vanka matrices, coarse
+ * inverse, load and lifting matrices and the small-level images are
+ * rewritten in place (same device memory, same SELL layouts and tuning);
+ * workspaces and serving reservations are kept, cached solve graphs are
+ * rebuilt on their next use.  The kind, the Dirichlet faces and pin_origin
+ * must stay the same (eps, beta, mu, lambda, supg_delta0, mass, nu, dt,
+ * lps_alpha0 and conv may change).  A solve afterwards equals a solve on a
+ * hierarchy set up with the new problem (same tuning) bit for bit.
+ * MG_ERR_INVALID if a request of h is queued or running, or the new problem
+ * changes the hierarchy's structure. */
+int mg_update_problem(mg_hier* h, const mg_problem* problem);
+
 /* Batched solve of many small problems in one kernel launch (the per-kernel
  * launch overhead that dominates small solves, Sec. 6.1, paid once for the
  * batch).  Problem k: hierarchy h[k], right-hand side b[k] (device, n_dofs
@@ -584,6 +599,8 @@ typedef struct {
   int nu;                      /* smoothing sweeps before and after the coarse
                                   correction on every level (default 4: on the
                                   graded cavity the fastest of 2, 3, 4, 6, 8)  */
+  int smoother;                /* mg_smoother of the pressure multigrid
+                                  (default MG_SMOOTHER_JACOBI)                 */
 } mg_ns_params;
 typedef struct {
   int steps;                   /* steps run                                    */

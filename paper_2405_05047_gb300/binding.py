@@ -101,7 +101,7 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class MgNsParams(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("graded", C.c_int), ("re", C.c_double),
                 ("dt", C.c_double), ("lid", C.c_double), ("prec", C.c_int), ("krylov", C.c_int),
-                ("rtol", C.c_double), ("max_it", C.c_int), ("nu", C.c_int)]
+                ("rtol", C.c_double), ("max_it", C.c_int), ("nu", C.c_int), ("smoother", C.c_int)]
 
 
 class MgNsStats(C.Structure):
@@ -156,6 +156,7 @@ _SIGS = {
     "mg_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                  C.POINTER(C.c_void_p), C.c_double, C.c_int, C.c_int, C.POINTER(MgStats)]),
     "mg_batch_fits": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_update_problem": (C.c_int, [C.c_void_p, C.POINTER(MgProblem)]),
     "mg_serve_batching": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_ns_default_params": (None, [C.POINTER(MgNsParams)]),
     "mg_ns_setup": (C.c_int, [C.c_void_p, C.POINTER(MgNsParams), C.POINTER(C.c_void_p)]),
@@ -539,6 +540,11 @@ class Hierarchy:
 
     def time_steps(self, theta, f, g, n_steps, rtol=1e-10, max_it=200, prec=MG_FP64):
         return mg_time_steps(self.handle, theta, f, g, n_steps, rtol, max_it, prec)
+
+    def update_problem(self, problem):
+        """mg_update_problem: new coefficients, same mesh and structure."""
+        _check(load_library().mg_update_problem(self.handle, C.byref(problem)))
+        self.info = mg_hier_info(self.handle)
 
     def batch_fits(self, prec=MG_MIXED_FP32):
         return mg_batch_fits(self.handle, prec)

@@ -360,6 +360,16 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   h->prob = *prob;
   h->prob.conv = nullptr;   // read during setup only
   h->opts = opts;
+  // the mesh, for re-assembly with new coefficients (mg_update_problem)
+  h->mesh = *mesh;
+  h->mesh_lev.assign(mesh->leaf_level, mesh->leaf_level + mesh->n_leaves);
+  h->mesh_anc.assign(mesh->leaf_anchor, mesh->leaf_anchor + mesh->n_leaves * mesh->dim);
+  for (int d = 0; d < 3; ++d) {
+    h->mesh_axis[d] = H.axis[d];
+    h->mesh.axis[d] = nullptr;
+  }
+  h->mesh.leaf_level = nullptr;
+  h->mesh.leaf_anchor = nullptr;
   h->has_fp64 = opts.store_fp64 != 0;
   h->has_fp32 = opts.store_fp32 != 0;
   h->has_bf16 = opts.store_bf16 != 0;
@@ -906,6 +916,41 @@ int mg_serve_reserve(mg_ctx* c, mg_hier* h, int slots, int prec) {
     if (h->opts.launch_mode != 1 && (rc = get_graph(h, *w, method, prec, &g))) return rc;
   }
   CU(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+int mg_update_problem(mg_hier* h, const mg_problem* prob) {
+  if (!h || !prob) return fail(MG_ERR_INVALID, "NULL argument");
+  const mg_problem& o = h->prob;
+  if (prob->kind != o.kind || prob->pin_origin != o.pin_origin ||
+      std::memcmp(prob->dirichlet_mask, o.dirichlet_mask, sizeof(o.dirichlet_mask)) != 0)
+    return fail(MG_ERR_INVALID, "the problem kind, Dirichlet faces and pin must stay the same");
+  mg_ctx* c = h->ctx;
+  {
+    // no request of h queued or in flight
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto& r : c->queue)
+      if (r->h == h) return fail(MG_ERR_INVALID, "the hierarchy has serving requests queued");
+    for (auto& r : c->running)
+      if (r->h == h) return fail(MG_ERR_INVALID, "the hierarchy has serving requests running");
+    for (auto& B : c->batches)
+      for (auto& r : B->reqs)
+        if (r->h == h) return fail(MG_ERR_INVALID, "the hierarchy has serving requests running");
+  }
+  CU(cudaSetDevice(c->device));
+  mg_mesh m = h->mesh;
+  m.leaf_level = h->mesh_lev.data();
+  m.leaf_anchor = h->mesh_anc.data();
+  for (int d = 0; d < 3; ++d) m.axis[d] = h->mesh_axis[d].empty() ? nullptr : h->mesh_axis[d].data();
+  HostHierarchy H;
+  Status st = build_hierarchy(m, *prob, h->opts, &H);
+  if (!st.good()) return fail(st.code, st.msg);
+  std::lock_guard<std::mutex> lk(h->solve_mu);
+  CU(cudaStreamSynchronize(c->stream));
+  int rc = update_hierarchy(h, H);
+  if (rc) return rc;
+  h->prob = *prob;
+  h->prob.conv = nullptr;
   return MG_OK;
 }
 

@@ -58,6 +58,19 @@ void* dev_alloc(mg_ctx* c, std::vector<Alloc>& list, size_t& total, size_t bytes
   return p;
 }
 
+// Frees the one allocation of list that starts at p (nothing if absent).
+void free_one(mg_ctx* c, std::vector<Alloc>& list, size_t& total, const void* p) {
+  for (size_t i = 0; i < list.size(); ++i)
+    if (list[i].p == p) {
+      if (!list[i].cuda) c->alloc.free_fn(list[i].p, c->alloc.user);
+      else cudaFree(list[i].p);
+      c->used -= list[i].bytes;
+      total -= list[i].bytes;
+      list.erase(list.begin() + (int64_t)i);
+      return;
+    }
+}
+
 void free_list(mg_ctx* c, std::vector<Alloc>& list, size_t& total) {
   for (auto& a : list) {
     if (!a.cuda) c->alloc.free_fn(a.p, c->alloc.user);
@@ -220,6 +233,8 @@ int upload_sell(mg_hier* h, const BlockCSR& M, SellBuf* out, int64_t sigma = 0, 
   out->v.n = out->t.n = M.n;
   out->v.nslices = out->t.nslices = (int64_t)sptr.size() - 1;
   out->slots = (int64_t)col.size();
+  out->sigma = sigma;
+  out->val_bytes = b_val;
   out->nnz_real = M.nnzb();
   return MG_OK;
 }
@@ -255,6 +270,23 @@ int64_t sigma_for(const mg_hier* h, int64_t rows) {
   const int o = h->opts.sell_sigma;
   if (o >= 0) return o;
   return rows >= kSigmaMinRows ? kSigma : 0;
+}
+
+// New values for a packed matrix whose pattern is unchanged: packs M the way
+// upload_sell packed it (same window, same pattern flag) and copies only the
+// value array into the existing device buffer.
+template <typename VT>
+int refill_sell(const BlockCSR& M, SellBuf& buf, bool pat6 = false) {
+  if (!buf.v.val || buf.val_bytes == 0) return MG_OK;
+  std::vector<int64_t> sptr;
+  std::vector<int32_t> col;
+  std::vector<VT> val;
+  std::vector<int32_t> perm;
+  pack_sell<VT>(M, buf.sigma, sptr, col, val, perm, pat6);
+  if (val.size() * sizeof(VT) != buf.val_bytes || (int64_t)col.size() != buf.slots)
+    return fail(MG_ERR_INVALID, "re-assembly changed a matrix pattern");
+  CU(cudaMemcpy(const_cast<void*>(buf.v.val), val.data(), buf.val_bytes, cudaMemcpyHostToDevice));
+  return MG_OK;
 }
 
 // ---------------------------------------------------------------- precision helpers
@@ -1789,6 +1821,70 @@ int solve_batch(mg_ctx* c, int count, mg_hier* const* hs, const double* const* b
   if (rc) return rc;
   CU(cudaEventSynchronize(c->batch.done));
   return batch_collect(c->batch, stats);
+}
+
+
+// ---------------------------------------------------------------- re-assembly
+int update_hierarchy(mg_hier* h, HostHierarchy& H) {
+  const int nc = h->nc, nb = nc * nc;
+  if ((int)H.levels.size() != h->nlev) return fail(MG_ERR_INVALID, "re-assembly changed the number of levels");
+  int rc;
+  for (int l = 0; l < h->nlev; ++l) {
+    HostLevel& lv = H.levels[l];
+    LevelMats& B = h->L[l];
+    const bool pat6 = velocity_pressure_pattern(lv.A);
+    if (lv.topo.n_nodes != B.n || lv.vanka != B.vanka || (pat6 ? 6 : nb) != h->level_block_values[l])
+      return fail(MG_ERR_INVALID, "re-assembly changed a level");
+    B.omega = lv.omega;
+    if (B.A64.slots && (rc = refill_sell<double>(lv.A, B.A64, pat6))) return rc;
+    if (B.A32.slots && (rc = refill_sell<float>(lv.A, B.A32, pat6))) return rc;
+    if (B.A16.slots && (rc = refill_sell<__nv_bfloat16>(lv.A, B.A16, pat6))) return rc;
+    if (B.S64) CU(cudaMemcpy(B.S64, lv.Sinv.data(), B.n * nb * 8, cudaMemcpyHostToDevice));
+    if (B.S32) {
+      std::vector<float> s32(lv.Sinv.begin(), lv.Sinv.end());
+      CU(cudaMemcpy(B.S32, s32.data(), B.n * nb * 4, cudaMemcpyHostToDevice));
+    }
+    if (B.vanka) {
+      if (B.V64.slots && (rc = refill_sell<double>(lv.Sv, B.V64))) return rc;
+      if (B.V32.slots && (rc = refill_sell<float>(lv.Sv, B.V32))) return rc;
+    }
+  }
+  if ((int64_t)H.coarse_inv.size() != h->coarse_n * h->coarse_n)
+    return fail(MG_ERR_INVALID, "re-assembly changed the coarse level");
+  CU(cudaMemcpy(h->coarse_inv, H.coarse_inv.data(), H.coarse_inv.size() * 8, cudaMemcpyHostToDevice));
+  if ((rc = refill_sell<double>(H.load, h->F))) return rc;
+  if ((H.lift.nnzb() > 0) != (h->Lift.slots > 0)) return fail(MG_ERR_INVALID, "re-assembly changed the lifting");
+  if (h->Lift.slots && (rc = refill_sell<double>(H.lift, h->Lift))) return rc;
+  // the copies ran on the legacy stream: complete them before any stream reads
+  CU(cudaStreamSynchronize(cudaStreamLegacy));
+  // the small-level images hold copies of the level matrices and damping:
+  // rebuild them for the current tail configuration
+  for (int pi = 0; pi < 3; ++pi)
+    if (h->batch_tp[pi]) {
+      free_one(h->ctx, h->allocs, h->bytes, h->batch_tp[pi]);
+      h->batch_tp[pi] = nullptr;
+      h->batch_smem[pi] = 0;
+    }
+  for (auto& kv : h->tail_img) free_one(h->ctx, h->allocs, h->bytes, kv.second.p);
+  h->tail_img.clear();
+  const int top = h->tail_top, cl = h->tail_cluster;
+  for (int pi = 0; pi < 3 && top > 0 && cl <= 0; ++pi) {
+    if (!has_slot(h, pi)) continue;
+    mg_hier::TailImage ti;
+    rc = cl < 0 ? tail_image_dsm(h, pi, top, -cl, &ti) : tail_image(h, pi, top, &ti);
+    if (rc) return rc;
+  }
+  // every workspace: the levels' damping in its tail parameters, the new
+  // images, and no cached graph (kernel arguments carry the damping)
+  auto refresh = [&](Workspace* w) {
+    for (TailParams* P : {&w->tail64, &w->tail32, &w->tail16})
+      for (int l = 0; l < h->nlev && l < kTailMax; ++l) P->lv[l].omega = h->L[l].omega;
+    apply_tail(h, w);
+  };
+  if (h->ws0) refresh(h->ws0);
+  std::lock_guard<std::mutex> lk(h->pool_mu);
+  for (Workspace* w : h->all_ws) refresh(w);
+  return MG_OK;
 }
 
 }  // namespace mgi

@@ -31,6 +31,8 @@ struct SellBuf {
   TransferView t;
   int64_t nnz_real = 0;
   int64_t slots = 0;
+  int64_t sigma = 0;          // SELL-C-sigma window it was packed with
+  size_t val_bytes = 0;       // bytes of its value array
 };
 
 // Read-only matrices of one level.
@@ -229,6 +231,11 @@ struct mg_hier {
   std::vector<mgi::Workspace*> all_ws;   // every serving workspace
   size_t ws_bytes = 0;                   // device bytes of one workspace
   int serve_cap = 0;                     // > 0: serving never holds more workspaces (mg_serve_reserve)
+  // the mesh it was set up on (leaf arrays and graded axes owned here), for
+  // re-assembly with new coefficients
+  mg_mesh mesh{};
+  std::vector<int32_t> mesh_lev, mesh_anc;
+  std::vector<double> mesh_axis[3];
   // batched solves: device copy of the staged tail over every level, per
   // precision slot (built on first use), and its shared-memory bytes
   const mgi::TailParams* batch_tp[3] = {nullptr, nullptr, nullptr};
@@ -246,6 +253,12 @@ size_t workspace_bytes(const mg_hier* h);
 int ws_create(mg_hier* h, bool ctx_alloc, cudaStream_t s, Workspace** out);
 void ws_destroy(mg_hier* h, Workspace* ws);
 int upload_hierarchy(mg_hier* h, HostHierarchy& H);
+// Rewrites the values of an uploaded hierarchy in place from H, a host
+// hierarchy of the same mesh with new coefficients (same levels, patterns
+// and layouts): operators, smoother blocks and damping, Vanka matrices,
+// coarse inverse, load and lifting matrices; rebuilds the small-level images,
+// refreshes the workspaces' level parameters and drops their solve graphs.
+int update_hierarchy(mg_hier* h, HostHierarchy& H);
 // Tail threshold (levels <= rows dofs) and cluster size for every workspace;
 // cached solve graphs are dropped (they embed the old configuration).
 // cluster 0: one CTA with the tail in shared memory (the threshold is lowered

@@ -129,6 +129,7 @@ void mg_ns_default_params(mg_ns_params* p) {
   p->rtol = 1e-8;
   p->max_it = 200;
   p->nu = 4;
+  p->smoother = MG_SMOOTHER_JACOBI;
 }
 
 int mg_ns_setup(mg_ctx* ctx, const mg_ns_params* par, mg_ns** out) {
@@ -138,6 +139,8 @@ int mg_ns_setup(mg_ctx* ctx, const mg_ns_params* par, mg_ns** out) {
     return fail(MG_ERR_INVALID, "nx, ny, nz must be in [2, 4096]");
   if (!(P.re > 0) || !(P.dt > 0) || !std::isfinite(P.lid) || !(P.rtol > 0) || P.max_it < 1 || P.nu < 1 || P.nu > 16)
     return fail(MG_ERR_INVALID, "need re > 0, dt > 0, a finite lid speed, rtol > 0, max_it >= 1, nu in [1, 16]");
+  if (P.smoother != MG_SMOOTHER_JACOBI && P.smoother != MG_SMOOTHER_VANKA)
+    return fail(MG_ERR_INVALID, "unknown smoother");
   if (P.prec != MG_FP64 && P.prec != MG_MIXED_FP32 && P.prec != MG_MIXED_BF16)
     return fail(MG_ERR_INVALID, "unknown precision");
   if (P.krylov != MG_KRYLOV_AUTO && P.krylov != MG_CG && P.krylov != MG_BICGSTAB && P.krylov != MG_GMRES)
@@ -187,6 +190,7 @@ int mg_ns_setup(mg_ctx* ctx, const mg_ns_params* par, mg_ns** out) {
   mg_default_opts(&o);
   o.krylov = P.krylov;
   o.nu1 = o.nu2 = P.nu;
+  o.smoother = P.smoother;
   o.store_bf16 = P.prec == MG_MIXED_BF16 ? 1 : 0;
   int rc = mg_setup(ctx, &m, &pr, &o, &ns->hp);
   if (rc != MG_OK) {
