@@ -494,7 +494,9 @@ int mg_solve_profiled(mg_hier* h, const double* b, double* x, double rtol, int m
  * lps_alpha0 and conv may change).  A solve afterwards equals a solve on a
  * hierarchy set up with the new problem (same tuning) bit for bit.
  * MG_ERR_INVALID if a request of h is queued or running, or the new problem
- * changes the hierarchy's structure. */
+ * changes the hierarchy's structure.  The call waits for synchronous solves
+ * of h and for batched solves of the context; the caller must not submit
+ * requests of h while it runs. */
 int mg_update_problem(mg_hier* h, const mg_problem* problem);
 
 /* Batched solve of many small problems in one kernel launch (the per-kernel

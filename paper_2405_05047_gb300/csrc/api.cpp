@@ -945,6 +945,9 @@ int mg_update_problem(mg_hier* h, const mg_problem* prob) {
   HostHierarchy H;
   Status st = build_hierarchy(m, *prob, h->opts, &H);
   if (!st.good()) return fail(st.code, st.msg);
+  // no synchronous batched solve (which reads the images being rebuilt) and
+  // no solve of h on the context's stream meanwhile
+  std::lock_guard<std::mutex> bk(c->batch_mu);
   std::lock_guard<std::mutex> lk(h->solve_mu);
   CU(cudaStreamSynchronize(c->stream));
   int rc = update_hierarchy(h, H);
