@@ -225,6 +225,16 @@ typedef struct {
                                   Jacobi levels                               */
   int vanka_rows;              /* see smoother (default 0: every level >= 1)  */
   double vanka_omega;          /* damping w of the Vanka levels (default 1)   */
+  int stage_x;                 /* FP32 / BF16 scalar sweeps with one lane per
+                                  row gather x from shared memory: each block
+                                  first loads the range of x its 256 rows'
+                                  columns span (when at most 4096 entries)
+                                  (-1: levels of >= 32768 rows; 0 (default):
+                                  never; 1: every such level).  Same bits
+                                  either way; off by default because the
+                                  gathers it replaces already hit in L1/L2
+                                  and the staging pass plus its barriers cost
+                                  more than they save.                         */
 } mg_opts;
 
 typedef struct {

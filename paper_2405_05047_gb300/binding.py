@@ -64,7 +64,7 @@ class MgOpts(C.Structure):
                 ("tail_rows", C.c_int), ("store_bf16", C.c_int), ("autotune", C.c_int),
                 ("inner_rtol", C.c_double), ("sell_sigma", C.c_int), ("col16", C.c_int),
                 ("row_lanes", C.c_int), ("smoother", C.c_int), ("vanka_rows", C.c_int),
-                ("vanka_omega", C.c_double)]
+                ("vanka_omega", C.c_double), ("stage_x", C.c_int)]
 
 
 class MgInfo(C.Structure):

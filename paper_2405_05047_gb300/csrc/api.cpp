@@ -272,6 +272,7 @@ void mg_default_opts(mg_opts* o) {
   o->smoother = MG_SMOOTHER_JACOBI;
   o->vanka_rows = 0;
   o->vanka_omega = 1.0;
+  o->stage_x = 0;
 }
 
 int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, mg_ctx** out) {
@@ -336,6 +337,7 @@ int mg_setup(mg_ctx* ctx, const mg_mesh* mesh, const mg_problem* prob, const mg_
   if (!(opts.inner_rtol >= 0.0 && opts.inner_rtol < 1.0)) return fail(MG_ERR_INVALID, "inner_rtol must be in [0, 1)");
   if (opts.col16 < -1 || opts.col16 > 1) return fail(MG_ERR_INVALID, "col16 must be -1, 0 or 1");
   if (opts.row_lanes != -1 && opts.row_lanes != 1) return fail(MG_ERR_INVALID, "row_lanes must be -1 or 1");
+  if (opts.stage_x < -1 || opts.stage_x > 1) return fail(MG_ERR_INVALID, "stage_x must be -1, 0 or 1");
   if (opts.smoother != MG_SMOOTHER_JACOBI && opts.smoother != MG_SMOOTHER_VANKA)
     return fail(MG_ERR_INVALID, "unknown smoother");
   if (opts.vanka_rows < 0 || !(opts.vanka_omega > 0) || !std::isfinite(opts.vanka_omega))

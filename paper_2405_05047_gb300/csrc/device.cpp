@@ -272,6 +272,39 @@ int64_t sigma_for(const mg_hier* h, int64_t rows) {
   return rows >= kSigmaMinRows ? kSigma : 0;
 }
 
+// Column range of every 256-row window of a scalar SELL packing (all stored
+// slots, padding included), on the device, for the staged sweep; nullptr
+// arrays when no window is narrow enough to be staged.
+int stage_windows(mg_hier* h, const BlockCSR& M, int64_t sigma, SellView& v) {
+  std::vector<int64_t> sptr;
+  std::vector<int32_t> col, perm;
+  std::vector<float> val;
+  pack_sell<float>(M, sigma, sptr, col, val, perm);
+  const int64_t ns = (int64_t)sptr.size() - 1, per = kCol16Window / kSlice;
+  const int64_t nw = (ns + per - 1) / per;
+  std::vector<int32_t> lo(nw), len(nw);
+  int64_t staged = 0;
+  for (int64_t w = 0; w < nw; ++w) {
+    int32_t mn = INT32_MAX, mx = INT32_MIN;
+    for (int64_t o = sptr[w * per]; o < sptr[std::min(ns, (w + 1) * per)]; ++o) {
+      mn = std::min(mn, col[o]);
+      mx = std::max(mx, col[o]);
+    }
+    if (mn > mx) mn = mx = 0;
+    lo[w] = mn;
+    len[w] = mx - mn + 1;
+    staged += len[w] <= kStageMax;
+  }
+  if (staged == 0) return MG_OK;
+  int32_t* d = (int32_t*)dev_alloc(h->ctx, h->allocs, h->bytes, (size_t)nw * 8, true);
+  if (!d) return fail(MG_ERR_OOM, "alloc");
+  CU(cudaMemcpy(d, lo.data(), nw * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(d + nw, len.data(), nw * 4, cudaMemcpyHostToDevice));
+  v.wlo = d;
+  v.wlen = d + nw;
+  return MG_OK;
+}
+
 // New values for a packed matrix whose pattern is unchanged: packs M the way
 // upload_sell packed it (same window, same pattern flag) and copies only the
 // value array into the existing device buffer.
@@ -798,6 +831,16 @@ int upload_hierarchy(mg_hier* h, HostHierarchy& H) {
         if ((rc = upload_sell<float>(h, lv.Sv, &B.V32, sigma_for(h, lv.Sv.n), idx16_for(h, lv.Sv.n)))) return rc;
         B.V32.v.tpr = tpr_for(h, nc, lv.Sv.n);
       }
+    }
+    // x staged per window for the one-lane scalar FP32 / BF16 sweeps
+    const SellView& av = B.A32.slots ? B.A32.v : B.A16.v;
+    const bool stage = nc == 1 && av.tpr == 1 && (B.A32.slots || B.A16.slots) &&
+                       (opts.stage_x == 1 || (opts.stage_x < 0 && lv.A.n >= kSigmaMinRows));
+    if (stage) {
+      SellView w;
+      if ((rc = stage_windows(h, lv.A, lay.sigma, w))) return rc;
+      B.A32.v.wlo = B.A16.v.wlo = w.wlo;
+      B.A32.v.wlen = B.A16.v.wlen = w.wlen;
     }
     h->level_nnzb.push_back(opts.store_fp64 ? B.A64.slots : B.A32.slots);
     h->level_col16.push_back(lay.idx16 ? 1 : 0);   // of the FP32 / BF16 copies

@@ -46,6 +46,42 @@ __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_smooth(SellView A, 
     row_smooth<T, NC, 0, VT, TPR>(A, t / TPR, x, b, Sinv, xo, omega, FROM_ZERO, (int)(t % TPR), xo64, sc);
 }
 
+// The scalar FP32 sweep with each window's x staged in shared memory: the
+// 256 rows of a window (8 slices) gather x over a column range [wlo,
+// wlo + wlen) a few thousand entries wide on most windows of a lexicographic
+// mesh; the block loads that range once (coalesced, every load independent),
+// and each gather becomes a shared-memory read instead of an L2 round trip
+// behind the column load.  Windows with a wider range gather from device
+// memory as in k_smooth.  Same row function, same summation order: the same
+// bits as k_smooth.
+template <typename VT>
+__global__ void __launch_bounds__(kBlock, 8) k_smooth_staged(SellView A, const float* __restrict__ x,
+                                                             const float* __restrict__ b,
+                                                             const float* __restrict__ Sinv, float* __restrict__ xo,
+                                                             float omega, const int* done, double* __restrict__ xo64,
+                                                             const double* scale) {
+  static_assert(kBlock == kCol16Window, "one block per 256-row window");
+  __shared__ float xs[kStageMax];
+  pdl_wait();
+  if (stopped(done)) return;
+  const double sc = xo64 ? *scale : 1.0;
+  const int64_t rows = A.nslices * 32;
+  const int64_t nwin = (rows + kBlock - 1) / kBlock;
+  for (int64_t w = blockIdx.x; w < nwin; w += gridDim.x) {
+    const int32_t lo = __ldg(A.wlo + w), len = __ldg(A.wlen + w);
+    const bool staged = len <= kStageMax;
+    __syncthreads();                                   // the previous window's gathers are done
+    if (staged)
+      for (int i = threadIdx.x; i < len; i += blockDim.x) xs[i] = __ldg(x + lo + i);
+    __syncthreads();
+    const int64_t row = w * kBlock + threadIdx.x;
+    if (row < rows) {
+      if (staged) row_smooth<float, 1, 4, VT, 1>(A, row, xs - lo, b, Sinv, xo, omega, false, 0, xo64, sc);
+      else row_smooth<float, 1, 0, VT, 1>(A, row, x, b, Sinv, xo, omega, false, 0, xo64, sc);
+    }
+  }
+}
+
 template <typename T, typename VT, int NC, int MODE, int TPR>   // MODE 0: y = A x; 1: y = b - A x
 __global__ void __launch_bounds__(kBlock, NC == 1 ? 8 : 4) k_apply(SellView A, const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ y, const int* done) {
@@ -1048,6 +1084,12 @@ static int grid_sell(int64_t nslices) { return grid_for_rows(nslices * 32); }
 template <typename T, typename V, int NC, int TPR>
 void launch_smooth_k(const SellView& A, int g, cudaStream_t s, const T* x, const T* b, const T* Sinv, T* xo, T om,
                      bool from_zero, const int* done, double* xo64, const double* scale) {
+  if constexpr (std::is_same<T, float>::value && NC == 1 && TPR == 1) {
+    if (!from_zero && A.wlo) {   // x staged per window
+      launch(k_smooth_staged<V>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+      return;
+    }
+  }
   if (from_zero) launch(k_smooth<T, V, NC, true, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
   else launch(k_smooth<T, V, NC, false, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
 }

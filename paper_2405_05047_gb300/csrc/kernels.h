@@ -29,6 +29,12 @@ struct SellView {
   // 32, so readers mask sptr with kSptrMask.
   const int16_t* col16 = nullptr;
   int tpr = 1;                // lanes per block row (1 or 4; small FP32/BF16 block levels use 4)
+  // Staged x (scalar FP32 / BF16 copies, one lane per row): per window of
+  // 256 SELL rows (8 slices) the range [wlo, wlo + wlen) of every column its
+  // stored slots name (padding included); windows of at most kStageMax
+  // columns are gathered from shared memory.  NULL: not staged.
+  const int32_t* wlo = nullptr;
+  const int32_t* wlen = nullptr;
   // 3x3 blocks of the velocity-pressure pattern [[a, 0, g1], [0, a, g2],
   // [d1, d2, c]] (both velocity components share one operator, no coupling
   // between them) are stored as the 6 values (a, g1, g2, d1, d2, c) per slot;
@@ -39,6 +45,7 @@ struct SellView {
 inline int block_values(const SellView& A, int nc) { return A.bpat ? 6 : nc * nc; }
 constexpr int64_t kSptrMask = ~int64_t(31);
 constexpr int kCol16Window = 256;       // rows per base of the 16-bit column offsets
+constexpr int kStageMax = 4096;         // x entries a staged window holds (16 KB of FP32)
 
 // Transfer matrices (P, R) are scalar SELL with float weights, applied to
 // every component.  fix (block problems with partly fixed nodes, else NULL):

@@ -53,7 +53,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // that rewrites its vectors between __syncthreads().
 // Load modes: 0 grid kernels (read-only path), 1 unstaged tail kernel (its
 // CTAs run on several SMs: vectors L2-coherent), 2 shared-memory-staged tail
-// kernel (plain generic loads, operands may sit in shared memory).
+// kernel (plain generic loads, operands may sit in shared memory), 4 the
+// staged sweep (matrices through the read-only path, vectors by plain
+// generic loads: the gathered x sits in shared memory).
 template <int LM, typename T>
 __device__ __forceinline__ T vld(const T* p) {
   if (LM == 0) return __ldg(p);
@@ -66,7 +68,7 @@ __device__ __forceinline__ T vld(const T* p) {
 // the tail kernel, whose matrices may sit in shared memory.
 template <int LM, typename T>
 __device__ __forceinline__ T mld(const T* p) {
-  if (LM <= 1) return __ldg(p);       // matrices never change during a kernel
+  if (LM <= 1 || LM == 4) return __ldg(p);   // matrices never change during a kernel
   return *p;
 }
 template <typename AT, int LM = 0, typename VT>

@@ -667,6 +667,53 @@ def test_row_lanes_reported_and_equivalent(ctx, case):
         hh.free()
 
 
+@pytest.mark.parametrize("case", ["transport2d", "poisson3d"])
+def test_staged_sweep_bitwise(ctx, case):
+    """The sweep that gathers x from a shared-memory copy of each window's
+    column range (stage_x) gives the same V-cycle and solve bits as the one
+    that gathers from device memory, in FP32 and with BF16-stored values;
+    3D windows span too many columns to be staged and take the fallback."""
+    if case == "transport2d":
+        lm = W.td_adaptive(rounds=5, gamma=1.0)
+        pb = B.make_problem(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    else:
+        lm = W.uniform_leaves(3, (1, 1, 1), 5)
+        pb = B.make_problem(kind=B.MG_POISSON)
+    hs = [G.Hierarchy(ctx, lm, pb, B.make_opts(stage_x=v, autotune=0, store_bf16=1)) for v in (0, 1, -1)]
+    rng = np.random.default_rng(16)
+    r = rng.standard_normal(hs[0].n_dofs)
+    f = dev(np.ones(hs[0].n_dofs))
+    for prec in (B.MG_MIXED_FP32, B.MG_MIXED_BF16):
+        outs, sols = [], []
+        for hh in hs:
+            z = torch.empty(hh.n_dofs, device="cuda", dtype=torch.float32)
+            hh.vcycle(dev(r, torch.float32), z, prec)
+            outs.append(z.cpu().numpy())
+            b = torch.empty(hh.n_dofs, device="cuda", dtype=torch.float64)
+            hh.assemble_rhs(f, b)
+            x = torch.zeros_like(b)
+            st = hh.solve(b, x, rtol=1e-10, max_it=200, prec=prec)
+            assert st.status == 0
+            sols.append((st.iters, x.cpu().numpy()))
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        for it, x in sols[1:]:
+            assert it == sols[0][0] and np.array_equal(x, sols[0][1])
+        # the level operator alone, on every level
+        for l in range(hs[0].levels):
+            n = hs[0].info.level_nodes[l]
+            xin = dev(rng.standard_normal(n), torch.float32)
+            bb = dev(rng.standard_normal(n), torch.float32)
+            res = []
+            for hh in hs[:2]:
+                out = torch.empty(n, device="cuda", dtype=torch.float32)
+                hh.apply(l, B.MG_OP_SMOOTH, xin, bb, out, prec)
+                res.append(out.cpu().numpy())
+            assert np.array_equal(res[0], res[1]), l
+    for hh in hs:
+        hh.free()
+
+
 def test_direct_launch_mode_equals_graph(ctx):
     lm = W.td_adaptive(rounds=4, gamma=1.0)
     pk = dict(kind=B.MG_TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
