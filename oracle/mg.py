@@ -139,6 +139,8 @@ def lambda_max_power(S, A, fixed, iters=20):
     n = A.shape[0]
     v = ((np.arange(n, dtype=np.uint64) * np.uint64(2654435761)) % np.uint64(2 ** 32)).astype(np.float64) / 2.0 ** 32 - 0.5
     v[fixed] = 0.0
+    if not np.any(v):
+        return 1.0          # no free dof: the level is never smoothed, any damping does
     lam = 0.0
     for _ in range(iters):
         w = S @ (A @ v)
