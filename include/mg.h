@@ -299,7 +299,9 @@ void mg_default_opts(mg_opts* opts);
 /* Context: one device, one stream (a cudaStream_t from the caller, e.g.
  * torch.cuda.current_stream().cuda_stream, or NULL for a private stream),
  * an HBM budget (bytes; 0 = no limit) that bounds every hierarchy and
- * workspace allocated through this context.  The allocator struct is copied. */
+ * workspace allocated through this context.  The allocator struct is copied.
+ * MG_ERR_INVALID for a device that gives a block less than 227 KB of shared
+ * memory on opt-in (the staged small-level kernel needs 226 KB). */
 int mg_init(int device, size_t hbm_budget_bytes, const mg_allocator* alloc, void* stream, mg_ctx** out);
 /* MG_ERR_INVALID while hierarchies of this context are still alive. */
 int mg_destroy(mg_ctx* ctx);
@@ -409,14 +411,14 @@ int mg_apply(mg_hier* h, int level, int op, const void* in, const void* in2, voi
  * (and all coarser ones) run as one kernel on a cluster of `cluster` CTAs
  * (1..16; sizes above the portable 8 only where the GPU schedules such a
  * cluster of 1024-thread CTAs), or, for cluster == 0, on one CTA that first copies their vectors
- * and, coarsest first, as many of their matrices as fit into 200 KB of
+ * and, coarsest first, as many of their matrices as fit into 226 KB of
  * shared memory (the threshold is lowered until the vectors fit), or, for
  * cluster = -2, -4, -8, -16 (scalar problems), cluster-resident on that many
  * CTAs: every level is cut into equal power-of-two row chunks, one per CTA;
  * each CTA keeps its chunks of the vectors and its rows of the level and
  * transfer matrices in shared memory and reads the other CTAs' vector entries
  * through distributed shared memory (MG_ERR_INVALID when the levels do not
- * fit 200 KB per CTA or the cluster is not schedulable).
+ * fit 226 KB per CTA or the cluster is not schedulable).
  * tail_rows < 0: time V-cycles of precision prec over a set of thresholds and
  * launch shapes and keep the fastest (what opts.autotune does at setup).
  * Results are bitwise identical for every choice.  Errors: MG_ERR_INVALID

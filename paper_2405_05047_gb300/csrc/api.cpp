@@ -281,6 +281,10 @@ int mg_init(int device, size_t budget, const mg_allocator* alloc, void* stream, 
   CU(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(MG_ERR_INVALID, "no such device");
   CU(cudaSetDevice(device));
+  int smem_optin = 0;
+  CU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  if (smem_optin < (int)kTailSmemMax + 1024)
+    return fail(MG_ERR_INVALID, "device gives a block less shared memory than the staged tail needs");
   mg_ctx* c = new mg_ctx();
   c->device = device;
   c->budget = budget;

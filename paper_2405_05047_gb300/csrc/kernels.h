@@ -186,7 +186,10 @@ struct TailParams {
   int dsm = 0;
   uint32_t section = 0;
 };
-constexpr uint32_t kTailSmemMax = 200 * 1024;   // dynamic shared memory of the staged tail
+// dynamic shared memory of the staged tail: sm_100 / sm_103 give a block up
+// to 227 KB (232448 B) on opt-in; 1 KB stays for the static arrays of the
+// batched kernel
+constexpr uint32_t kTailSmemMax = 226 * 1024;
 // true when the GPU schedules a cluster of cl tail CTAs (always for cl <= 8)
 bool tail_cluster_fits(int cl);
 // true when the GPU schedules a cluster-resident tail of cl CTAs with smem

@@ -3,6 +3,8 @@
   python -m paper_2405_05047_gb300.opbench --workload td_adaptive --op smooth --prec fp32 --reps 3
   python -m paper_2405_05047_gb300.opbench --workload ns_cavity --steps 3     (driven-cavity steps)
   python -m paper_2405_05047_gb300.opbench --workload batch_small            (one batched launch)
+  python -m paper_2405_05047_gb300.opbench --workload td_adaptive --op vcycle --nu 5 --tail-rows 1024
+                                                                (whole FP32 V-cycles, small-level kernel)
 
 Sets up the hierarchy of the named workload, runs the operator `reps` times
 back to back on the finest level (or --level) through mg_time_op and prints
@@ -106,12 +108,43 @@ def run_batch():
     ctx.close()
 
 
+def run_vcycle(G, ctx, lm, pb, okw, prec, args):
+    """`reps` V-cycles of the finest level from a seeded residual; wall time
+    per cycle (mg_vcycle synchronises after each one)."""
+    import time
+
+    import numpy as np
+    import torch
+    if args.nu > 0:
+        okw.update(nu1=args.nu, nu2=args.nu)
+    h = G.Hierarchy(ctx, lm, pb, B.make_opts(**okw))
+    if args.tail_rows >= 0:
+        h.tune(prec, tail_rows=args.tail_rows, cluster=0)
+    dt = torch.float64 if prec == B.MG_FP64 else torch.float32
+    r = torch.from_numpy(np.random.default_rng(7).standard_normal(h.n_dofs)).to(device="cuda", dtype=dt)
+    z = torch.empty_like(r)
+    h.vcycle(r, z, prec)
+    t0 = time.perf_counter()
+    for _ in range(args.reps):
+        h.vcycle(r, z, prec)
+    ms = (time.perf_counter() - t0) * 1e3 / args.reps
+    print(json.dumps({"workload": args.workload, "op": "vcycle", "prec": args.prec, "levels": h.levels,
+                      "tail_levels": h.info.tail_levels, "tail_cluster": h.info.tail_cluster,
+                      "nu": args.nu, "ms_per_cycle_wall": ms}))
+    h.free()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="td_adaptive",
                     help="a hierarchy workload (level operator timing), or ns_cavity / batch_small")
     ap.add_argument("--steps", type=int, default=3, help="ns_cavity: time steps")
-    ap.add_argument("--op", default="smooth", choices=sorted(OPS))
+    ap.add_argument("--op", default="smooth", choices=sorted(OPS) + ["vcycle"])
+    ap.add_argument("--nu", type=int, default=0, help="vcycle: pre- and post-smoothing sweeps (0: default)")
+    ap.add_argument("--tail-rows", type=int, default=-1,
+                    help="vcycle: small-level kernel over the levels of at most this many rows, one CTA in "
+                         "shared memory (-1: the setup default)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--level", type=int, default=-1)
     ap.add_argument("--reps", type=int, default=3)
@@ -128,6 +161,8 @@ def main():
     # same kernels ahead of the timed ones in a profiler's launch list
     okw.update(store_fp64=int(prec == B.MG_FP64), store_fp32=int(prec != B.MG_FP64), autotune=0)
     ctx = G.Context(0)
+    if args.op == "vcycle":
+        return run_vcycle(G, ctx, lm, pb, okw, prec, args)
     h = G.Hierarchy(ctx, lm, pb, B.make_opts(**okw))
     level = args.level if args.level >= 0 else h.levels - 1
     ms = h.time_op(level, OPS[args.op], prec, reps=args.reps)

@@ -109,7 +109,7 @@ def graph_solve(c, b, rtol, prec, x0=None):
     return st, x.cpu().numpy()
 
 
-SMEM = 200 * 1024          # shared memory of the staged tail
+SMEM = 226 * 1024          # shared memory of the staged tail
 
 
 def vec_bytes(c, prec):
@@ -125,7 +125,7 @@ def fitting(cases, prec):
 
 def test_fit_rule(cases):
     """A problem fits exactly when its V-cycle vectors (plus the level
-    headers, under 8 KiB) fit in the 200 KiB of the staged tail; every case
+    headers, under 8 KiB) fit in the 226 KiB of the staged tail; every case
     fits with the FP32 V-cycle."""
     for c in cases.values():
         for prec in (B.MG_FP64, B.MG_MIXED_FP32, B.MG_MIXED_BF16):
