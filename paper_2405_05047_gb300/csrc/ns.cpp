@@ -199,18 +199,21 @@ int mg_ns_setup(mg_ctx* ctx, const mg_ns_params* par, mg_ns** out) {
   }
   // velocity operators: per-axis 1D coefficients
   NsView& V = ns->V;
+  V.nu = 1.0 / P.re;
   for (int d = 0; d < 3; ++d) {
     const Axis1D A = axis_ops(vx[d]);
     const int64_t n = (int64_t)vx[d].size();
-    double* buf = dvec(ns, 13 * n);
+    double* buf = dvec(ns, 17 * n);
     if (!buf) { ns_release(ns); return fail(MG_ERR_OOM, "alloc"); }
-    std::vector<double> h(13 * n);
+    std::vector<double> h(17 * n);
     std::copy(A.M.begin(), A.M.end(), h.begin());
     std::copy(A.K.begin(), A.K.end(), h.begin() + 3 * n);
     std::copy(A.G.begin(), A.G.end(), h.begin() + 6 * n);
     std::copy(A.GT.begin(), A.GT.end(), h.begin() + 9 * n);
     std::copy(A.m1.begin(), A.m1.end(), h.begin() + 12 * n);
-    if (cudaMemcpy(buf, h.data(), 13 * n * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+    for (int64_t e = 0; e < 3 * n; ++e) h[13 * n + e] = -V.nu * A.K[e];
+    for (int64_t i = 0; i < n; ++i) h[16 * n + i] = 1.0 / A.m1[i];
+    if (cudaMemcpy(buf, h.data(), 17 * n * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
       ns_release(ns);
       return fail(MG_ERR_CUDA, "upload");
     }
@@ -219,10 +222,11 @@ int mg_ns_setup(mg_ctx* ctx, const mg_ns_params* par, mg_ns** out) {
     V.ax[d].G = buf + 6 * n;
     V.ax[d].GT = buf + 9 * n;
     V.ax[d].m1 = buf + 12 * n;
+    V.ax[d].Kn = buf + 13 * n;
+    V.ax[d].im1 = buf + 16 * n;
     V.nv[d] = (int)n;
     V.np[d] = nc[d] + 1;
   }
-  V.nu = 1.0 / P.re;
   V.dt = P.dt;
   V.lid = P.lid;
   const int64_t nv = (int64_t)V.nv[0] * V.nv[1] * V.nv[2], np = (int64_t)V.np[0] * V.np[1] * V.np[2];

@@ -15,12 +15,16 @@ namespace mgi {
 //   G[3i + a]  = (phi_{i+a-1}, phi_i')       convection (rows of C_d along d)
 //   GT[3i + a] = G[3(i+a-1) + 2 - a]         transposed (the divergence)
 //   m1[i]      = sum_a M[3i + a]             lumped mass
+//   Kn[3i + a] = -nu K[3i + a]               (the viscous factor of Step 1)
+//   im1[i]     = 1 / m1[i]
 struct NsAxis {
   const double* M = nullptr;
   const double* K = nullptr;
   const double* G = nullptr;
   const double* GT = nullptr;
   const double* m1 = nullptr;
+  const double* Kn = nullptr;
+  const double* im1 = nullptr;
 };
 
 struct NsView {
