@@ -604,6 +604,30 @@ def test_power_iteration_damping_poisson_and_rule():
     assert mg.Hierarchy(lm, PB.Problem(PB.POISSON)).fine.omega == 0.8
 
 
+def test_degenerate_hierarchies():
+    """A mesh that is its own coarsest level gives a one-level hierarchy whose
+    V-cycle is the LU solve of A (any smoothing count); with every node
+    fixed the damping estimate is defined (no free dof, no power iteration)
+    and the condensed system is the identity with b = g."""
+    lm = W.uniform_leaves(2, (2, 2), 1)
+    prob = PB.Problem(PB.TRANSPORT, eps=1e-3, beta=(1.0, 0.5))
+    for nu in (1, 5):
+        h = mg.Hierarchy(lm, prob, nu1=nu, nu2=nu)
+        assert len(h.levels) == 1
+        r = np.random.default_rng(3).standard_normal(h.fine.A.shape[0])
+        z = h.precondition(r)
+        assert np.abs(h.fine.A @ z - r).max() <= 1e-12 * np.abs(r).max()
+    el = PB.Problem(PB.ELASTICITY, mu=1.0, lam=10.0, dirichlet=(0x3F,))
+    h = mg.Hierarchy(W.uniform_leaves(3, (1, 1, 1), 0), el)
+    lv = h.fine
+    assert lv.sys.fixed.all() and np.isfinite(lv.omega)
+    assert mg.lambda_max_power(lv.S, lv.A, lv.sys.fixed) == 1.0
+    g = np.random.default_rng(4).standard_normal(lv.A.shape[0])
+    s = PB.build_system(h.fine.mesh, el)
+    assert np.array_equal(s.rhs(np.ones_like(g), g), g)
+    assert abs(lv.A - sp.identity(lv.A.shape[0])).max() == 0.0
+
+
 # ---------------------------------------------------------------- SUPG terms
 def _linear_td_case(rounds=3):
     """Transport-diffusion with SUPG on an adaptive mesh with hanging nodes,
