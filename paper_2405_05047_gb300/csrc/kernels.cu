@@ -1072,6 +1072,44 @@ static void launch(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... a
   launch_ex(cfg, kernel, args...);
 }
 
+// Row grids stop at 1216 blocks (152 SMs x 8).  A kernel with more than 32
+// registers per thread holds fewer than 8 blocks of kBlock threads per SM;
+// where that leaves a last wave filling less than half of the SMs' block
+// slots (6 per SM: 1216 = 1.33 waves), the grid-stride kernel gets one full
+// wave instead.  Applied to the scalar row kernels and the vector kernels;
+// the 3x3-block kernels keep their grid (one wave was measured slower there:
+// their rows of 9 to 27 blocks balance better over two waves).
+static int wave_grid(const void* fn, int grid) {
+  thread_local std::map<const void*, int> cap;
+  auto it = cap.find(fn);
+  int c;
+  if (it != cap.end()) {
+    c = it->second;
+  } else {
+    int dev = 0, sms = 0, occ = 0;
+    c = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) == cudaSuccess && occ > 0 && sms > 0)
+      c = sms * occ;
+    cap[fn] = c;
+  }
+  return (c > 0 && grid > c && 2 * grid < 3 * c) ? c : grid;
+}
+
+// launch() for grid-stride kernels over rows or vector entries
+template <typename... KArgs, typename... Args>
+static void launch_rows(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  launch(kernel, wave_grid((const void*)kernel, grid), s, args...);
+}
+
+// launch_rows for scalar kernels (NC = 1), launch() for 3x3-block ones
+template <int NC, typename... KArgs, typename... Args>
+static void launch_nc(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  if constexpr (NC == 1) launch_rows(kernel, grid, s, args...);
+  else launch(kernel, grid, s, args...);
+}
+
 int grid_for_rows(int64_t rows) {
   int64_t g = (rows + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
@@ -1086,12 +1124,12 @@ void launch_smooth_k(const SellView& A, int g, cudaStream_t s, const T* x, const
                      bool from_zero, const int* done, double* xo64, const double* scale) {
   if constexpr (std::is_same<T, float>::value && NC == 1 && TPR == 1) {
     if (!from_zero && A.wlo) {   // x staged per window
-      launch(k_smooth_staged<V>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+      launch_rows(k_smooth_staged<V>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
       return;
     }
   }
-  if (from_zero) launch(k_smooth<T, V, NC, true, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
-  else launch(k_smooth<T, V, NC, false, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+  if (from_zero) launch_nc<NC>(k_smooth<T, V, NC, true, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
+  else launch_nc<NC>(k_smooth<T, V, NC, false, TPR>, g, s, A, x, b, Sinv, xo, om, done, xo64, scale);
 }
 
 template <typename T, typename V>
@@ -1125,8 +1163,8 @@ template <typename T, typename V, int MODE>
 void launch_apply_v(const SellView& A, int nc, int g, cudaStream_t s, const T* x, const T* b, T* y, const int* done) {
   const bool four = A.tpr == 4;
   if (nc == 1) {
-    if (four) launch(k_apply<T, V, 1, MODE, 4>, g, s, A, x, b, y, done);
-    else launch(k_apply<T, V, 1, MODE, 1>, g, s, A, x, b, y, done);
+    if (four) launch_rows(k_apply<T, V, 1, MODE, 4>, g, s, A, x, b, y, done);
+    else launch_rows(k_apply<T, V, 1, MODE, 1>, g, s, A, x, b, y, done);
   } else {
     if (four) launch(k_apply<T, V, 3, MODE, 4>, g, s, A, x, b, y, done);
     else launch(k_apply<T, V, 3, MODE, 1>, g, s, A, x, b, y, done);
@@ -1163,10 +1201,10 @@ void launch_restrict(const TransferView& R, int nc, const T* r, T* d, const T* S
   const int g = grid_sell(R.nslices);
   const T om = (T)omega;
   if (x0) {
-    if (nc == 1) launch(k_restrict<T, 1, true>, g, s, R, r, d, Sinv, x0, om, done);
+    if (nc == 1) launch_rows(k_restrict<T, 1, true>, g, s, R, r, d, Sinv, x0, om, done);
     else launch(k_restrict<T, 3, true>, g, s, R, r, d, Sinv, x0, om, done);
   } else {
-    if (nc == 1) launch(k_restrict<T, 1, false>, g, s, R, r, d, Sinv, x0, om, done);
+    if (nc == 1) launch_rows(k_restrict<T, 1, false>, g, s, R, r, d, Sinv, x0, om, done);
     else launch(k_restrict<T, 3, false>, g, s, R, r, d, Sinv, x0, om, done);
   }
 }
@@ -1175,7 +1213,7 @@ template <typename T>
 void launch_prolong_add(const TransferView& P, int nc, const T* y, const T* xin, T* xo, const int* done,
                         cudaStream_t s) {
   const int g = grid_sell(P.nslices);
-  if (nc == 1) launch(k_prolong<T, 1>, g, s, P, y, xin, xo, done);
+  if (nc == 1) launch_rows(k_prolong<T, 1>, g, s, P, y, xin, xo, done);
   else launch(k_prolong<T, 3>, g, s, P, y, xin, xo, done);
 }
 
@@ -1186,8 +1224,8 @@ void launch_vanka(const SellView& S, int nc, const T* r, const T* xin, T* xo, do
   const T om = (T)omega;
   const bool four = S.tpr == 4;
   if (nc == 1) {
-    if (four) launch(k_vanka<T, T, 1, 4>, g, s, S, r, xin, xo, om, done, xo64, scale);
-    else launch(k_vanka<T, T, 1, 1>, g, s, S, r, xin, xo, om, done, xo64, scale);
+    if (four) launch_rows(k_vanka<T, T, 1, 4>, g, s, S, r, xin, xo, om, done, xo64, scale);
+    else launch_rows(k_vanka<T, T, 1, 1>, g, s, S, r, xin, xo, om, done, xo64, scale);
   } else {
     if (four) launch(k_vanka<T, T, 3, 4>, g, s, S, r, xin, xo, om, done, xo64, scale);
     else launch(k_vanka<T, T, 3, 1>, g, s, S, r, xin, xo, om, done, xo64, scale);
@@ -1349,47 +1387,47 @@ bool tail_dsm_fits(int cl, uint32_t smem) {
 
 void launch_rhs(const SellView& F, int nc, const double* f, const uint8_t* fixmask, const uint8_t* dirmask,
                 const double* g, double* b, cudaStream_t s) {
-  launch(k_rhs, grid_sell(F.nslices), s, F, nc, f, fixmask, dirmask, g, b);
+  launch_rows(k_rhs, grid_sell(F.nslices), s, F, nc, f, fixmask, dirmask, g, b);
 }
 void launch_lift(const SellView& L, int nc, const double* g, double* b, cudaStream_t s) {
   if (L.n == 0) return;
-  if (nc == 1) launch(k_lift<1>, grid_sell(L.nslices), s, L, g, b);
+  if (nc == 1) launch_rows(k_lift<1>, grid_sell(L.nslices), s, L, g, b);
   else launch(k_lift<3>, grid_sell(L.nslices), s, L, g, b);
 }
 void launch_fill_hanging(const TransferView& Hc, int nc, double* x, cudaStream_t s) {
-  launch(k_fill_hanging, grid_sell(Hc.nslices), s, Hc, nc, x);
+  launch_rows(k_fill_hanging, grid_sell(Hc.nslices), s, Hc, nc, x);
 }
 void launch_copy_fixed(int64_t n, int nc, const uint8_t* fixmask, const double* b, const double* xin, double* x,
                        cudaStream_t s) {
-  launch(k_copy_fixed, grid_for_rows(n), s, n, nc, fixmask, b, xin, x);
+  launch_rows(k_copy_fixed, grid_for_rows(n), s, n, nc, fixmask, b, xin, x);
 }
 void launch_step_load2(int64_t n, double inv_dt, const double* u, double* v, const double* f, double* out,
                        cudaStream_t s) {
-  launch(k_step_load2, grid_for_rows(n), s, n, inv_dt, u, v, f, out);
+  launch_rows(k_step_load2, grid_for_rows(n), s, n, inv_dt, u, v, f, out);
 }
 void launch_step_velocity(int64_t n, double inv_dt, const double* u, double* v, cudaStream_t s) {
-  launch(k_step_velocity, grid_for_rows(n), s, n, inv_dt, u, v);
+  launch_rows(k_step_velocity, grid_for_rows(n), s, n, inv_dt, u, v);
 }
 void launch_step_load(int64_t n, double sc, const double* theta, const double* f, double* out, cudaStream_t s) {
-  launch(k_step_load, grid_for_rows(n), s, n, sc, theta, f, out);
+  launch_rows(k_step_load, grid_for_rows(n), s, n, sc, theta, f, out);
 }
 void launch_residual_norm(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
                           KrylovState* st, int test, cudaStream_t s, unsigned long long cond) {
   const int g = grid_sell(A64.nslices);
-  if (nc == 1) launch(k_residual_norm<1>, g, s, A64, x, b, r, part.p, st, test, cond);
+  if (nc == 1) launch_rows(k_residual_norm<1>, g, s, A64, x, b, r, part.p, st, test, cond);
   else launch(k_residual_norm<3>, g, s, A64, x, b, r, part.p, st, test, cond);
 }
 
 void launch_norm_init(int64_t n_nodes, int nc, const uint8_t* fixmask, const double* b, Partials part,
                       KrylovState* st, double rtol, int max_it, cudaStream_t s) {
-  launch(k_norm_init, grid_for_rows(n_nodes), s, n_nodes, nc, fixmask, b, part.p, st, rtol, max_it);
+  launch_rows(k_norm_init, grid_for_rows(n_nodes), s, n_nodes, nc, fixmask, b, part.p, st, rtol, max_it);
 }
 static int grid_vec4(int64_t n) {  // 4 entries per thread (k_bicg_x: 2, capped grid)
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
 void launch_mgi_update(int64_t n, PVec z, double* x, KrylovState* st, cudaStream_t s) {
-  launch(k_mgi_update, grid_vec4(n), s, n, z, x, st);
+  launch_rows(k_mgi_update, grid_vec4(n), s, n, z, x, st);
 }
 void launch_to_f32(int64_t n, const double* v, float* v32, const KrylovState* st, cudaStream_t s) {
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
@@ -1397,48 +1435,48 @@ void launch_to_f32(int64_t n, const double* v, float* v32, const KrylovState* st
 }
 void launch_cg_dots(int64_t n, PVec z, const double* r, const double* q, Partials part, KrylovState* st,
                     cudaStream_t s) {
-  launch(k_cg_dots, grid_vec4(n), s, n, z, r, q, part.p, st);
+  launch_rows(k_cg_dots, grid_vec4(n), s, n, z, r, q, part.p, st);
 }
 void launch_cg_update_p(int64_t n, PVec z, double* p, KrylovState* st, cudaStream_t s) {
-  launch(k_cg_update_p, grid_vec4(n), s, n, z, p, st);
+  launch_rows(k_cg_update_p, grid_vec4(n), s, n, z, p, st);
 }
 void launch_spmv_dot(const SellView& A64, int nc, PVec p, const double* w, double* out, Partials part, int k,
                      KrylovState* st, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
   if (p.f) {
-    if (nc == 1) launch(k_spmv_dot<1, true>, g, s, A64, p, w, out, part.p, k, st);
+    if (nc == 1) launch_rows(k_spmv_dot<1, true>, g, s, A64, p, w, out, part.p, k, st);
     else launch(k_spmv_dot<3, true>, g, s, A64, p, w, out, part.p, k, st);
   } else {
-    if (nc == 1) launch(k_spmv_dot<1, false>, g, s, A64, p, w, out, part.p, k, st);
+    if (nc == 1) launch_rows(k_spmv_dot<1, false>, g, s, A64, p, w, out, part.p, k, st);
     else launch(k_spmv_dot<3, false>, g, s, A64, p, w, out, part.p, k, st);
   }
 }
 void launch_cg_update_xr(int64_t n, const double* p, const double* q, double* x, double* r, Partials part,
                          KrylovState* st, unsigned long long cond, cudaStream_t s) {
-  launch(k_cg_update_xr, grid_vec4(n), s, n, p, q, x, r, part.p, st, cond);
+  launch_rows(k_cg_update_xr, grid_vec4(n), s, n, p, q, x, r, part.p, st, cond);
 }
 void launch_bicg_p(int64_t n, const double* r, const double* v, double* p, float* p32, KrylovState* st,
                    cudaStream_t s) {
-  launch(k_bicg_p, grid_vec4(n), s, n, r, v, p, p32, st);
+  launch_rows(k_bicg_p, grid_vec4(n), s, n, r, v, p, p32, st);
 }
 void launch_bicg_s(int64_t n, const double* r, const double* v, double* sv, float* s32, KrylovState* st,
                    cudaStream_t s) {
-  launch(k_bicg_s, grid_vec4(n), s, n, r, v, sv, s32, st);
+  launch_rows(k_bicg_s, grid_vec4(n), s, n, r, v, sv, s32, st);
 }
 void launch_spmv_2dots(const SellView& A64, int nc, PVec sh, const double* sv, double* t, Partials part,
                        KrylovState* st, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
   if (sh.f) {
-    if (nc == 1) launch(k_spmv_2dots<1, true>, g, s, A64, sh, sv, t, part.p, st);
+    if (nc == 1) launch_rows(k_spmv_2dots<1, true>, g, s, A64, sh, sv, t, part.p, st);
     else launch(k_spmv_2dots<3, true>, g, s, A64, sh, sv, t, part.p, st);
   } else {
-    if (nc == 1) launch(k_spmv_2dots<1, false>, g, s, A64, sh, sv, t, part.p, st);
+    if (nc == 1) launch_rows(k_spmv_2dots<1, false>, g, s, A64, sh, sv, t, part.p, st);
     else launch(k_spmv_2dots<3, false>, g, s, A64, sh, sv, t, part.p, st);
   }
 }
 void launch_bicg_x(int64_t n, PVec ph, PVec sh, const double* sv, const double* t, const double* rhat, double* x,
                    double* r, Partials part, KrylovState* st, unsigned long long cond, cudaStream_t s) {
-  launch(k_bicg_x, grid_vec4(n), s, n, ph, sh, sv, t, rhat, x, r, part.p, st, cond);
+  launch_rows(k_bicg_x, grid_vec4(n), s, n, ph, sh, sv, t, rhat, x, r, part.p, st, cond);
 }
 
 void launch_cond_reset(unsigned long long cond, cudaStream_t s) { launch(k_cond_reset, 1, s, cond); }
@@ -1446,15 +1484,15 @@ void launch_cond_reset(unsigned long long cond, cudaStream_t s) { launch(k_cond_
 // ---- GMRES launchers
 void launch_gm_start(int64_t n, const double* r, float* v32, double* v64, GmresView G, KrylovState* st,
                      cudaStream_t s) {
-  launch(k_gm_start, grid_for_rows(n), s, n, r, v32, v64, G, st);
+  launch_rows(k_gm_start, grid_for_rows(n), s, n, r, v32, v64, G, st);
 }
 void launch_gm_spmv(const SellView& A64, int nc, PVec z, double* w, GmresView G, KrylovState* st, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
   if (z.f) {
-    if (nc == 1) launch(k_gm_spmv<1, true>, g, s, A64, z, w, G, st);
+    if (nc == 1) launch_rows(k_gm_spmv<1, true>, g, s, A64, z, w, G, st);
     else launch(k_gm_spmv<3, true>, g, s, A64, z, w, G, st);
   } else {
-    if (nc == 1) launch(k_gm_spmv<1, false>, g, s, A64, z, w, G, st);
+    if (nc == 1) launch_rows(k_gm_spmv<1, false>, g, s, A64, z, w, G, st);
     else launch(k_gm_spmv<3, false>, g, s, A64, z, w, G, st);
   }
 }
@@ -1477,21 +1515,21 @@ void launch_gm_orth(int64_t n, double* w, GmresView G, KrylovState* st, int pass
     launch_ex(cfg, k_gm_dots, n, (const double*)w, G, st);
   }
   launch(k_gm_reduce, G.m + 1, s, G, st, gx, pass);
-  launch(k_gm_axpy, grid_for_rows(n), s, n, w, G, st, part.p, pass);
+  launch_rows(k_gm_axpy, grid_for_rows(n), s, n, w, G, st, part.p, pass);
 }
 void launch_gm_givens(GmresView G, KrylovState* st, cudaStream_t s) { launch(k_gm_givens, 1, s, G, st); }
 void launch_gm_next(int64_t n, const double* w, float* v32, double* v64, GmresView G, KrylovState* st,
                     cudaStream_t s) {
-  launch(k_gm_next, grid_for_rows(n), s, n, w, v32, v64, G, st);
+  launch_rows(k_gm_next, grid_for_rows(n), s, n, w, v32, v64, G, st);
   launch(k_gm_advance, 1, s, st);
 }
 void launch_gm_update_x(int64_t n, double* x, GmresView G, KrylovState* st, cudaStream_t s) {
-  launch(k_gm_update_x, grid_for_rows(n), s, n, x, G, st);
+  launch_rows(k_gm_update_x, grid_for_rows(n), s, n, x, G, st);
 }
 void launch_gm_residual(const SellView& A64, int nc, const double* x, const double* b, double* r, Partials part,
                         KrylovState* st, unsigned long long cond, cudaStream_t s) {
   const int g = grid_sell(A64.nslices);
-  if (nc == 1) launch(k_gm_residual<1>, g, s, A64, x, b, r, part.p, st, cond);
+  if (nc == 1) launch_rows(k_gm_residual<1>, g, s, A64, x, b, r, part.p, st, cond);
   else launch(k_gm_residual<3>, g, s, A64, x, b, r, part.p, st, cond);
 }
 
